@@ -1,0 +1,285 @@
+"""Seeded synthetic inputs for the transfer checks.
+
+This module only *produces inputs*: host shadow images (packed addressability
+bitmap + per-byte definedness masks), device allocation tables and copy
+request streams, each with the ground truth of what was planted.  It holds
+none of the checking arithmetic, and both the GPU library's tests and the CPU
+oracle draw their inputs from here.
+
+Layouts (the same ones the library documents):
+  * A bitmap: 1 bit per host byte, byte ``p`` <-> bit ``p & 7`` of
+    ``a_bits[p >> 3]``, 1 = addressable (``np.packbits(..., 'little')``).
+  * V mask: 1 byte per host byte, bit set = that data bit is undefined.
+  * requests: ``REQ_DTYPE`` records (kind, reserved, dst, src, n); for a
+    host->device copy ``src`` is an offset into the host image, for a
+    device->host copy ``dst`` is.
+
+All draws use numpy's PCG64 generator, which gives identical streams on x86
+and Arm hosts.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HTOD, DTOH, DTOD = 1, 2, 3
+REQ_DTYPE = np.dtype([("kind", "<u4"), ("reserved", "<u4"), ("dst", "<u8"),
+                      ("src", "<u8"), ("n", "<u8")])
+ADDR_SPACE = 1 << 48
+
+
+@dataclass
+class HostImage:
+    a_bits: np.ndarray            # uint8, ceil(n/8) bytes (padded to 16)
+    v: np.ndarray                 # uint8, n bytes
+    undef_runs: list = field(default_factory=list)   # (start, length) planted
+    unaddr: np.ndarray | None = None                 # planted positions (sorted)
+
+    @property
+    def n(self) -> int:
+        return int(self.v.size)
+
+
+@dataclass
+class AllocTable:
+    base: np.ndarray              # uint64
+    size: np.ndarray              # uint64
+    freed: np.ndarray             # indices into base/size freed after registration
+
+
+def rng_for(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def pack_a(addressable: np.ndarray) -> np.ndarray:
+    """bool per byte -> packed LSB-first bitmap, padded to a 16-byte multiple."""
+    bits = np.packbits(addressable.astype(np.uint8), bitorder="little")
+    pad = (-bits.size) % 16
+    if pad:
+        bits = np.concatenate([bits, np.zeros(pad, np.uint8)])
+    return bits
+
+
+def log_uniform_int(rng, lo: int, hi: int, size) -> np.ndarray:
+    """Integers log-uniform on [lo, hi]."""
+    x = np.exp(rng.uniform(np.log(lo), np.log(hi + 1), size=size))
+    return np.clip(np.floor(x), lo, hi).astype(np.uint64)
+
+
+def partial_masks(rng, count: int) -> np.ndarray:
+    """Random nonzero definedness masks other than 0xFF."""
+    return rng.integers(1, 255, size=count, dtype=np.uint8)
+
+
+def host_image_runs(rng, n: int, undef_frac: float, mean_run: float = 8.0,
+                    partial_frac: float = 0.5, unaddr_p: float = 0.0) -> HostImage:
+    """Undefined bytes planted as runs of geometric length until ``undef_frac``
+    of the bytes are covered; each run is fully undefined (0xFF) or carries
+    random partial masks.  Unaddressable bytes are Bernoulli(unaddr_p)."""
+    v = np.zeros(n, dtype=np.uint8)
+    runs = []
+    target = int(round(undef_frac * n))
+    covered = 0
+    while covered < target and n > 0:
+        length = int(min(rng.geometric(1.0 / mean_run), n))
+        start = int(rng.integers(0, n - length + 1))
+        if rng.random() < partial_frac:
+            v[start:start + length] = partial_masks(rng, length)
+        else:
+            v[start:start + length] = 0xFF
+        runs.append((start, length))
+        covered += length
+    if unaddr_p > 0:
+        k = rng.binomial(n, unaddr_p)
+        unaddr = np.unique(rng.integers(0, n, size=k))
+    else:
+        unaddr = np.zeros(0, dtype=np.int64)
+    addressable = np.ones(n, dtype=bool)
+    addressable[unaddr] = False
+    return HostImage(pack_a(addressable), v, runs, unaddr)
+
+
+def host_image_dense(rng, n: int, partial_p: float, unaddr_p: float,
+                     chunk: int = 1 << 26) -> HostImage:
+    """Every byte independently carries a random partial mask with
+    probability ``partial_p`` and is unaddressable with probability
+    ``unaddr_p`` (the adversarial-density workload)."""
+    v = np.empty(n, dtype=np.uint8)
+    a_bits = np.empty((n + 7) // 8, dtype=np.uint8)
+    for lo in range(0, n, chunk):
+        hi = min(n, lo + chunk)
+        m = hi - lo
+        has = rng.random(m) < partial_p
+        v[lo:hi] = np.where(has, rng.integers(1, 255, size=m, dtype=np.uint8), 0)
+        addr = rng.random(m) >= unaddr_p
+        a_bits[lo // 8:(hi + 7) // 8] = np.packbits(addr.astype(np.uint8), bitorder="little")
+    pad = (-a_bits.size) % 16
+    if pad:
+        a_bits = np.concatenate([a_bits, np.zeros(pad, np.uint8)])
+    return HostImage(a_bits, v, [], None)
+
+
+def host_image_clean(n: int) -> HostImage:
+    return HostImage(pack_a(np.ones(n, dtype=bool)), np.zeros(n, dtype=np.uint8), [],
+                     np.zeros(0, dtype=np.int64))
+
+
+def disjoint_bases(rng, sizes: np.ndarray, align: int = 256,
+                   space: int = ADDR_SPACE) -> np.ndarray:
+    """Random, ``align``-aligned, pairwise disjoint bases in [0, space): the
+    space is cut into one slot per allocation (slots shuffled) and each
+    allocation lands at a random aligned offset inside its slot."""
+    k = len(sizes)
+    slot = space // k
+    slot -= slot % align
+    assert int(sizes.max()) <= slot, "allocations larger than their slots"
+    order = rng.permutation(k).astype(np.uint64)
+    room = (slot - sizes.astype(np.uint64)) // align
+    off = (rng.random(k) * (room.astype(np.float64) + 1)).astype(np.uint64) * align
+    return order * np.uint64(slot) + off
+
+
+def alloc_table(rng, count: int, size_lo: int, size_hi: int, log_sizes: bool,
+                n_freed: int = 0, round_to: int = 1) -> AllocTable:
+    if log_sizes:
+        sizes = log_uniform_int(rng, size_lo, size_hi, count)
+    else:
+        sizes = rng.integers(size_lo, size_hi + 1, size=count).astype(np.uint64)
+    if round_to > 1:
+        sizes = ((sizes + np.uint64(round_to - 1)) // np.uint64(round_to)) * np.uint64(round_to)
+    bases = disjoint_bases(rng, sizes)
+    freed = rng.choice(count, size=n_freed, replace=False) if n_freed else np.zeros(0, np.int64)
+    return AllocTable(bases.astype(np.uint64), sizes.astype(np.uint64), np.sort(freed))
+
+
+def _device_target(rng, table: AllocTable, live_idx: np.ndarray, n: int,
+                   p_freed: float, p_overrun: float, p_wild: float) -> int:
+    u = rng.random()
+    if u < p_freed and table.freed.size:
+        j = int(table.freed[rng.integers(0, table.freed.size)])
+        return int(table.base[j]) + int(rng.integers(0, int(table.size[j])))
+    u -= p_freed
+    if u < p_wild:
+        return int(rng.integers(0, ADDR_SPACE))
+    u -= p_wild
+    j = int(live_idx[rng.integers(0, live_idx.size)])
+    base, size = int(table.base[j]), int(table.size[j])
+    if u < p_overrun and n >= 2:
+        k = int(rng.integers(1, min(n - 1, size) + 1))
+        return base + size - k
+    if n <= size:
+        return base + int(rng.integers(0, size - n + 1))
+    return base
+
+
+def requests(rng, count: int, table: AllocTable, host_n: int, n_lo: int, n_hi: int,
+             mix=(0.6, 0.3, 0.1), p_freed: float = 0.0, p_overrun: float = 0.0,
+             p_wild: float = 0.0, p_same_alloc_dtod: float = 0.1) -> np.ndarray:
+    """A copy stream: kinds drawn from ``mix`` (HtoD, DtoH, DtoD), sizes
+    log-uniform in [n_lo, n_hi] (capped at the host image), host offsets
+    uniform, device targets inside live allocations except for the planted
+    overruns, freed-pointer targets and wild pointers."""
+    live = np.setdiff1d(np.arange(len(table.base)), table.freed)
+    reqs = np.zeros(count, dtype=REQ_DTYPE)
+    kinds = rng.choice([HTOD, DTOH, DTOD], size=count, p=list(mix))
+    sizes = log_uniform_int(rng, n_lo, n_hi, count)
+    for i in range(count):
+        kind = int(kinds[i])
+        n = int(min(int(sizes[i]), host_n)) if kind != DTOD else int(sizes[i])
+        reqs[i]["kind"] = kind
+        reqs[i]["n"] = n
+        if kind == HTOD:
+            reqs[i]["src"] = int(rng.integers(0, host_n - n + 1))
+            reqs[i]["dst"] = _device_target(rng, table, live, n, p_freed, p_overrun, p_wild)
+        elif kind == DTOH:
+            reqs[i]["dst"] = int(rng.integers(0, host_n - n + 1))
+            reqs[i]["src"] = _device_target(rng, table, live, n, p_freed, p_overrun, p_wild)
+        else:
+            s = _device_target(rng, table, live, n, p_freed, p_overrun, p_wild)
+            if rng.random() < p_same_alloc_dtod:
+                # destination a few bytes away from the source: exercises
+                # overlapping device->device copies
+                k = min(n, 64)
+                d = max(s + int(rng.integers(-k, k + 1)), 0)
+            else:
+                d = _device_target(rng, table, live, n, p_freed, p_overrun, p_wild)
+            reqs[i]["src"] = s
+            reqs[i]["dst"] = d
+    return reqs
+
+
+# ----------------------------------------------------------------- configs
+
+@dataclass
+class Workload:
+    name: str
+    image: HostImage
+    table: AllocTable
+    reqs: np.ndarray
+    note: str = ""
+
+
+def small(seed: int = 0) -> Workload:
+    """64 live device allocations (72 registered, 8 freed), sizes uniform
+    1-16 KiB rounded to 256 B; 1 MiB host image, 1 % undefined bytes in runs
+    of geometric mean length 8 (half partial masks), 0.1 % unaddressable;
+    1,000 requests 60/30/10 HtoD/DtoH/DtoD, sizes log-uniform 1 B-16 KiB,
+    10 % overrunning, 2 % aimed at freed allocations."""
+    rng = rng_for(seed)
+    table = alloc_table(rng, 72, 1, 16 * 1024, log_sizes=False, n_freed=8, round_to=256)
+    img = host_image_runs(rng, 1 << 20, 0.01, 8.0, 0.5, 0.001)
+    reqs = requests(rng, 1000, table, img.n, 1, 16 * 1024, p_freed=0.02, p_overrun=0.10,
+                    p_wild=0.01)
+    return Workload("small-1k-requests-1MiB-image", img, table, reqs)
+
+
+LARGE_SIZES = (256 << 20, 1 << 30, 4 << 30)
+
+
+def large(seed: int = 0, sizes=LARGE_SIZES) -> Workload:
+    """Large single host->device transfers (default 256 MiB, 1 GiB, 4 GiB)
+    from one host image of the largest size, undefined density 1e-6 in sparse
+    runs, fully addressable, against a 16-entry allocation table in which one
+    allocation per transfer holds the destination at offset 0."""
+    rng = rng_for(seed)
+    n_img = int(max(sizes))
+    img = host_image_runs(rng, n_img, 1e-6, 8.0, 0.5, 0.0)
+    small_sizes = rng.integers(4096, 1 << 20, size=16 - len(sizes)).astype(np.uint64)
+    all_sizes = np.concatenate([np.array(sizes, dtype=np.uint64), small_sizes])
+    bases = disjoint_bases(rng, all_sizes, align=1 << 16)
+    table = AllocTable(bases, all_sizes, np.zeros(0, np.int64))
+    reqs = np.zeros(len(sizes), dtype=REQ_DTYPE)
+    for i, n in enumerate(sizes):
+        reqs[i] = (HTOD, 0, int(bases[i]), 0, int(n))
+    return Workload("large-htod-" + "-".join(_human(s) for s in sizes), img, table, reqs)
+
+
+def batched(seed: int = 0, n_req: int = 100_000, n_alloc: int = 1_000_000,
+            host_n: int = 1 << 30, n_hi: int = 64 << 20) -> Workload:
+    """100,000 requests, sizes log-uniform 16 B-64 MiB, against 1,000,000
+    allocations log-uniform 256 B-1 MiB; 1 GiB host image, 0.01 % undefined."""
+    rng = rng_for(seed)
+    table = alloc_table(rng, n_alloc, 256, 1 << 20, log_sizes=True)
+    img = host_image_runs(rng, host_n, 1e-4, 8.0, 0.5, 1e-5)
+    reqs = requests(rng, n_req, table, host_n, 16, n_hi, p_wild=0.01)
+    return Workload(f"batched-{n_req}-req-{n_alloc}-allocs", img, table, reqs)
+
+
+def adversarial(seed: int = 0, n_req: int = 10_000, host_n: int = 1 << 30,
+                n_alloc: int = 1024) -> Workload:
+    """10,000 copies of 4 KiB-16 MiB over a host image where 50 % of the
+    bytes carry random partial masks and 5 % are unaddressable; 1,024
+    allocations log-uniform 4 KiB-32 MiB."""
+    rng = rng_for(seed)
+    table = alloc_table(rng, n_alloc, 4096, 32 << 20, log_sizes=True)
+    img = host_image_dense(rng, host_n, 0.5, 0.05)
+    reqs = requests(rng, n_req, table, host_n, 4096, 16 << 20)
+    return Workload(f"adversarial-{n_req}-req", img, table, reqs)
+
+
+def _human(n: int) -> str:
+    for unit, sh in (("GiB", 30), ("MiB", 20), ("KiB", 10)):
+        if n >= 1 << sh and n % (1 << sh) == 0:
+            return f"{n >> sh}{unit}"
+    return f"{n}B"

@@ -1,0 +1,227 @@
+"""Plain CPU oracle for the Cudagrind transfer checks (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The GPU library never loads it, and it shares
+no code with the GPU library: the C source (``cg_oracle.c``) keeps its own
+definitions, and this binding declares its own ctypes structures.
+
+The checker follows the paper's Sec. 2 itemize (unallocated device memory,
+undefined host data sent to the device, copies larger than the allocation),
+Listing 5 (expected vs found bytes), Sec. 1.1 (bit-precise A/V shadow) and
+Sec. 5 (definedness tracked through all three copy directions).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "cg_oracle.c")
+LIB = os.path.join(HERE, "libcg_oracle.so")
+
+HTOD, DTOH, DTOD = 1, 2, 3
+BYTE_GOOD, BYTE_UNADDR, BYTE_UNDEF = 0, 1, 2
+FLAG_NAMES = [
+    "UNALLOC_DST", "UNALLOC_SRC", "OVERRUN_DST", "OVERRUN_SRC",
+    "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP",
+]
+FLAGS = {name: 1 << i for i, name in enumerate(FLAG_NAMES)}
+FREE_NAMES = {0: "OK", 1: "UNKNOWN", 2: "DOUBLE", 3: "INTERIOR"}
+STATUS = {0: "OK", -1: "E_ARG", -2: "E_KIND", -3: "E_HOST_RANGE",
+          -4: "E_ZERO_SIZE", -5: "E_WRAP", -6: "E_OVERLAP", -7: "E_NOMEM",
+          -8: "E_RANGE"}
+
+
+class OrReport(ctypes.Structure):
+    _fields_ = [
+        ("flags", ctypes.c_uint32), ("first_bad_kind", ctypes.c_uint32),
+        ("first_bad_off", ctypes.c_int64), ("first_unaddr_off", ctypes.c_int64),
+        ("first_undef_off", ctypes.c_int64), ("n_good", ctypes.c_uint64),
+        ("n_unaddr", ctypes.c_uint64), ("n_undef", ctypes.c_uint64),
+        ("expected", ctypes.c_uint64), ("found_dst", ctypes.c_uint64),
+        ("found_src", ctypes.c_uint64), ("alloc_base_dst", ctypes.c_uint64),
+        ("alloc_size_dst", ctypes.c_uint64), ("alloc_base_src", ctypes.c_uint64),
+        ("alloc_size_src", ctypes.c_uint64),
+    ]
+
+
+class OrRecord(ctypes.Structure):
+    _fields_ = [
+        ("req", ctypes.c_uint64), ("cls", ctypes.c_uint32),
+        ("severity", ctypes.c_uint32), ("off", ctypes.c_int64),
+        ("count", ctypes.c_uint64), ("expected", ctypes.c_uint64),
+        ("found", ctypes.c_uint64),
+    ]
+
+
+REPORT_FIELDS = [f for f, _ in OrReport._fields_]
+RECORD_FIELDS = [f for f, _ in OrRecord._fields_]
+
+
+def build(src: str = SRC, out: str = LIB, werror: bool = True) -> str:
+    """Compile the oracle with plain gcc (no vector intrinsics, portable)."""
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-Wextra"]
+    cmd += ["-Werror"] if werror else []
+    cmd += ["-o", out, src]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def _needs_build(lib: str, src: str) -> bool:
+    if not os.path.exists(lib):
+        return True
+    hdr = os.path.join(os.path.dirname(src), "cg_oracle.h")
+    newest = max(os.path.getmtime(src), os.path.getmtime(hdr) if os.path.exists(hdr) else 0)
+    return os.path.getmtime(lib) < newest
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load (building first if stale) the oracle shared library."""
+    if path is None:
+        path = LIB
+        if _needs_build(path, SRC):
+            build(SRC, path)
+    lib = ctypes.CDLL(path)
+    u64, i32, u32, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p
+    lib.or_create.restype = vp
+    lib.or_create.argtypes = [u64, vp, vp, i32, i32]
+    lib.or_destroy.argtypes = [vp]
+    lib.or_destroy.restype = None
+    lib.or_register_alloc.argtypes = [vp, u64, u64]
+    lib.or_register_alloc.restype = i32
+    lib.or_free.argtypes = [vp, u64, ctypes.POINTER(u32)]
+    lib.or_free.restype = i32
+    lib.or_mark.argtypes = [vp, u64, u64, ctypes.c_uint8]
+    lib.or_mark.restype = i32
+    lib.or_check_copy.argtypes = [vp, u32, u64, u64, u64, ctypes.POINTER(OrReport)]
+    lib.or_check_copy.restype = i32
+    lib.or_check_batch.argtypes = [vp, vp, vp, vp, vp, u64, vp, ctypes.POINTER(u64)]
+    lib.or_check_batch.restype = i32
+    lib.or_emit_records.argtypes = [vp, vp, vp, vp, vp, u64, i32, vp, u64]
+    lib.or_emit_records.restype = u64
+    lib.or_read_host_v.argtypes = [vp, u64, u64, vp]
+    lib.or_read_host_v.restype = i32
+    lib.or_read_dev_v.argtypes = [vp, u64, u64, vp]
+    lib.or_read_dev_v.restype = i32
+    lib.or_live_count.argtypes = [vp]
+    lib.or_live_count.restype = u64
+    return lib
+
+
+def build_variant(source_text: str, tag: str) -> str:
+    """Compile a modified copy of the oracle source (used by the mutation
+    tests, which plant a mistake in the oracle and expect a pin to fail)."""
+    d = tempfile.mkdtemp(prefix=f"cg_oracle_{tag}_")
+    with open(os.path.join(d, "cg_oracle.h"), "w") as f:
+        f.write(open(os.path.join(HERE, "cg_oracle.h")).read())
+    src = os.path.join(d, "cg_oracle.c")
+    with open(src, "w") as f:
+        f.write(source_text)
+    return build(src, os.path.join(d, "libcg_oracle.so"), werror=False)
+
+
+def report_dict(r: OrReport) -> dict:
+    return {f: getattr(r, f) for f in REPORT_FIELDS}
+
+
+def _u8ptr(a: np.ndarray) -> int:
+    assert a.dtype == np.uint8 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+class Oracle:
+    """A checker state: host shadow image, live allocations, device shadow."""
+
+    def __init__(self, a_bits: np.ndarray, v: np.ndarray, carry: bool = True,
+                 strict: bool = False, lib: ctypes.CDLL | None = None):
+        self.lib = lib if lib is not None else load()
+        v = np.ascontiguousarray(v, dtype=np.uint8)
+        a_bits = np.ascontiguousarray(a_bits, dtype=np.uint8)
+        assert a_bits.size >= (v.size + 7) // 8
+        self.host_n = int(v.size)
+        self.strict = bool(strict)
+        self._h = self.lib.or_create(self.host_n, _u8ptr(a_bits) if a_bits.size else None,
+                                     _u8ptr(v) if v.size else None, int(carry), int(strict))
+        if not self._h:
+            raise MemoryError("oracle state allocation failed")
+
+    def close(self):
+        if self._h:
+            self.lib.or_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register_alloc(self, base: int, size: int) -> int:
+        return self.lib.or_register_alloc(self._h, base, size)
+
+    def free(self, base: int) -> str:
+        v = ctypes.c_uint32(99)
+        st = self.lib.or_free(self._h, base, ctypes.byref(v))
+        assert st == 0, st
+        return FREE_NAMES[v.value]
+
+    def mark(self, dptr: int, n: int, value: int) -> int:
+        return self.lib.or_mark(self._h, dptr, n, value)
+
+    def check_copy(self, kind: int, dst: int, src: int, n: int):
+        r = OrReport()
+        st = self.lib.or_check_copy(self._h, kind, dst, src, n, ctypes.byref(r))
+        return st, report_dict(r)
+
+    def check_batch(self, reqs: np.ndarray):
+        """reqs: structured array with fields kind, dst, src, n."""
+        k = np.ascontiguousarray(reqs["kind"], dtype=np.uint32)
+        d = np.ascontiguousarray(reqs["dst"], dtype=np.uint64)
+        s = np.ascontiguousarray(reqs["src"], dtype=np.uint64)
+        n = np.ascontiguousarray(reqs["n"], dtype=np.uint64)
+        reps = (OrReport * max(1, len(reqs)))()
+        bad = ctypes.c_uint64(0)
+        st = self.lib.or_check_batch(self._h, k.ctypes.data, d.ctypes.data, s.ctypes.data,
+                                     n.ctypes.data, len(reqs), ctypes.addressof(reps),
+                                     ctypes.byref(bad))
+        return st, [report_dict(reps[i]) for i in range(len(reqs))], int(bad.value)
+
+    def read_host_v(self, off: int = 0, n: int | None = None) -> np.ndarray:
+        n = self.host_n - off if n is None else n
+        out = np.empty(n, dtype=np.uint8)
+        st = self.lib.or_read_host_v(self._h, off, n, out.ctypes.data if n else None)
+        assert st == 0, st
+        return out
+
+    def read_dev_v(self, dptr: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint8)
+        st = self.lib.or_read_dev_v(self._h, dptr, n, out.ctypes.data if n else None)
+        assert st == 0, st
+        return out
+
+    def live_count(self) -> int:
+        return int(self.lib.or_live_count(self._h))
+
+
+def emit_records(reports: list[dict], reqs: np.ndarray, strict: bool = False,
+                 lib: ctypes.CDLL | None = None) -> list[dict]:
+    lib = lib if lib is not None else load()
+    nreq = len(reqs)
+    reps = (OrReport * max(1, nreq))()
+    for i, r in enumerate(reports):
+        for f in REPORT_FIELDS:
+            setattr(reps[i], f, r[f])
+    k = np.ascontiguousarray(reqs["kind"], dtype=np.uint32)
+    d = np.ascontiguousarray(reqs["dst"], dtype=np.uint64)
+    s = np.ascontiguousarray(reqs["src"], dtype=np.uint64)
+    n = np.ascontiguousarray(reqs["n"], dtype=np.uint64)
+    total = lib.or_emit_records(ctypes.addressof(reps), k.ctypes.data, d.ctypes.data,
+                                s.ctypes.data, n.ctypes.data, nreq, int(strict), None, 0)
+    out = (OrRecord * max(1, total))()
+    lib.or_emit_records(ctypes.addressof(reps), k.ctypes.data, d.ctypes.data, s.ctypes.data,
+                        n.ctypes.data, nreq, int(strict), ctypes.addressof(out), total)
+    return [{f: getattr(out[i], f) for f in RECORD_FIELDS} for i in range(total)]

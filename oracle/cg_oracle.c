@@ -1,0 +1,438 @@
+/*
+ * cg_oracle.c -- plain, byte-by-byte CPU checker (see cg_oracle.h).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the product path.  No code is shared
+ * with the GPU library.
+ *
+ * Every rule below is the plain definition of a check the paper names:
+ *   Sec. 2 itemize: copies into or from unallocated device memory; undefined
+ *     host data copied to the device; copies larger than the allocation.
+ *   Listing 5: the overrun report carries the expected byte count (the copy
+ *     size) and the bytes actually found in the allocation.
+ *   Sec. 1.1: Memcheck's shadow is bit-precise (A = addressable, V = defined).
+ *   Sec. 5: definedness is tracked through host/device, device/host and
+ *     device/device transfers, i.e. the V shadow moves with the data.
+ * Where the paper is silent the readings are fixed as follows (the GPU
+ * library implements the same readings):
+ *   R1  A bit of host byte p is bit (p & 7) of byte a[p >> 3]; 1 = addressable.
+ *   R2  V byte != 0 means the byte is (partly) undefined; carries copy V
+ *       masks exactly.
+ *   R3  an unaddressable byte counts only as UNADDR, whatever its V.
+ *   R4  offsets are relative to the copy start; -1 when there is none.
+ *   R5  device->host / device->device: undefined device-source bytes are
+ *       counted as UNDEF and raise a warning (an error in strict mode); the
+ *       device source V is only read when the source range is valid.
+ *   R6  a new allocation's shadow is all undefined (0xFF).
+ *   R7  a copy may start inside an allocation but must end inside the same
+ *       allocation; adjacent allocations never combine.
+ *   R8  found = bytes from the pointer to its allocation's end; 0 when no
+ *       live allocation contains the pointer.
+ *   R9  n == 0 is a no-op: no device check, no carry.
+ *   R11 host checks run even when a device range fails; the carry does not.
+ *   R12 an overlapping device->device copy carries with memmove semantics
+ *       and raises a warning.
+ *   R13 free: live base -> ok; inside a live allocation -> interior; a freed
+ *       base not reused since -> double free; anything else -> unknown.
+ *   R14 registering an allocation that overlaps a live one is refused.
+ */
+#include "cg_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+  uint64_t base;
+  uint64_t size;
+  uint8_t *shadow; /* NULL: never written, every byte reads 0xFF (R6) */
+} live_alloc;
+
+struct or_state {
+  uint64_t host_n;
+  uint8_t *a_bits;
+  uint8_t *host_v;
+  int carry;
+  int strict;
+  live_alloc *live; /* sorted by base, pairwise disjoint */
+  uint64_t n_live, cap_live;
+  uint64_t *freed; /* sorted freed bases */
+  uint64_t n_freed, cap_freed;
+};
+
+/* ---------------------------------------------------------------- state */
+
+or_state *or_create(uint64_t host_n, const uint8_t *a_bits, const uint8_t *v,
+                    int carry, int strict) {
+  or_state *s = (or_state *)calloc(1, sizeof *s);
+  if (!s) return NULL;
+  uint64_t a_len = (host_n + 7) / 8;
+  s->host_n = host_n;
+  s->a_bits = (uint8_t *)malloc(a_len ? a_len : 1);
+  s->host_v = (uint8_t *)malloc(host_n ? host_n : 1);
+  if (!s->a_bits || !s->host_v) {
+    or_destroy(s);
+    return NULL;
+  }
+  if (a_len) memcpy(s->a_bits, a_bits, a_len);
+  if (host_n) memcpy(s->host_v, v, host_n);
+  s->carry = carry;
+  s->strict = strict;
+  return s;
+}
+
+void or_destroy(or_state *s) {
+  if (!s) return;
+  for (uint64_t j = 0; j < s->n_live; j++) free(s->live[j].shadow);
+  free(s->live);
+  free(s->freed);
+  free(s->a_bits);
+  free(s->host_v);
+  free(s);
+}
+
+uint64_t or_live_count(const or_state *s) { return s->n_live; }
+
+/* index of the first live allocation whose base is > addr */
+static uint64_t upper_bound_base(const or_state *s, uint64_t addr) {
+  uint64_t lo = 0, hi = s->n_live;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (s->live[mid].base <= addr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+/* the live allocation containing addr, or NULL */
+static live_alloc *find_alloc(const or_state *s, uint64_t addr) {
+  uint64_t ub = upper_bound_base(s, addr);
+  if (ub == 0) return NULL;
+  live_alloc *a = &s->live[ub - 1];
+  if (addr - a->base < a->size) return a;
+  return NULL;
+}
+
+/* position of the first freed base >= addr */
+static uint64_t lower_bound_freed(const or_state *s, uint64_t addr) {
+  uint64_t lo = 0, hi = s->n_freed;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (s->freed[mid] < addr)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+int or_register_alloc(or_state *s, uint64_t base, uint64_t size) {
+  if (size == 0) return OR_E_ZERO_SIZE;
+  if (base + size < base) return OR_E_WRAP; /* [base, base+size) wraps */
+  uint64_t ub = upper_bound_base(s, base);
+  /* R14: the predecessor must end at or before base, the successor must
+   * start at or after base+size */
+  if (ub > 0) {
+    live_alloc *p = &s->live[ub - 1];
+    if (base - p->base < p->size) return OR_E_OVERLAP;
+  }
+  if (ub < s->n_live && s->live[ub].base < base + size) return OR_E_OVERLAP;
+  if (s->n_live == s->cap_live) {
+    uint64_t cap = s->cap_live ? 2 * s->cap_live : 64;
+    live_alloc *nl = (live_alloc *)realloc(s->live, cap * sizeof *nl);
+    if (!nl) return OR_E_NOMEM;
+    s->live = nl;
+    s->cap_live = cap;
+  }
+  memmove(&s->live[ub + 1], &s->live[ub], (s->n_live - ub) * sizeof *s->live);
+  s->live[ub].base = base;
+  s->live[ub].size = size;
+  s->live[ub].shadow = NULL;
+  s->n_live++;
+  /* R13: freed bases covered by the new allocation are live memory again */
+  uint64_t lo = lower_bound_freed(s, base);
+  uint64_t hi = lo;
+  while (hi < s->n_freed && s->freed[hi] - base < size) hi++;
+  memmove(&s->freed[lo], &s->freed[hi], (s->n_freed - hi) * sizeof *s->freed);
+  s->n_freed -= hi - lo;
+  return OR_OK;
+}
+
+int or_free(or_state *s, uint64_t base, uint32_t *verdict) {
+  if (!verdict) return OR_E_ARG;
+  live_alloc *a = find_alloc(s, base);
+  if (a && a->base == base) {
+    uint64_t j = (uint64_t)(a - s->live);
+    free(a->shadow);
+    memmove(&s->live[j], &s->live[j + 1], (s->n_live - j - 1) * sizeof *s->live);
+    s->n_live--;
+    uint64_t pos = lower_bound_freed(s, base);
+    if (pos == s->n_freed || s->freed[pos] != base) {
+      if (s->n_freed == s->cap_freed) {
+        uint64_t cap = s->cap_freed ? 2 * s->cap_freed : 64;
+        uint64_t *nf = (uint64_t *)realloc(s->freed, cap * sizeof *nf);
+        if (!nf) return OR_E_NOMEM;
+        s->freed = nf;
+        s->cap_freed = cap;
+      }
+      memmove(&s->freed[pos + 1], &s->freed[pos], (s->n_freed - pos) * sizeof *s->freed);
+      s->freed[pos] = base;
+      s->n_freed++;
+    }
+    *verdict = OR_FREE_OK;
+    return OR_OK;
+  }
+  if (a) {
+    *verdict = OR_FREE_INTERIOR;
+    return OR_OK;
+  }
+  uint64_t pos = lower_bound_freed(s, base);
+  if (pos < s->n_freed && s->freed[pos] == base)
+    *verdict = OR_FREE_DOUBLE;
+  else
+    *verdict = OR_FREE_UNKNOWN;
+  return OR_OK;
+}
+
+/* ------------------------------------------------------- shadow access */
+
+static int host_a_bit(const or_state *s, uint64_t pos) {
+  return (s->a_bits[pos >> 3] >> (pos & 7)) & 1;
+}
+
+static uint8_t dev_v(const live_alloc *a, uint64_t off) {
+  return a->shadow ? a->shadow[off] : 0xFF;
+}
+
+static int materialise(live_alloc *a) {
+  if (a->shadow) return OR_OK;
+  a->shadow = (uint8_t *)malloc(a->size);
+  if (!a->shadow) return OR_E_NOMEM;
+  memset(a->shadow, 0xFF, a->size);
+  return OR_OK;
+}
+
+int or_mark(or_state *s, uint64_t dptr, uint64_t n, uint8_t value) {
+  if (n == 0) return OR_OK;
+  live_alloc *a = find_alloc(s, dptr);
+  if (!a || n > a->base + a->size - dptr) return OR_E_RANGE;
+  int st = materialise(a);
+  if (st) return st;
+  memset(a->shadow + (dptr - a->base), value, n);
+  return OR_OK;
+}
+
+int or_read_host_v(const or_state *s, uint64_t off, uint64_t n, uint8_t *out) {
+  if (off > s->host_n || n > s->host_n - off) return OR_E_HOST_RANGE;
+  memcpy(out, s->host_v + off, n);
+  return OR_OK;
+}
+
+int or_read_dev_v(const or_state *s, uint64_t dptr, uint64_t n, uint8_t *out) {
+  if (n == 0) return OR_OK;
+  live_alloc *a = find_alloc(s, dptr);
+  if (!a || n > a->base + a->size - dptr) return OR_E_RANGE;
+  for (uint64_t i = 0; i < n; i++) out[i] = dev_v(a, dptr - a->base + i);
+  return OR_OK;
+}
+
+/* ---------------------------------------------------------------- checks */
+
+/* The device side of a copy (Sec. 2 itemize, Listing 5, R7/R8): returns the
+ * containing allocation when [p, p+n) lies wholly inside it, else NULL. */
+static live_alloc *device_side(const or_state *s, uint64_t p, uint64_t n,
+                               uint64_t *found, uint64_t *abase,
+                               uint64_t *asize, uint32_t *flags,
+                               uint32_t f_unalloc, uint32_t f_overrun) {
+  live_alloc *a = find_alloc(s, p);
+  if (!a) {
+    *found = 0;
+    *abase = 0;
+    *asize = 0;
+    *flags |= f_unalloc;
+    return NULL;
+  }
+  *found = a->base + a->size - p;
+  *abase = a->base;
+  *asize = a->size;
+  if (n > *found) {
+    *flags |= f_overrun;
+    return NULL;
+  }
+  return a;
+}
+
+static int validate(const or_state *s, uint32_t kind, uint64_t dst,
+                    uint64_t src, uint64_t n) {
+  if (kind != OR_HTOD && kind != OR_DTOH && kind != OR_DTOD) return OR_E_KIND;
+  if (kind == OR_HTOD || kind == OR_DTOH) {
+    uint64_t h = kind == OR_HTOD ? src : dst;
+    if (h > s->host_n || n > s->host_n - h) return OR_E_HOST_RANGE;
+  }
+  return OR_OK;
+}
+
+static int check_one(or_state *s, uint32_t kind, uint64_t dst, uint64_t src,
+                     uint64_t n, or_report *r) {
+  memset(r, 0, sizeof *r);
+  r->first_bad_off = -1;
+  r->first_unaddr_off = -1;
+  r->first_undef_off = -1;
+  r->expected = n;
+  if (n == 0) return OR_OK; /* R9 */
+
+  live_alloc *da = NULL, *sa = NULL;
+  if (kind == OR_HTOD || kind == OR_DTOD)
+    da = device_side(s, dst, n, &r->found_dst, &r->alloc_base_dst,
+                     &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_DST,
+                     OR_F_OVERRUN_DST);
+  if (kind == OR_DTOH || kind == OR_DTOD)
+    sa = device_side(s, src, n, &r->found_src, &r->alloc_base_src,
+                     &r->alloc_size_src, &r->flags, OR_F_UNALLOC_SRC,
+                     OR_F_OVERRUN_SRC);
+
+  /* classify every byte (R1-R5) */
+  for (uint64_t i = 0; i < n; i++) {
+    uint32_t cls = OR_BYTE_GOOD;
+    if (kind == OR_HTOD) {
+      if (!host_a_bit(s, src + i))
+        cls = OR_BYTE_UNADDR;
+      else if (s->host_v[src + i] != 0)
+        cls = OR_BYTE_UNDEF;
+    } else if (kind == OR_DTOH) {
+      if (!host_a_bit(s, dst + i))
+        cls = OR_BYTE_UNADDR;
+      else if (sa && dev_v(sa, src - sa->base + i) != 0)
+        cls = OR_BYTE_UNDEF;
+    } else {
+      if (sa && dev_v(sa, src - sa->base + i) != 0) cls = OR_BYTE_UNDEF;
+    }
+    if (cls == OR_BYTE_GOOD) {
+      r->n_good++;
+    } else if (cls == OR_BYTE_UNADDR) {
+      r->n_unaddr++;
+      if (r->first_unaddr_off < 0) r->first_unaddr_off = (int64_t)i;
+    } else {
+      r->n_undef++;
+      if (r->first_undef_off < 0) r->first_undef_off = (int64_t)i;
+    }
+    if (cls != OR_BYTE_GOOD && r->first_bad_off < 0) {
+      r->first_bad_off = (int64_t)i;
+      r->first_bad_kind = cls;
+    }
+  }
+  if (r->n_unaddr) r->flags |= OR_F_HOST_UNADDR;
+  if (r->n_undef) r->flags |= kind == OR_HTOD ? OR_F_HOST_UNDEF : OR_F_DEV_UNDEF_SRC;
+  if (kind == OR_DTOD) {
+    uint64_t dist = src <= dst ? dst - src : src - dst;
+    if (dist < n) r->flags |= OR_F_DTOD_OVERLAP;
+  }
+
+  /* carry the V shadow with the data (Sec. 5), only over valid ranges (R11) */
+  if (!s->carry) return OR_OK;
+  if (kind == OR_HTOD && da) {
+    int st = materialise(da);
+    if (st) return st;
+    uint64_t o = dst - da->base;
+    for (uint64_t i = 0; i < n; i++)
+      da->shadow[o + i] = host_a_bit(s, src + i) ? s->host_v[src + i] : 0xFF;
+  } else if (kind == OR_DTOH && sa) {
+    uint64_t o = src - sa->base;
+    for (uint64_t i = 0; i < n; i++)
+      if (host_a_bit(s, dst + i)) s->host_v[dst + i] = dev_v(sa, o + i);
+  } else if (kind == OR_DTOD && sa && da) {
+    uint8_t *tmp = (uint8_t *)malloc(n); /* R12: read everything first */
+    if (!tmp) return OR_E_NOMEM;
+    uint64_t os = src - sa->base;
+    for (uint64_t i = 0; i < n; i++) tmp[i] = dev_v(sa, os + i);
+    int st = materialise(da);
+    if (st) {
+      free(tmp);
+      return st;
+    }
+    uint64_t od = dst - da->base;
+    for (uint64_t i = 0; i < n; i++) da->shadow[od + i] = tmp[i];
+    free(tmp);
+  }
+  return OR_OK;
+}
+
+int or_check_copy(or_state *s, uint32_t kind, uint64_t dst, uint64_t src,
+                  uint64_t n, or_report *rep) {
+  if (!s || !rep) return OR_E_ARG;
+  int st = validate(s, kind, dst, src, n);
+  if (st) return st;
+  return check_one(s, kind, dst, src, n, rep);
+}
+
+int or_check_batch(or_state *s, const uint32_t *kind, const uint64_t *dst,
+                   const uint64_t *src, const uint64_t *n, uint64_t nreq,
+                   or_report *reps, uint64_t *bad_index) {
+  if (!s || (nreq && (!kind || !dst || !src || !n || !reps))) return OR_E_ARG;
+  for (uint64_t i = 0; i < nreq; i++) {
+    int st = validate(s, kind[i], dst[i], src[i], n[i]);
+    if (st) {
+      if (bad_index) *bad_index = i;
+      return st;
+    }
+  }
+  for (uint64_t i = 0; i < nreq; i++) {
+    int st = check_one(s, kind[i], dst[i], src[i], n[i], &reps[i]);
+    if (st) {
+      if (bad_index) *bad_index = i;
+      return st;
+    }
+  }
+  return OR_OK;
+}
+
+/* One record per set flag, in (request, flag bit) order. */
+uint64_t or_emit_records(const or_report *reps, const uint32_t *kind,
+                         const uint64_t *dst, const uint64_t *src,
+                         const uint64_t *n, uint64_t nreq, int strict,
+                         or_record *out, uint64_t cap) {
+  uint64_t k = 0;
+  for (uint64_t i = 0; i < nreq; i++) {
+    const or_report *r = &reps[i];
+    for (uint32_t b = 0; b < OR_NFLAGS; b++) {
+      uint32_t f = 1u << b;
+      if (!(r->flags & f)) continue;
+      or_record rec;
+      memset(&rec, 0, sizeof rec);
+      rec.req = i;
+      rec.cls = b;
+      rec.expected = n[i];
+      rec.severity = 0;
+      if (f == OR_F_UNALLOC_DST || f == OR_F_UNALLOC_SRC) {
+        rec.off = 0;
+        rec.count = n[i];
+        rec.found = 0;
+      } else if (f == OR_F_OVERRUN_DST || f == OR_F_OVERRUN_SRC) {
+        uint64_t found = f == OR_F_OVERRUN_DST ? r->found_dst : r->found_src;
+        rec.off = (int64_t)found;
+        rec.count = n[i] - found;
+        rec.found = found;
+      } else if (f == OR_F_HOST_UNADDR) {
+        rec.off = r->first_unaddr_off;
+        rec.count = r->n_unaddr;
+        rec.found = n[i] - r->n_unaddr;
+      } else if (f == OR_F_HOST_UNDEF || f == OR_F_DEV_UNDEF_SRC) {
+        rec.off = r->first_undef_off;
+        rec.count = r->n_undef;
+        rec.found = r->n_good;
+        if (f == OR_F_DEV_UNDEF_SRC && !strict) rec.severity = 1;
+      } else { /* OR_F_DTOD_OVERLAP */
+        uint64_t dist = src[i] <= dst[i] ? dst[i] - src[i] : src[i] - dst[i];
+        rec.off = (int64_t)(dst[i] - src[i]);
+        rec.count = n[i] - dist;
+        rec.found = 0;
+        rec.severity = 1;
+        (void)kind;
+      }
+      if (k < cap) out[k] = rec;
+      k++;
+    }
+  }
+  return k;
+}

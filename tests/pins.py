@@ -1,0 +1,475 @@
+"""Pins for the CPU oracle: facts fixed by the paper or by mathematics that a
+plausible mistake in the oracle would break.
+
+Each ``pin_*`` takes a loaded oracle library and raises ``AssertionError`` if
+the oracle disagrees.  ``tests/test_oracle_pins.py`` runs them against the
+real oracle; ``tests/test_oracle_mutants.py`` plants mistakes in a copy of the
+oracle source and checks that some pin fails for every mistake.
+
+Where a pin needs an expected value it comes from (a) the paper (the
+Listing 5 fixture), (b) construction (the inputs are built from a list of
+intended byte classes or planted runs), (c) a different formulation (set
+membership over every address instead of a sorted-table search; Python's
+slice assignment for memmove), or (d) an invariant.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import cg_synth as S  # noqa: E402
+import oracle as O  # noqa: E402
+
+HTOD, DTOH, DTOD = O.HTOD, O.DTOH, O.DTOD
+F = O.FLAGS
+
+# (A bit, V byte) states a host byte can take; the class each one belongs to
+# is written down here as data: unaddressable wins, else any set V bit means
+# undefined (Sec. 1.1 bit precision; readings R1-R3).
+BYTE_STATES = [
+    (0, 0x00, O.BYTE_UNADDR), (0, 0x01, O.BYTE_UNADDR), (0, 0x80, O.BYTE_UNADDR),
+    (0, 0xFF, O.BYTE_UNADDR), (1, 0x00, O.BYTE_GOOD), (1, 0x01, O.BYTE_UNDEF),
+    (1, 0x80, O.BYTE_UNDEF), (1, 0xFF, O.BYTE_UNDEF),
+]
+
+
+def _image(addressable: np.ndarray, v: np.ndarray):
+    return S.pack_a(addressable.astype(bool)), np.ascontiguousarray(v, dtype=np.uint8)
+
+
+def _expect_from_classes(classes):
+    n_unaddr = sum(1 for c in classes if c == O.BYTE_UNADDR)
+    n_undef = sum(1 for c in classes if c == O.BYTE_UNDEF)
+    bad = [i for i, c in enumerate(classes) if c != O.BYTE_GOOD]
+    fu = [i for i, c in enumerate(classes) if c == O.BYTE_UNADDR]
+    fd = [i for i, c in enumerate(classes) if c == O.BYTE_UNDEF]
+    return dict(
+        n_good=len(classes) - n_unaddr - n_undef, n_unaddr=n_unaddr, n_undef=n_undef,
+        first_bad_off=bad[0] if bad else -1,
+        first_bad_kind=classes[bad[0]] if bad else 0,
+        first_unaddr_off=fu[0] if fu else -1, first_undef_off=fd[0] if fd else -1)
+
+
+def _sub(d: dict, keys) -> dict:
+    return {k: d[k] for k in keys}
+
+
+SCAN_KEYS = ["n_good", "n_unaddr", "n_undef", "first_bad_off", "first_bad_kind",
+             "first_unaddr_off", "first_undef_off"]
+
+
+# --------------------------------------------------------------------- pins
+
+def pin_listing5(lib):
+    """Sec. 4, Listings 2 and 5: a device->host copy of size*sizeof(double)
+    from an allocation of size*sizeof(float) is reported as too large, with
+    8000000 bytes expected and 4000000 found."""
+    g = json.load(open(os.path.join(HERE, "golden", "listing5_dtoh_overrun.json")))
+    n = g["copy_bytes"]
+    a_bits, v = _image(np.ones(n, bool), np.full(n, 0xFF, np.uint8))
+    o = O.Oracle(a_bits, v, lib=lib)
+    c, a, b = 0x7f0000000000, 0x7f0000400000, 0x7f0000c00000
+    assert o.register_alloc(c, g["alloc_c_bytes"]) == 0
+    assert o.register_alloc(a, g["alloc_a_bytes"]) == 0
+    assert o.register_alloc(b, g["alloc_b_bytes"]) == 0
+    st, r = o.check_copy(DTOH, 0, c, n)
+    assert st == 0
+    assert r["flags"] & F["OVERRUN_SRC"], r
+    assert not r["flags"] & (F["UNALLOC_SRC"] | F["UNALLOC_DST"] | F["OVERRUN_DST"])
+    assert r["expected"] == g["expected"]
+    assert r["found_src"] == g["found"]
+    assert r["alloc_base_src"] == c and r["alloc_size_src"] == g["alloc_c_bytes"]
+    # the correctly sized copy of c is in range
+    st, r = o.check_copy(DTOH, 0, c, g["alloc_c_bytes"])
+    assert st == 0 and not r["flags"] & (F["OVERRUN_SRC"] | F["UNALLOC_SRC"])
+    assert r["found_src"] == g["alloc_c_bytes"]
+    # the two inputs (doubles) copy in range
+    for p in (a, b):
+        st, r = o.check_copy(HTOD, p, 0, n)
+        assert st == 0 and not r["flags"] & (F["OVERRUN_DST"] | F["UNALLOC_DST"]), r
+
+
+def pin_htod_bytes_by_construction(lib, max_n: int = 4):
+    """Every assignment of the 8 (A, V) states to n <= 4 bytes, at every A-bit
+    phase 0..15: counts and first offsets must equal those of the class list
+    the input was built from.  The surrounding bytes hold other states, so a
+    read outside the copy changes the answer."""
+    img_n = 64
+    noise_rng = np.random.default_rng(7)
+    for n in range(1, max_n + 1):
+        combos = list(itertools.product(range(len(BYTE_STATES)), repeat=n))
+        if n == 4:  # thin the 4096 patterns out but keep every state per slot
+            combos = combos[::3]
+        for ci, combo in enumerate(combos):
+            h = ci % 16 + 8
+            addr = noise_rng.integers(0, 2, img_n).astype(bool)
+            v = noise_rng.integers(0, 256, img_n).astype(np.uint8)
+            for i, st in enumerate(combo):
+                addr[h + i] = bool(BYTE_STATES[st][0])
+                v[h + i] = BYTE_STATES[st][1]
+            classes = [BYTE_STATES[st][2] for st in combo]
+            a_bits, vv = _image(addr, v)
+            o = O.Oracle(a_bits, vv, lib=lib)
+            assert o.register_alloc(1 << 20, 4096) == 0
+            stat, r = o.check_copy(HTOD, (1 << 20) + 16, h, n)
+            assert stat == 0
+            exp = _expect_from_classes(classes)
+            assert _sub(r, SCAN_KEYS) == exp, (combo, h, r, exp)
+            want_flags = (F["HOST_UNADDR"] if exp["n_unaddr"] else 0) | \
+                         (F["HOST_UNDEF"] if exp["n_undef"] else 0)
+            assert r["flags"] == want_flags, (combo, r["flags"])
+            o.close()
+
+
+def pin_dtoh_bytes_by_construction(lib):
+    """Device->host: the destination's A bit and the device source's V byte
+    (placed there by an exact host->device carry from a fully addressable
+    staging area) decide each byte's class."""
+    rng = np.random.default_rng(11)
+    for trial in range(400):
+        n = int(rng.integers(1, 9))
+        states = rng.integers(0, len(BYTE_STATES), n)
+        img_n = 128
+        addr = rng.integers(0, 2, img_n).astype(bool)
+        v = rng.integers(0, 256, img_n).astype(np.uint8)
+        stage = 96  # staging area: addressable, V = the device values wanted
+        addr[stage:stage + n] = True
+        h = int(rng.integers(0, 40))
+        for i, st in enumerate(states):
+            addr[h + i] = bool(BYTE_STATES[st][0])
+            v[stage + i] = BYTE_STATES[st][1]
+        classes = [BYTE_STATES[st][2] for st in states]
+        a_bits, vv = _image(addr, v)
+        o = O.Oracle(a_bits, vv, lib=lib)
+        dev = 0x5000_0000
+        assert o.register_alloc(dev, 256) == 0
+        st0, _ = o.check_copy(HTOD, dev + 7, stage, n)
+        assert st0 == 0
+        stat, r = o.check_copy(DTOH, h, dev + 7, n)
+        assert stat == 0
+        exp = _expect_from_classes(classes)
+        assert _sub(r, SCAN_KEYS) == exp, (trial, r, exp)
+        want = (F["HOST_UNADDR"] if exp["n_unaddr"] else 0) | \
+               (F["DEV_UNDEF_SRC"] if exp["n_undef"] else 0)
+        assert r["flags"] == want
+        o.close()
+
+
+def _owner(layout, addr):
+    for k, (b, s) in enumerate(layout):
+        if b <= addr < b + s:
+            return k
+    return None
+
+
+def _range_truth(layout, d, n):
+    """Set membership over every address: the copy is in range iff every
+    address of [d, d+n) belongs to one and the same allocation."""
+    own = _owner(layout, d)
+    if own is None:
+        return "UNALLOC", 0
+    found = 0
+    a = d
+    while _owner(layout, a) == own:
+        found += 1
+        a += 1
+    ok = all(_owner(layout, x) == own for x in range(d, d + n))
+    return ("OK" if ok else "OVERRUN"), found
+
+
+def pin_range_bruteforce(lib, trials: int = 300):
+    """Up to three allocations in a 64-address space, random copies: the
+    verdict and the found count equal the set-membership truth (Sec. 2
+    itemize; R7, R8)."""
+    rng = np.random.default_rng(3)
+    v = np.zeros(128, np.uint8)
+    a_bits, vv = _image(np.ones(128, bool), v)
+    for t in range(trials):
+        k = int(rng.integers(0, 4))
+        cuts = np.sort(rng.choice(np.arange(0, 65), size=2 * k, replace=False))
+        layout = [(int(cuts[2 * i]), int(cuts[2 * i + 1] - cuts[2 * i])) for i in range(k)]
+        layout = [(b, s) for b, s in layout if s > 0]
+        o = O.Oracle(a_bits, vv, lib=lib)
+        base0 = 1 << 32
+        for b, s in layout:
+            assert o.register_alloc(base0 + b, s) == 0
+        for _ in range(30):
+            d = int(rng.integers(0, 64))
+            n = int(rng.integers(1, 40))
+            verdict, found = _range_truth(layout, d, n)
+            stat, r = o.check_copy(HTOD, base0 + d, 0, n)
+            assert stat == 0
+            got = "UNALLOC" if r["flags"] & F["UNALLOC_DST"] else \
+                "OVERRUN" if r["flags"] & F["OVERRUN_DST"] else "OK"
+            assert got == verdict, (layout, d, n, r)
+            assert r["found_dst"] == found, (layout, d, n, r["found_dst"], found)
+            if verdict != "UNALLOC":
+                b, s = layout[_owner(layout, d)]
+                assert (r["alloc_base_dst"], r["alloc_size_dst"]) == (base0 + b, s)
+        o.close()
+
+
+def pin_free_sequences(lib):
+    """Frees of live, interior, already freed and unknown pointers; refused
+    registrations (the error classes named for frees; R13, R14)."""
+    o = O.Oracle(*_image(np.ones(16, bool), np.zeros(16, np.uint8)), lib=lib)
+    assert o.register_alloc(100, 10) == 0
+    assert o.register_alloc(105, 10) == -6          # overlaps [100, 110)
+    assert o.register_alloc(90, 11) == -6           # ends inside
+    assert o.register_alloc(90, 10) == 0            # touches, no overlap
+    assert o.register_alloc(200, 0) == -4           # zero size
+    assert o.register_alloc((1 << 64) - 8, 16) == -5  # wraps
+    assert o.free(105) == "INTERIOR"
+    assert o.free(100) == "OK"
+    assert o.free(100) == "DOUBLE"
+    assert o.free(300) == "UNKNOWN"
+    assert o.free(90) == "OK"
+    assert o.free(90) == "DOUBLE"
+    assert o.live_count() == 0
+    o.close()
+
+
+def pin_free_sequences_reuse(lib):
+    """A freed base that a later allocation covers is no longer a double
+    free target; after that allocation's free it is unknown, not double."""
+    o = O.Oracle(*_image(np.ones(16, bool), np.zeros(16, np.uint8)), lib=lib)
+    assert o.register_alloc(100, 10) == 0
+    assert o.free(100) == "OK"
+    assert o.register_alloc(96, 20) == 0
+    assert o.free(100) == "INTERIOR"
+    assert o.free(96) == "OK"
+    assert o.free(100) == "UNKNOWN"
+    assert o.free(96) == "DOUBLE"
+    assert o.register_alloc(96, 4) == 0
+    assert o.free(96) == "OK"
+    assert o.live_count() == 0
+    o.close()
+
+
+def pin_generator_truth(lib):
+    """Counts of a host->device scan equal what the generator planted: the
+    undefined bytes are the union of the planted runs (all masks nonzero by
+    construction) minus the planted unaddressable positions."""
+    rng = S.rng_for(5)
+    img = S.host_image_runs(rng, 1 << 16, 0.02, 8.0, 0.5, 0.003)
+    undef = np.zeros(img.n, bool)
+    for s0, ln in img.undef_runs:
+        undef[s0:s0 + ln] = True
+    unaddr = np.zeros(img.n, bool)
+    unaddr[img.unaddr] = True
+    o = O.Oracle(img.a_bits, img.v, carry=False, lib=lib)
+    assert o.register_alloc(1 << 40, 1 << 16) == 0
+    for _ in range(300):
+        n = int(rng.integers(1, 5000))
+        h = int(rng.integers(0, img.n - n + 1))
+        st, r = o.check_copy(HTOD, 1 << 40, h, n)
+        assert st == 0
+        ua = unaddr[h:h + n]
+        ud = undef[h:h + n] & ~ua
+        assert r["n_unaddr"] == int(ua.sum())
+        assert r["n_undef"] == int(ud.sum())
+        assert r["first_unaddr_off"] == (int(np.argmax(ua)) if ua.any() else -1)
+        assert r["first_undef_off"] == (int(np.argmax(ud)) if ud.any() else -1)
+    o.close()
+
+
+def pin_invariants(lib):
+    """good + unaddr + undef = n; the first bad offset is the smaller of the
+    per-class first offsets; counts add up when a copy is split in two."""
+    rng = S.rng_for(9)
+    img = S.host_image_runs(rng, 1 << 15, 0.05, 8.0, 0.5, 0.01)
+    o = O.Oracle(img.a_bits, img.v, carry=False, lib=lib)
+    assert o.register_alloc(1 << 30, 1 << 15) == 0
+    for _ in range(300):
+        n = int(rng.integers(2, 3000))
+        h = int(rng.integers(0, img.n - n + 1))
+        k = int(rng.integers(1, n))
+        _, w = o.check_copy(HTOD, 1 << 30, h, n)
+        _, a = o.check_copy(HTOD, 1 << 30, h, k)
+        _, b = o.check_copy(HTOD, (1 << 30) + k, h + k, n - k)
+        assert w["n_good"] + w["n_unaddr"] + w["n_undef"] == n
+        for key in ("n_good", "n_unaddr", "n_undef"):
+            assert w[key] == a[key] + b[key]
+        for key in ("first_unaddr_off", "first_undef_off", "first_bad_off"):
+            want = a[key] if a[key] >= 0 else (b[key] + k if b[key] >= 0 else -1)
+            assert w[key] == want
+        firsts = [x for x in (w["first_unaddr_off"], w["first_undef_off"]) if x >= 0]
+        assert w["first_bad_off"] == (min(firsts) if firsts else -1)
+    o.close()
+
+
+def pin_carry_roundtrip(lib):
+    """Sec. 5 (definedness follows the data): host->device then device->host
+    of fully addressable bytes restores the V masks exactly; a fresh
+    allocation reads back as undefined (R6); a failed copy carries nothing
+    (R11); unaddressable destination bytes keep their masks."""
+    rng = S.rng_for(13)
+    n_img = 1 << 14
+    v = rng.integers(0, 256, n_img).astype(np.uint8)
+    v[rng.random(n_img) < 0.5] = 0
+    addr = np.ones(n_img, bool)
+    addr[8192:] = rng.random(n_img - 8192) > 0.2   # second half: holes
+    a_bits, vv = _image(addr, v)
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev = 1 << 36
+    assert o.register_alloc(dev, 4096) == 0
+    # fresh allocation -> every addressable destination byte becomes 0xFF
+    st, r = o.check_copy(DTOH, 8192, dev, 1000)
+    assert st == 0
+    hv = o.read_host_v(8192, 1000)
+    exp = np.where(addr[8192:9192], 0xFF, v[8192:9192]).astype(np.uint8)
+    assert np.array_equal(hv, exp)
+    assert r["n_undef"] == int(addr[8192:9192].sum())
+    assert r["n_unaddr"] == int((~addr[8192:9192]).sum())
+    # round trip over the fully addressable first half
+    st, _ = o.check_copy(HTOD, dev + 100, 0, 3000)
+    assert st == 0
+    assert np.array_equal(o.read_dev_v(dev + 100, 3000), v[:3000])
+    st, _ = o.check_copy(DTOH, 4000, dev + 100, 3000)
+    assert np.array_equal(o.read_host_v(4000, 3000), v[:3000])
+    # the untouched device bytes are still undefined
+    assert np.all(o.read_dev_v(dev, 100) == 0xFF)
+    # unaddressable source bytes arrive on the device undefined
+    st, r = o.check_copy(HTOD, dev + 3200, 9500, 800)
+    assert st == 0 and r["n_unaddr"] == int((~addr[9500:10300]).sum())
+    got = o.read_dev_v(dev + 3200, 800)
+    holes = ~addr[9500:10300]
+    assert np.all(got[holes] == 0xFF)
+    assert np.array_equal(got[~holes], v[9500:10300][~holes])
+    # an overrunning copy carries nothing
+    before = o.read_dev_v(dev, 4096).copy()
+    st, r = o.check_copy(HTOD, dev + 4000, 8192, 200)
+    assert r["flags"] & F["OVERRUN_DST"]
+    assert np.array_equal(o.read_dev_v(dev, 4096), before)
+    # n == 0 is a no-op (R9) even on a wild pointer
+    st, r = o.check_copy(HTOD, 12345, 0, 0)
+    assert st == 0 and r["flags"] == 0 and r["first_bad_off"] == -1
+    o.close()
+
+
+def pin_dtod_memmove(lib):
+    """Device->device carries like memmove, compared against Python's slice
+    assignment (which reads the whole source before writing); overlapping
+    copies raise the overlap warning (R12).  A chain X->Y->Z leaves Z as
+    a direct X->Z copy would."""
+    rng = S.rng_for(17)
+    n_img = 4096
+    v = rng.integers(0, 256, n_img).astype(np.uint8)
+    a_bits, vv = _image(np.ones(n_img, bool), v)
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev = 1 << 33
+    assert o.register_alloc(dev, 4096) == 0
+    assert o.check_copy(HTOD, dev, 0, 4096)[0] == 0
+    model = bytearray(v.tobytes())
+    for _ in range(200):
+        n = int(rng.integers(1, 600))
+        s0 = int(rng.integers(0, 4096 - n + 1))
+        d0 = int(np.clip(s0 + rng.integers(-n, n + 1), 0, 4096 - n))
+        st, r = o.check_copy(DTOD, dev + d0, dev + s0, n)
+        assert st == 0
+        model[d0:d0 + n] = model[s0:s0 + n]
+        assert bool(r["flags"] & F["DTOD_OVERLAP"]) == (abs(d0 - s0) < n)
+        assert o.read_dev_v(dev, 4096).tobytes() == bytes(model)
+    # chain X -> Y -> Z versus X -> Z'
+    for p in (1 << 34, 2 << 34, 3 << 34):
+        assert o.register_alloc(p, 1024) == 0
+    o.check_copy(HTOD, 1 << 34, 100, 1024)
+    o.check_copy(DTOD, 2 << 34, 1 << 34, 1024)
+    o.check_copy(DTOD, 3 << 34, 2 << 34, 1024)
+    assert o.read_dev_v(3 << 34, 1024).tobytes() == bytes(v[100:1124])
+    o.close()
+
+
+def pin_records(lib):
+    """Records: one per set flag, in (request, flag bit) order, with the
+    offsets and counts of the report; strict mode makes undefined
+    device-source bytes an error."""
+    n_img = 256
+    addr = np.ones(n_img, bool)
+    addr[10] = False
+    v = np.zeros(n_img, np.uint8)
+    v[20] = 0x40
+    a_bits, vv = _image(addr, v)
+    o = O.Oracle(a_bits, vv, lib=lib)
+    A, B = 1 << 20, 1 << 21
+    assert o.register_alloc(A, 64) == 0
+    assert o.register_alloc(B, 64) == 0
+    reqs = np.zeros(5, S.REQ_DTYPE)
+    reqs[0] = (HTOD, 0, A, 0, 32)       # unaddr at 10, undef at 20
+    reqs[1] = (HTOD, 0, A + 58, 0, 8)   # overrun dst, found 6
+    reqs[2] = (DTOH, 0, 0, B, 8)        # fresh alloc -> dev undef
+    reqs[3] = (DTOD, 0, B + 4, B, 16)   # overlap + dev undef src
+    reqs[4] = (DTOD, 0, 77, 99, 5)      # both unallocated
+    st, reps, _ = o.check_batch(reqs)
+    assert st == 0
+    recs = O.emit_records(reps, reqs, strict=False, lib=lib)
+    got = [(r["req"], O.FLAG_NAMES[r["cls"]], r["severity"], r["off"], r["count"],
+            r["expected"], r["found"]) for r in recs]
+    want = [
+        (0, "HOST_UNADDR", 0, 10, 1, 32, 31),
+        (0, "HOST_UNDEF", 0, 20, 1, 32, 30),
+        (1, "OVERRUN_DST", 0, 6, 2, 8, 6),
+        (2, "DEV_UNDEF_SRC", 1, 0, 8, 8, 0),
+        (3, "DEV_UNDEF_SRC", 1, 0, 16, 16, 0),
+        (3, "DTOD_OVERLAP", 1, 4, 12, 16, 0),
+        (4, "UNALLOC_DST", 0, 0, 5, 5, 0),
+        (4, "UNALLOC_SRC", 0, 0, 5, 5, 0),
+    ]
+    assert got == want, got
+    strict = O.emit_records(reps, reqs, strict=True, lib=lib)
+    assert [r["severity"] for r in strict if O.FLAG_NAMES[r["cls"]] == "DEV_UNDEF_SRC"] == [0, 0]
+    o.close()
+
+
+def pin_host_range_errors(lib):
+    """Requests outside the host image or of an unknown kind are API errors,
+    and a batch holding one is refused before anything runs."""
+    a_bits, vv = _image(np.ones(64, bool), np.zeros(64, np.uint8))
+    o = O.Oracle(a_bits, vv, lib=lib)
+    assert o.register_alloc(1 << 20, 64) == 0
+    assert o.check_copy(HTOD, 1 << 20, 60, 8)[0] == -3
+    assert o.check_copy(DTOH, (1 << 64) - 1, 1 << 20, 2)[0] == -3
+    assert o.check_copy(7, 0, 0, 1)[0] == -2
+    reqs = np.zeros(3, S.REQ_DTYPE)
+    reqs[0] = (HTOD, 0, 1 << 20, 0, 64)
+    reqs[1] = (DTOH, 0, 60, 1 << 20, 8)
+    reqs[2] = (HTOD, 0, 1 << 20, 0, 64)
+    st, _, bad = o.check_batch(reqs)
+    assert st == -3 and bad == 1
+    assert np.all(o.read_dev_v(1 << 20, 64) == 0xFF)   # nothing ran
+    o.close()
+
+
+ALL_PINS = [
+    pin_listing5, pin_htod_bytes_by_construction, pin_dtoh_bytes_by_construction,
+    pin_range_bruteforce, pin_free_sequences, pin_free_sequences_reuse, pin_generator_truth,
+    pin_invariants, pin_carry_roundtrip, pin_dtod_memmove, pin_records,
+    pin_host_range_errors,
+]
+
+
+def run_all(lib_path: str | None = None) -> list[str]:
+    """Run every pin; return the names of those that failed."""
+    lib = O.load(lib_path)
+    failed = []
+    for p in ALL_PINS:
+        try:
+            p(lib)
+        except AssertionError:
+            failed.append(p.__name__)
+    return failed
+
+
+if __name__ == "__main__":
+    bad = run_all(sys.argv[1] if len(sys.argv) > 1 else None)
+    print("FAILED:" + ",".join(bad) if bad else "ALL PINS PASS")
+    sys.exit(1 if bad else 0)

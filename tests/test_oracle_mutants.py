@@ -1,0 +1,95 @@
+"""Plant plausible mistakes in a copy of the CPU oracle and check that the
+pins catch every one of them (a pin suite that a dropped term, a flipped
+comparison or a wrong index can pass would not pin anything).
+
+Each mutant is compiled from the oracle source with one textual change and
+run through ``tests/pins.py`` in a child process, so that a mutant that
+crashes counts as caught without taking the test run down.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+
+SRC = open(os.path.join(ROOT, "oracle", "cg_oracle.c")).read()
+
+MUTANTS = {
+    "a_bit_msb_first": ("return (s->a_bits[pos >> 3] >> (pos & 7)) & 1;",
+                        "return (s->a_bits[pos >> 3] >> (7 - (pos & 7))) & 1;"),
+    "a_bit_no_offset": ("if (!host_a_bit(s, src + i))", "if (!host_a_bit(s, i))"),
+    "undef_only_full_mask": ("else if (s->host_v[src + i] != 0)",
+                             "else if (s->host_v[src + i] == 0xFF)"),
+    "undef_before_unaddr": (
+        "      if (!host_a_bit(s, src + i))\n        cls = OR_BYTE_UNADDR;\n"
+        "      else if (s->host_v[src + i] != 0)\n        cls = OR_BYTE_UNDEF;",
+        "      if (s->host_v[src + i] != 0)\n        cls = OR_BYTE_UNDEF;\n"
+        "      else if (!host_a_bit(s, src + i))\n        cls = OR_BYTE_UNADDR;"),
+    "dtoh_ignores_dest_a": ("if (!host_a_bit(s, dst + i))\n        cls = OR_BYTE_UNADDR;",
+                            "if (0)\n        cls = OR_BYTE_UNADDR;"),
+    "last_unaddr_not_first": ("if (r->first_unaddr_off < 0) r->first_unaddr_off = (int64_t)i;",
+                              "r->first_unaddr_off = (int64_t)i;"),
+    "first_bad_kind_unset": ("r->first_bad_kind = cls;", "r->first_bad_kind = OR_BYTE_UNDEF;"),
+    "good_count_dropped": ("      r->n_good++;", "      ;"),
+    "overrun_off_by_one": ("if (n > *found) {", "if (n >= *found) {"),
+    "found_off_by_one": ("*found = a->base + a->size - p;", "*found = a->base + a->size - p - 1;"),
+    "containment_inclusive": ("if (addr - a->base < a->size) return a;",
+                              "if (addr - a->base <= a->size) return a;"),
+    "lookup_first_not_last": ("  live_alloc *a = &s->live[ub - 1];",
+                              "  live_alloc *a = &s->live[0];"),
+    "fresh_shadow_defined": ("return a->shadow ? a->shadow[off] : 0xFF;",
+                             "return a->shadow ? a->shadow[off] : 0x00;"),
+    "htod_carry_ignores_a": (
+        "da->shadow[o + i] = host_a_bit(s, src + i) ? s->host_v[src + i] : 0xFF;",
+        "da->shadow[o + i] = s->host_v[src + i];"),
+    "dtoh_carry_ignores_a": ("if (host_a_bit(s, dst + i)) s->host_v[dst + i] = dev_v(sa, o + i);",
+                             "s->host_v[dst + i] = dev_v(sa, o + i);"),
+    "carry_on_overrun": ("if (kind == OR_HTOD && da) {", "if (kind == OR_HTOD && r->alloc_size_dst) {\n"
+                         "    if (!da) da = find_alloc(s, dst);"),
+    "dtod_forward_copy": ("for (uint64_t i = 0; i < n; i++) da->shadow[od + i] = tmp[i];",
+                          "for (uint64_t i = 0; i < n; i++) da->shadow[od + i] = dev_v(sa, os + i);"),
+    "overlap_inclusive": ("if (dist < n) r->flags |= OR_F_DTOD_OVERLAP;",
+                          "if (dist <= n) r->flags |= OR_F_DTOD_OVERLAP;"),
+    "double_free_as_unknown": ("    *verdict = OR_FREE_DOUBLE;", "    *verdict = OR_FREE_UNKNOWN;"),
+    "freed_set_never_pruned": ("while (hi < s->n_freed && s->freed[hi] - base < size) hi++;",
+                               "(void)size;"),
+    "overlap_check_skips_successor": (
+        "if (ub < s->n_live && s->live[ub].base < base + size) return OR_E_OVERLAP;", ""),
+    "overrun_record_count": ("rec.count = n[i] - found;", "rec.count = found;"),
+    "warning_severity_lost": ("if (f == OR_F_DEV_UNDEF_SRC && !strict) rec.severity = 1;", ""),
+    "batch_not_validated_first": (
+        "    int st = validate(s, kind[i], dst[i], src[i], n[i]);\n    if (st) {",
+        "    int st = 0;\n    if (st) {"),
+}
+
+
+def _run_mutant(name: str) -> tuple[str, int, str]:
+    old, new = MUTANTS[name]
+    assert SRC.count(old) == 1, f"mutation {name}: anchor text not found exactly once"
+    path = O.build_variant(SRC.replace(old, new), name)
+    p = subprocess.run([sys.executable, os.path.join(HERE, "pins.py"), path],
+                       capture_output=True, text=True, timeout=600)
+    return name, p.returncode, (p.stdout + p.stderr)[-300:]
+
+
+@pytest.mark.timeout(900)
+def test_every_planted_mistake_is_caught():
+    with ThreadPoolExecutor(max_workers=max(2, (os.cpu_count() or 2))) as ex:
+        results = list(ex.map(_run_mutant, sorted(MUTANTS)))
+    survivors = [(n, out) for n, rc, out in results if rc == 0]
+    assert not survivors, f"pins missed these planted mistakes: {survivors}"
+
+
+def test_real_oracle_passes_pins():
+    p = subprocess.run([sys.executable, os.path.join(HERE, "pins.py")],
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stdout + p.stderr
