@@ -1,0 +1,364 @@
+"""Benchmark: single-transfer shadow checks (host->device scan + V carry) on
+large synthetic transfers, through libcg's C ABI.
+
+Workload (default): one host->device check each of 256 MiB, 1 GiB and
+4 GiB from a 4 GiB host shadow image (V undefined density 1e-6 in sparse
+runs, fully addressable) against a 16-entry allocation table.  One step =
+the three checks.  Every input is larger than L2 (129 MB), so no flush is
+needed between iterations.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cg_synth as S  # noqa: E402
+
+GB = 1e9
+BYTES_PER_BYTE_CARRY = 2.125  # V read 1 + A read 1/8 + device V write 1
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def build_workload(sizes):
+    w = S.large(0, sizes=sizes)
+    return w
+
+
+def run_cg(args, world, rank, local):
+    import torch
+
+    import paper_1310_0901_gb300 as cg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = tuple(int(x) << 20 for x in args.sizes_mib.split(","))
+    w = build_workload(sizes)
+    n_img = w.image.n
+    a_host = torch.from_numpy(w.image.a_bits[: n_img // 8].copy()).pin_memory()
+    v_host = torch.from_numpy(w.image.v).pin_memory()
+    a_dev = a_host.to(dev)
+    v_dev = v_host.to(dev)
+    ctx = cg.Context()
+    ctx.bind_host_shadow(a_dev, v_dev)
+    order = np.argsort(w.table.base)
+    for b, s in zip(w.table.base[order], w.table.size[order]):
+        cg.check(ctx.register_alloc(int(b), int(s)), "register")
+    reqs = [cg.cg_copy(int(q["kind"]), 0, int(q["dst"]), int(q["src"]), int(q["n"]))
+            for q in w.reqs]
+    bytes_per_step = sum(int(q["n"]) for q in w.reqs)
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    rep_dev = torch.zeros((len(reqs), 112), dtype=torch.uint8, device=dev)
+    import ctypes
+
+    def step_async(events=None):
+        for i, q in enumerate(reqs):
+            if events is not None:
+                events[i][0].record(stream)
+            cg.check(cg.cg_check_copy_async(ctx.handle, ctypes.byref(q),
+                                            rep_dev[i].data_ptr(), sh), "check_async")
+            if events is not None:
+                events[i][1].record(stream)
+
+    # warm-up (also validates the reports once against expectations)
+    for _ in range(args.warmup):
+        step_async()
+    torch.cuda.synchronize()
+    reps = np.frombuffer(rep_dev.cpu().numpy().tobytes(), dtype=cg.REPORT_DTYPE)
+    planted = np.zeros(n_img, bool)
+    for s0, ln in w.image.undef_runs:
+        planted[s0:s0 + ln] = True
+    for i, q in enumerate(w.reqs):
+        n = int(q["n"])
+        assert int(reps[i]["n_undef"]) == int(planted[:n].sum()), "report mismatch"
+        assert int(reps[i]["flags"]) in (0, cg.FLAGS["HOST_UNDEF"])
+
+    k0 = ctx.stats()["kernels"]
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in reqs] for _ in range(args.steps)]
+    t0.record(stream)
+    for k in range(args.steps):
+        step_async(ev[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = ctx.stats()["kernels"] - k0
+    elapsed_ms = t0.elapsed_time(t1)
+    # per-kernel durations (the scan kernel is the only launch per check)
+    kern_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(len(reqs))]
+                        for k in range(args.steps)])
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_bytes = bytes_per_step * args.steps * world
+    value = total_bytes / (elapsed_ms / 1e3) / GB
+
+    # roofline of the dominant kernel: the largest transfer's scan+carry
+    big = int(np.argmax([int(q["n"]) for q in w.reqs]))
+    kmean = float(kern_ms[:, big].mean())
+    alg_bytes = BYTES_PER_BYTE_CARRY * int(w.reqs[big]["n"])
+    achieved = alg_bytes / (kmean / 1e3) / GB
+    peak, peak_kind = _peaks()
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "scan_htod_traffic.json")
+    if os.path.exists(tp):
+        try:
+            tj = json.load(open(tp))
+            if tj.get("kernel_version") == _kernel_version():
+                traffic = tj["dram_bytes_per_launch_scaled"]
+        except Exception:
+            traffic = None
+
+    # end to end through the C ABI: per step upload each transfer's host
+    # shadow (V + A) from pinned host memory, check, read the report
+    e2e_ms = None
+    h2d = 0
+    d2h = 0
+    if args.e2e_steps > 0:
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for q in w.reqs:
+                n = int(q["n"])
+                ctx.upload_host_shadow(a_host, v_host, int(q["src"]), n, stream)
+                st, rep = ctx.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), n, stream)
+                cg.check(st, "check_copy")
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - s0) * 1e3
+        h2d = int(sum(int(q["n"]) + int(q["n"]) // 8 for q in w.reqs))
+        d2h = 112 * len(reqs)
+    if world > 1:
+        t = torch.tensor([e2e_ms or 0.0], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    out = {
+        "metric": "shadow GB/s checked vs HBM peak (single large host->device transfer checks)",
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(elapsed_ms / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded cg_synth.large: V undefined density 1e-6 in runs, A all addressable)",
+        "config": {"workload": w.name, "checks_per_step": len(reqs),
+                   "bytes_checked_per_step": bytes_per_step,
+                   "l2": "inputs larger than L2 (each transfer >= 256 MiB); no flush",
+                   "parallelism": f"replicas x{world}", "carry": True},
+        "roofline": {"bound": "hbm", "kernel": "scan_single_kernel<HTOD,carry>",
+                     "bytes_per_checked_byte": BYTES_PER_BYTE_CARRY,
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "traffic": traffic, "kernel_ms_mean": round(kmean, 4),
+                     "kernel_ms_per_size": {f"{int(q['n']) >> 20}MiB":
+                                            round(float(kern_ms[:, i].mean()), 4)
+                                            for i, q in enumerate(w.reqs)}},
+        "gpu_launches": int(launches),
+    }
+    if e2e_ms is not None:
+        out["e2e"] = {"value": round(bytes_per_step * args.e2e_steps * world / (e2e_ms / 1e3) / GB, 2),
+                      "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                      "steps": args.e2e_steps}
+    if clk is not None:
+        out["clocks"] = clk
+    ctx.close()
+    return out, w
+
+
+def _kernel_version() -> str:
+    import hashlib
+    src = os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", "cg_kernels.cu")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+def cpu_sample(w, budget_s: float):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    host->device checks of the workload's transfers in order (smallest
+    first) until the time budget is used; one thread."""
+    import oracle as O
+    sizes = sorted(int(q["n"]) for q in w.reqs)
+    reqs = sorted(w.reqs, key=lambda q: int(q["n"]))
+    n_img = sizes[-1]
+    done = 0
+    t = 0.0
+    used = []
+    img_n = min(n_img, max(sizes[0], 1 << 28))
+    orc = O.Oracle(w.image.a_bits[: (img_n + 7) // 8], w.image.v[:img_n])
+    order = np.argsort(w.table.base)
+    for b, s in zip(w.table.base[order], w.table.size[order]):
+        orc.register_alloc(int(b), int(s))
+    while t < budget_s:
+        q = reqs[0]
+        n = min(int(q["n"]), img_n)
+        s0 = time.perf_counter()
+        st, _ = orc.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), n)
+        t += time.perf_counter() - s0
+        assert st == 0
+        done += n
+        used.append(n)
+    orc.close()
+    return done / t / GB, f"{len(used)} x host->device check of {used[0] >> 20} MiB (first transfer of the workload), 1 thread, {t:.1f} s"
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle on the host cores, rank 0 only."""
+    if rank != 0:
+        return None
+    sizes = tuple(int(x) << 20 for x in args.sizes_mib.split(","))
+    w = build_workload(sizes)
+    import oracle as O
+    n0 = min(int(q["n"]) for q in w.reqs)
+    orc = O.Oracle(w.image.a_bits[: n0 // 8], w.image.v[:n0])
+    order = np.argsort(w.table.base)
+    for b, s in zip(w.table.base[order], w.table.size[order]):
+        orc.register_alloc(int(b), int(s))
+    q = min(w.reqs, key=lambda r: int(r["n"]))
+    sample = min(int(q["n"]), 64 << 20)  # each step: the first 64 MiB of the smallest transfer
+    for _ in range(args.warmup):
+        orc.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), sample)
+    s0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = orc.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), sample)
+        assert st == 0
+    dt = time.perf_counter() - s0
+    val = sample * args.steps / dt / GB
+    orc.close()
+    return {
+        "impl": "reference",
+        "metric": "shadow GB/s checked vs HBM peak (single large host->device transfer checks)",
+        "value": round(val, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": {"workload": w.name, "parallelism": "cpu oracle, 1 thread"},
+        "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {sample >> 20} MiB of the {int(q['n']) >> 20} MiB "
+                                   "host->device check per step"},
+        "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cg", choices=["cg", "reference"])
+    ap.add_argument("--sizes-mib", default="256,1024,4096")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out, w = run_cg(args, world, rank, local)
+    if rank == 0:
+        if world == 1 and args.cpu_budget_s > 0:
+            val, sample = cpu_sample(w, args.cpu_budget_s)
+            out["cpu_baseline"] = {"value": round(val, 4), "unit": "GB/s", "cores": 1,
+                                   "kind": "oracle", "sample": sample}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

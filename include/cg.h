@@ -1,0 +1,292 @@
+/*
+ * cg.h -- C ABI of libcg, GPU transfer checks in the manner of Cudagrind
+ * (Baumann & Gracia, "Cudagrind: A Valgrind Extension for CUDA", 2013).
+ *
+ * Cudagrind wraps the CUDA driver calls that allocate, free and copy device
+ * memory.  It keeps a list of live device allocations (paper, Fig. 2 caption)
+ * and checks every copy against that list and against Memcheck's shadow of
+ * host memory (Sec. 2 itemize): copies into or out of unallocated device
+ * memory, undefined host data copied to the device, copies larger than their
+ * allocation.  Definedness then travels with the data in all three directions
+ * (Sec. 5).  libcg runs those checks on the GPU.
+ *
+ * Model
+ *  - Device addresses are plain 64-bit integers (the caller's pointers); libcg
+ *    never touches the memory they name.  It keeps, per live allocation, a
+ *    device-resident V shadow (1 byte per device byte, bit set = undefined),
+ *    all 0xFF when the allocation is registered.
+ *  - The host shadow image is caller-owned DEVICE memory (e.g. a torch
+ *    tensor) bound with cg_bind_host_shadow: a packed A bitmap (host byte p
+ *    <-> bit p&7 of a_bits[p>>3], 1 = addressable) and a V mask (1 byte per
+ *    host byte, bit set = undefined).  "Host addresses" in requests are byte
+ *    offsets into this image.
+ *  - Per byte of a copy: UNADDR if its host byte is unaddressable; else UNDEF
+ *    if its V mask is nonzero; else GOOD.  Unaddressable takes precedence.
+ *
+ * Conventions
+ *  - Every function returns cg_status: CG_OK (0) or a negative API error.
+ *    Check verdicts are never status codes; they live in cg_report.
+ *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).  libcg enqueues its work there.
+ *  - One cg_ctx must not be used from two host threads at once.
+ *  - Pointers documented "device" must be device-accessible memory of the
+ *    current device; "host" pointers are ordinary host memory.
+ */
+#ifndef CG_H
+#define CG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------- constants */
+
+typedef int32_t cg_status;
+#define CG_OK 0
+#define CG_E_ARG -1         /* null pointer or bad argument */
+#define CG_E_KIND -2        /* copy kind not HTOD/DTOH/DTOD */
+#define CG_E_HOST_RANGE -3  /* host range outside the bound host image */
+#define CG_E_ZERO_SIZE -4   /* registering a zero-size allocation */
+#define CG_E_WRAP -5        /* allocation range wraps 2^64 */
+#define CG_E_OVERLAP -6     /* allocation overlaps a live one; table unchanged */
+#define CG_E_NOMEM -7       /* device or host memory for the shadow ran out */
+#define CG_E_RANGE -8       /* mark/read range not inside one live allocation */
+#define CG_E_CUDA -9        /* a CUDA runtime call failed (see cg_last_error) */
+#define CG_E_NO_HOST -10    /* no host shadow image bound */
+#define CG_E_ALIGN -11      /* pointer or size breaks an alignment rule */
+#define CG_E_STATE -12      /* call not allowed in the context's state */
+#define CG_E_TIMEOUT -13    /* a bounded wait ran out */
+#define CG_E_FULL -14       /* a queue or ring is full */
+#define CG_E_TOO_BIG -15    /* size above a documented maximum */
+
+/* copy kinds (Sec. 5: host/device, device/host, device/device) */
+#define CG_HTOD 1u
+#define CG_DTOH 2u
+#define CG_DTOD 3u
+
+/* per-byte classes, cg_report.first_bad_kind */
+#define CG_BYTE_GOOD 0u
+#define CG_BYTE_UNADDR 1u
+#define CG_BYTE_UNDEF 2u
+
+/* cg_report.flags; cg_err_record.cls is the bit index */
+#define CG_F_UNALLOC_DST (1u << 0)   /* dst pointer in no live allocation */
+#define CG_F_UNALLOC_SRC (1u << 1)   /* src pointer in no live allocation */
+#define CG_F_OVERRUN_DST (1u << 2)   /* dst range runs past its allocation */
+#define CG_F_OVERRUN_SRC (1u << 3)   /* src range runs past its allocation */
+#define CG_F_HOST_UNADDR (1u << 4)   /* host bytes not addressable */
+#define CG_F_HOST_UNDEF (1u << 5)    /* HtoD: undefined host bytes sent */
+#define CG_F_DEV_UNDEF_SRC (1u << 6) /* DtoH/DtoD: undefined device bytes (warning) */
+#define CG_F_DTOD_OVERLAP (1u << 7)  /* DtoD src and dst overlap (warning) */
+#define CG_NFLAGS 8
+
+/* cg_free verdicts */
+#define CG_FREE_OK 0u
+#define CG_FREE_UNKNOWN 1u  /* no allocation ever had this base */
+#define CG_FREE_DOUBLE 2u   /* base of an allocation already freed */
+#define CG_FREE_INTERIOR 3u /* inside a live allocation, not its base */
+
+/* ----------------------------------------------------------------- types */
+
+/* One copy to check.  kind selects which fields are host offsets:
+ *   CG_HTOD: dst = device address, src = host offset
+ *   CG_DTOH: dst = host offset,    src = device address
+ *   CG_DTOD: dst = device address, src = device address
+ * reserved must be 0.  32 bytes. */
+typedef struct cg_copy {
+  uint32_t kind;
+  uint32_t reserved;
+  uint64_t dst;
+  uint64_t src;
+  uint64_t n;
+} cg_copy;
+
+/* The verdict of one copy check (Sec. 2 itemize; Listing 5's expected and
+ * found bytes).  Offsets are relative to the copy start; -1 = none.
+ * found_x = bytes from the x pointer to the end of the allocation holding
+ * it (0 when none does, or when x is the host side).  alloc_*_x describe
+ * that allocation.  n_good + n_unaddr + n_undef == expected == n. */
+typedef struct cg_report {
+  uint32_t flags;
+  uint32_t first_bad_kind;
+  int64_t first_bad_off;
+  int64_t first_unaddr_off;
+  int64_t first_undef_off;
+  uint64_t n_good;
+  uint64_t n_unaddr;
+  uint64_t n_undef;
+  uint64_t expected;
+  uint64_t found_dst;
+  uint64_t found_src;
+  uint64_t alloc_base_dst;
+  uint64_t alloc_size_dst;
+  uint64_t alloc_base_src;
+  uint64_t alloc_size_src;
+} cg_report; /* 112 bytes */
+
+/* One error or warning, emitted per set report flag in (req, cls) order.
+ *   UNALLOC_*:     off 0,            count n,             found 0
+ *   OVERRUN_*:     off found,        count n - found,     found = found
+ *   HOST_UNADDR:   off first unaddr, count n_unaddr,      found n - n_unaddr
+ *   HOST_UNDEF / DEV_UNDEF_SRC: off first undef, count n_undef, found n_good
+ *   DTOD_OVERLAP:  off dst - src,    count overlap bytes, found 0
+ * severity: 0 error, 1 warning (DEV_UNDEF_SRC unless strict; DTOD_OVERLAP). */
+typedef struct cg_err_record {
+  uint64_t req;
+  uint32_t cls;
+  uint32_t severity;
+  int64_t off;
+  uint64_t count;
+  uint64_t expected;
+  uint64_t found;
+} cg_err_record; /* 48 bytes */
+
+typedef struct cg_config {
+  uint32_t carry;               /* 1 (default): V shadow travels with copies */
+  uint32_t strict_device_undef; /* 1: undefined device-source bytes are errors */
+  uint64_t shadow_slab_bytes;   /* device shadow pool slab; 0 = 1 GiB */
+  uint64_t shadow_budget_bytes; /* cap on the device shadow pool; 0 = none */
+  uint32_t scan_ctas_per_sm;    /* single-check grid; 0 = automatic */
+  uint32_t batch_segment_kib;   /* batched work split; 0 = automatic */
+  uint32_t batch_ctas_per_sm;   /* batched grid; 0 = automatic */
+  uint32_t reserved[9];
+} cg_config;
+
+typedef struct cg_ctx cg_ctx;
+
+typedef struct cg_stats {
+  uint64_t checks;        /* copies checked (single + batched) */
+  uint64_t bytes_checked; /* sum of n */
+  uint64_t batches;
+  uint64_t levels;        /* dependency levels run by batches */
+  uint64_t kernels;       /* kernels launched by this context */
+  uint64_t errors[CG_NFLAGS]; /* reports per flag */
+  uint64_t live_allocs;
+  uint64_t shadow_bytes;  /* device shadow pool held */
+} cg_stats;
+
+/* ------------------------------------------------------------- lifetime */
+
+/* Fill *cfg with the defaults. */
+cg_status cg_config_default(cg_config *cfg);
+
+/* Create a context on the current CUDA device.  cfg may be NULL (defaults).
+ * Owns: the allocation table (host mirror + device copy), the device V
+ * shadow pool, small device scratch and pinned staging buffers. */
+cg_status cg_create(cg_ctx **out, const cg_config *cfg);
+
+/* Synchronises the context's work and frees everything it owns. */
+cg_status cg_destroy(cg_ctx *ctx);
+
+/* Bind the host shadow image (Memcheck's A and V bits of host memory,
+ * Sec. 1.1).  a_bits_dev: device, n_bytes/8 bytes; v_dev: device, n_bytes
+ * bytes.  Both 16-byte aligned; n_bytes a multiple of 128 (so both arrays
+ * are whole 16-byte vectors).  The caller keeps ownership and must keep them
+ * alive while bound; DtoH checks write v_dev (the carry).  Rebinding
+ * replaces the previous image.  CG_E_ALIGN on a broken rule. */
+cg_status cg_bind_host_shadow(cg_ctx *ctx, const uint8_t *a_bits_dev,
+                              uint8_t *v_dev, uint64_t n_bytes);
+
+/* Copy host-side shadow bytes [off, off+n) of an image held in host memory
+ * (pinned for speed) into the bound device image: V bytes [off, off+n) and
+ * A bytes [off/8, (off+n)/8).  off and n multiples of 8.  Asynchronous on
+ * `stream`; the host buffers must stay valid until the stream reaches it. */
+cg_status cg_upload_host_shadow(cg_ctx *ctx, const uint8_t *a_bits_host,
+                                const uint8_t *v_host, uint64_t off,
+                                uint64_t n, void *stream);
+
+/* --------------------------------------------------- allocation table */
+
+/* Record a device allocation [dptr, dptr+size) (the cuMemAlloc wrapper's
+ * bookkeeping, Fig. 2).  Its V shadow starts all undefined.  Frees bases
+ * it covers from the freed set.  CG_E_ZERO_SIZE, CG_E_WRAP, CG_E_OVERLAP
+ * (table unchanged), CG_E_NOMEM (shadow pool exhausted or over budget). */
+cg_status cg_register_alloc(cg_ctx *ctx, uint64_t dptr, uint64_t size);
+
+/* Register many; st_out[i] (host, may be NULL) gets each status.  Returns
+ * CG_OK if all succeeded, else the first failure's status. */
+cg_status cg_register_allocs(cg_ctx *ctx, const uint64_t *dptr,
+                             const uint64_t *size, uint64_t count,
+                             cg_status *st_out);
+
+/* The cuMemFree wrapper's check: *verdict gets CG_FREE_OK (allocation
+ * removed, its shadow released), CG_FREE_INTERIOR, CG_FREE_DOUBLE or
+ * CG_FREE_UNKNOWN (table unchanged for the last three). */
+cg_status cg_free(cg_ctx *ctx, uint64_t dptr, uint32_t *verdict);
+
+/* Memcheck-style client requests on device memory: mark [dptr, dptr+n) as
+ * defined (V = 0) or undefined (V = 0xFF), e.g. a kernel's output.  The
+ * range must lie in one live allocation (CG_E_RANGE).  Asynchronous. */
+cg_status cg_mark_defined(cg_ctx *ctx, uint64_t dptr, uint64_t n, void *stream);
+cg_status cg_mark_undefined(cg_ctx *ctx, uint64_t dptr, uint64_t n, void *stream);
+
+/* Copy the device V shadow of [dptr, dptr+n) (one live allocation) into
+ * host memory `out`.  Synchronous.  CG_E_RANGE otherwise. */
+cg_status cg_read_device_shadow(cg_ctx *ctx, uint64_t dptr, uint64_t n,
+                                uint8_t *out);
+
+/* ---------------------------------------------------------------- checks */
+
+/* Check one copy and carry its V shadow (Sec. 2 itemize, Listing 5,
+ * Sec. 5).  req, rep: host.  Synchronous: returns once *rep is filled.
+ * API errors: CG_E_KIND, CG_E_HOST_RANGE, CG_E_NO_HOST (HtoD/DtoH with no
+ * image bound); nothing is checked or carried then. */
+cg_status cg_check_copy(cg_ctx *ctx, const cg_copy *req, cg_report *rep,
+                        void *stream);
+
+/* The same check, enqueued on `stream` without waiting: the report is
+ * written to rep_dev (device memory, or mapped pinned host memory) when
+ * the stream reaches it.  Validation and the allocation lookup use the
+ * table as it is at call time.  Checks of one context must all be
+ * enqueued on one stream (they share a small device scratch area and the
+ * staging buffer for overlapping device->device copies). */
+cg_status cg_check_copy_async(cg_ctx *ctx, const cg_copy *req, cg_report *rep_dev,
+                              void *stream);
+
+/* Check copies reqs[0..nreq) with the result of checking them one after
+ * another in order (the same reports, records and final shadow state).
+ * Independent copies run together: one persistent kernel per dependency
+ * level over byte segments of all copies of the level.  reqs, reps, recs,
+ * n_rec: host.  reps may be NULL; recs may be NULL when rec_cap is 0.
+ * *n_rec gets the total record count, which may exceed rec_cap (then only
+ * the first rec_cap records are written).  Synchronous.  A batch holding an
+ * invalid request is refused as a whole (*n_rec untouched, nothing runs);
+ * *bad_index (may be NULL) gets its index. */
+cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
+                         cg_report *reps, cg_err_record *recs,
+                         uint64_t rec_cap, uint64_t *n_rec,
+                         uint64_t *bad_index, void *stream);
+
+/* ----------------------------------------------------------- diagnostics */
+
+/* The dependency levels cg_check_batch runs reqs[0..nreq) in (host only,
+ * no GPU work): level[i] = 1 + the highest level of an earlier request that
+ * reads what request i writes, writes what it reads, or writes what it
+ * writes (every request counted as writing its whole destination range);
+ * 0 when there is none, and all 0 when carry is 0.  reqs, level: host.
+ * *n_levels (may be NULL) gets 1 + the highest level (0 when nreq is 0). */
+cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry,
+                         int32_t *level, uint32_t *n_levels);
+
+cg_status cg_get_stats(const cg_ctx *ctx, cg_stats *out);
+
+/* Text for a report, e.g. for a device->host overrun:
+ *   "device->host copy of 8000000 bytes overruns its source allocation:
+ *    only 4000000 bytes from the pointer to its end"
+ * Writes at most cap bytes (NUL-terminated); returns CG_OK. */
+cg_status cg_format_report(const cg_report *rep, uint32_t kind, char *buf,
+                           size_t cap);
+
+/* The last CUDA or internal error message of this thread ("" if none). */
+const char *cg_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char *cg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CG_H */

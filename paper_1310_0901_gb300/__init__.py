@@ -1,0 +1,265 @@
+"""Python binding of libcg (``include/cg.h``): GPU transfer checks in the
+manner of Cudagrind (Baumann & Gracia, 2013).
+
+Argument marshalling only: every check runs in libcg's CUDA kernels.  The
+shared library is built in-tree by ``paper_1310_0901_gb300.build.build()``;
+importing this package without it raises, so there is no silent fallback.
+
+The C entry points are exposed under their own names (``cg_create``,
+``cg_check_copy``, ...) with ctypes signatures; ``Context`` wraps them for
+torch tensors (device memory) and numpy request arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libcg.so")
+
+HTOD, DTOH, DTOD = 1, 2, 3
+BYTE_GOOD, BYTE_UNADDR, BYTE_UNDEF = 0, 1, 2
+FLAG_NAMES = ["UNALLOC_DST", "UNALLOC_SRC", "OVERRUN_DST", "OVERRUN_SRC",
+              "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP"]
+FLAGS = {n: 1 << i for i, n in enumerate(FLAG_NAMES)}
+FREE_NAMES = {0: "OK", 1: "UNKNOWN", 2: "DOUBLE", 3: "INTERIOR"}
+STATUS = {0: "OK", -1: "E_ARG", -2: "E_KIND", -3: "E_HOST_RANGE", -4: "E_ZERO_SIZE",
+          -5: "E_WRAP", -6: "E_OVERLAP", -7: "E_NOMEM", -8: "E_RANGE", -9: "E_CUDA",
+          -10: "E_NO_HOST", -11: "E_ALIGN", -12: "E_STATE", -13: "E_TIMEOUT",
+          -14: "E_FULL", -15: "E_TOO_BIG"}
+
+u32, u64, i32, i64, vp = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
+                          ctypes.c_void_p)
+
+
+class cg_copy(ctypes.Structure):
+    _fields_ = [("kind", u32), ("reserved", u32), ("dst", u64), ("src", u64), ("n", u64)]
+
+
+class cg_report(ctypes.Structure):
+    _fields_ = [("flags", u32), ("first_bad_kind", u32), ("first_bad_off", i64),
+                ("first_unaddr_off", i64), ("first_undef_off", i64), ("n_good", u64),
+                ("n_unaddr", u64), ("n_undef", u64), ("expected", u64), ("found_dst", u64),
+                ("found_src", u64), ("alloc_base_dst", u64), ("alloc_size_dst", u64),
+                ("alloc_base_src", u64), ("alloc_size_src", u64)]
+
+
+class cg_err_record(ctypes.Structure):
+    _fields_ = [("req", u64), ("cls", u32), ("severity", u32), ("off", i64), ("count", u64),
+                ("expected", u64), ("found", u64)]
+
+
+class cg_config(ctypes.Structure):
+    _fields_ = [("carry", u32), ("strict_device_undef", u32), ("shadow_slab_bytes", u64),
+                ("shadow_budget_bytes", u64), ("scan_ctas_per_sm", u32),
+                ("batch_segment_kib", u32), ("batch_ctas_per_sm", u32),
+                ("reserved", u32 * 9)]
+
+
+class cg_stats(ctypes.Structure):
+    _fields_ = [("checks", u64), ("bytes_checked", u64), ("batches", u64), ("levels", u64),
+                ("kernels", u64), ("errors", u64 * 8), ("live_allocs", u64),
+                ("shadow_bytes", u64)]
+
+
+REPORT_FIELDS = [f for f, _ in cg_report._fields_]
+RECORD_FIELDS = [f for f, _ in cg_err_record._fields_]
+REPORT_DTYPE = np.dtype([(f, "<i8" if t is i64 else ("<u4" if t is u32 else "<u8"))
+                         for f, t in cg_report._fields_])
+RECORD_DTYPE = np.dtype([(f, "<i8" if t is i64 else ("<u4" if t is u32 else "<u8"))
+                         for f, t in cg_err_record._fields_])
+assert ctypes.sizeof(cg_copy) == 32 and ctypes.sizeof(cg_report) == 112
+assert ctypes.sizeof(cg_err_record) == 48
+assert REPORT_DTYPE.itemsize == 112 and RECORD_DTYPE.itemsize == 48
+
+# (name, restype, argtypes) of every entry point declared in include/cg.h
+SIGNATURES = [
+    ("cg_config_default", i32, [ctypes.POINTER(cg_config)]),
+    ("cg_create", i32, [ctypes.POINTER(vp), ctypes.POINTER(cg_config)]),
+    ("cg_destroy", i32, [vp]),
+    ("cg_bind_host_shadow", i32, [vp, vp, vp, u64]),
+    ("cg_upload_host_shadow", i32, [vp, vp, vp, u64, u64, vp]),
+    ("cg_register_alloc", i32, [vp, u64, u64]),
+    ("cg_register_allocs", i32, [vp, vp, vp, u64, vp]),
+    ("cg_free", i32, [vp, u64, ctypes.POINTER(u32)]),
+    ("cg_mark_defined", i32, [vp, u64, u64, vp]),
+    ("cg_mark_undefined", i32, [vp, u64, u64, vp]),
+    ("cg_read_device_shadow", i32, [vp, u64, u64, vp]),
+    ("cg_check_copy", i32, [vp, ctypes.POINTER(cg_copy), ctypes.POINTER(cg_report), vp]),
+    ("cg_check_copy_async", i32, [vp, ctypes.POINTER(cg_copy), vp, vp]),
+    ("cg_check_batch", i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(u64),
+                             ctypes.POINTER(u64), vp]),
+    ("cg_plan_levels", i32, [vp, u64, u32, vp, ctypes.POINTER(u32)]),
+    ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
+    ("cg_format_report", i32, [ctypes.POINTER(cg_report), u32, ctypes.c_char_p, ctypes.c_size_t]),
+    ("cg_last_error", ctypes.c_char_p, []),
+    ("cg_version", ctypes.c_char_p, []),
+]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libcg.so is not built ({LIB_PATH} missing): run "
+            "`python paper_1310_0901_gb300/build.py` or __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+for _name, _, _ in SIGNATURES:
+    globals()[_name] = getattr(_lib, _name)
+
+
+class CgError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = cg_last_error().decode(errors="replace")
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})")
+        self.status = status
+
+
+def check(status: int, what: str = "libcg") -> None:
+    if status != 0:
+        raise CgError(status, what)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def report_to_dict(r: cg_report) -> dict:
+    return {f: getattr(r, f) for f in REPORT_FIELDS}
+
+
+class Context:
+    """One libcg context: allocation table, device shadow pool, bound image."""
+
+    def __init__(self, carry: bool = True, strict: bool = False, **cfg):
+        c = cg_config()
+        check(cg_config_default(ctypes.byref(c)))
+        c.carry = int(carry)
+        c.strict_device_undef = int(strict)
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        self.cfg = c
+        h = vp()
+        check(cg_create(ctypes.byref(h), ctypes.byref(c)), "cg_create")
+        self._h = h
+        self._image = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            cg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind_host_shadow(self, a_bits, v) -> None:
+        """a_bits, v: CUDA uint8 tensors (kept referenced while bound)."""
+        check(cg_bind_host_shadow(self._h, a_bits.data_ptr(), v.data_ptr(), v.numel()),
+              "cg_bind_host_shadow")
+        self._image = (a_bits, v)
+
+    def upload_host_shadow(self, a_host, v_host, off: int, n: int, stream=None) -> None:
+        check(cg_upload_host_shadow(self._h, a_host.data_ptr(), v_host.data_ptr(), off, n,
+                                    _stream_handle(stream)), "cg_upload_host_shadow")
+
+    def register_alloc(self, dptr: int, size: int) -> int:
+        return cg_register_alloc(self._h, dptr, size)
+
+    def register_allocs(self, bases: np.ndarray, sizes: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(bases, dtype=np.uint64)
+        s = np.ascontiguousarray(sizes, dtype=np.uint64)
+        st = np.zeros(len(b), dtype=np.int32)
+        cg_register_allocs(self._h, b.ctypes.data, s.ctypes.data, len(b), st.ctypes.data)
+        return st
+
+    def free(self, dptr: int) -> str:
+        v = u32(99)
+        check(cg_free(self._h, dptr, ctypes.byref(v)), "cg_free")
+        return FREE_NAMES[v.value]
+
+    def mark_defined(self, dptr: int, n: int, stream=None) -> int:
+        return cg_mark_defined(self._h, dptr, n, _stream_handle(stream))
+
+    def mark_undefined(self, dptr: int, n: int, stream=None) -> int:
+        return cg_mark_undefined(self._h, dptr, n, _stream_handle(stream))
+
+    def read_device_shadow(self, dptr: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint8)
+        check(cg_read_device_shadow(self._h, dptr, n, out.ctypes.data if n else None),
+              "cg_read_device_shadow")
+        return out
+
+    def check_copy(self, kind: int, dst: int, src: int, n: int, stream=None):
+        q = cg_copy(kind, 0, dst, src, n)
+        r = cg_report()
+        st = cg_check_copy(self._h, ctypes.byref(q), ctypes.byref(r), _stream_handle(stream))
+        return st, report_to_dict(r)
+
+    def check_batch(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None):
+        """reqs: structured array with the layout of cg_copy (cg_synth.REQ_DTYPE).
+        Returns (status, reports as a structured array, records as a
+        structured array, total record count, bad index)."""
+        reqs = np.ascontiguousarray(reqs)
+        assert reqs.dtype.itemsize == 32
+        n = len(reqs)
+        if rec_cap is None:
+            rec_cap = 8 * n
+        reps = np.zeros(n, dtype=REPORT_DTYPE)
+        recs = np.zeros(max(1, rec_cap), dtype=RECORD_DTYPE)
+        n_rec = u64(0)
+        bad = u64(0)
+        st = cg_check_batch(self._h, reqs.ctypes.data if n else None, n,
+                            reps.ctypes.data if n else None,
+                            recs.ctypes.data if rec_cap else None, rec_cap,
+                            ctypes.byref(n_rec), ctypes.byref(bad), _stream_handle(stream))
+        total = int(n_rec.value)
+        return st, reps, recs[:min(total, rec_cap)], total, int(bad.value)
+
+    def stats(self) -> dict:
+        s = cg_stats()
+        check(cg_get_stats(self._h, ctypes.byref(s)))
+        d = {f: getattr(s, f) for f, _ in cg_stats._fields_ if f != "errors"}
+        d["errors"] = list(s.errors)
+        return d
+
+
+def plan_levels(reqs: np.ndarray, carry: bool = True) -> tuple[np.ndarray, int]:
+    """Dependency levels of a batch (host only, see cg_plan_levels)."""
+    reqs = np.ascontiguousarray(reqs)
+    lv = np.zeros(len(reqs), dtype=np.int32)
+    nl = u32(0)
+    check(cg_plan_levels(reqs.ctypes.data if len(reqs) else None, len(reqs), int(carry),
+                         lv.ctypes.data if len(reqs) else None, ctypes.byref(nl)),
+          "cg_plan_levels")
+    return lv, int(nl.value)
+
+
+def format_report(rep: dict, kind: int) -> str:
+    r = cg_report(**{k: rep[k] for k in REPORT_FIELDS})
+    buf = ctypes.create_string_buffer(4096)
+    check(cg_format_report(ctypes.byref(r), kind, buf, len(buf)))
+    return buf.value.decode()

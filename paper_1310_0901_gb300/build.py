@@ -1,0 +1,59 @@
+"""Build libcg.so in-tree with nvcc for sm_103a (GB300)."""
+from __future__ import annotations
+
+import os
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+OUT_DIR = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libcg.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC = os.environ.get("NVCC", "nvcc")
+
+SOURCES = ["cg_kernels.cu", "cg_host.cpp"]
+
+
+def _cmd_compile(src: str, obj: str) -> list[str]:
+    common = [NVCC, "-c", "-std=c++17", "-O3", "-Xcompiler", "-fPIC,-Wall",
+              "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", obj]
+    if src.endswith(".cu"):
+        return common + ARCH + ["-lineinfo", "-Xptxas", "-v" if os.environ.get("CG_PTXAS_V") else "-O3",
+                                src]
+    return common + [src]
+
+
+def build(verbose: bool = False) -> str:
+    """Compile every source in parallel, then link the shared library."""
+    os.makedirs(OUT_DIR, exist_ok=True)
+    procs = []
+    objs = []
+    for s in SOURCES:
+        src = os.path.join(CSRC, s)
+        obj = os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o")
+        objs.append(obj)
+        cmd = _cmd_compile(src, obj)
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                            text=True)))
+    failed = []
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if out and (verbose or p.returncode):
+            sys.stderr.write(out)
+        if p.returncode:
+            failed.append(" ".join(cmd))
+    if failed:
+        raise RuntimeError("libcg compile failed:\n" + "\n".join(failed))
+    tmp = LIB + ".tmp"
+    link = [NVCC, "-shared", "-o", tmp] + ARCH + objs + ["-Xcompiler", "-fPIC"]
+    subprocess.run(link, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

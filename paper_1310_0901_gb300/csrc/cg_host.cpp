@@ -1,0 +1,1129 @@
+// cg_host.cpp -- host runtime of libcg: the allocation table, the device V
+// shadow pool, the batch planner and the C ABI entry points of cg.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "cg_internal.h"
+
+using namespace cgi;
+
+// ------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+static cg_status set_error(cg_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+static cg_status cuda_fail(cudaError_t e, const char *what) {
+  return set_error(CG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CG_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+#define CG_TRY(call)                \
+  do {                              \
+    cg_status s_ = (call);          \
+    if (s_ != CG_OK) return s_;     \
+  } while (0)
+
+static inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// -------------------------------------------------- device shadow pool
+
+// Device V shadow of every live allocation (R6: all 0xFF on registration).
+// Slabs of device memory are carved best-fit in 256-byte units; free space
+// is kept at 0xFF, so a new allocation's shadow needs no initialisation.
+// Released ranges are refilled with 0xFF (queued, flushed on the next
+// stream operation of the context).
+class ShadowArena {
+ public:
+  uint64_t slab_bytes = 1ull << 30;
+  uint64_t budget = 0;
+  uint64_t held = 0;
+
+  ~ShadowArena() { release_all(); }
+
+  void release_all() {
+    for (auto &s : slabs_)
+      if (s.base) cudaFree(s.base);
+    slabs_.clear();
+    by_size_.clear();
+    free_by_off_.clear();
+    slab_index_.clear();
+    held = 0;
+  }
+
+  cg_status alloc(uint64_t size, uint64_t *out) {
+    const uint64_t sz = round_up(size, 256);
+    if (sz > slab_bytes / 2) {  // its own slab
+      if (budget && held + sz > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
+      uint8_t *p = nullptr;
+      cudaError_t e = cudaMalloc(&p, sz);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
+      }
+      e = cudaMemset(p, 0xFF, sz);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
+      add_slab(p, sz, true);
+      held += sz;
+      *out = reinterpret_cast<uint64_t>(p);
+      return CG_OK;
+    }
+    auto it = by_size_.lower_bound(sz);
+    if (it == by_size_.end()) {
+      if (budget && held + slab_bytes > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
+      uint8_t *p = nullptr;
+      cudaError_t e = cudaMalloc(&p, slab_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
+      }
+      e = cudaMemset(p, 0xFF, slab_bytes);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
+      const uint32_t si = add_slab(p, slab_bytes, false);
+      held += slab_bytes;
+      insert_free(si, 0, slab_bytes);
+      it = by_size_.lower_bound(sz);
+    }
+    const uint64_t bsize = it->first;
+    const uint32_t si = it->second.first;
+    const uint64_t off = it->second.second;
+    by_size_.erase(it);
+    free_by_off_[si].erase(off);
+    if (bsize > sz) insert_free(si, off + sz, bsize - sz);
+    *out = reinterpret_cast<uint64_t>(slabs_[si].base) + off;
+    return CG_OK;
+  }
+
+  // The caller queues the 0xFF refill of [ptr, ptr+size) before reuse.
+  void release(uint64_t ptr, uint64_t size) {
+    const uint64_t sz = round_up(size, 256);
+    auto it = slab_index_.upper_bound(ptr);
+    --it;
+    const uint32_t si = it->second;
+    Slab &s = slabs_[si];
+    if (s.dedicated) {
+      cudaFree(s.base);  // synchronises the device; dedicated slabs are rare
+      held -= s.size;
+      slab_index_.erase(it);
+      s.base = nullptr;
+      s.size = 0;
+      return;
+    }
+    uint64_t off = ptr - reinterpret_cast<uint64_t>(s.base);
+    uint64_t len = sz;
+    auto &fm = free_by_off_[si];
+    auto nx = fm.lower_bound(off);
+    if (nx != fm.end() && nx->first == off + len) {  // merge with the next block
+      len += nx->second;
+      erase_free(si, nx->first, nx->second);
+      nx = fm.lower_bound(off);
+    }
+    if (nx != fm.begin()) {  // merge with the previous block
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        off = pv->first;
+        len += pv->second;
+        erase_free(si, pv->first, pv->second);
+      }
+    }
+    insert_free(si, off, len);
+  }
+
+ private:
+  struct Slab {
+    uint8_t *base;
+    uint64_t size;
+    bool dedicated;
+  };
+  std::vector<Slab> slabs_;
+  std::multimap<uint64_t, std::pair<uint32_t, uint64_t>> by_size_;  // size -> (slab, off)
+  std::vector<std::map<uint64_t, uint64_t>> free_by_off_;           // per slab: off -> size
+  std::map<uint64_t, uint32_t> slab_index_;                         // base -> slab
+
+  uint32_t add_slab(uint8_t *p, uint64_t size, bool dedicated) {
+    slabs_.push_back({p, size, dedicated});
+    free_by_off_.emplace_back();
+    const uint32_t si = (uint32_t)(slabs_.size() - 1);
+    slab_index_[reinterpret_cast<uint64_t>(p)] = si;
+    return si;
+  }
+  void insert_free(uint32_t si, uint64_t off, uint64_t len) {
+    free_by_off_[si][off] = len;
+    by_size_.insert({len, {si, off}});
+  }
+  void erase_free(uint32_t si, uint64_t off, uint64_t len) {
+    free_by_off_[si].erase(off);
+    auto r = by_size_.equal_range(len);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.first == si && it->second.second == off) {
+        by_size_.erase(it);
+        break;
+      }
+  }
+};
+
+// ---------------------------------------------------- allocation table
+
+// The list of live device allocations (Fig. 2 caption) as a sorted main
+// array (size 0 = tombstone of a freed entry) plus an ordered delta of
+// recent registrations, merged into the main array in bulk.
+class AllocTable {
+ public:
+  std::vector<uint64_t> base, size, shadow;  // main, sorted by base
+  std::map<uint64_t, std::pair<uint64_t, uint64_t>> delta;  // base -> (size, shadow)
+  std::set<uint64_t> freed;
+  uint64_t dead = 0;
+  uint64_t live = 0;
+  uint64_t version = 0;
+
+  struct Hit {
+    bool ok;
+    uint64_t base, size, shadow;
+  };
+
+  Hit find(uint64_t addr) const {
+    auto ub = std::upper_bound(base.begin(), base.end(), addr);
+    if (ub != base.begin()) {
+      const size_t j = (size_t)(ub - base.begin()) - 1;
+      if (size[j] && addr - base[j] < size[j]) return {true, base[j], size[j], shadow[j]};
+    }
+    auto it = delta.upper_bound(addr);
+    if (it != delta.begin()) {
+      --it;
+      if (addr - it->first < it->second.first)
+        return {true, it->first, it->second.first, it->second.second};
+    }
+    return {false, 0, 0, 0};
+  }
+
+  bool overlaps(uint64_t b, uint64_t s) const {  // [b, b+s), no wrap
+    auto ub = std::upper_bound(base.begin(), base.end(), b);
+    if (ub != base.begin()) {
+      const size_t j = (size_t)(ub - base.begin()) - 1;
+      if (size[j] && b - base[j] < size[j]) return true;
+    }
+    for (auto k = ub; k != base.end() && *k < b + s; ++k)
+      if (size[(size_t)(k - base.begin())]) return true;
+    auto it = delta.upper_bound(b);
+    if (it != delta.end() && it->first < b + s) return true;
+    if (it != delta.begin()) {
+      --it;
+      if (b - it->first < it->second.first) return true;
+    }
+    return false;
+  }
+
+  void insert(uint64_t b, uint64_t s, uint64_t sh) {
+    delta[b] = {s, sh};
+    live++;
+    version++;
+    freed.erase(freed.lower_bound(b), freed.lower_bound(b + s));  // R13
+    if (delta.size() > std::max<uint64_t>(4096, base.size() / 8)) merge();
+  }
+
+  // Remove the live allocation whose base is exactly b.
+  bool remove_base(uint64_t b, uint64_t *sz, uint64_t *sh) {
+    auto lb = std::lower_bound(base.begin(), base.end(), b);
+    if (lb != base.end() && *lb == b) {
+      const size_t j = (size_t)(lb - base.begin());
+      if (size[j]) {
+        *sz = size[j];
+        *sh = shadow[j];
+        size[j] = 0;
+        dead++;
+        goto removed;
+      }
+    }
+    {
+      auto it = delta.find(b);
+      if (it == delta.end()) return false;
+      *sz = it->second.first;
+      *sh = it->second.second;
+      delta.erase(it);
+    }
+  removed:
+    live--;
+    version++;
+    freed.insert(b);
+    if (dead > 1024 && dead > base.size() / 4) merge();
+    return true;
+  }
+
+  void merge() {
+    if (delta.empty() && dead == 0) return;
+    std::vector<uint64_t> nb, ns, nh;
+    nb.reserve(live);
+    ns.reserve(live);
+    nh.reserve(live);
+    auto it = delta.begin();
+    for (size_t j = 0; j <= base.size(); j++) {
+      const uint64_t limit = j < base.size() ? base[j] : ~0ull;
+      while (it != delta.end() && (j == base.size() || it->first < limit)) {
+        nb.push_back(it->first);
+        ns.push_back(it->second.first);
+        nh.push_back(it->second.second);
+        ++it;
+      }
+      if (j < base.size() && size[j]) {
+        nb.push_back(base[j]);
+        ns.push_back(size[j]);
+        nh.push_back(shadow[j]);
+      }
+    }
+    base.swap(nb);
+    size.swap(ns);
+    shadow.swap(nh);
+    delta.clear();
+    dead = 0;
+  }
+};
+
+// ---------------------------------------------------- batch planner
+
+// Chmax-update / max-query segment tree over elementary intervals.
+class MaxTree {
+ public:
+  void init(int n) {
+    n_ = std::max(1, n);
+    mx_.assign(4 * (size_t)n_, -1);
+    tag_.assign(4 * (size_t)n_, -1);
+  }
+  int query(int l, int r) const { return l < r ? q(1, 0, n_, l, r) : -1; }
+  void update(int l, int r, int v) {
+    if (l < r) u(1, 0, n_, l, r, v);
+  }
+
+ private:
+  int n_ = 1;
+  mutable std::vector<int> mx_, tag_;
+  void push(int x) const {
+    if (tag_[x] >= 0) {
+      for (int c = 2 * x; c <= 2 * x + 1; c++) {
+        mx_[c] = std::max(mx_[c], tag_[x]);
+        tag_[c] = std::max(tag_[c], tag_[x]);
+      }
+      tag_[x] = -1;
+    }
+  }
+  int q(int x, int l, int r, int ql, int qr) const {
+    if (qr <= l || r <= ql) return -1;
+    if (ql <= l && r <= qr) return mx_[x];
+    push(x);
+    const int m = (l + r) / 2;
+    return std::max(q(2 * x, l, m, ql, qr), q(2 * x + 1, m, r, ql, qr));
+  }
+  void u(int x, int l, int r, int ql, int qr, int v) {
+    if (qr <= l || r <= ql) return;
+    if (ql <= l && r <= qr) {
+      mx_[x] = std::max(mx_[x], v);
+      tag_[x] = std::max(tag_[x], v);
+      return;
+    }
+    push(x);
+    const int m = (l + r) / 2;
+    u(2 * x, l, m, ql, qr, v);
+    u(2 * x + 1, m, r, ql, qr, v);
+    mx_[x] = std::max(mx_[2 * x], mx_[2 * x + 1]);
+  }
+};
+
+// Dependency levels for sequential semantics (R15): a copy's level is one
+// more than the highest level of any earlier copy it conflicts with (it
+// reads what that copy writes, writes what it reads, or writes what it
+// writes), counting every copy as writing its whole destination range.
+// Levels run in order; copies within a level touch disjoint shadow.
+static std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry) {
+  std::vector<int> lvl(nreq, 0);
+  if (!carry || nreq < 2) return lvl;
+  struct Iv {
+    uint64_t a, b;
+  };
+  auto end_of = [](uint64_t a, uint64_t n) { return a + n < a ? ~0ull : a + n; };
+  std::vector<uint64_t> hc, dc;
+  hc.reserve(2 * nreq);
+  dc.reserve(4 * nreq);
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_copy &q = reqs[i];
+    if (q.n == 0) continue;
+    if (q.kind == CG_HTOD) {
+      hc.push_back(q.src);
+      hc.push_back(q.src + q.n);
+      dc.push_back(q.dst);
+      dc.push_back(end_of(q.dst, q.n));
+    } else if (q.kind == CG_DTOH) {
+      hc.push_back(q.dst);
+      hc.push_back(q.dst + q.n);
+      dc.push_back(q.src);
+      dc.push_back(end_of(q.src, q.n));
+    } else {
+      dc.push_back(q.src);
+      dc.push_back(end_of(q.src, q.n));
+      dc.push_back(q.dst);
+      dc.push_back(end_of(q.dst, q.n));
+    }
+  }
+  std::sort(hc.begin(), hc.end());
+  hc.erase(std::unique(hc.begin(), hc.end()), hc.end());
+  std::sort(dc.begin(), dc.end());
+  dc.erase(std::unique(dc.begin(), dc.end()), dc.end());
+  MaxTree hw, hr, dw, dr;  // host/device space: writer and reader levels
+  hw.init((int)hc.size());
+  hr.init((int)hc.size());
+  dw.init((int)dc.size());
+  dr.init((int)dc.size());
+  auto hidx = [&](uint64_t x) { return (int)(std::lower_bound(hc.begin(), hc.end(), x) - hc.begin()); };
+  auto didx = [&](uint64_t x) { return (int)(std::lower_bound(dc.begin(), dc.end(), x) - dc.begin()); };
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_copy &q = reqs[i];
+    if (q.n == 0) continue;
+    int l = -1;
+    if (q.kind == CG_HTOD) {
+      const int ra = hidx(q.src), rb = hidx(q.src + q.n);
+      const int wa = didx(q.dst), wb = didx(end_of(q.dst, q.n));
+      l = std::max({hw.query(ra, rb), dw.query(wa, wb), dr.query(wa, wb)}) + 1;
+      hr.update(ra, rb, l);
+      dw.update(wa, wb, l);
+    } else if (q.kind == CG_DTOH) {
+      const int ra = didx(q.src), rb = didx(end_of(q.src, q.n));
+      const int wa = hidx(q.dst), wb = hidx(q.dst + q.n);
+      l = std::max({dw.query(ra, rb), hw.query(wa, wb), hr.query(wa, wb)}) + 1;
+      dr.update(ra, rb, l);
+      hw.update(wa, wb, l);
+    } else {
+      const int ra = didx(q.src), rb = didx(end_of(q.src, q.n));
+      const int wa = didx(q.dst), wb = didx(end_of(q.dst, q.n));
+      l = std::max({dw.query(ra, rb), dw.query(wa, wb), dr.query(wa, wb)}) + 1;
+      dr.update(ra, rb, l);
+      dw.update(wa, wb, l);
+    }
+    lvl[i] = l;
+  }
+  return lvl;
+}
+
+// --------------------------------------------------------------- context
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  uint64_t cap = 0;
+  cg_status ensure(uint64_t n) {
+    if (n <= cap) return CG_OK;
+    uint64_t c = std::max<uint64_t>(n, cap * 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(1, c) * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(CG_E_NOMEM, std::string("device buffer: ") + cudaGetErrorString(e));
+    }
+    cap = c;
+    return CG_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+template <typename T>
+struct PinBuf {
+  T *p = nullptr;
+  uint64_t cap = 0;
+  cg_status ensure(uint64_t n) {
+    if (n <= cap) return CG_OK;
+    uint64_t c = std::max<uint64_t>(n, cap * 2);
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMallocHost(&p, std::max<uint64_t>(1, c) * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(CG_E_NOMEM, std::string("pinned buffer: ") + cudaGetErrorString(e));
+    }
+    cap = c;
+    return CG_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct cg_ctx {
+  cg_config cfg{};
+  int device = 0;
+  int sm_count = 1;
+  Image img{nullptr, nullptr, 0};
+  bool img_bound = false;
+  ShadowArena arena;
+  AllocTable table;
+  SingleScratch *d_scratch = nullptr;
+  cg_report *h_result = nullptr;  // mapped pinned
+  cg_report *d_result = nullptr;
+  DevBuf<uint8_t> stage;
+  std::vector<uint64_t> fill_ptr, fill_size;
+  DevBuf<uint64_t> d_fill;
+  PinBuf<uint64_t> h_fill;
+  DevBuf<uint64_t> t_base, t_size, t_shadow;
+  uint64_t t_version = ~0ull;
+  uint64_t t_count = 0;
+  // batch buffers
+  DevBuf<cg_copy> b_reqs;
+  DevBuf<uint32_t> b_order;
+  DevBuf<uint64_t> b_segfirst, b_stage;
+  DevBuf<ScanJob> b_jobs;
+  DevBuf<RangeInfo> b_info;
+  DevBuf<Acc> b_acc;
+  DevBuf<cg_report> b_reps;
+  DevBuf<uint32_t> b_counts;
+  DevBuf<uint64_t> b_blocksums;
+  DevBuf<cg_err_record> b_recs;
+  PinBuf<uint8_t> h_stage_in;  // pinned upload staging
+  PinBuf<cg_report> h_reps;
+  PinBuf<cg_err_record> h_recs;
+  PinBuf<uint64_t> h_total;
+  cg_stats stats{};
+};
+
+// Queue 0xFF refills of released shadow ranges on `st`.
+static cg_status flush_fills(cg_ctx *c, cudaStream_t st) {
+  const uint64_t n = c->fill_ptr.size();
+  if (n == 0) return CG_OK;
+  if (n <= 8) {
+    for (uint64_t i = 0; i < n; i++)
+      CG_CUDA(cudaMemsetAsync(reinterpret_cast<void *>(c->fill_ptr[i]), 0xFF,
+                              round_up(c->fill_size[i], 256), st));
+  } else {
+    CG_TRY(c->h_fill.ensure(2 * n));
+    CG_TRY(c->d_fill.ensure(2 * n));
+    for (uint64_t i = 0; i < n; i++) {
+      c->h_fill.p[i] = c->fill_ptr[i];
+      c->h_fill.p[n + i] = round_up(c->fill_size[i], 256);
+    }
+    CG_CUDA(cudaMemcpyAsync(c->d_fill.p, c->h_fill.p, 2 * n * sizeof(uint64_t),
+                            cudaMemcpyHostToDevice, st));
+    CG_CUDA(launch_fill(c->d_fill.p, c->d_fill.p + n, n, 0xFF, st));
+    c->stats.kernels++;
+    // the pinned list is reused by the next flush: wait for this copy
+    CG_CUDA(cudaStreamSynchronize(st));
+  }
+  c->fill_ptr.clear();
+  c->fill_size.clear();
+  return CG_OK;
+}
+
+static cg_status ensure_device_table(cg_ctx *c, cudaStream_t st) {
+  AllocTable &t = c->table;
+  if (!t.delta.empty() || t.dead) t.merge();
+  if (c->t_version == t.version && c->t_count == t.base.size()) return CG_OK;
+  const uint64_t n = t.base.size();
+  CG_TRY(c->t_base.ensure(n));
+  CG_TRY(c->t_size.ensure(n));
+  CG_TRY(c->t_shadow.ensure(n));
+  if (n) {
+    CG_CUDA(cudaMemcpyAsync(c->t_base.p, t.base.data(), n * 8, cudaMemcpyHostToDevice, st));
+    CG_CUDA(cudaMemcpyAsync(c->t_size.p, t.size.data(), n * 8, cudaMemcpyHostToDevice, st));
+    CG_CUDA(cudaMemcpyAsync(c->t_shadow.p, t.shadow.data(), n * 8, cudaMemcpyHostToDevice, st));
+    CG_CUDA(cudaStreamSynchronize(st));  // host vectors may change after return
+  }
+  c->t_version = t.version;
+  c->t_count = n;
+  return CG_OK;
+}
+
+static cg_status validate(const cg_ctx *c, const cg_copy &q) {
+  if (q.kind != CG_HTOD && q.kind != CG_DTOH && q.kind != CG_DTOD)
+    return set_error(CG_E_KIND, "copy kind must be CG_HTOD, CG_DTOH or CG_DTOD");
+  if (q.reserved != 0) return set_error(CG_E_ARG, "cg_copy.reserved must be 0");
+  if (q.kind != CG_DTOD) {
+    if (!c->img_bound) return set_error(CG_E_NO_HOST, "no host shadow image bound");
+    const uint64_t h = q.kind == CG_HTOD ? q.src : q.dst;
+    if (h > c->img.n || q.n > c->img.n - h)
+      return set_error(CG_E_HOST_RANGE, "host range outside the bound host image");
+  }
+  return CG_OK;
+}
+
+// Host-mirror lookup of one device side (Sec. 2 itemize; R7, R8).
+static bool host_side(const cg_ctx *c, uint64_t p, uint64_t n, uint64_t *found, uint64_t *abase,
+                      uint64_t *asize, uint64_t *shadow, uint32_t *flags, uint32_t f_unalloc,
+                      uint32_t f_overrun) {
+  const AllocTable::Hit h = c->table.find(p);
+  if (!h.ok) {
+    *found = *abase = *asize = *shadow = 0;
+    *flags |= f_unalloc;
+    return false;
+  }
+  *found = h.base + h.size - p;
+  *abase = h.base;
+  *asize = h.size;
+  *shadow = h.shadow + (p - h.base);
+  if (n > *found) {
+    *flags |= f_overrun;
+    return false;
+  }
+  return true;
+}
+
+// --------------------------------------------------------------- C ABI
+
+extern "C" {
+
+cg_status cg_config_default(cg_config *cfg) {
+  if (!cfg) return set_error(CG_E_ARG, "cfg is NULL");
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->carry = 1;
+  return CG_OK;
+}
+
+const char *cg_last_error(void) { return g_last_error.c_str(); }
+
+const char *cg_version(void) { return "0.1.0"; }
+
+cg_status cg_create(cg_ctx **out, const cg_config *cfg) {
+  if (!out) return set_error(CG_E_ARG, "out is NULL");
+  *out = nullptr;
+  cg_ctx *c = new (std::nothrow) cg_ctx();
+  if (!c) return set_error(CG_E_NOMEM, "context");
+  if (cfg)
+    c->cfg = *cfg;
+  else
+    cg_config_default(&c->cfg);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, sizeof(SingleScratch));
+  if (e == cudaSuccess) e = cudaHostAlloc(&c->h_result, sizeof(cg_report), cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->d_result, c->h_result, 0);
+  if (e == cudaSuccess) e = launch_init_single_scratch(c->d_scratch, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cg_status st = cuda_fail(e, "cg_create");
+    cg_destroy(c);
+    return st;
+  }
+  c->arena.slab_bytes = c->cfg.shadow_slab_bytes ? round_up(c->cfg.shadow_slab_bytes, 1 << 20)
+                                                 : (1ull << 30);
+  c->arena.budget = c->cfg.shadow_budget_bytes;
+  *out = c;
+  return CG_OK;
+}
+
+cg_status cg_destroy(cg_ctx *c) {
+  if (!c) return CG_OK;
+  cudaDeviceSynchronize();
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->h_result) cudaFreeHost(c->h_result);
+  c->stage.release();
+  c->d_fill.release();
+  c->h_fill.release();
+  c->t_base.release();
+  c->t_size.release();
+  c->t_shadow.release();
+  c->b_reqs.release();
+  c->b_order.release();
+  c->b_segfirst.release();
+  c->b_stage.release();
+  c->b_jobs.release();
+  c->b_info.release();
+  c->b_acc.release();
+  c->b_reps.release();
+  c->b_counts.release();
+  c->b_blocksums.release();
+  c->b_recs.release();
+  c->h_stage_in.release();
+  c->h_reps.release();
+  c->h_recs.release();
+  c->h_total.release();
+  c->arena.release_all();
+  delete c;
+  return CG_OK;
+}
+
+cg_status cg_bind_host_shadow(cg_ctx *c, const uint8_t *a_bits_dev, uint8_t *v_dev,
+                              uint64_t n_bytes) {
+  if (!c) return set_error(CG_E_ARG, "ctx is NULL");
+  if (n_bytes && (!a_bits_dev || !v_dev)) return set_error(CG_E_ARG, "image pointer is NULL");
+  if ((reinterpret_cast<uintptr_t>(a_bits_dev) & 15) || (reinterpret_cast<uintptr_t>(v_dev) & 15))
+    return set_error(CG_E_ALIGN, "host shadow arrays must be 16-byte aligned");
+  if (n_bytes % 128) return set_error(CG_E_ALIGN, "host image size must be a multiple of 128");
+  c->img.a_bits = a_bits_dev;
+  c->img.v = v_dev;
+  c->img.n = n_bytes;
+  c->img_bound = true;
+  return CG_OK;
+}
+
+cg_status cg_upload_host_shadow(cg_ctx *c, const uint8_t *a_bits_host, const uint8_t *v_host,
+                                uint64_t off, uint64_t n, void *stream) {
+  if (!c || !a_bits_host || !v_host) return set_error(CG_E_ARG, "NULL argument");
+  if (!c->img_bound) return set_error(CG_E_NO_HOST, "no host shadow image bound");
+  if ((off | n) & 7) return set_error(CG_E_ALIGN, "off and n must be multiples of 8");
+  if (off > c->img.n || n > c->img.n - off) return set_error(CG_E_HOST_RANGE, "range outside image");
+  if (n == 0) return CG_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CG_CUDA(cudaMemcpyAsync(c->img.v + off, v_host + off, n, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(const_cast<uint8_t *>(c->img.a_bits) + off / 8, a_bits_host + off / 8,
+                          n / 8, cudaMemcpyHostToDevice, st));
+  return CG_OK;
+}
+
+cg_status cg_register_alloc(cg_ctx *c, uint64_t dptr, uint64_t size) {
+  if (!c) return set_error(CG_E_ARG, "ctx is NULL");
+  if (size == 0) return set_error(CG_E_ZERO_SIZE, "zero-size allocation");
+  if (dptr + size < dptr) return set_error(CG_E_WRAP, "allocation wraps 2^64");
+  if (c->table.overlaps(dptr, size))
+    return set_error(CG_E_OVERLAP, "allocation overlaps a live allocation");
+  uint64_t sh = 0;
+  CG_TRY(c->arena.alloc(size, &sh));
+  c->table.insert(dptr, size, sh);
+  return CG_OK;
+}
+
+cg_status cg_register_allocs(cg_ctx *c, const uint64_t *dptr, const uint64_t *size,
+                             uint64_t count, cg_status *st_out) {
+  if (!c || (count && (!dptr || !size))) return set_error(CG_E_ARG, "NULL argument");
+  cg_status first = CG_OK;
+  for (uint64_t i = 0; i < count; i++) {
+    const cg_status s = cg_register_alloc(c, dptr[i], size[i]);
+    if (st_out) st_out[i] = s;
+    if (s != CG_OK && first == CG_OK) first = s;
+  }
+  return first;
+}
+
+cg_status cg_free(cg_ctx *c, uint64_t dptr, uint32_t *verdict) {
+  if (!c || !verdict) return set_error(CG_E_ARG, "NULL argument");
+  uint64_t sz = 0, sh = 0;
+  if (c->table.remove_base(dptr, &sz, &sh)) {
+    c->arena.release(sh, sz);
+    c->fill_ptr.push_back(sh);
+    c->fill_size.push_back(sz);
+    *verdict = CG_FREE_OK;
+    return CG_OK;
+  }
+  if (c->table.find(dptr).ok)
+    *verdict = CG_FREE_INTERIOR;
+  else if (c->table.freed.count(dptr))
+    *verdict = CG_FREE_DOUBLE;
+  else
+    *verdict = CG_FREE_UNKNOWN;
+  return CG_OK;
+}
+
+static cg_status mark(cg_ctx *c, uint64_t dptr, uint64_t n, int value, void *stream) {
+  if (!c) return set_error(CG_E_ARG, "ctx is NULL");
+  if (n == 0) return CG_OK;
+  const AllocTable::Hit h = c->table.find(dptr);
+  if (!h.ok || n > h.base + h.size - dptr)
+    return set_error(CG_E_RANGE, "range not inside one live allocation");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CG_TRY(flush_fills(c, st));
+  CG_CUDA(cudaMemsetAsync(reinterpret_cast<void *>(h.shadow + (dptr - h.base)), value, n, st));
+  return CG_OK;
+}
+
+cg_status cg_mark_defined(cg_ctx *c, uint64_t dptr, uint64_t n, void *stream) {
+  return mark(c, dptr, n, 0x00, stream);
+}
+
+cg_status cg_mark_undefined(cg_ctx *c, uint64_t dptr, uint64_t n, void *stream) {
+  return mark(c, dptr, n, 0xFF, stream);
+}
+
+cg_status cg_read_device_shadow(cg_ctx *c, uint64_t dptr, uint64_t n, uint8_t *out) {
+  if (!c || (n && !out)) return set_error(CG_E_ARG, "NULL argument");
+  if (n == 0) return CG_OK;
+  const AllocTable::Hit h = c->table.find(dptr);
+  if (!h.ok || n > h.base + h.size - dptr)
+    return set_error(CG_E_RANGE, "range not inside one live allocation");
+  CG_TRY(flush_fills(c, 0));
+  CG_CUDA(cudaDeviceSynchronize());
+  CG_CUDA(cudaMemcpy(out, reinterpret_cast<const void *>(h.shadow + (dptr - h.base)), n,
+                     cudaMemcpyDeviceToHost));
+  return CG_OK;
+}
+
+static int single_grid(const cg_ctx *c, const ScanJob &job) {
+  const uint64_t chunks = (job.n + 30) >> 4;
+  const uint64_t groups = (chunks + 32 * 4 - 1) / (32 * 4);  // kU rows of 32 chunks per warp
+  const uint64_t ctas_needed = (groups + 7) / 8;             // 8 warps per CTA
+  int per_sm = (int)c->cfg.scan_ctas_per_sm;
+  if (per_sm <= 0) per_sm = scan_single_max_ctas_per_sm(job.kind, job.mode);
+  const uint64_t cap = (uint64_t)c->sm_count * (uint64_t)per_sm;
+  const uint64_t g = std::min<uint64_t>(std::max<uint64_t>(ctas_needed, 1), cap);
+  return (int)g;
+}
+
+static void count_stats(cg_ctx *c, const cg_report &r) {
+  c->stats.checks++;
+  c->stats.bytes_checked += r.expected;
+  for (int b = 0; b < CG_NFLAGS; b++)
+    if (r.flags & (1u << b)) c->stats.errors[b]++;
+}
+
+// Host part of one check: validation (a1), the device-range lookup on the
+// host mirror (a2) and the scan job.  *trivial is set when no byte needs
+// reading (n == 0, or a device->device copy whose source has no shadow).
+static cg_status prepare_single(cg_ctx *c, const cg_copy &q, RangeInfo *ri, ScanJob *job,
+                                bool *overlap_stage, uint64_t *stage_src, bool *trivial) {
+  CG_TRY(validate(c, q));
+  *ri = RangeInfo{};
+  ri->kind = q.kind;
+  ri->n = q.n;
+  *job = ScanJob{};
+  job->kind = q.kind;
+  job->n = q.n;
+  job->host_off = q.kind == CG_HTOD ? q.src : (q.kind == CG_DTOH ? q.dst : 0);
+  *overlap_stage = false;
+  *trivial = q.n == 0;  // R9
+  if (q.n == 0) return CG_OK;
+  bool dst_ok = true, src_ok = true;
+  uint64_t dsh = 0, ssh = 0;
+  if (q.kind != CG_DTOH)
+    dst_ok = host_side(c, q.dst, q.n, &ri->found_dst, &ri->base_dst, &ri->size_dst, &dsh,
+                       &ri->flags, CG_F_UNALLOC_DST, CG_F_OVERRUN_DST);
+  if (q.kind != CG_HTOD)
+    src_ok = host_side(c, q.src, q.n, &ri->found_src, &ri->base_src, &ri->size_src, &ssh,
+                       &ri->flags, CG_F_UNALLOC_SRC, CG_F_OVERRUN_SRC);
+  bool overlap = false;
+  if (q.kind == CG_DTOD) {
+    const uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
+    overlap = dist < q.n;
+    if (overlap) ri->flags |= CG_F_DTOD_OVERLAP;
+  }
+  if (q.kind != CG_HTOD && src_ok) {
+    job->mode |= kModeReadDev;
+    job->dev_src = ssh;
+  }
+  if (c->cfg.carry && dst_ok && src_ok) {
+    job->mode |= kModeCarry;
+    if (q.kind != CG_DTOH) job->dev_dst = dsh;
+  }
+  if (q.kind == CG_DTOD && !(job->mode & (kModeCarry | kModeReadDev))) *trivial = true;
+  if (overlap && (job->mode & kModeCarry)) {  // R12: read the whole source first
+    *overlap_stage = true;
+    *stage_src = ssh;
+  }
+  return CG_OK;
+}
+
+// Device part: flush queued refills, stage an overlapping source, launch
+// the scan; the kernel's last CTA writes the report to `out`.
+static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, bool stage,
+                                uint64_t stage_src, cg_report *out, cudaStream_t st) {
+  CG_TRY(flush_fills(c, st));
+  if (stage) {
+    CG_TRY(c->stage.ensure(round_up(job.n, 256)));
+    CG_CUDA(cudaMemcpyAsync(c->stage.p, reinterpret_cast<const void *>(stage_src), job.n,
+                            cudaMemcpyDeviceToDevice, st));
+    job.dev_src = reinterpret_cast<uint64_t>(c->stage.p);
+  }
+  CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
+  c->stats.kernels++;
+  c->stats.checks++;
+  c->stats.bytes_checked += job.n;
+  return CG_OK;
+}
+
+cg_status cg_check_copy(cg_ctx *c, const cg_copy *req, cg_report *rep, void *stream) {
+  if (!c || !req || !rep) return set_error(CG_E_ARG, "NULL argument");
+  RangeInfo ri;
+  ScanJob job;
+  bool stage, trivial;
+  uint64_t stage_src = 0;
+  CG_TRY(prepare_single(c, *req, &ri, &job, &stage, &stage_src, &trivial));
+  if (trivial) {
+    const Acc none{0, 0, kNone, kNone};
+    assemble_report(rep, ri, none);
+    count_stats(c, *rep);
+    return CG_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CG_TRY(enqueue_single(c, ri, job, stage, stage_src, c->d_result, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(rep, c->h_result, sizeof(cg_report));
+  c->stats.checks--;  // counted again with its flags below
+  c->stats.bytes_checked -= job.n;
+  count_stats(c, *rep);
+  return CG_OK;
+}
+
+cg_status cg_check_copy_async(cg_ctx *c, const cg_copy *req, cg_report *rep_dev, void *stream) {
+  if (!c || !req || !rep_dev) return set_error(CG_E_ARG, "NULL argument");
+  RangeInfo ri;
+  ScanJob job;
+  bool stage, trivial;
+  uint64_t stage_src = 0;
+  CG_TRY(prepare_single(c, *req, &ri, &job, &stage, &stage_src, &trivial));
+  if (trivial) {  // the kernel with no chunks only writes the report
+    job.mode = 0;
+    job.kind = CG_DTOD;
+  }
+  return enqueue_single(c, ri, job, stage, stage_src, rep_dev, static_cast<cudaStream_t>(stream));
+}
+
+cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_report *reps,
+                         cg_err_record *recs, uint64_t rec_cap, uint64_t *n_rec,
+                         uint64_t *bad_index, void *stream) {
+  if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
+    return set_error(CG_E_ARG, "NULL argument");
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_status s = validate(c, reqs[i]);
+    if (s != CG_OK) {
+      if (bad_index) *bad_index = i;
+      return s;
+    }
+  }
+  if (nreq == 0) {
+    *n_rec = 0;
+    return CG_OK;
+  }
+  if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CG_TRY(flush_fills(c, st));
+  CG_TRY(ensure_device_table(c, st));
+
+  // dependency levels and the segment split
+  uint32_t seg_kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : 64;
+  seg_kib = std::max<uint32_t>(2, (seg_kib + 1) / 2 * 2);  // a multiple of 2 KiB (kU rows)
+  const uint64_t seg_chunks = (uint64_t)seg_kib * 1024 / 16;
+  const std::vector<int> lvl = plan_levels(reqs, nreq, c->cfg.carry != 0);
+  int nlev = 0;
+  for (int l : lvl) nlev = std::max(nlev, l + 1);
+  std::vector<uint64_t> lev_start(nlev + 1, 0);
+  for (int l : lvl) lev_start[l + 1]++;
+  for (int l = 0; l < nlev; l++) lev_start[l + 1] += lev_start[l];
+
+  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8);
+  CG_TRY(c->h_stage_in.ensure(upload_bytes));
+  cg_copy *h_reqs = reinterpret_cast<cg_copy *>(c->h_stage_in.p);
+  uint32_t *h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
+  uint64_t *h_segfirst = reinterpret_cast<uint64_t *>(
+      c->h_stage_in.p + round_up(nreq * (sizeof(cg_copy) + 4), 8));
+  uint64_t *h_stagep = h_segfirst + nreq;
+  std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
+  {
+    std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
+    for (uint64_t i = 0; i < nreq; i++) h_order[fill[lvl[i]]++] = (uint32_t)i;
+  }
+  std::vector<uint64_t> lev_segs(nlev, 0);
+  for (int l = 0; l < nlev; l++) {
+    uint64_t acc_segs = 0;
+    for (uint64_t pos = lev_start[l]; pos < lev_start[l + 1]; pos++) {
+      const cg_copy &q = reqs[h_order[pos]];
+      h_segfirst[pos] = acc_segs;
+      const uint64_t chunks_ub = q.n ? (q.n + 30) >> 4 : 0;
+      acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
+    }
+    lev_segs[l] = acc_segs;
+  }
+  // overlapping device->device copies are staged (R12)
+  struct StageCopy {
+    int level;
+    uint64_t src, dst, n;
+  };
+  std::vector<StageCopy> stage_copies;
+  uint64_t stage_total = 0;
+  std::memset(h_stagep, 0, nreq * sizeof(uint64_t));
+  if (c->cfg.carry) {
+    for (uint64_t i = 0; i < nreq; i++) {
+      const cg_copy &q = reqs[i];
+      if (q.kind != CG_DTOD || q.n == 0) continue;
+      const uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
+      if (dist >= q.n) continue;
+      uint64_t f, b, s, sh, dsh;
+      uint32_t fl = 0;
+      const bool sok = host_side(c, q.src, q.n, &f, &b, &s, &sh, &fl, 1, 2);
+      const bool dok = host_side(c, q.dst, q.n, &f, &b, &s, &dsh, &fl, 1, 2);
+      if (!sok || !dok) continue;
+      stage_copies.push_back({lvl[i], sh, stage_total, q.n});
+      h_stagep[i] = stage_total + 1;  // patched to an address below
+      stage_total += round_up(q.n, 256);
+    }
+    if (stage_total) {
+      CG_TRY(c->stage.ensure(stage_total));
+      const uint64_t base = reinterpret_cast<uint64_t>(c->stage.p);
+      for (uint64_t i = 0; i < nreq; i++)
+        if (h_stagep[i]) h_stagep[i] = base + h_stagep[i] - 1;
+      for (auto &sc : stage_copies) sc.dst += base;
+    }
+  }
+
+  CG_TRY(c->b_reqs.ensure(nreq));
+  CG_TRY(c->b_order.ensure(nreq));
+  CG_TRY(c->b_segfirst.ensure(nreq));
+  CG_TRY(c->b_stage.ensure(nreq));
+  CG_TRY(c->b_jobs.ensure(nreq));
+  CG_TRY(c->b_info.ensure(nreq));
+  CG_TRY(c->b_acc.ensure(nreq));
+  CG_TRY(c->b_reps.ensure(nreq));
+  CG_TRY(c->b_counts.ensure(nreq));
+  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
+  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
+  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
+  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
+  CG_CUDA(cudaMemcpyAsync(c->b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(c->b_order.p, h_order, nreq * 4, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, h_segfirst, nreq * 8, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(c->b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, st));
+
+  BatchPlan plan{};
+  plan.reqs = c->b_reqs.p;
+  plan.order = c->b_order.p;
+  plan.seg_first = c->b_segfirst.p;
+  plan.stage = c->b_stage.p;
+  plan.jobs = c->b_jobs.p;
+  plan.info = c->b_info.p;
+  plan.acc = c->b_acc.p;
+  plan.nreq = nreq;
+  plan.seg_chunks = (uint32_t)seg_chunks;
+  DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
+  CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, st));
+  c->stats.kernels++;
+  int per_sm = (int)c->cfg.batch_ctas_per_sm;
+  if (per_sm <= 0) per_sm = 8;
+  const int grid = c->sm_count * per_sm;
+  size_t sci = 0;
+  std::sort(stage_copies.begin(), stage_copies.end(),
+            [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
+  for (int l = 0; l < nlev; l++) {
+    for (; sci < stage_copies.size() && stage_copies[sci].level == l; sci++)
+      CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(stage_copies[sci].dst),
+                              reinterpret_cast<const void *>(stage_copies[sci].src),
+                              stage_copies[sci].n, cudaMemcpyDeviceToDevice, st));
+    CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l], grid, st));
+    c->stats.kernels++;
+  }
+  const int strict = (int)c->cfg.strict_device_undef;
+  CG_CUDA(launch_finalize(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_scan_block_sums(c->b_blocksums.p, nblocks, nullptr, st));
+  CG_CUDA(launch_emit_records(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems,
+                              strict, c->b_recs.p, dev_rec_cap, st));
+  c->stats.kernels += dev_rec_cap ? 3 : 2;
+  CG_TRY(c->h_total.ensure(1));
+  CG_TRY(c->h_reps.ensure(nreq));
+  CG_CUDA(cudaMemcpyAsync(c->h_total.p, c->b_blocksums.p + nblocks, 8, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
+                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  const uint64_t total = c->h_total.p[0];
+  const uint64_t take = std::min(total, dev_rec_cap);
+  if (take) {
+    CG_TRY(c->h_recs.ensure(take));
+    CG_CUDA(cudaMemcpyAsync(c->h_recs.p, c->b_recs.p, take * sizeof(cg_err_record),
+                            cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(recs, c->h_recs.p, take * sizeof(cg_err_record));
+  }
+  if (reps) std::memcpy(reps, c->h_reps.p, nreq * sizeof(cg_report));
+  for (uint64_t i = 0; i < nreq; i++) count_stats(c, c->h_reps.p[i]);
+  *n_rec = total;
+  c->stats.batches++;
+  c->stats.levels += (uint64_t)nlev;
+  return CG_OK;
+}
+
+cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, int32_t *level,
+                         uint32_t *n_levels) {
+  if ((nreq && (!reqs || !level))) return set_error(CG_E_ARG, "NULL argument");
+  const std::vector<int> lvl = plan_levels(reqs, nreq, carry != 0);
+  int top = -1;
+  for (uint64_t i = 0; i < nreq; i++) {
+    level[i] = lvl[i];
+    top = std::max(top, lvl[i]);
+  }
+  if (n_levels) *n_levels = (uint32_t)(top + 1);
+  return CG_OK;
+}
+
+cg_status cg_get_stats(const cg_ctx *c, cg_stats *out) {
+  if (!c || !out) return set_error(CG_E_ARG, "NULL argument");
+  *out = c->stats;
+  out->live_allocs = c->table.live;
+  out->shadow_bytes = c->arena.held;
+  return CG_OK;
+}
+
+cg_status cg_format_report(const cg_report *r, uint32_t kind, char *buf, size_t cap) {
+  if (!r || !buf || cap == 0) return set_error(CG_E_ARG, "NULL argument");
+  const char *dir = kind == CG_HTOD ? "host->device" : kind == CG_DTOH ? "device->host"
+                                                                       : "device->device";
+  std::string s;
+  char line[320];
+  if (r->flags == 0) {
+    std::snprintf(line, sizeof line, "%s copy of %llu bytes: no findings", dir,
+                  (unsigned long long)r->expected);
+    s += line;
+  }
+  auto add = [&](const char *t) {
+    if (!s.empty()) s += "\n";
+    s += t;
+  };
+  if (r->flags & CG_F_UNALLOC_DST) {
+    std::snprintf(line, sizeof line, "%s copy of %llu bytes: destination pointer lies in no live allocation",
+                  dir, (unsigned long long)r->expected);
+    add(line);
+  }
+  if (r->flags & CG_F_UNALLOC_SRC) {
+    std::snprintf(line, sizeof line, "%s copy of %llu bytes: source pointer lies in no live allocation",
+                  dir, (unsigned long long)r->expected);
+    add(line);
+  }
+  if (r->flags & CG_F_OVERRUN_DST) {
+    std::snprintf(line, sizeof line,
+                  "%s copy of %llu bytes overruns its destination allocation: only %llu bytes "
+                  "from the pointer to its end",
+                  dir, (unsigned long long)r->expected, (unsigned long long)r->found_dst);
+    add(line);
+  }
+  if (r->flags & CG_F_OVERRUN_SRC) {
+    std::snprintf(line, sizeof line,
+                  "%s copy of %llu bytes overruns its source allocation: only %llu bytes from "
+                  "the pointer to its end",
+                  dir, (unsigned long long)r->expected, (unsigned long long)r->found_src);
+    add(line);
+  }
+  if (r->flags & CG_F_HOST_UNADDR) {
+    std::snprintf(line, sizeof line, "%s copy: %llu host bytes not addressable, first at offset %lld",
+                  dir, (unsigned long long)r->n_unaddr, (long long)r->first_unaddr_off);
+    add(line);
+  }
+  if (r->flags & CG_F_HOST_UNDEF) {
+    std::snprintf(line, sizeof line,
+                  "%s copy: %llu host bytes (partly) undefined, first at offset %lld", dir,
+                  (unsigned long long)r->n_undef, (long long)r->first_undef_off);
+    add(line);
+  }
+  if (r->flags & CG_F_DEV_UNDEF_SRC) {
+    std::snprintf(line, sizeof line,
+                  "%s copy (warning): %llu device source bytes (partly) undefined, first at "
+                  "offset %lld",
+                  dir, (unsigned long long)r->n_undef, (long long)r->first_undef_off);
+    add(line);
+  }
+  if (r->flags & CG_F_DTOD_OVERLAP) add("device->device copy (warning): source and destination overlap");
+  std::snprintf(buf, cap, "%s", s.c_str());
+  return CG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+"""libcg loads and exports every entry point include/cg.h declares; struct
+layouts agree; host-only entry points work without a GPU.  No GPU needed."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import cg_synth as S
+import oracle as O
+import paper_1310_0901_gb300 as cg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = open(os.path.join(ROOT, "include", "cg.h")).read()
+
+
+def declared_functions():
+    body = re.sub(r"/\*.*?\*/", "", HEADER, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:cg_status|const char \*)\s*(cg_\w+)\s*\(", body,
+                                 flags=re.M)))
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for must in ("cg_register_alloc", "cg_free", "cg_check_copy", "cg_check_batch",
+                 "cg_create", "cg_destroy", "cg_bind_host_shadow"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    out = subprocess.run(["nm", "-D", "--defined-only", cg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(cg_\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {n for n, _, _ in cg.SIGNATURES}
+    assert set(declared_functions()) == bound
+
+
+def test_struct_sizes_match_header_comments():
+    assert ctypes.sizeof(cg.cg_copy) == 32
+    assert ctypes.sizeof(cg.cg_report) == 112
+    assert ctypes.sizeof(cg.cg_err_record) == 48
+    assert S.REQ_DTYPE.itemsize == 32
+
+
+def test_flag_and_field_vocabulary_agrees_with_oracle():
+    # both sides define the encoding independently; they must agree by name
+    assert cg.FLAG_NAMES == O.FLAG_NAMES
+    assert cg.FLAGS == O.FLAGS
+    assert cg.REPORT_FIELDS == O.REPORT_FIELDS
+    assert cg.RECORD_FIELDS == O.RECORD_FIELDS
+    assert (cg.HTOD, cg.DTOH, cg.DTOD) == (O.HTOD, O.DTOH, O.DTOD)
+    for k, v in O.STATUS.items():
+        assert cg.STATUS[k] == v
+
+
+def test_host_only_entry_points():
+    assert cg.cg_version().decode() == "0.1.0"
+    c = cg.cg_config()
+    assert cg.cg_config_default(ctypes.byref(c)) == 0
+    assert c.carry == 1 and c.strict_device_undef == 0
+    rep = {f: 0 for f in cg.REPORT_FIELDS}
+    rep.update(flags=cg.FLAGS["OVERRUN_SRC"], expected=8000000, found_src=4000000)
+    text = cg.format_report(rep, cg.DTOH)
+    assert "8000000" in text and "4000000" in text and "device->host" in text
+
+
+def _brute_levels(reqs):
+    """Pairwise definition: request i depends on every earlier request j
+    whose write range meets i's read or write range, or whose read range
+    meets i's write range (host and device spaces apart)."""
+    def rw(q):
+        k, d, s, n = int(q["kind"]), int(q["dst"]), int(q["src"]), int(q["n"])
+        if n == 0:
+            return [], []
+        if k == S.HTOD:
+            return [("h", s, s + n)], [("d", d, d + n)]
+        if k == S.DTOH:
+            return [("d", s, s + n)], [("h", d, d + n)]
+        return [("d", s, s + n)], [("d", d, d + n)]
+
+    def meet(xs, ys):
+        return any(a[0] == b[0] and a[1] < b[2] and b[1] < a[2] for a in xs for b in ys)
+
+    sets = [rw(q) for q in reqs]
+    lv = []
+    for i, (ri, wi) in enumerate(sets):
+        best = -1
+        for j in range(i):
+            rj, wj = sets[j]
+            if meet(wj, ri) or meet(wj, wi) or meet(rj, wi):
+                best = max(best, lv[j])
+        lv.append(best + 1)
+    return lv
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_planner_matches_pairwise_definition(seed):
+    rng = np.random.default_rng(seed)
+    n = 300
+    reqs = np.zeros(n, S.REQ_DTYPE)
+    reqs["kind"] = rng.integers(1, 4, n)
+    reqs["n"] = rng.integers(0, 40, n)
+    reqs["dst"] = rng.integers(0, 400, n)
+    reqs["src"] = rng.integers(0, 400, n)
+    lv, nl = cg.plan_levels(reqs, carry=True)
+    want = _brute_levels(reqs)
+    assert lv.tolist() == want
+    assert nl == max(want) + 1
+    lv0, nl0 = cg.plan_levels(reqs, carry=False)
+    assert not lv0.any() and nl0 == 1
+
+
+def test_planner_on_small_workload_is_exact():
+    w = S.small(0)
+    lv, nl = cg.plan_levels(w.reqs, carry=True)
+    assert lv.tolist() == _brute_levels(w.reqs)
