@@ -114,7 +114,7 @@ def run_cg(args, world, rank, local):
     v_host = torch.from_numpy(w.image.v).pin_memory()
     a_dev = a_host.to(dev)
     v_dev = v_host.to(dev)
-    ctx = cg.Context()
+    ctx = cg.Context(single_engine=args.engine)
     ctx.bind_host_shadow(a_dev, v_dev)
     order = np.argsort(w.table.base)
     for b, s in zip(w.table.base[order], w.table.size[order]):
@@ -235,7 +235,9 @@ def run_cg(args, world, rank, local):
                    "bytes_checked_per_step": bytes_per_step,
                    "l2": "inputs larger than L2 (each transfer >= 256 MiB); no flush",
                    "parallelism": f"replicas x{world}", "carry": True},
-        "roofline": {"bound": "hbm", "kernel": "scan_single_kernel<HTOD,carry>",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("scan_single_kernel<HTOD,carry>" if args.engine == 1
+                                else "scan_single_tma_kernel<HTOD,carry>"),
                      "bytes_per_checked_byte": BYTES_PER_BYTE_CARRY,
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
@@ -337,6 +339,7 @@ def main():
     ap.add_argument("--sizes-mib", default="256,1024,4096")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 register loads, 2 TMA bulk")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist()

@@ -82,6 +82,10 @@ typedef int32_t cg_status;
 #define CG_F_DEV_UNDEF_SRC (1u << 6) /* DtoH/DtoD: undefined device bytes (warning) */
 #define CG_F_DTOD_OVERLAP (1u << 7)  /* DtoD src and dst overlap (warning) */
 #define CG_NFLAGS 8
+/* Not a finding: set when a kernel's bounded wait for its own data ran out;
+ * the counts of such a report are not valid (cg_check_copy then returns
+ * CG_E_TIMEOUT).  Never produces a record. */
+#define CG_F_INCOMPLETE (1u << 31)
 
 /* cg_free verdicts */
 #define CG_FREE_OK 0u
@@ -152,7 +156,8 @@ typedef struct cg_config {
   uint32_t scan_ctas_per_sm;    /* single-check grid; 0 = automatic */
   uint32_t batch_segment_kib;   /* batched work split; 0 = automatic */
   uint32_t batch_ctas_per_sm;   /* batched grid; 0 = automatic */
-  uint32_t reserved[9];
+  uint32_t single_engine;       /* 0 auto (= 2), 1 register loads, 2 TMA bulk */
+  uint32_t reserved[8];
 } cg_config;
 
 typedef struct cg_ctx cg_ctx;

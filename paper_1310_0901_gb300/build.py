@@ -13,11 +13,12 @@ LIB = os.path.join(PKG, "libcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
-SOURCES = ["cg_kernels.cu", "cg_host.cpp"]
+SOURCES = ["cg_kernels.cu", "cg_scan_tma.cu", "cg_host.cpp"]
 
 
 def _cmd_compile(src: str, obj: str) -> list[str]:
-    common = [NVCC, "-c", "-std=c++17", "-O3", "-Xcompiler", "-fPIC,-Wall",
+    extra = os.environ.get("CG_NVCC_FLAGS", "").split()
+    common = [NVCC, "-c", "-std=c++17", "-O3", "-Xcompiler", "-fPIC,-Wall"] + extra + [
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", obj]
     if src.endswith(".cu"):
         return common + ARCH + ["-lineinfo", "-Xptxas", "-v" if os.environ.get("CG_PTXAS_V") else "-O3",

@@ -838,7 +838,11 @@ static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, boo
                             cudaMemcpyDeviceToDevice, st));
     job.dev_src = reinterpret_cast<uint64_t>(c->stage.p);
   }
-  CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
+  if (c->cfg.single_engine == 1)
+    CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
+  else
+    CG_CUDA(launch_scan_single_tma(c->img, job, ri, c->d_scratch, out,
+                                   scan_single_tma_grid(c->sm_count, job.n), st));
   c->stats.kernels++;
   c->stats.checks++;
   c->stats.bytes_checked += job.n;
@@ -862,6 +866,8 @@ cg_status cg_check_copy(cg_ctx *c, const cg_copy *req, cg_report *rep, void *str
   CG_TRY(enqueue_single(c, ri, job, stage, stage_src, c->d_result, st));
   CG_CUDA(cudaStreamSynchronize(st));
   std::memcpy(rep, c->h_result, sizeof(cg_report));
+  if (rep->flags & CG_F_INCOMPLETE)
+    return set_error(CG_E_TIMEOUT, "a bounded wait in the scan kernel ran out");
   c->stats.checks--;  // counted again with its flags below
   c->stats.bytes_checked -= job.n;
   count_stats(c, *rep);

@@ -53,7 +53,8 @@ struct Acc {
 struct SingleScratch {
   Acc acc;
   unsigned int ctas_done;
-  unsigned int pad[7];
+  unsigned int error;  // nonzero: a bounded wait ran out (report flagged incomplete)
+  unsigned int pad[6];
 };
 
 // Device-side verdict of the range part of a request (batched path).
@@ -170,6 +171,10 @@ cudaError_t launch_scan_single(const Image &img, const ScanJob &job, const Range
                                SingleScratch *scratch, cg_report *out, int grid,
                                cudaStream_t st);
 int scan_single_max_ctas_per_sm(uint32_t kind, uint32_t mode);
+cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const RangeInfo &ri,
+                                   SingleScratch *scr, cg_report *out, int grid,
+                                   cudaStream_t st);
+int scan_single_tma_grid(int sm_count, uint64_t n);
 cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int carry,
                           cudaStream_t st);
 cudaError_t launch_scan_level(const Image &img, const BatchPlan &p, uint64_t pos_begin,

@@ -1,0 +1,272 @@
+// cg_scan_tma.cu -- the single-copy scan with its loads on the TMA engine.
+//
+// Every warp runs its own pipeline of kNS shared-memory stages.  Lane 0
+// issues 1-D bulk copies (cp.async.bulk, completion counted on an mbarrier)
+// of the next tiles' V and A bytes; all 32 lanes wait on the stage's
+// mbarrier, classify and carry the tile out of shared memory, and hand the
+// stage back.  Bytes in flight no longer cost registers, so a few warps per
+// SM keep HBM busy.  A tile is kR warp rows (kR x 512 bytes of the anchor
+// grid).  Misaligned input streams are realigned when read from shared
+// memory (two aligned 16-byte reads and a byte funnel shift).
+//
+// Every wait is bounded (about one second of %globaltimer); on expiry the
+// warp stops, waits (bounded again) for its copies still in flight, and the
+// report is flagged CG_F_INCOMPLETE.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cg_device.cuh"
+
+#ifndef CG_TMA_R
+#define CG_TMA_R 8
+#endif
+#ifndef CG_TMA_NS
+#define CG_TMA_NS 4
+#endif
+#ifndef CG_TMA_WARPS
+#define CG_TMA_WARPS 8
+#endif
+
+namespace cgi {
+
+constexpr int kR = CG_TMA_R;       // warp rows per tile
+constexpr int kNS = CG_TMA_NS;     // stages per warp
+constexpr int kTW = CG_TMA_WARPS;  // warps per CTA
+constexpr uint32_t kVBytes = 16u * (32u * kR + 1u);                 // V window of a tile
+constexpr uint32_t kABytes = 64u * kR + 64u;                        // A window of a tile
+constexpr uint32_t kStage = ((kVBytes + kABytes) + 127u) & ~127u;  // one stage
+constexpr uint32_t kWarpSmem = kNS * kStage;
+constexpr size_t kSmemBytes = (size_t)kTW * kWarpSmem + (size_t)kTW * kNS * 8 + 128;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for a stage; false if about one second passes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ int64_t floor16(int64_t x) { return x & ~(int64_t)15; }
+__device__ __forceinline__ int64_t ceil16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+// Lane 0: queue the V and A bytes of the tile starting at anchor chunk c0
+// into the stage at `st` (shared address), completion on `bar`.
+template <uint32_t KIND>
+__device__ __forceinline__ void issue_tile(const Geo &g, const uint8_t *a_bytes, int64_t c0,
+                                           uint32_t st, uint32_t bar) {
+  uint32_t tx = 0, vbytes = 0, abytes = 0, voff = 0, aoff = 0;
+  uintptr_t vsrc = 0;
+  int64_t asrc = 0;
+  if (KIND == CG_HTOD || g.has_vin) {
+    // aligned V chunks of the tile, clipped to the chunks the copy touches
+    const uintptr_t vbeg = g.vin_al + 16 * (uintptr_t)c0;
+    const uintptr_t vend = vbeg + kVBytes;
+    const uintptr_t lo_lim = g.vin_lo & ~(uintptr_t)15;
+    const uintptr_t hi_lim = (g.vin_hi + 15) & ~(uintptr_t)15;
+    const uintptr_t lo = vbeg > lo_lim ? vbeg : lo_lim;
+    const uintptr_t hi = vend < hi_lim ? vend : hi_lim;
+    if (hi > lo) {
+      vbytes = (uint32_t)(hi - lo);
+      voff = (uint32_t)(lo - vbeg);
+      vsrc = lo;
+      tx += vbytes;
+    }
+  }
+  if (KIND != CG_DTOD) {
+    // A bytes holding bits [p0, p1 + 32), clipped to the copy's host bits
+    const int64_t p0 = g.hb0 + 16 * c0;
+    const int64_t p1 = p0 + 512 * kR;
+    const int64_t aorig = floor16(p0 >> 3);
+    const int64_t q0 = p0 > g.hlo ? p0 : g.hlo;
+    const int64_t q1 = (p1 + 32) < g.hhi ? (p1 + 32) : g.hhi;
+    if (q1 > q0) {
+      const int64_t b0 = floor16(q0 >> 3);
+      const int64_t b1 = ceil16((q1 + 7) >> 3);
+      abytes = (uint32_t)(b1 - b0);
+      aoff = (uint32_t)(b0 - aorig);
+      asrc = b0;
+      tx += abytes;
+    }
+  }
+  mbar_arrive_expect_tx(bar, tx);
+  if (vbytes) bulk_g2s(st + voff, reinterpret_cast<const void *>(vsrc), vbytes, bar);
+  if (abytes) bulk_g2s(st + kVBytes + aoff, a_bytes + asrc, abytes, bar);
+}
+
+// All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
+template <uint32_t KIND, bool CARRY>
+__device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uint8_t *sp,
+                                             int lane, LaneAcc &la) {
+  const uint4 *vs = reinterpret_cast<const uint4 *>(sp);
+  const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
+  const int64_t aorig = floor16((g.hb0 + 16 * c0) >> 3);
+#pragma unroll 4
+  for (int u = 0; u < kR; u++) {
+    const int k = 32 * u + lane;
+    const int64_t c = c0 + k;
+    uint4 V = make_uint4(0, 0, 0, 0);
+    if (KIND == CG_HTOD || g.has_vin) {
+      V = vs[k];
+      if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
+    }
+    uint32_t a16 = 0xFFFFu;
+    if (KIND != CG_DTOD) {
+      const int64_t q = g.hb0 + 16 * c;
+      const int sh = (int)(q & 31);
+      const int64_t wi = (((q >> 5) << 2) - aorig) >> 2;
+      const uint32_t w0 = as[wi];
+      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
+      a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
+    }
+    chunk_step<KIND, CARRY>(g, c, V, a16, la);
+  }
+}
+
+template <uint32_t KIND, bool CARRY>
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_single_tma_kernel(Image img, ScanJob job, RangeInfo ri, SingleScratch *scr,
+                           cg_report *out) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  const Geo g = make_geo(job, img);
+  const int64_t rows = (g.nchunks + 31) >> 5;
+  const int64_t ntiles = (rows + kR - 1) / kR;
+  const int64_t gw = (int64_t)blockIdx.x * kTW + wid;
+  const int64_t nw = (int64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t err = 0;
+  if (lane == 0)
+    for (int s = 0; s < kNS; s++) {
+      const int64_t t = gw + (int64_t)s * nw;
+      if (t < ntiles)
+        issue_tile<KIND>(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
+                         smem_addr(&bars[s]));
+    }
+  uint32_t parity = 0;
+  int s = 0;
+  int64_t t = gw;
+  for (; t < ntiles; t += nw) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      err = 1;
+      break;
+    }
+    parity ^= 1u << s;
+    consume_tile<KIND, CARRY>(g, t * kR * 32, wbase + s * kStage, lane, la);
+    __syncwarp();
+    const int64_t tn = t + (int64_t)kNS * nw;
+    if (lane == 0 && tn < ntiles) {
+      fence_proxy_async();
+      issue_tile<KIND>(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
+                       smem_addr(&bars[s]));
+    }
+    s = s + 1 == kNS ? 0 : s + 1;
+  }
+  if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
+    for (int d = 0; d < kNS; d++) {
+      const int64_t td = t + (int64_t)d * nw;
+      if (td >= ntiles) break;
+      const int sd = (s + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+  }
+  single_epilogue(la, scr, ri, out, err);
+}
+
+template <uint32_t KIND, bool CARRY>
+static cudaError_t launch_tma_t(const Image &img, const ScanJob &job, const RangeInfo &ri,
+                                SingleScratch *scr, cg_report *out, int grid, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(scan_single_tma_kernel<KIND, CARRY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  scan_single_tma_kernel<KIND, CARRY><<<grid, kTW * 32, kSmemBytes, st>>>(img, job, ri, scr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const RangeInfo &ri,
+                                   SingleScratch *scr, cg_report *out, int grid,
+                                   cudaStream_t st) {
+  const bool carry = job.mode & kModeCarry;
+  switch (job.kind) {
+    case CG_HTOD:
+      return carry ? launch_tma_t<CG_HTOD, true>(img, job, ri, scr, out, grid, st)
+                   : launch_tma_t<CG_HTOD, false>(img, job, ri, scr, out, grid, st);
+    case CG_DTOH:
+      return carry ? launch_tma_t<CG_DTOH, true>(img, job, ri, scr, out, grid, st)
+                   : launch_tma_t<CG_DTOH, false>(img, job, ri, scr, out, grid, st);
+    default:
+      return carry ? launch_tma_t<CG_DTOD, true>(img, job, ri, scr, out, grid, st)
+                   : launch_tma_t<CG_DTOD, false>(img, job, ri, scr, out, grid, st);
+  }
+}
+
+int scan_single_tma_grid(int sm_count, uint64_t n) {
+  // tiles of kR rows; one CTA (kTW warps) per SM at most
+  const uint64_t tiles = ((n + 30) / 16 / 32 + kR) / kR + 1;
+  const uint64_t ctas = (tiles + kTW - 1) / kTW;
+  return (int)(ctas < (uint64_t)sm_count ? (ctas ? ctas : 1) : (uint64_t)sm_count);
+}
+
+}  // namespace cgi

@@ -36,11 +36,15 @@ def _run_single(ctx, orc, reqs, what):
     return reports
 
 
+ENGINES = {"regs": 1, "tma": 2}
+
+
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("carry", [True, False])
-def test_small_workload_single_checks(cg, carry):
+def test_small_workload_single_checks(cg, carry, engine):
     """1,000 mixed copies over 64 live allocations, one cg_check_copy each."""
     w = S.small(0)
-    ctx, orc, (a, v) = U.make_pair(w.image, w.table, carry=carry)
+    ctx, orc, (a, v) = U.make_pair(w.image, w.table, carry=carry, single_engine=ENGINES[engine])
     _run_single(ctx, orc, w.reqs, "small/single")
     U.assert_same_state(ctx, orc, v, w.table)
 
@@ -87,21 +91,24 @@ def _mixed_image(n, seed):
     return S.HostImage(S.pack_a(addr), v, [], None)
 
 
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("kind", [HTOD, DTOH, DTOD])
-def test_alignment_sweep(cg, kind):
+def test_alignment_sweep(cg, kind, engine):
     """Every host offset mod 16 against every device offset mod 16, sizes
-    around the 16-byte vector, the 512-byte warp row and the 2 KiB step."""
+    around the 16-byte vector, the 512-byte warp row, the 2 KiB step and the
+    4 KiB TMA tile."""
     img = _mixed_image(1 << 16, 5)
     base = 1 << 40
     table = S.AllocTable(np.array([base, base + (1 << 20)], np.uint64),
                          np.array([1 << 18, 1 << 18], np.uint64), np.zeros(0, np.int64))
-    ctx, orc, (a, v) = U.make_pair(img, table)
+    ctx, orc, (a, v) = U.make_pair(img, table, single_engine=ENGINES[engine])
     # give the device shadows mixed content first
     for off in range(0, 1 << 18, 1 << 15):
         for b in (base, base + (1 << 20)):
             assert ctx.check_copy(HTOD, b + off, off % (1 << 15), 1 << 15)[0] == 0
             orc.check_copy(HTOD, b + off, off % (1 << 15), 1 << 15)
-    sizes = [1, 2, 15, 16, 17, 31, 33, 100, 511, 512, 513, 2047, 2048, 2049, 5000]
+    sizes = [1, 2, 15, 16, 17, 31, 33, 100, 511, 512, 513, 2047, 2048, 2049, 4095, 4096,
+             4097, 5000, 8193, 20000]
     rng = np.random.default_rng(kind)
     reqs = []
     for ho in range(16):
@@ -129,13 +136,14 @@ def test_alignment_sweep(cg, kind):
     U.assert_same_state(ctx2, orc2, v2, table)
 
 
-def test_edge_cases(cg):
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_edge_cases(cg, engine):
     """Empty copies, wild and wrapping pointers, API errors, frees."""
     img = _mixed_image(8192, 1)
     base = 1 << 30
     table = S.AllocTable(np.array([base, base + 4096], np.uint64),
                          np.array([4096, 256], np.uint64), np.zeros(0, np.int64))
-    ctx, orc, (a, v) = U.make_pair(img, table)
+    ctx, orc, (a, v) = U.make_pair(img, table, single_engine=ENGINES[engine])
     cases = [
         (HTOD, base, 0, 0), (DTOH, 0, 12345, 0), (DTOD, 1, 2, 0),           # n == 0
         (HTOD, base + 4096 - 1, 10, 1), (HTOD, base + 4095, 10, 2),          # last byte / overrun
