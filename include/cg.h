@@ -265,6 +265,53 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                          uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream);
 
+/* --------------------------------------------- allocation-free variant */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory.  A checker that runs inside a
+ * program's own allocation and copy calls (an interposer around the
+ * driver's memory functions, as the paper's wrappers are) cannot call
+ * cudaMalloc without re-entering the allocator it wraps, and a process
+ * whose device memory is owned by another allocator may have none to give.
+ * cg_create allocates; this call does not: no cudaMalloc, cudaFree or other
+ * allocating routine, and no context.
+ *
+ * It runs the single-copy scan of cg_check_copy (per-byte classes, counts,
+ * first offsets, and the V carry when carry != 0) over buffers the caller
+ * passes; there is no allocation table, so the report's range fields
+ * (found_*, alloc_*, UNALLOC/OVERRUN flags) stay zero.
+ *   kind            CG_HTOD, CG_DTOH or CG_DTOD
+ *   a_bits_dev,     host shadow image as in cg_bind_host_shadow (device,
+ *   host_v_dev,     16-byte aligned, host_n a multiple of 128); unused and
+ *   host_n          may be NULL/0 for CG_DTOD
+ *   host_off        offset of the copy in the host image (HtoD source,
+ *                   DtoH destination)
+ *   dev_src_shadow  device V shadow of the source bytes (DtoH/DtoD); NULL =
+ *                   source definedness unknown (not counted, no carry)
+ *   dev_dst_shadow  device V shadow receiving the carry (HtoD/DtoD); NULL =
+ *                   no carry
+ *   rep_dev         device memory (or mapped pinned host memory) receiving
+ *                   the report when the stream reaches it
+ * Device shadows are read in whole 16-byte-aligned blocks around
+ * [ptr, ptr+n) (those blocks must be readable); only [ptr, ptr+n) is
+ * written.
+ *
+ * Its scratch (the kernel's accumulators and an 8 MiB staging area for an
+ * overlapping device->device carry) is a fixed array inside the library
+ * that every GPU loading libcg holds until the process exits.  An
+ * overlapping device->device carry above 8 MiB is refused (CG_E_TOO_BIG).
+ * Every call shares that array and the accumulators are reset at the start
+ * of each call, so calls whose work overlaps on the GPU (e.g. on two
+ * streams, or from two threads) race and their reports are wrong: order
+ * them on one stream.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, no allocation); make that first
+ * call before any stream capture.  Asynchronous; errors as cg_check_copy,
+ * plus CG_E_TOO_BIG, with text in cg_last_error(). */
+cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, uint8_t *host_v_dev,
+                          uint64_t host_n, uint64_t host_off, const uint8_t *dev_src_shadow,
+                          uint8_t *dev_dst_shadow, uint64_t n, uint32_t carry,
+                          cg_report *rep_dev, void *stream);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The dependency levels cg_check_batch runs reqs[0..nreq) in (host only,

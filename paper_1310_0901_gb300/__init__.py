@@ -91,6 +91,7 @@ SIGNATURES = [
     ("cg_check_copy_async", i32, [vp, ctypes.POINTER(cg_copy), vp, vp]),
     ("cg_check_batch", i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(u64),
                              ctypes.POINTER(u64), vp]),
+    ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
     ("cg_plan_levels", i32, [vp, u64, u32, vp, ctypes.POINTER(u32)]),
     ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
     ("cg_format_report", i32, [ctypes.POINTER(cg_report), u32, ctypes.c_char_p, ctypes.c_size_t]),

@@ -23,6 +23,8 @@ static cg_status set_error(cg_status st, const std::string &msg) {
   return st;
 }
 
+void cgi::set_error_text(const char *msg) { g_last_error = msg; }
+
 static cg_status cuda_fail(cudaError_t e, const char *what) {
   return set_error(CG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }

@@ -191,4 +191,7 @@ cudaError_t launch_fill(const uint64_t *ptrs, const uint64_t *sizes, uint64_t co
 
 constexpr int kFinalizeItems = 1024;  // requests per finalize/emit block
 
+// Set the text cg_last_error() returns on this thread (cg_host.cpp).
+void set_error_text(const char *msg);
+
 }  // namespace cgi
