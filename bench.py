@@ -185,15 +185,7 @@ def run_cg(args, world, rank, local):
     alg_bytes = BYTES_PER_BYTE_CARRY * int(w.reqs[big]["n"])
     achieved = alg_bytes / (kmean / 1e3) / GB
     peak, peak_kind = _peaks()
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "scan_htod_traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("kernel_version") == _kernel_version():
-                traffic = tj["dram_bytes_per_launch_scaled"]
-        except Exception:
-            traffic = None
+    traffic = _profiled_traffic() if args.engine != 1 and sizes == LARGE_DEFAULT else None
 
     # end to end through the C ABI: per step upload each transfer's host
     # shadow (V + A) from pinned host memory, check, read the report
@@ -257,10 +249,28 @@ def run_cg(args, world, rank, local):
     return out, w
 
 
-def _kernel_version() -> str:
+LARGE_DEFAULT = (256 << 20, 1 << 30, 4 << 30)
+
+
+def _kernel_hash() -> str:
     import hashlib
-    src = os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", "cg_kernels.cu")
-    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for f in ("cg_scan_tma.cu", "cg_device.cuh", "cg_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def _profiled_traffic():
+    """DRAM bytes per 4 GiB launch from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    import re
+    p = os.path.join(ROOT, "profiles", "scan_single_tma_htod_256MiB.md")
+    if not os.path.exists(p):
+        return None
+    m = re.search(r"traffic_per_launch_bytes=(\d+); kernel_hash=(\w+)", open(p).read())
+    if not m or m.group(2) != _kernel_hash():
+        return None
+    return int(m.group(1))
 
 
 def cpu_sample(w, budget_s: float):
