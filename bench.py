@@ -114,7 +114,7 @@ def run_cg(args, world, rank, local):
     v_host = torch.from_numpy(w.image.v).pin_memory()
     a_dev = a_host.to(dev)
     v_dev = v_host.to(dev)
-    ctx = cg.Context(single_engine=args.engine)
+    ctx = cg.Context(scan_engine=args.engine)
     ctx.bind_host_shadow(a_dev, v_dev)
     order = np.argsort(w.table.base)
     for b, s in zip(w.table.base[order], w.table.size[order]):
@@ -252,6 +252,83 @@ def run_cg(args, world, rank, local):
 LARGE_DEFAULT = (256 << 20, 1 << 30, 4 << 30)
 
 
+def run_batched_workload(args, which: str):
+    """Batched checks (one cg_check_batch per step) against one synchronous
+    cg_check_copy per copy, on the same GPU and workload."""
+    import torch
+
+    import paper_1310_0901_gb300 as cg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t_gen = time.perf_counter()
+    w = S.batched(0) if which == "batched" else S.adversarial(0)
+    t_gen = time.perf_counter() - t_gen
+    n_img = w.image.n
+    a_dev = torch.from_numpy(w.image.a_bits[: n_img // 8].copy()).to(dev)
+    v_dev = torch.from_numpy(w.image.v).to(dev)
+    ctx = cg.Context(batch_segment_kib=args.segment_kib)
+    ctx.bind_host_shadow(a_dev, v_dev)
+    order = np.argsort(w.table.base)
+    t_reg = time.perf_counter()
+    st = ctx.register_allocs(w.table.base[order], w.table.size[order])
+    assert not st.any()
+    t_reg = time.perf_counter() - t_reg
+    reqs = w.reqs
+    nreq = len(reqs)
+    bytes_per_batch = int(reqs["n"].sum())
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        stt, reps, recs, total, _ = ctx.check_batch(reqs, rec_cap=8 * nreq)
+        cg.check(stt, "check_batch")
+    s0 = ctx.stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        stt, reps, recs, total, _ = ctx.check_batch(reqs, rec_cap=8 * nreq)
+        cg.check(stt, "check_batch")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s1 = ctx.stats()
+    levels = (s1["levels"] - s0["levels"]) / args.steps
+    launches = (s1["kernels"] - s0["kernels"]) / args.steps
+    per_batch_ms = {k: round((s1[k] - s0[k]) / args.steps / 1e6, 2)
+                    for k in ("batch_ns", "batch_plan_ns", "batch_lookup_ns")}
+    # one launch per copy: every copy of the same stream, one cg_check_copy each
+    m = min(nreq, args.single_sample)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for q in reqs[:m]:
+        stt, _ = ctx.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), int(q["n"]), stream)
+        cg.check(stt, "check_copy")
+    torch.cuda.synchronize()
+    dt1 = time.perf_counter() - t1
+    batch_cps = nreq * args.steps / dt
+    single_cps = m / dt1
+    out = {
+        "metric": "batched checks/sec",
+        "value": round(batch_cps, 1), "unit": "checks/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded cg_synth." + which + ")",
+        "config": {"workload": w.name, "requests": nreq, "allocations": int(len(w.table.base)),
+                   "bytes_checked_per_batch": bytes_per_batch,
+                   "segment_kib": args.segment_kib or 64, "levels_per_batch": levels,
+                   "l2": "working set larger than L2", "carry": True},
+        "batched_gb_per_s": round(bytes_per_batch * args.steps / dt / GB, 1),
+        "one_launch_per_copy": {"checks_per_s": round(single_cps, 1), "sample": m,
+                                "gb_per_s": round(int(reqs["n"][:m].sum()) / dt1 / GB, 1)},
+        "speedup_vs_one_launch_per_copy": round(batch_cps / single_cps, 2),
+        "records_per_batch": int(total),
+        "batch_breakdown_ms": {"total": per_batch_ms["batch_ns"],
+                               "host_plan": per_batch_ms["batch_plan_ns"],
+                               "lookup_and_readback": per_batch_ms["batch_lookup_ns"]},
+        "gpu_launches": launches,
+        "setup_s": {"generate": round(t_gen, 1), "register": round(t_reg, 1)},
+    }
+    ctx.close()
+    return out
+
+
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -350,6 +427,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 register loads, 2 TMA bulk")
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "adversarial"])
+    ap.add_argument("--segment-kib", type=int, default=0)
+    ap.add_argument("--single-sample", type=int, default=100_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist()
@@ -357,6 +437,10 @@ def main():
         out = run_reference(args, world, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload != "large":
+        if rank == 0:
+            print(json.dumps(run_batched_workload(args, args.workload)), flush=True)
         return
     if world > 1:
         import torch

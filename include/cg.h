@@ -154,9 +154,12 @@ typedef struct cg_config {
   uint64_t shadow_slab_bytes;   /* device shadow pool slab; 0 = 1 GiB */
   uint64_t shadow_budget_bytes; /* cap on the device shadow pool; 0 = none */
   uint32_t scan_ctas_per_sm;    /* single-check grid; 0 = automatic */
-  uint32_t batch_segment_kib;   /* batched work split; 0 = automatic */
+  uint32_t batch_segment_kib;   /* batched work split, rounded up to whole
+                                   engine steps (4 KiB TMA, 2 KiB registers);
+                                   0 = 64 */
   uint32_t batch_ctas_per_sm;   /* batched grid; 0 = automatic */
-  uint32_t single_engine;       /* 0 auto (= 2), 1 register loads, 2 TMA bulk */
+  uint32_t scan_engine;         /* scan loads, single and batched checks:
+                                   0 auto (= 2), 1 registers, 2 TMA bulk copies */
   uint32_t reserved[8];
 } cg_config;
 
@@ -171,6 +174,9 @@ typedef struct cg_stats {
   uint64_t errors[CG_NFLAGS]; /* reports per flag */
   uint64_t live_allocs;
   uint64_t shadow_bytes;  /* device shadow pool held */
+  uint64_t batch_ns;      /* wall time inside cg_check_batch */
+  uint64_t batch_plan_ns; /* of which: host dependency planning */
+  uint64_t batch_lookup_ns; /* of which: device lookup incl. its read-back */
 } cg_stats;
 
 /* ------------------------------------------------------------- lifetime */
@@ -317,11 +323,14 @@ cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, uint8_t *hos
 /* The dependency levels cg_check_batch runs reqs[0..nreq) in (host only,
  * no GPU work): level[i] = 1 + the highest level of an earlier request that
  * reads what request i writes, writes what it reads, or writes what it
- * writes (every request counted as writing its whole destination range);
- * 0 when there is none, and all 0 when carry is 0.  reqs, level: host.
- * *n_levels (may be NULL) gets 1 + the highest level (0 when nreq is 0). */
+ * writes; 0 when there is none, and all 0 when carry is 0.  modes (host,
+ * may be NULL) gives per request bit 0 = it carries (writes its
+ * destination's V), bit 1 = its device source is valid (its V is read);
+ * cg_check_batch passes the values its device lookup found.  With NULL,
+ * every request is taken to read its source and write its destination.
+ * reqs, level: host.  *n_levels (may be NULL) gets 1 + the highest level. */
 cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry,
-                         int32_t *level, uint32_t *n_levels);
+                         const uint8_t *modes, int32_t *level, uint32_t *n_levels);
 
 cg_status cg_get_stats(const cg_ctx *ctx, cg_stats *out);
 

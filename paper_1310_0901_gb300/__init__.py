@@ -55,13 +55,14 @@ class cg_config(ctypes.Structure):
     _fields_ = [("carry", u32), ("strict_device_undef", u32), ("shadow_slab_bytes", u64),
                 ("shadow_budget_bytes", u64), ("scan_ctas_per_sm", u32),
                 ("batch_segment_kib", u32), ("batch_ctas_per_sm", u32),
-                ("single_engine", u32), ("reserved", u32 * 8)]
+                ("scan_engine", u32), ("reserved", u32 * 8)]
 
 
 class cg_stats(ctypes.Structure):
     _fields_ = [("checks", u64), ("bytes_checked", u64), ("batches", u64), ("levels", u64),
                 ("kernels", u64), ("errors", u64 * 8), ("live_allocs", u64),
-                ("shadow_bytes", u64)]
+                ("shadow_bytes", u64), ("batch_ns", u64), ("batch_plan_ns", u64),
+                ("batch_lookup_ns", u64)]
 
 
 REPORT_FIELDS = [f for f, _ in cg_report._fields_]
@@ -92,7 +93,7 @@ SIGNATURES = [
     ("cg_check_batch", i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(u64),
                              ctypes.POINTER(u64), vp]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
-    ("cg_plan_levels", i32, [vp, u64, u32, vp, ctypes.POINTER(u32)]),
+    ("cg_plan_levels", i32, [vp, u64, u32, vp, vp, ctypes.POINTER(u32)]),
     ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
     ("cg_format_report", i32, [ctypes.POINTER(cg_report), u32, ctypes.c_char_p, ctypes.c_size_t]),
     ("cg_last_error", ctypes.c_char_p, []),
@@ -248,12 +249,17 @@ class Context:
         return d
 
 
-def plan_levels(reqs: np.ndarray, carry: bool = True) -> tuple[np.ndarray, int]:
+def plan_levels(reqs: np.ndarray, carry: bool = True,
+                modes: np.ndarray | None = None) -> tuple[np.ndarray, int]:
     """Dependency levels of a batch (host only, see cg_plan_levels)."""
     reqs = np.ascontiguousarray(reqs)
     lv = np.zeros(len(reqs), dtype=np.int32)
     nl = u32(0)
-    check(cg_plan_levels(reqs.ctypes.data if len(reqs) else None, len(reqs), int(carry),
+    mp = None
+    if modes is not None:
+        modes = np.ascontiguousarray(modes, dtype=np.uint8)
+        mp = modes.ctypes.data
+    check(cg_plan_levels(reqs.ctypes.data if len(reqs) else None, len(reqs), int(carry), mp,
                          lv.ctypes.data if len(reqs) else None, ctypes.byref(nl)),
           "cg_plan_levels")
     return lv, int(nl.value)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -42,6 +43,12 @@ static cg_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 static inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+static inline uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
 // -------------------------------------------------- device shadow pool
 
@@ -297,122 +304,166 @@ class AllocTable {
 
 // ---------------------------------------------------- batch planner
 
-// Chmax-update / max-query segment tree over elementary intervals.
-class MaxTree {
+// Range-chmax / range-max segment tree over the elementary intervals of one
+// address space, holding two values per leaf: the highest level of a copy
+// that wrote it (w) and of one that read it (r).
+class LevelTree {
  public:
   void init(int n) {
     n_ = std::max(1, n);
-    mx_.assign(4 * (size_t)n_, -1);
-    tag_.assign(4 * (size_t)n_, -1);
+    size_t m = 1;
+    while (m < (size_t)n_) m <<= 1;
+    nodes_.assign(2 * m, Node{-1, -1, -1, -1});
   }
-  int query(int l, int r) const { return l < r ? q(1, 0, n_, l, r) : -1; }
-  void update(int l, int r, int v) {
-    if (l < r) u(1, 0, n_, l, r, v);
+  // max of w (and of r when want_r) over leaves [l, r)
+  int query(int l, int r, bool want_r) const {
+    if (l >= r) return -1;
+    return q(1, 0, n_, l, r, want_r);
+  }
+  void update_w(int l, int r, int v) {
+    if (l < r) u(1, 0, n_, l, r, v, true);
+  }
+  void update_r(int l, int r, int v) {
+    if (l < r) u(1, 0, n_, l, r, v, false);
   }
 
  private:
+  struct Node {
+    int w, r, tw, tr;  // subtree maxima and pending chmax for the children
+  };
   int n_ = 1;
-  mutable std::vector<int> mx_, tag_;
+  mutable std::vector<Node> nodes_;
   void push(int x) const {
-    if (tag_[x] >= 0) {
-      for (int c = 2 * x; c <= 2 * x + 1; c++) {
-        mx_[c] = std::max(mx_[c], tag_[x]);
-        tag_[c] = std::max(tag_[c], tag_[x]);
+    Node &p = nodes_[x];
+    if (p.tw < 0 && p.tr < 0) return;
+    for (int c = 2 * x; c <= 2 * x + 1; c++) {
+      Node &k = nodes_[c];
+      if (p.tw >= 0) {
+        k.w = std::max(k.w, p.tw);
+        k.tw = std::max(k.tw, p.tw);
       }
-      tag_[x] = -1;
+      if (p.tr >= 0) {
+        k.r = std::max(k.r, p.tr);
+        k.tr = std::max(k.tr, p.tr);
+      }
     }
+    p.tw = p.tr = -1;
   }
-  int q(int x, int l, int r, int ql, int qr) const {
-    if (qr <= l || r <= ql) return -1;
-    if (ql <= l && r <= qr) return mx_[x];
+  int q(int x, int l, int r, int ql, int qr, bool want_r) const {
+    if (ql <= l && r <= qr) return want_r ? std::max(nodes_[x].w, nodes_[x].r) : nodes_[x].w;
     push(x);
-    const int m = (l + r) / 2;
-    return std::max(q(2 * x, l, m, ql, qr), q(2 * x + 1, m, r, ql, qr));
+    const int m = (l + r) >> 1;
+    int v = -1;
+    if (ql < m) v = q(2 * x, l, m, ql, qr, want_r);
+    if (qr > m) v = std::max(v, q(2 * x + 1, m, r, ql, qr, want_r));
+    return v;
   }
-  void u(int x, int l, int r, int ql, int qr, int v) {
-    if (qr <= l || r <= ql) return;
+  void u(int x, int l, int r, int ql, int qr, int v, bool is_w) {
+    Node &nd = nodes_[x];
     if (ql <= l && r <= qr) {
-      mx_[x] = std::max(mx_[x], v);
-      tag_[x] = std::max(tag_[x], v);
+      if (is_w) {
+        nd.w = std::max(nd.w, v);
+        nd.tw = std::max(nd.tw, v);
+      } else {
+        nd.r = std::max(nd.r, v);
+        nd.tr = std::max(nd.tr, v);
+      }
       return;
     }
     push(x);
-    const int m = (l + r) / 2;
-    u(2 * x, l, m, ql, qr, v);
-    u(2 * x + 1, m, r, ql, qr, v);
-    mx_[x] = std::max(mx_[2 * x], mx_[2 * x + 1]);
+    const int m = (l + r) >> 1;
+    if (ql < m) u(2 * x, l, m, ql, qr, v, is_w);
+    if (qr > m) u(2 * x + 1, m, r, ql, qr, v, is_w);
+    nodes_[x].w = std::max(nodes_[2 * x].w, nodes_[2 * x + 1].w);
+    nodes_[x].r = std::max(nodes_[2 * x].r, nodes_[2 * x + 1].r);
   }
 };
 
 // Dependency levels for sequential semantics (R15): a copy's level is one
 // more than the highest level of any earlier copy it conflicts with (it
 // reads what that copy writes, writes what it reads, or writes what it
-// writes), counting every copy as writing its whole destination range.
-// Levels run in order; copies within a level touch disjoint shadow.
-static std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry) {
+// writes).  With `modes` (the device lookup's per-copy job modes) a copy
+// writes its destination only if it carries and reads a device source only
+// if that source is valid; without, every copy is taken to read its source
+// and write its destination.  Levels run in order; copies within a level
+// touch disjoint shadow.
+static std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry,
+                                    const uint8_t *modes = nullptr) {
   std::vector<int> lvl(nreq, 0);
   if (!carry || nreq < 2) return lvl;
-  struct Iv {
-    uint64_t a, b;
-  };
   auto end_of = [](uint64_t a, uint64_t n) { return a + n < a ? ~0ull : a + n; };
-  std::vector<uint64_t> hc, dc;
-  hc.reserve(2 * nreq);
-  dc.reserve(4 * nreq);
+  auto reads_dev = [&](uint64_t i) { return !modes || (modes[i] & kModeReadDev); };
+  auto writes = [&](uint64_t i) { return !modes || (modes[i] & kModeCarry); };
+  // endpoints of every range, tagged (request, slot): slots 0/1 host read,
+  // 2/3 host write, 4/5 device read, 6/7 device write
+  struct Ep {
+    uint64_t v;
+    uint32_t req;
+    uint32_t slot;
+  };
+  std::vector<Ep> he, de;
+  he.reserve(2 * nreq);
+  de.reserve(2 * nreq);
   for (uint64_t i = 0; i < nreq; i++) {
     const cg_copy &q = reqs[i];
     if (q.n == 0) continue;
+    const uint32_t r = (uint32_t)i;
     if (q.kind == CG_HTOD) {
-      hc.push_back(q.src);
-      hc.push_back(q.src + q.n);
-      dc.push_back(q.dst);
-      dc.push_back(end_of(q.dst, q.n));
+      he.push_back({q.src, r, 0});
+      he.push_back({q.src + q.n, r, 1});
+      if (writes(i)) {
+        de.push_back({q.dst, r, 6});
+        de.push_back({end_of(q.dst, q.n), r, 7});
+      }
     } else if (q.kind == CG_DTOH) {
-      hc.push_back(q.dst);
-      hc.push_back(q.dst + q.n);
-      dc.push_back(q.src);
-      dc.push_back(end_of(q.src, q.n));
+      if (writes(i)) {
+        he.push_back({q.dst, r, 2});
+        he.push_back({q.dst + q.n, r, 3});
+      }
+      if (reads_dev(i)) {
+        de.push_back({q.src, r, 4});
+        de.push_back({end_of(q.src, q.n), r, 5});
+      }
     } else {
-      dc.push_back(q.src);
-      dc.push_back(end_of(q.src, q.n));
-      dc.push_back(q.dst);
-      dc.push_back(end_of(q.dst, q.n));
+      if (reads_dev(i)) {
+        de.push_back({q.src, r, 4});
+        de.push_back({end_of(q.src, q.n), r, 5});
+      }
+      if (writes(i)) {
+        de.push_back({q.dst, r, 6});
+        de.push_back({end_of(q.dst, q.n), r, 7});
+      }
     }
   }
-  std::sort(hc.begin(), hc.end());
-  hc.erase(std::unique(hc.begin(), hc.end()), hc.end());
-  std::sort(dc.begin(), dc.end());
-  dc.erase(std::unique(dc.begin(), dc.end()), dc.end());
-  MaxTree hw, hr, dw, dr;  // host/device space: writer and reader levels
-  hw.init((int)hc.size());
-  hr.init((int)hc.size());
-  dw.init((int)dc.size());
-  dr.init((int)dc.size());
-  auto hidx = [&](uint64_t x) { return (int)(std::lower_bound(hc.begin(), hc.end(), x) - hc.begin()); };
-  auto didx = [&](uint64_t x) { return (int)(std::lower_bound(dc.begin(), dc.end(), x) - dc.begin()); };
-  for (uint64_t i = 0; i < nreq; i++) {
-    const cg_copy &q = reqs[i];
-    if (q.n == 0) continue;
-    int l = -1;
-    if (q.kind == CG_HTOD) {
-      const int ra = hidx(q.src), rb = hidx(q.src + q.n);
-      const int wa = didx(q.dst), wb = didx(end_of(q.dst, q.n));
-      l = std::max({hw.query(ra, rb), dw.query(wa, wb), dr.query(wa, wb)}) + 1;
-      hr.update(ra, rb, l);
-      dw.update(wa, wb, l);
-    } else if (q.kind == CG_DTOH) {
-      const int ra = didx(q.src), rb = didx(end_of(q.src, q.n));
-      const int wa = hidx(q.dst), wb = hidx(q.dst + q.n);
-      l = std::max({dw.query(ra, rb), hw.query(wa, wb), hr.query(wa, wb)}) + 1;
-      dr.update(ra, rb, l);
-      hw.update(wa, wb, l);
-    } else {
-      const int ra = didx(q.src), rb = didx(end_of(q.src, q.n));
-      const int wa = didx(q.dst), wb = didx(end_of(q.dst, q.n));
-      l = std::max({dw.query(ra, rb), dw.query(wa, wb), dr.query(wa, wb)}) + 1;
-      dr.update(ra, rb, l);
-      dw.update(wa, wb, l);
+  // compress: each endpoint gets the rank of its value among distinct values
+  std::vector<int32_t> idx(8 * nreq, -1);
+  auto compress = [&](std::vector<Ep> &e) -> int {
+    std::sort(e.begin(), e.end(), [](const Ep &a, const Ep &b) { return a.v < b.v; });
+    int rank = -1;
+    uint64_t prev = 0;
+    for (size_t k = 0; k < e.size(); k++) {
+      if (k == 0 || e[k].v != prev) rank++;
+      prev = e[k].v;
+      idx[8 * (size_t)e[k].req + e[k].slot] = rank;
     }
+    return rank + 1;
+  };
+  LevelTree ht, dt;
+  ht.init(compress(he));
+  dt.init(compress(de));
+  for (uint64_t i = 0; i < nreq; i++) {
+    if (reqs[i].n == 0) continue;
+    const int32_t *x = &idx[8 * i];
+    int l = -1;
+    if (x[0] >= 0) l = std::max(l, ht.query(x[0], x[1], false));
+    if (x[2] >= 0) l = std::max(l, ht.query(x[2], x[3], true));
+    if (x[4] >= 0) l = std::max(l, dt.query(x[4], x[5], false));
+    if (x[6] >= 0) l = std::max(l, dt.query(x[6], x[7], true));
+    l += 1;
+    if (x[0] >= 0) ht.update_r(x[0], x[1], l);
+    if (x[2] >= 0) ht.update_w(x[2], x[3], l);
+    if (x[4] >= 0) dt.update_r(x[4], x[5], l);
+    if (x[6] >= 0) dt.update_w(x[6], x[7], l);
     lvl[i] = l;
   }
   return lvl;
@@ -499,6 +550,9 @@ struct cg_ctx {
   DevBuf<uint32_t> b_counts;
   DevBuf<uint64_t> b_blocksums;
   DevBuf<cg_err_record> b_recs;
+  DevBuf<unsigned int> b_err;
+  DevBuf<uint8_t> b_modes;
+  PinBuf<uint8_t> h_modes;
   PinBuf<uint8_t> h_stage_in;  // pinned upload staging
   PinBuf<cg_report> h_reps;
   PinBuf<cg_err_record> h_recs;
@@ -652,6 +706,9 @@ cg_status cg_destroy(cg_ctx *c) {
   c->b_counts.release();
   c->b_blocksums.release();
   c->b_recs.release();
+  c->b_err.release();
+  c->b_modes.release();
+  c->h_modes.release();
   c->h_stage_in.release();
   c->h_reps.release();
   c->h_recs.release();
@@ -840,7 +897,7 @@ static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, boo
                             cudaMemcpyDeviceToDevice, st));
     job.dev_src = reinterpret_cast<uint64_t>(c->stage.p);
   }
-  if (c->cfg.single_engine == 1)
+  if (c->cfg.scan_engine == 1)
     CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
   else
     CG_CUDA(launch_scan_single_tma(c->img, job, ri, c->d_scratch, out,
@@ -907,48 +964,43 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
     return CG_OK;
   }
   if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
+  const uint64_t t_begin = now_ns();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CG_TRY(flush_fills(c, st));
   CG_TRY(ensure_device_table(c, st));
 
-  // dependency levels and the segment split
-  uint32_t seg_kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : 64;
-  seg_kib = std::max<uint32_t>(2, (seg_kib + 1) / 2 * 2);  // a multiple of 2 KiB (kU rows)
-  const uint64_t seg_chunks = (uint64_t)seg_kib * 1024 / 16;
-  const std::vector<int> lvl = plan_levels(reqs, nreq, c->cfg.carry != 0);
-  int nlev = 0;
-  for (int l : lvl) nlev = std::max(nlev, l + 1);
-  std::vector<uint64_t> lev_start(nlev + 1, 0);
-  for (int l : lvl) lev_start[l + 1]++;
-  for (int l = 0; l < nlev; l++) lev_start[l + 1] += lev_start[l];
+  // device lookup first (a2): it decides which copies carry and read a
+  // device source, which the level plan needs
+  CG_TRY(c->b_reqs.ensure(nreq));
+  CG_TRY(c->b_order.ensure(nreq));
+  CG_TRY(c->b_segfirst.ensure(nreq));
+  CG_TRY(c->b_stage.ensure(nreq));
+  CG_TRY(c->b_jobs.ensure(nreq));
+  CG_TRY(c->b_info.ensure(nreq));
+  CG_TRY(c->b_acc.ensure(nreq));
+  CG_TRY(c->b_reps.ensure(nreq));
+  CG_TRY(c->b_counts.ensure(nreq));
+  CG_TRY(c->b_modes.ensure(nreq));
+  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
+  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
+  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
+  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
 
-  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8);
+  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8) + 64;
   CG_TRY(c->h_stage_in.ensure(upload_bytes));
+  CG_TRY(c->h_modes.ensure(nreq));
   cg_copy *h_reqs = reinterpret_cast<cg_copy *>(c->h_stage_in.p);
   uint32_t *h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
   uint64_t *h_segfirst = reinterpret_cast<uint64_t *>(
       c->h_stage_in.p + round_up(nreq * (sizeof(cg_copy) + 4), 8));
   uint64_t *h_stagep = h_segfirst + nreq;
   std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
-  {
-    std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
-    for (uint64_t i = 0; i < nreq; i++) h_order[fill[lvl[i]]++] = (uint32_t)i;
-  }
-  std::vector<uint64_t> lev_segs(nlev, 0);
-  for (int l = 0; l < nlev; l++) {
-    uint64_t acc_segs = 0;
-    for (uint64_t pos = lev_start[l]; pos < lev_start[l + 1]; pos++) {
-      const cg_copy &q = reqs[h_order[pos]];
-      h_segfirst[pos] = acc_segs;
-      const uint64_t chunks_ub = q.n ? (q.n + 30) >> 4 : 0;
-      acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
-    }
-    lev_segs[l] = acc_segs;
-  }
-  // overlapping device->device copies are staged (R12)
+
+  // overlapping device->device copies are staged (R12); their source and
+  // destination are looked up on the host mirror (they are rare)
   struct StageCopy {
     int level;
-    uint64_t src, dst, n;
+    uint64_t src, dst, n, req;
   };
   std::vector<StageCopy> stage_copies;
   uint64_t stage_total = 0;
@@ -959,12 +1011,12 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
       if (q.kind != CG_DTOD || q.n == 0) continue;
       const uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
       if (dist >= q.n) continue;
-      uint64_t f, b, s, sh, dsh;
+      uint64_t f, b, sz, sh, dsh;
       uint32_t fl = 0;
-      const bool sok = host_side(c, q.src, q.n, &f, &b, &s, &sh, &fl, 1, 2);
-      const bool dok = host_side(c, q.dst, q.n, &f, &b, &s, &dsh, &fl, 1, 2);
+      const bool sok = host_side(c, q.src, q.n, &f, &b, &sz, &sh, &fl, 1, 2);
+      const bool dok = host_side(c, q.dst, q.n, &f, &b, &sz, &dsh, &fl, 1, 2);
       if (!sok || !dok) continue;
-      stage_copies.push_back({lvl[i], sh, stage_total, q.n});
+      stage_copies.push_back({0, sh, stage_total, q.n, i});
       h_stagep[i] = stage_total + 1;  // patched to an address below
       stage_total += round_up(q.n, 256);
     }
@@ -976,25 +1028,8 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
       for (auto &sc : stage_copies) sc.dst += base;
     }
   }
-
-  CG_TRY(c->b_reqs.ensure(nreq));
-  CG_TRY(c->b_order.ensure(nreq));
-  CG_TRY(c->b_segfirst.ensure(nreq));
-  CG_TRY(c->b_stage.ensure(nreq));
-  CG_TRY(c->b_jobs.ensure(nreq));
-  CG_TRY(c->b_info.ensure(nreq));
-  CG_TRY(c->b_acc.ensure(nreq));
-  CG_TRY(c->b_reps.ensure(nreq));
-  CG_TRY(c->b_counts.ensure(nreq));
-  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
-  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
-  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
-  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
   CG_CUDA(cudaMemcpyAsync(c->b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_order.p, h_order, nreq * 4, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, h_segfirst, nreq * 8, cudaMemcpyHostToDevice, st));
   CG_CUDA(cudaMemcpyAsync(c->b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, st));
-
   BatchPlan plan{};
   plan.reqs = c->b_reqs.p;
   plan.order = c->b_order.p;
@@ -1004,13 +1039,60 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   plan.info = c->b_info.p;
   plan.acc = c->b_acc.p;
   plan.nreq = nreq;
-  plan.seg_chunks = (uint32_t)seg_chunks;
   DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
+  const uint64_t t_lookup = now_ns();
   CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, st));
   c->stats.kernels++;
+  CG_CUDA(launch_job_modes(plan, c->b_modes.p, st));
+  c->stats.kernels++;
+  CG_CUDA(cudaMemcpyAsync(c->h_modes.p, c->b_modes.p, nreq, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  const uint8_t *modes = c->h_modes.p;
+  const uint64_t t_plan = now_ns();
+  c->stats.batch_lookup_ns += t_plan - t_lookup;
+
+  // dependency levels (exact on validity) and the segment split
+  const bool tma = c->cfg.scan_engine != 1;
+  // a segment is a whole number of steps of the engine: kU rows (2 KiB) for
+  // register loads, one tile for the TMA engine
+  const uint64_t quantum = tma ? scan_tma_tile_bytes() : 2048;
+  uint64_t seg_bytes = (uint64_t)(c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : 64) * 1024;
+  seg_bytes = std::max<uint64_t>(quantum, (seg_bytes + quantum - 1) / quantum * quantum);
+  const uint64_t seg_chunks = seg_bytes / 16;
+  plan.seg_chunks = (uint32_t)seg_chunks;
+  const std::vector<int> lvl = plan_levels(reqs, nreq, c->cfg.carry != 0, modes);
+  int nlev = 0;
+  for (int l : lvl) nlev = std::max(nlev, l + 1);
+  std::vector<uint64_t> lev_start(nlev + 1, 0);
+  for (int l : lvl) lev_start[l + 1]++;
+  for (int l = 0; l < nlev; l++) lev_start[l + 1] += lev_start[l];
+  {
+    std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
+    for (uint64_t i = 0; i < nreq; i++) h_order[fill[lvl[i]]++] = (uint32_t)i;
+  }
+  std::vector<uint64_t> lev_segs(nlev, 0);
+  for (int l = 0; l < nlev; l++) {
+    uint64_t acc_segs = 0;
+    for (uint64_t pos = lev_start[l]; pos < lev_start[l + 1]; pos++) {
+      const uint32_t i = h_order[pos];
+      const cg_copy &q = reqs[i];
+      h_segfirst[pos] = acc_segs;
+      const bool idle = q.kind == CG_DTOD && !(modes[i] & (kModeCarry | kModeReadDev));
+      const uint64_t chunks_ub = (q.n && !idle) ? (q.n + 30) >> 4 : 0;
+      acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
+    }
+    lev_segs[l] = acc_segs;
+  }
+  for (auto &sc : stage_copies) sc.level = lvl[sc.req];
+  c->stats.batch_plan_ns += now_ns() - t_plan;
+  CG_CUDA(cudaMemcpyAsync(c->b_order.p, h_order, nreq * 4, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, h_segfirst, nreq * 8, cudaMemcpyHostToDevice, st));
+
   int per_sm = (int)c->cfg.batch_ctas_per_sm;
-  if (per_sm <= 0) per_sm = 8;
+  if (per_sm <= 0) per_sm = tma ? 1 : 8;
   const int grid = c->sm_count * per_sm;
+  CG_TRY(c->b_err.ensure(1));
+  CG_CUDA(cudaMemsetAsync(c->b_err.p, 0, sizeof(unsigned int), st));
   size_t sci = 0;
   std::sort(stage_copies.begin(), stage_copies.end(),
             [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
@@ -1019,7 +1101,12 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
       CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(stage_copies[sci].dst),
                               reinterpret_cast<const void *>(stage_copies[sci].src),
                               stage_copies[sci].n, cudaMemcpyDeviceToDevice, st));
-    CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l], grid, st));
+    if (tma)
+      CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
+                                    grid, c->b_err.p, st));
+    else
+      CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l], grid,
+                                st));
     c->stats.kernels++;
   }
   const int strict = (int)c->cfg.strict_device_undef;
@@ -1028,12 +1115,16 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   CG_CUDA(launch_emit_records(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems,
                               strict, c->b_recs.p, dev_rec_cap, st));
   c->stats.kernels += dev_rec_cap ? 3 : 2;
-  CG_TRY(c->h_total.ensure(1));
+  CG_TRY(c->h_total.ensure(2));
   CG_TRY(c->h_reps.ensure(nreq));
   CG_CUDA(cudaMemcpyAsync(c->h_total.p, c->b_blocksums.p + nblocks, 8, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(c->h_total.p + 1, c->b_err.p, sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
                           cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
+  if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
+    return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
   const uint64_t total = c->h_total.p[0];
   const uint64_t take = std::min(total, dev_rec_cap);
   if (take) {
@@ -1046,15 +1137,16 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   if (reps) std::memcpy(reps, c->h_reps.p, nreq * sizeof(cg_report));
   for (uint64_t i = 0; i < nreq; i++) count_stats(c, c->h_reps.p[i]);
   *n_rec = total;
+  c->stats.batch_ns += now_ns() - t_begin;
   c->stats.batches++;
   c->stats.levels += (uint64_t)nlev;
   return CG_OK;
 }
 
-cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, int32_t *level,
-                         uint32_t *n_levels) {
+cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, const uint8_t *modes,
+                         int32_t *level, uint32_t *n_levels) {
   if ((nreq && (!reqs || !level))) return set_error(CG_E_ARG, "NULL argument");
-  const std::vector<int> lvl = plan_levels(reqs, nreq, carry != 0);
+  const std::vector<int> lvl = plan_levels(reqs, nreq, carry != 0, modes);
   int top = -1;
   for (uint64_t i = 0; i < nreq; i++) {
     level[i] = lvl[i];

@@ -175,8 +175,13 @@ cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const R
                                    SingleScratch *scr, cg_report *out, int grid,
                                    cudaStream_t st);
 int scan_single_tma_grid(int sm_count, uint64_t n);
+uint32_t scan_tma_tile_bytes();  // a batched segment is a whole number of these
+cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
+                                  uint64_t pos_end, uint64_t n_segs, int max_ctas,
+                                  unsigned int *err_flag, cudaStream_t st);
 cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int carry,
                           cudaStream_t st);
+cudaError_t launch_job_modes(const BatchPlan &p, uint8_t *modes, cudaStream_t st);
 cudaError_t launch_scan_level(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                               uint64_t pos_end, uint64_t n_segs, int grid, cudaStream_t st);
 cudaError_t launch_finalize(const BatchPlan &p, cg_report *reps, uint32_t *counts,

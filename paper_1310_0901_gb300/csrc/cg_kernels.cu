@@ -271,6 +271,22 @@ cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int
   return cudaGetLastError();
 }
 
+// The job mode bits of every request, packed one byte each for the host's
+// level planner.
+__global__ void job_modes_kernel(const ScanJob *jobs, uint64_t nreq, uint8_t *modes) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nreq;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    modes[i] = (uint8_t)jobs[i].mode;
+}
+
+cudaError_t launch_job_modes(const BatchPlan &p, uint8_t *modes, cudaStream_t st) {
+  if (p.nreq == 0) return cudaSuccess;
+  uint64_t blocks = (p.nreq + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  job_modes_kernel<<<(unsigned)blocks, 256, 0, st>>>(p.jobs, p.nreq, modes);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------- batched: one level
 
 // Persistent-style kernel over the byte segments of every copy of one

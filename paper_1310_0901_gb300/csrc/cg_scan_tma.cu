@@ -230,6 +230,185 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   single_epilogue(la, scr, ri, out, err);
 }
 
+// ------------------------------------------------ batched: one level
+
+// The tiles a warp processes in one level, in order: segments w, w + W, ...
+// of the level's segment list, each segment's tiles in turn.  Producer and
+// consumer walk identical iterators, the producer kNS tiles ahead.
+struct SegIter {
+  uint64_t s;      // current segment id
+  uint32_t req;    // its request
+  ScanJob job;
+  Geo g;
+  int64_t t, t_end;  // tile range of the segment
+  bool valid;
+};
+
+__device__ __forceinline__ void seg_load(SegIter &it, const BatchPlan &p, const Image &img,
+                                         uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
+                                         uint64_t step) {
+  const int64_t seg_rows = p.seg_chunks >> 5;
+  while (it.s < n_segs) {
+    uint64_t lo = pos_begin, hi = pos_end;  // last position whose first segment <= s
+    while (hi - lo > 1) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (__ldg(p.seg_first + mid) <= it.s)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    it.req = __ldg(p.order + lo);
+    it.job = p.jobs[it.req];
+    it.g = make_geo(it.job, img);
+    const int64_t k = (int64_t)(it.s - __ldg(p.seg_first + lo));
+    const int64_t rows = (it.g.nchunks + 31) >> 5;
+    const int64_t r0 = k * seg_rows;
+    const int64_t r1 = r0 + seg_rows < rows ? r0 + seg_rows : rows;
+    if (r0 < r1) {
+      it.t = r0 / kR;
+      it.t_end = (r1 + kR - 1) / kR;
+      it.valid = true;
+      return;
+    }
+    it.s += step;
+  }
+  it.valid = false;
+}
+
+__device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bits, uint32_t st,
+                                          uint32_t bar) {
+  const int64_t c0 = it.t * kR * 32;
+  switch (it.job.kind) {
+    case CG_HTOD:
+      issue_tile<CG_HTOD>(it.g, a_bits, c0, st, bar);
+      break;
+    case CG_DTOH:
+      issue_tile<CG_DTOH>(it.g, a_bits, c0, st, bar);
+      break;
+    default:
+      issue_tile<CG_DTOD>(it.g, a_bits, c0, st, bar);
+      break;
+  }
+}
+
+__device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp, int lane,
+                                            LaneAcc &la) {
+  const int64_t c0 = it.t * kR * 32;
+  const bool carry = it.job.mode & kModeCarry;
+  switch (it.job.kind) {
+    case CG_HTOD:
+      if (carry)
+        consume_tile<CG_HTOD, true>(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_HTOD, false>(it.g, c0, sp, lane, la);
+      break;
+    case CG_DTOH:
+      if (carry)
+        consume_tile<CG_DTOH, true>(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_DTOH, false>(it.g, c0, sp, lane, la);
+      break;
+    default:
+      if (carry)
+        consume_tile<CG_DTOD, true>(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_DTOD, false>(it.g, c0, sp, lane, la);
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_level_tma_kernel(Image img, BatchPlan p, uint64_t pos_begin, uint64_t pos_end,
+                          uint64_t n_segs, unsigned int *err_flag) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
+  const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  SegIter prod, cons;
+  prod.s = gw;
+  seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
+  cons = prod;
+  int issued = 0;
+  for (int s = 0; s < kNS && prod.valid; s++) {
+    if (lane == 0) seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    issued++;
+    if (++prod.t >= prod.t_end) {
+      prod.s += nw;
+      seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
+    }
+  }
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t parity = 0;
+  int stage = 0;
+  bool failed = false;
+  while (cons.valid) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), (parity >> stage) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u << stage;
+    issued--;
+    seg_consume(cons, wbase + stage * kStage, lane, la);
+    __syncwarp();
+    if (prod.valid) {
+      if (lane == 0) {
+        fence_proxy_async();
+        seg_issue(prod, img.a_bits, smem_addr(wbase + stage * kStage), smem_addr(&bars[stage]));
+      }
+      issued++;
+      if (++prod.t >= prod.t_end) {
+        prod.s += nw;
+        seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
+      }
+    }
+    if (++cons.t >= cons.t_end) {  // segment done: its counts go to its request
+      warp_flush(la, &p.acc[cons.req], lane);
+      cons.s += nw;
+      seg_load(cons, p, img, pos_begin, pos_end, n_segs, nw);
+    }
+    stage = stage + 1 == kNS ? 0 : stage + 1;
+  }
+  if (failed) {  // drain the copies still in flight, bounded
+    for (int d = 0; d < issued; d++) {
+      const int sd = (stage + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+    if (lane == 0) atomicOr(err_flag, 1u);
+  }
+}
+
+cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
+                                  uint64_t pos_end, uint64_t n_segs, int max_ctas,
+                                  unsigned int *err_flag, cudaStream_t st) {
+  if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(scan_level_tma_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const uint64_t ctas = (n_segs + kTW - 1) / kTW;
+  const unsigned g = (unsigned)(ctas < (uint64_t)max_ctas ? ctas : (uint64_t)max_ctas);
+  scan_level_tma_kernel<<<g, kTW * 32, kSmemBytes, st>>>(img, p, pos_begin, pos_end, n_segs,
+                                                         err_flag);
+  return cudaGetLastError();
+}
+
 template <uint32_t KIND, bool CARRY>
 static cudaError_t launch_tma_t(const Image &img, const ScanJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int grid, cudaStream_t st) {
@@ -261,6 +440,8 @@ cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const R
                    : launch_tma_t<CG_DTOD, false>(img, job, ri, scr, out, grid, st);
   }
 }
+
+uint32_t scan_tma_tile_bytes() { return 512u * kR; }
 
 int scan_single_tma_grid(int sm_count, uint64_t n) {
   // tiles of kR rows; one CTA (kTW warps) per SM at most

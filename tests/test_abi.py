@@ -71,24 +71,29 @@ def test_host_only_entry_points():
     assert "8000000" in text and "4000000" in text and "device->host" in text
 
 
-def _brute_levels(reqs):
+def _brute_levels(reqs, modes=None):
     """Pairwise definition: request i depends on every earlier request j
     whose write range meets i's read or write range, or whose read range
-    meets i's write range (host and device spaces apart)."""
-    def rw(q):
+    meets i's write range (host and device spaces apart).  With modes, a
+    request writes only if it carries (bit 0) and reads a device source only
+    if that source is valid (bit 1)."""
+    def rw(i, q):
         k, d, s, n = int(q["kind"]), int(q["dst"]), int(q["src"]), int(q["n"])
+        carries = modes is None or bool(modes[i] & 1)
+        rdev = modes is None or bool(modes[i] & 2)
         if n == 0:
             return [], []
+        w = [("d", d, d + n)] if carries else []
         if k == S.HTOD:
-            return [("h", s, s + n)], [("d", d, d + n)]
+            return [("h", s, s + n)], w
         if k == S.DTOH:
-            return [("d", s, s + n)], [("h", d, d + n)]
-        return [("d", s, s + n)], [("d", d, d + n)]
+            return ([("d", s, s + n)] if rdev else []), ([("h", d, d + n)] if carries else [])
+        return ([("d", s, s + n)] if rdev else []), w
 
     def meet(xs, ys):
         return any(a[0] == b[0] and a[1] < b[2] and b[1] < a[2] for a in xs for b in ys)
 
-    sets = [rw(q) for q in reqs]
+    sets = [rw(i, q) for i, q in enumerate(reqs)]
     lv = []
     for i, (ri, wi) in enumerate(sets):
         best = -1
@@ -115,6 +120,9 @@ def test_planner_matches_pairwise_definition(seed):
     assert nl == max(want) + 1
     lv0, nl0 = cg.plan_levels(reqs, carry=False)
     assert not lv0.any() and nl0 == 1
+    modes = rng.integers(0, 4, n).astype(np.uint8)
+    lvm, _ = cg.plan_levels(reqs, carry=True, modes=modes)
+    assert lvm.tolist() == _brute_levels(reqs, modes)
 
 
 def test_planner_on_small_workload_is_exact():

@@ -44,18 +44,20 @@ ENGINES = {"regs": 1, "tma": 2}
 def test_small_workload_single_checks(cg, carry, engine):
     """1,000 mixed copies over 64 live allocations, one cg_check_copy each."""
     w = S.small(0)
-    ctx, orc, (a, v) = U.make_pair(w.image, w.table, carry=carry, single_engine=ENGINES[engine])
+    ctx, orc, (a, v) = U.make_pair(w.image, w.table, carry=carry, scan_engine=ENGINES[engine])
     _run_single(ctx, orc, w.reqs, "small/single")
     U.assert_same_state(ctx, orc, v, w.table)
 
 
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("seed", [0, 1])
 @pytest.mark.parametrize("seg_kib", [2, 64])
-def test_small_workload_batch(cg, seed, seg_kib):
+def test_small_workload_batch(cg, seed, seg_kib, engine):
     """The same stream as one cg_check_batch: reports, records (order and
     content) and final state equal the oracle's sequential result."""
     w = S.small(seed)
-    ctx, orc, (a, v) = U.make_pair(w.image, w.table, batch_segment_kib=seg_kib)
+    ctx, orc, (a, v) = U.make_pair(w.image, w.table, batch_segment_kib=seg_kib,
+                                   scan_engine=ENGINES[engine])
     st, reps, recs, total, _ = ctx.check_batch(w.reqs)
     assert st == 0, cg.cg_last_error()
     st_o, oreps, _ = orc.check_batch(w.reqs)
@@ -101,7 +103,7 @@ def test_alignment_sweep(cg, kind, engine):
     base = 1 << 40
     table = S.AllocTable(np.array([base, base + (1 << 20)], np.uint64),
                          np.array([1 << 18, 1 << 18], np.uint64), np.zeros(0, np.int64))
-    ctx, orc, (a, v) = U.make_pair(img, table, single_engine=ENGINES[engine])
+    ctx, orc, (a, v) = U.make_pair(img, table, scan_engine=ENGINES[engine])
     # give the device shadows mixed content first
     for off in range(0, 1 << 18, 1 << 15):
         for b in (base, base + (1 << 20)):
@@ -127,7 +129,7 @@ def test_alignment_sweep(cg, kind, engine):
     _run_single(ctx, orc, reqs, "sweep")
     U.assert_same_state(ctx, orc, v, table)
     # the same requests again as one batch, on fresh state
-    ctx2, orc2, (a2, v2) = U.make_pair(img, table)
+    ctx2, orc2, (a2, v2) = U.make_pair(img, table, scan_engine=ENGINES[engine])
     st, reps, recs, total, _ = ctx2.check_batch(reqs)
     st_o, oreps, _ = orc2.check_batch(reqs)
     assert st == st_o == 0
@@ -143,7 +145,7 @@ def test_edge_cases(cg, engine):
     base = 1 << 30
     table = S.AllocTable(np.array([base, base + 4096], np.uint64),
                          np.array([4096, 256], np.uint64), np.zeros(0, np.int64))
-    ctx, orc, (a, v) = U.make_pair(img, table, single_engine=ENGINES[engine])
+    ctx, orc, (a, v) = U.make_pair(img, table, scan_engine=ENGINES[engine])
     cases = [
         (HTOD, base, 0, 0), (DTOH, 0, 12345, 0), (DTOD, 1, 2, 0),           # n == 0
         (HTOD, base + 4096 - 1, 10, 1), (HTOD, base + 4095, 10, 2),          # last byte / overrun
