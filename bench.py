@@ -329,6 +329,63 @@ def run_batched_workload(args, which: str):
     return out
 
 
+def run_serving(args):
+    """The serving loop under Poisson arrivals from 8 client threads:
+    sustained checks/s and submit-to-result latency percentiles."""
+    import torch
+
+    import paper_1310_0901_gb300 as cg
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    host_n = args.serve_image_gib << 30
+    tr = S.serving(0, seconds=args.serve_seconds, rate=args.serve_rate, host_n=host_n)
+    v = torch.zeros(host_n, dtype=torch.uint8, device=dev)
+    a = torch.full((host_n // 8,), 0xFF, dtype=torch.uint8, device=dev)
+    starts, lengths, values = S.serving_image_runs(0, host_n)
+    idx = np.concatenate([np.arange(s0, s0 + ln) for s0, ln in zip(starts, lengths)])
+    vals = np.repeat(values, lengths)
+    v[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+    ctx = cg.Context()
+    ctx.bind_host_shadow(a, v)
+    order = np.argsort(tr.table.base)
+    st = ctx.register_allocs(tr.table.base[order], tr.table.size[order])
+    assert not st.any()
+    cfg = dict(clients=8, ring_capacity=1 << 14, max_round=8192, streams=args.serve_streams,
+               budget_bytes=8 << 30)
+    ctx.serve_start(**cfg)
+    # warm-up: a short checks-only trace (no allocation events)
+    wt = S.serve_trace(S.rng_for(99), 20_000, args.serve_rate, 8, tr.table, host_n,
+                       event_frac=0.0)
+    ctx.serve_replay(wt.reqs, wt.client, wt.arrival_ns)
+    res = ctx.serve_replay(tr.reqs, tr.client, tr.arrival_ns)
+    stats = ctx.serve_stop()
+    ctx.close()
+    checks = tr.reqs["op"] == S.OP_CHECK
+    ok = res["status"] == 0
+    lat_us = (res["done_ns"][checks] - res["submit_ns"][checks]).astype(np.float64) / 1e3
+    span_s = (int(res["done_ns"].max()) - int(res["submit_ns"].min())) / 1e9
+    n_checks = int(checks.sum())
+    pct = {f"p{p}": round(float(np.percentile(lat_us, p)), 1) for p in (50, 90, 99, 99.9)}
+    pct["max"] = round(float(lat_us.max()), 1)
+    sizes = tr.reqs["n"][checks]
+    small = sizes <= 4096
+    return {
+        "metric": "sustained checks/sec and p50/p99 check latency (serving)",
+        "value": round(n_checks / span_s, 1), "unit": "checks/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "u8", "data": "synthetic (seeded cg_synth.serving)",
+        "config": {"workload": tr.note, "requests": int(len(tr.reqs)), "checks": n_checks,
+                   "offered_rate_per_s": args.serve_rate, "clients": 8,
+                   "allocations": int(len(tr.table.base)), "host_image_bytes": host_n,
+                   "serve_config": cfg},
+        "latency_us": pct,
+        "latency_us_checks_le_4KiB": {f"p{p}": round(float(np.percentile(lat_us[small], p)), 1)
+                                      for p in (50, 99)},
+        "all_ok": bool(ok.all()), "span_s": round(span_s, 3),
+        "offered_gb_per_s": round(float(sizes.sum()) / (args.serve_seconds * 1e9), 1),
+        "serve_stats": stats,
+    }
+
+
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -427,7 +484,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 register loads, 2 TMA bulk")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "adversarial"])
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "batched", "adversarial", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=S.SERVE_RATE)
+    ap.add_argument("--serve-image-gib", type=int, default=32)
+    ap.add_argument("--serve-streams", type=int, default=2)
     ap.add_argument("--segment-kib", type=int, default=0)
     ap.add_argument("--single-sample", type=int, default=100_000)
     args = ap.parse_args()
@@ -437,6 +499,10 @@ def main():
         out = run_reference(args, world, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(run_serving(args)), flush=True)
         return
     if args.workload != "large":
         if rank == 0:

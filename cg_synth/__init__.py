@@ -283,3 +283,124 @@ def _human(n: int) -> str:
         if n >= 1 << sh and n % (1 << sh) == 0:
             return f"{n >> sh}{unit}"
     return f"{n}B"
+
+
+# ----------------------------------------------------------------- serving
+
+OP_CHECK, OP_ALLOC, OP_FREE, OP_MARK_DEFINED, OP_MARK_UNDEFINED = 1, 2, 3, 4, 5
+SERVE_DTYPE = np.dtype([("op", "<u4"), ("kind", "<u4"), ("dst", "<u8"), ("src", "<u8"),
+                        ("n", "<u8")])
+
+
+@dataclass
+class ServeTrace:
+    reqs: np.ndarray        # SERVE_DTYPE
+    client: np.ndarray      # uint32
+    arrival_ns: np.ndarray  # uint64, nondecreasing
+    table: AllocTable       # allocations live before the trace starts
+    note: str = ""
+
+
+def serve_trace(rng, n_req: int, rate: float, clients: int, table: AllocTable, host_n: int,
+                big: np.ndarray | None = None, event_frac: float = 0.05,
+                size_mix=((0.80, 1, 4096), (0.19, 4096, 1 << 20), (0.01, 1 << 20, 256 << 20)),
+                dyn_slots_per_client: int = 512, dyn_size=(256, 64 << 10),
+                mark_frac: float = 0.0) -> ServeTrace:
+    """Poisson arrivals at `rate` requests/s spread over `clients` streams.
+    A fraction `event_frac` are allocation events (half allocations, half
+    frees) on each client's own pool of address slots, so every client's
+    frees follow its own allocations; the rest are checks (60/30/10
+    HtoD/DtoH/DtoD) of the size classes in `size_mix` against the
+    allocations of `table` (the largest class against `big`, the indices of
+    large allocations, when given).  A fraction `mark_frac` of the checks
+    becomes mark-defined/undefined requests."""
+    gaps = rng.exponential(1.0 / rate, n_req)
+    arrival = np.cumsum(gaps) * 1e9
+    client = rng.integers(0, clients, n_req).astype(np.uint32)
+    reqs = np.zeros(n_req, SERVE_DTYPE)
+    is_event = rng.random(n_req) < event_frac
+    # checks, vectorised
+    kinds = rng.choice([HTOD, DTOH, DTOD], size=n_req, p=[0.6, 0.3, 0.1]).astype(np.uint32)
+    cls = rng.choice(len(size_mix), size=n_req, p=[c[0] for c in size_mix])
+    sizes = np.zeros(n_req, np.uint64)
+    for k, (_, lo, hi) in enumerate(size_mix):
+        m = cls == k
+        sizes[m] = log_uniform_int(rng, lo, hi, int(m.sum()))
+    sizes = np.minimum(sizes, np.uint64(host_n))
+    live = np.arange(len(table.base))
+    tgt = live[rng.integers(0, live.size, n_req)]
+    if big is not None and big.size:
+        bigm = cls == len(size_mix) - 1
+        tgt[bigm] = big[rng.integers(0, big.size, int(bigm.sum()))]
+    tsize = table.size[tgt].astype(np.uint64)
+    room = np.where(sizes <= tsize, tsize - sizes, 0).astype(np.float64)
+    off = (rng.random(n_req) * (room + 1)).astype(np.uint64)
+    dev = table.base[tgt].astype(np.uint64) + off
+    tgt2 = live[rng.integers(0, live.size, n_req)]
+    tsize2 = table.size[tgt2].astype(np.uint64)
+    room2 = np.where(sizes <= tsize2, tsize2 - sizes, 0).astype(np.float64)
+    dev2 = table.base[tgt2].astype(np.uint64) + (rng.random(n_req) * (room2 + 1)).astype(np.uint64)
+    host = (rng.random(n_req) * (host_n - sizes.astype(np.float64) + 1)).astype(np.uint64)
+    reqs["op"] = OP_CHECK
+    reqs["kind"] = kinds
+    reqs["n"] = sizes
+    reqs["dst"] = np.where(kinds == DTOH, host, dev)
+    reqs["src"] = np.where(kinds == HTOD, host, np.where(kinds == DTOD, dev2, dev))
+    if mark_frac > 0:
+        mk = (~is_event) & (rng.random(n_req) < mark_frac)
+        reqs["op"][mk] = np.where(rng.random(int(mk.sum())) < 0.5, OP_MARK_DEFINED,
+                                  OP_MARK_UNDEFINED)
+        reqs["dst"][mk] = dev[mk]
+        reqs["src"][mk] = 0
+        reqs["n"][mk] = np.minimum(sizes[mk], tsize[mk] - np.minimum(off[mk], tsize[mk]))
+    # allocation events: each client owns a pool of address slots above the table
+    top = int(table.base.max() + table.size.max()) if len(table.base) else 0
+    slot_span = 1 << 20
+    region = ((top >> 30) + 1) << 30
+    live_dyn = [[] for _ in range(clients)]
+    free_dyn = [list(range(dyn_slots_per_client)) for _ in range(clients)]
+    for i in np.nonzero(is_event)[0]:
+        c = int(client[i])
+        if live_dyn[c] and (rng.random() < 0.5 or not free_dyn[c]):
+            k = live_dyn[c].pop(int(rng.integers(0, len(live_dyn[c]))))
+            free_dyn[c].append(k)
+            reqs[i] = (OP_FREE, 0, region + (c * dyn_slots_per_client + k) * slot_span, 0, 0)
+        else:
+            k = free_dyn[c].pop(int(rng.integers(0, len(free_dyn[c]))))
+            live_dyn[c].append(k)
+            size = int(log_uniform_int(rng, dyn_size[0], dyn_size[1], 1)[0])
+            reqs[i] = (OP_ALLOC, 0, region + (c * dyn_slots_per_client + k) * slot_span, 0, size)
+    return ServeTrace(reqs, client, arrival.astype(np.uint64), table)
+
+
+SERVE_RATE = 200_000.0
+
+
+def serving(seed: int = 0, seconds: float = 10.0, rate: float = SERVE_RATE, clients: int = 8,
+            host_n: int = 32 << 30, n_alloc: int = 100_000, n_big: int = 100) -> ServeTrace:
+    """Poisson arrivals from 8 client streams at 200k requests/s: 80 % of
+    the checks 1 B-4 KiB, 19 % 4 KiB-1 MiB, 1 % 1 MiB-256 MiB; allocation
+    events 5 % of the traffic; 100,000 live allocations (log-uniform
+    256 B-1 MiB) plus 100 of 256 MiB for the largest copies; a 32 GiB host
+    image (described, not materialised: see serving_image_runs)."""
+    rng = rng_for(seed)
+    small_sizes = log_uniform_int(rng, 256, 1 << 20, n_alloc)
+    sizes = np.concatenate([small_sizes, np.full(n_big, 256 << 20, np.uint64)])
+    bases = disjoint_bases(rng, sizes, space=1 << 47)
+    table = AllocTable(bases.astype(np.uint64), sizes.astype(np.uint64), np.zeros(0, np.int64))
+    n_req = int(seconds * rate)
+    tr = serve_trace(rng, n_req, rate, clients, table, host_n,
+                     big=np.arange(n_alloc, n_alloc + n_big))
+    tr.note = f"serving-{clients}-clients-{int(rate)}-req-per-s-{seconds}s-{host_n >> 30}GiB-image"
+    return tr
+
+
+def serving_image_runs(seed: int, host_n: int, undef_frac: float = 1e-5, mean_run: float = 8.0):
+    """Planted undefined runs of a large host image, without materialising
+    it: (starts, lengths, values) with values a nonzero mask per run."""
+    rng = rng_for(seed + 1)
+    k = max(1, int(undef_frac * host_n / mean_run))
+    starts = rng.integers(0, host_n - 64, k).astype(np.int64)
+    lengths = np.minimum(rng.geometric(1.0 / mean_run, k), 64).astype(np.int64)
+    values = rng.integers(1, 256, k).astype(np.uint8)
+    return starts, lengths, values

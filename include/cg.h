@@ -271,6 +271,98 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                          uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream);
 
+/* --------------------------------------------------------------- serving */
+
+/* A serving loop in the context: client threads submit requests into
+ * per-client rings as they arrive; one scheduler thread admits them in one
+ * global order (result.seq), applies allocation events to the table at
+ * their place in that order, and packs the checks that arrive while others
+ * are on the GPU into rounds ("continuous batching").  A round is planned
+ * like cg_check_batch (dependency levels) and runs on one of `streams`
+ * streams; rounds overlap on the device unless one touches shadow another
+ * in-flight round touches, in which case it waits for that round.
+ * Admission stops while the bytes of admitted, unfinished checks would
+ * exceed budget_bytes.  Every result equals the one the same request gets
+ * when all requests are applied one by one in seq order (cg_check_copy,
+ * cg_register_alloc, cg_free, cg_mark_*).  Sec. 2's wrappers check each
+ * call as it happens; serving keeps that order while batching the work. */
+
+#define CG_OP_CHECK 1u
+#define CG_OP_ALLOC 2u          /* dst = base, n = size */
+#define CG_OP_FREE 3u           /* dst = base */
+#define CG_OP_MARK_DEFINED 4u   /* dst, n */
+#define CG_OP_MARK_UNDEFINED 5u /* dst, n */
+
+#define CG_PENDING 1 /* cg_poll: the result is not ready yet (not an error) */
+
+typedef struct cg_request {
+  uint32_t op;   /* CG_OP_* */
+  uint32_t kind; /* CG_OP_CHECK: the copy kind */
+  uint64_t dst;
+  uint64_t src;
+  uint64_t n;
+} cg_request; /* 32 bytes */
+
+typedef struct cg_result {
+  uint64_t seq;       /* place in the global order the request took effect in */
+  int32_t status;     /* CG_OK or the request's own API error */
+  uint32_t verdict;   /* CG_OP_FREE: CG_FREE_* */
+  uint64_t submit_ns; /* steady clock at cg_submit */
+  uint64_t done_ns;   /* steady clock when the result became visible */
+  cg_report report;   /* CG_OP_CHECK */
+} cg_result; /* 144 bytes */
+
+typedef struct cg_serve_config {
+  uint32_t clients;       /* client rings, 1..64 (0 = 8) */
+  uint32_t ring_capacity; /* requests per client, a power of two (0 = 4096) */
+  uint32_t max_round;     /* checks per round at most (0 = 8192) */
+  uint32_t streams;       /* rounds on the GPU at once, 1..8 (0 = 2) */
+  uint64_t budget_bytes;  /* bytes of admitted, unfinished checks (0 = 8 GiB);
+                             a single larger check is still admitted alone */
+  uint32_t reserved[10];
+} cg_serve_config;
+
+typedef struct cg_serve_stats {
+  uint64_t requests;       /* admitted */
+  uint64_t checks;
+  uint64_t rounds;
+  uint64_t round_checks_max;
+  uint64_t conflict_waits; /* rounds that had to wait for an in-flight round */
+  uint64_t budget_stalls;  /* admissions stopped by the budget */
+  uint64_t bytes_checked;
+  uint64_t inflight_bytes_max;
+} cg_serve_stats;
+
+/* Start serving.  While serving, the context accepts only cg_submit,
+ * cg_poll, cg_wait, cg_serve_replay, cg_get_stats and cg_serve_stop
+ * (CG_E_STATE otherwise).  Allocates the rings and per-stream round
+ * buffers and starts the scheduler thread. */
+cg_status cg_serve_start(cg_ctx *ctx, const cg_serve_config *cfg);
+
+/* Submit one request from client `client` (0..clients-1).  Each client
+ * index must be driven by one thread at a time (cg_submit and cg_poll /
+ * cg_wait of its tickets).  *ticket identifies the result.  CG_E_FULL when
+ * the client has ring_capacity requests submitted and not yet collected. */
+cg_status cg_submit(cg_ctx *ctx, uint32_t client, const cg_request *req, uint64_t *ticket);
+
+/* Collect a result: CG_OK (copied to *out, ticket released), CG_PENDING,
+ * or CG_E_ARG for an unknown or already collected ticket. */
+cg_status cg_poll(cg_ctx *ctx, uint64_t ticket, cg_result *out);
+
+/* cg_poll until done or timeout_ms pass (CG_E_TIMEOUT). */
+cg_status cg_wait(cg_ctx *ctx, uint64_t ticket, uint32_t timeout_ms, cg_result *out);
+
+/* Replay a timed trace: request i is submitted by client client[i] at
+ * arrival_ns[i] after the call starts (one host thread per client; each
+ * client's requests in index order), and its result lands in results[i].
+ * Returns once every result is in.  Host arrays. */
+cg_status cg_serve_replay(cg_ctx *ctx, const cg_request *reqs, const uint32_t *client,
+                          const uint64_t *arrival_ns, uint64_t n, cg_result *results);
+
+/* Finish the admitted work, stop the scheduler, free the serving buffers.
+ * out (may be NULL) gets the serving counters. */
+cg_status cg_serve_stop(cg_ctx *ctx, cg_serve_stats *out);
+
 /* --------------------------------------------- allocation-free variant */
 
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -65,14 +65,42 @@ class cg_stats(ctypes.Structure):
                 ("batch_lookup_ns", u64)]
 
 
+class cg_request(ctypes.Structure):
+    _fields_ = [("op", u32), ("kind", u32), ("dst", u64), ("src", u64), ("n", u64)]
+
+
+class cg_result(ctypes.Structure):
+    _fields_ = [("seq", u64), ("status", i32), ("verdict", u32), ("submit_ns", u64),
+                ("done_ns", u64), ("report", cg_report)]
+
+
+class cg_serve_config(ctypes.Structure):
+    _fields_ = [("clients", u32), ("ring_capacity", u32), ("max_round", u32), ("streams", u32),
+                ("budget_bytes", u64), ("reserved", u32 * 10)]
+
+
+class cg_serve_stats(ctypes.Structure):
+    _fields_ = [("requests", u64), ("checks", u64), ("rounds", u64), ("round_checks_max", u64),
+                ("conflict_waits", u64), ("budget_stalls", u64), ("bytes_checked", u64),
+                ("inflight_bytes_max", u64)]
+
+
+OP_CHECK, OP_ALLOC, OP_FREE, OP_MARK_DEFINED, OP_MARK_UNDEFINED = 1, 2, 3, 4, 5
+PENDING = 1
+REQUEST_DTYPE = np.dtype([("op", "<u4"), ("kind", "<u4"), ("dst", "<u8"), ("src", "<u8"),
+                          ("n", "<u8")])
+
 REPORT_FIELDS = [f for f, _ in cg_report._fields_]
 RECORD_FIELDS = [f for f, _ in cg_err_record._fields_]
 REPORT_DTYPE = np.dtype([(f, "<i8" if t is i64 else ("<u4" if t is u32 else "<u8"))
                          for f, t in cg_report._fields_])
 RECORD_DTYPE = np.dtype([(f, "<i8" if t is i64 else ("<u4" if t is u32 else "<u8"))
                          for f, t in cg_err_record._fields_])
+RESULT_DTYPE = np.dtype([("seq", "<u8"), ("status", "<i4"), ("verdict", "<u4"),
+                         ("submit_ns", "<u8"), ("done_ns", "<u8"), ("report", REPORT_DTYPE)])
 assert ctypes.sizeof(cg_copy) == 32 and ctypes.sizeof(cg_report) == 112
 assert ctypes.sizeof(cg_err_record) == 48
+assert ctypes.sizeof(cg_request) == 32 and ctypes.sizeof(cg_result) == 144
 assert REPORT_DTYPE.itemsize == 112 and RECORD_DTYPE.itemsize == 48
 
 # (name, restype, argtypes) of every entry point declared in include/cg.h
@@ -92,6 +120,12 @@ SIGNATURES = [
     ("cg_check_copy_async", i32, [vp, ctypes.POINTER(cg_copy), vp, vp]),
     ("cg_check_batch", i32, [vp, vp, u64, vp, vp, u64, ctypes.POINTER(u64),
                              ctypes.POINTER(u64), vp]),
+    ("cg_serve_start", i32, [vp, ctypes.POINTER(cg_serve_config)]),
+    ("cg_submit", i32, [vp, u32, ctypes.POINTER(cg_request), ctypes.POINTER(u64)]),
+    ("cg_poll", i32, [vp, u64, ctypes.POINTER(cg_result)]),
+    ("cg_wait", i32, [vp, u64, u32, ctypes.POINTER(cg_result)]),
+    ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
+    ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
     ("cg_plan_levels", i32, [vp, u64, u32, vp, vp, ctypes.POINTER(u32)]),
     ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
@@ -240,6 +274,42 @@ class Context:
                             ctypes.byref(n_rec), ctypes.byref(bad), _stream_handle(stream))
         total = int(n_rec.value)
         return st, reps, recs[:min(total, rec_cap)], total, int(bad.value)
+
+    # ------------------------------------------------------------ serving
+    def serve_start(self, **cfg) -> None:
+        c = cg_serve_config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        check(cg_serve_start(self._h, ctypes.byref(c)), "cg_serve_start")
+
+    def submit(self, client: int, op: int, kind: int = 0, dst: int = 0, src: int = 0,
+               n: int = 0) -> tuple[int, int]:
+        t = u64(0)
+        st = cg_submit(self._h, client, ctypes.byref(cg_request(op, kind, dst, src, n)),
+                       ctypes.byref(t))
+        return st, int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        r = cg_result()
+        st = cg_wait(self._h, ticket, timeout_ms, ctypes.byref(r))
+        return st, r
+
+    def serve_replay(self, reqs: np.ndarray, clients: np.ndarray,
+                     arrival_ns: np.ndarray) -> np.ndarray:
+        """Replay a timed trace (REQUEST_DTYPE records); returns RESULT_DTYPE."""
+        reqs = np.ascontiguousarray(reqs)
+        assert reqs.dtype.itemsize == 32
+        cl = np.ascontiguousarray(clients, dtype=np.uint32)
+        ar = np.ascontiguousarray(arrival_ns, dtype=np.uint64)
+        out = np.zeros(len(reqs), dtype=RESULT_DTYPE)
+        check(cg_serve_replay(self._h, reqs.ctypes.data, cl.ctypes.data, ar.ctypes.data,
+                              len(reqs), out.ctypes.data), "cg_serve_replay")
+        return out
+
+    def serve_stop(self) -> dict:
+        s = cg_serve_stats()
+        check(cg_serve_stop(self._h, ctypes.byref(s)), "cg_serve_stop")
+        return {f: getattr(s, f) for f, _ in cg_serve_stats._fields_}
 
     def stats(self) -> dict:
         s = cg_stats()

@@ -1,0 +1,485 @@
+// cg_ctx.h -- the context of libcg and the host-side structures behind it
+// (allocation table, device shadow pool, dependency planner), shared by the
+// C ABI (cg_host.cpp) and the serving engine (cg_serve.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "cg_internal.h"
+
+namespace cgi {
+
+// ------------------------------------------------------------- errors
+
+cg_status set_error(cg_status st, const std::string &msg);
+cg_status cuda_fail(cudaError_t e, const char *what);
+
+#define CG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cgi::cuda_fail(e_, #call); \
+  } while (0)
+
+#define CG_TRY(call)            \
+  do {                          \
+    cg_status s_ = (call);      \
+    if (s_ != CG_OK) return s_; \
+  } while (0)
+
+inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+inline uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// -------------------------------------------------- device shadow pool
+
+// Device V shadow of every live allocation (R6: all 0xFF on registration).
+// Slabs of device memory are carved best-fit in 256-byte units; free space
+// is kept at 0xFF, so a new allocation's shadow needs no initialisation.
+// Released ranges are refilled with 0xFF (queued, flushed on the next
+// stream operation of the context).
+class ShadowArena {
+ public:
+  uint64_t slab_bytes = 1ull << 30;
+  uint64_t budget = 0;
+  uint64_t held = 0;
+
+  ~ShadowArena() { release_all(); }
+
+  void release_all() {
+    for (auto &s : slabs_)
+      if (s.base) cudaFree(s.base);
+    slabs_.clear();
+    by_size_.clear();
+    free_by_off_.clear();
+    slab_index_.clear();
+    held = 0;
+  }
+
+  cg_status alloc(uint64_t size, uint64_t *out) {
+    const uint64_t sz = round_up(size, 256);
+    if (sz > slab_bytes / 2) {  // its own slab
+      if (budget && held + sz > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
+      uint8_t *p = nullptr;
+      cudaError_t e = cudaMalloc(&p, sz);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
+      }
+      e = cudaMemset(p, 0xFF, sz);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
+      add_slab(p, sz, true);
+      held += sz;
+      *out = reinterpret_cast<uint64_t>(p);
+      return CG_OK;
+    }
+    auto it = by_size_.lower_bound(sz);
+    if (it == by_size_.end()) {
+      if (budget && held + slab_bytes > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
+      uint8_t *p = nullptr;
+      cudaError_t e = cudaMalloc(&p, slab_bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
+      }
+      e = cudaMemset(p, 0xFF, slab_bytes);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
+      const uint32_t si = add_slab(p, slab_bytes, false);
+      held += slab_bytes;
+      insert_free(si, 0, slab_bytes);
+      it = by_size_.lower_bound(sz);
+    }
+    const uint64_t bsize = it->first;
+    const uint32_t si = it->second.first;
+    const uint64_t off = it->second.second;
+    by_size_.erase(it);
+    free_by_off_[si].erase(off);
+    if (bsize > sz) insert_free(si, off + sz, bsize - sz);
+    *out = reinterpret_cast<uint64_t>(slabs_[si].base) + off;
+    return CG_OK;
+  }
+
+  // The caller queues the 0xFF refill of [ptr, ptr+size) before reuse.
+  void release(uint64_t ptr, uint64_t size) {
+    const uint64_t sz = round_up(size, 256);
+    auto it = slab_index_.upper_bound(ptr);
+    --it;
+    const uint32_t si = it->second;
+    Slab &s = slabs_[si];
+    if (s.dedicated) {
+      cudaFree(s.base);  // synchronises the device; dedicated slabs are rare
+      held -= s.size;
+      slab_index_.erase(it);
+      s.base = nullptr;
+      s.size = 0;
+      return;
+    }
+    uint64_t off = ptr - reinterpret_cast<uint64_t>(s.base);
+    uint64_t len = sz;
+    auto &fm = free_by_off_[si];
+    auto nx = fm.lower_bound(off);
+    if (nx != fm.end() && nx->first == off + len) {  // merge with the next block
+      len += nx->second;
+      erase_free(si, nx->first, nx->second);
+      nx = fm.lower_bound(off);
+    }
+    if (nx != fm.begin()) {  // merge with the previous block
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        off = pv->first;
+        len += pv->second;
+        erase_free(si, pv->first, pv->second);
+      }
+    }
+    insert_free(si, off, len);
+  }
+
+ private:
+  struct Slab {
+    uint8_t *base;
+    uint64_t size;
+    bool dedicated;
+  };
+  std::vector<Slab> slabs_;
+  std::multimap<uint64_t, std::pair<uint32_t, uint64_t>> by_size_;  // size -> (slab, off)
+  std::vector<std::map<uint64_t, uint64_t>> free_by_off_;           // per slab: off -> size
+  std::map<uint64_t, uint32_t> slab_index_;                         // base -> slab
+
+  uint32_t add_slab(uint8_t *p, uint64_t size, bool dedicated) {
+    slabs_.push_back({p, size, dedicated});
+    free_by_off_.emplace_back();
+    const uint32_t si = (uint32_t)(slabs_.size() - 1);
+    slab_index_[reinterpret_cast<uint64_t>(p)] = si;
+    return si;
+  }
+  void insert_free(uint32_t si, uint64_t off, uint64_t len) {
+    free_by_off_[si][off] = len;
+    by_size_.insert({len, {si, off}});
+  }
+  void erase_free(uint32_t si, uint64_t off, uint64_t len) {
+    free_by_off_[si].erase(off);
+    auto r = by_size_.equal_range(len);
+    for (auto it = r.first; it != r.second; ++it)
+      if (it->second.first == si && it->second.second == off) {
+        by_size_.erase(it);
+        break;
+      }
+  }
+};
+
+// ---------------------------------------------------- allocation table
+
+// The list of live device allocations (Fig. 2 caption) as a sorted main
+// array (size 0 = tombstone of a freed entry) plus an ordered delta of
+// recent registrations, merged into the main array in bulk.
+class AllocTable {
+ public:
+  std::vector<uint64_t> base, size, shadow;  // main, sorted by base
+  std::map<uint64_t, std::pair<uint64_t, uint64_t>> delta;  // base -> (size, shadow)
+  std::set<uint64_t> freed;
+  uint64_t dead = 0;
+  uint64_t live = 0;
+  uint64_t version = 0;
+
+  struct Hit {
+    bool ok;
+    uint64_t base, size, shadow;
+  };
+
+  Hit find(uint64_t addr) const {
+    auto ub = std::upper_bound(base.begin(), base.end(), addr);
+    if (ub != base.begin()) {
+      const size_t j = (size_t)(ub - base.begin()) - 1;
+      if (size[j] && addr - base[j] < size[j]) return {true, base[j], size[j], shadow[j]};
+    }
+    auto it = delta.upper_bound(addr);
+    if (it != delta.begin()) {
+      --it;
+      if (addr - it->first < it->second.first)
+        return {true, it->first, it->second.first, it->second.second};
+    }
+    return {false, 0, 0, 0};
+  }
+
+  bool overlaps(uint64_t b, uint64_t s) const {  // [b, b+s), no wrap
+    auto ub = std::upper_bound(base.begin(), base.end(), b);
+    if (ub != base.begin()) {
+      const size_t j = (size_t)(ub - base.begin()) - 1;
+      if (size[j] && b - base[j] < size[j]) return true;
+    }
+    for (auto k = ub; k != base.end() && *k < b + s; ++k)
+      if (size[(size_t)(k - base.begin())]) return true;
+    auto it = delta.upper_bound(b);
+    if (it != delta.end() && it->first < b + s) return true;
+    if (it != delta.begin()) {
+      --it;
+      if (b - it->first < it->second.first) return true;
+    }
+    return false;
+  }
+
+  void insert(uint64_t b, uint64_t s, uint64_t sh) {
+    delta[b] = {s, sh};
+    live++;
+    version++;
+    freed.erase(freed.lower_bound(b), freed.lower_bound(b + s));  // R13
+    if (delta.size() > std::max<uint64_t>(4096, base.size() / 8)) merge();
+  }
+
+  // Remove the live allocation whose base is exactly b.
+  bool remove_base(uint64_t b, uint64_t *sz, uint64_t *sh) {
+    auto lb = std::lower_bound(base.begin(), base.end(), b);
+    if (lb != base.end() && *lb == b) {
+      const size_t j = (size_t)(lb - base.begin());
+      if (size[j]) {
+        *sz = size[j];
+        *sh = shadow[j];
+        size[j] = 0;
+        dead++;
+        goto removed;
+      }
+    }
+    {
+      auto it = delta.find(b);
+      if (it == delta.end()) return false;
+      *sz = it->second.first;
+      *sh = it->second.second;
+      delta.erase(it);
+    }
+  removed:
+    live--;
+    version++;
+    freed.insert(b);
+    if (dead > 1024 && dead > base.size() / 4) merge();
+    return true;
+  }
+
+  void merge() {
+    if (delta.empty() && dead == 0) return;
+    std::vector<uint64_t> nb, ns, nh;
+    nb.reserve(live);
+    ns.reserve(live);
+    nh.reserve(live);
+    auto it = delta.begin();
+    for (size_t j = 0; j <= base.size(); j++) {
+      const uint64_t limit = j < base.size() ? base[j] : ~0ull;
+      while (it != delta.end() && (j == base.size() || it->first < limit)) {
+        nb.push_back(it->first);
+        ns.push_back(it->second.first);
+        nh.push_back(it->second.second);
+        ++it;
+      }
+      if (j < base.size() && size[j]) {
+        nb.push_back(base[j]);
+        ns.push_back(size[j]);
+        nh.push_back(shadow[j]);
+      }
+    }
+    base.swap(nb);
+    size.swap(ns);
+    shadow.swap(nh);
+    delta.clear();
+    dead = 0;
+  }
+};
+
+// ---------------------------------------------------- batch planner
+
+// Range-chmax / range-max segment tree over the elementary intervals of one
+// address space, holding two values per leaf: the highest level of a copy
+// that wrote it (w) and of one that read it (r).
+class LevelTree {
+ public:
+  void init(int n) {
+    n_ = std::max(1, n);
+    size_t m = 1;
+    while (m < (size_t)n_) m <<= 1;
+    nodes_.assign(2 * m, Node{-1, -1, -1, -1});
+  }
+  // max of w (and of r when want_r) over leaves [l, r)
+  int query(int l, int r, bool want_r) const {
+    if (l >= r) return -1;
+    return q(1, 0, n_, l, r, want_r);
+  }
+  void update_w(int l, int r, int v) {
+    if (l < r) u(1, 0, n_, l, r, v, true);
+  }
+  void update_r(int l, int r, int v) {
+    if (l < r) u(1, 0, n_, l, r, v, false);
+  }
+
+ private:
+  struct Node {
+    int w, r, tw, tr;  // subtree maxima and pending chmax for the children
+  };
+  int n_ = 1;
+  mutable std::vector<Node> nodes_;
+  void push(int x) const {
+    Node &p = nodes_[x];
+    if (p.tw < 0 && p.tr < 0) return;
+    for (int c = 2 * x; c <= 2 * x + 1; c++) {
+      Node &k = nodes_[c];
+      if (p.tw >= 0) {
+        k.w = std::max(k.w, p.tw);
+        k.tw = std::max(k.tw, p.tw);
+      }
+      if (p.tr >= 0) {
+        k.r = std::max(k.r, p.tr);
+        k.tr = std::max(k.tr, p.tr);
+      }
+    }
+    p.tw = p.tr = -1;
+  }
+  int q(int x, int l, int r, int ql, int qr, bool want_r) const {
+    if (ql <= l && r <= qr) return want_r ? std::max(nodes_[x].w, nodes_[x].r) : nodes_[x].w;
+    push(x);
+    const int m = (l + r) >> 1;
+    int v = -1;
+    if (ql < m) v = q(2 * x, l, m, ql, qr, want_r);
+    if (qr > m) v = std::max(v, q(2 * x + 1, m, r, ql, qr, want_r));
+    return v;
+  }
+  void u(int x, int l, int r, int ql, int qr, int v, bool is_w) {
+    Node &nd = nodes_[x];
+    if (ql <= l && r <= qr) {
+      if (is_w) {
+        nd.w = std::max(nd.w, v);
+        nd.tw = std::max(nd.tw, v);
+      } else {
+        nd.r = std::max(nd.r, v);
+        nd.tr = std::max(nd.tr, v);
+      }
+      return;
+    }
+    push(x);
+    const int m = (l + r) >> 1;
+    if (ql < m) u(2 * x, l, m, ql, qr, v, is_w);
+    if (qr > m) u(2 * x + 1, m, r, ql, qr, v, is_w);
+    nodes_[x].w = std::max(nodes_[2 * x].w, nodes_[2 * x + 1].w);
+    nodes_[x].r = std::max(nodes_[2 * x].r, nodes_[2 * x + 1].r);
+  }
+};
+
+std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry,
+                             const uint8_t *modes = nullptr);
+
+// --------------------------------------------------------------- context
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  uint64_t cap = 0;
+  cg_status ensure(uint64_t n) {
+    if (n <= cap) return CG_OK;
+    uint64_t c = std::max<uint64_t>(n, cap * 2);
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(1, c) * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(CG_E_NOMEM, std::string("device buffer: ") + cudaGetErrorString(e));
+    }
+    cap = c;
+    return CG_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+template <typename T>
+struct PinBuf {
+  T *p = nullptr;
+  uint64_t cap = 0;
+  cg_status ensure(uint64_t n) {
+    if (n <= cap) return CG_OK;
+    uint64_t c = std::max<uint64_t>(n, cap * 2);
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMallocHost(&p, std::max<uint64_t>(1, c) * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(CG_E_NOMEM, std::string("pinned buffer: ") + cudaGetErrorString(e));
+    }
+    cap = c;
+    return CG_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+struct ServeEngine;
+
+}  // namespace cgi
+
+struct cg_ctx {
+  cg_config cfg{};
+  int device = 0;
+  int sm_count = 1;
+  cgi::Image img{nullptr, nullptr, 0};
+  bool img_bound = false;
+  cgi::ShadowArena arena;
+  cgi::AllocTable table;
+  cgi::SingleScratch *d_scratch = nullptr;
+  cg_report *h_result = nullptr;  // mapped pinned
+  cg_report *d_result = nullptr;
+  cgi::DevBuf<uint8_t> stage;
+  std::vector<uint64_t> fill_ptr, fill_size;
+  cgi::DevBuf<uint64_t> d_fill;
+  cgi::PinBuf<uint64_t> h_fill;
+  cgi::DevBuf<uint64_t> t_base, t_size, t_shadow;
+  uint64_t t_version = ~0ull;
+  uint64_t t_count = 0;
+  // batch buffers
+  cgi::DevBuf<cg_copy> b_reqs;
+  cgi::DevBuf<uint32_t> b_order;
+  cgi::DevBuf<uint64_t> b_segfirst, b_stage;
+  cgi::DevBuf<cgi::ScanJob> b_jobs;
+  cgi::DevBuf<cgi::RangeInfo> b_info;
+  cgi::DevBuf<cgi::Acc> b_acc;
+  cgi::DevBuf<cg_report> b_reps;
+  cgi::DevBuf<uint32_t> b_counts;
+  cgi::DevBuf<uint64_t> b_blocksums;
+  cgi::DevBuf<cg_err_record> b_recs;
+  cgi::DevBuf<unsigned int> b_err;
+  cgi::DevBuf<uint8_t> b_modes;
+  cgi::PinBuf<uint8_t> h_modes;
+  cgi::PinBuf<uint8_t> h_stage_in;  // pinned upload staging
+  cgi::PinBuf<cg_report> h_reps;
+  cgi::PinBuf<cg_err_record> h_recs;
+  cgi::PinBuf<uint64_t> h_total;
+  cg_stats stats{};
+  std::mutex stats_mu;                // guards stats while serving
+  cgi::ServeEngine *serve = nullptr;  // non-null while serving
+};
+
+namespace cgi {
+
+cg_status flush_fills(cg_ctx *c, cudaStream_t st);
+cg_status ensure_device_table(cg_ctx *c, cudaStream_t st);
+cg_status validate(const cg_ctx *c, const cg_copy &q);
+bool host_side(const cg_ctx *c, uint64_t p, uint64_t n, uint64_t *found, uint64_t *abase,
+               uint64_t *asize, uint64_t *shadow, uint32_t *flags, uint32_t f_unalloc,
+               uint32_t f_overrun);
+void count_stats(cg_ctx *c, const cg_report &r);
+
+}  // namespace cgi

@@ -1,17 +1,8 @@
-// cg_host.cpp -- host runtime of libcg: the allocation table, the device V
-// shadow pool, the batch planner and the C ABI entry points of cg.h.
+// cg_host.cpp -- host runtime of libcg: the C ABI entry points of cg.h
+// (the structures they use are in cg_ctx.h).
 #include <cuda_runtime.h>
 
-#include <algorithm>
-#include <chrono>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <set>
-#include <string>
-#include <vector>
-
-#include "cg_internal.h"
+#include "cg_ctx.h"
 
 using namespace cgi;
 
@@ -19,365 +10,16 @@ using namespace cgi;
 
 static thread_local std::string g_last_error;
 
-static cg_status set_error(cg_status st, const std::string &msg) {
+cg_status cgi::set_error(cg_status st, const std::string &msg) {
   g_last_error = msg;
   return st;
 }
 
 void cgi::set_error_text(const char *msg) { g_last_error = msg; }
 
-static cg_status cuda_fail(cudaError_t e, const char *what) {
+cg_status cgi::cuda_fail(cudaError_t e, const char *what) {
   return set_error(CG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
-
-#define CG_CUDA(call)                                 \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-  } while (0)
-
-#define CG_TRY(call)                \
-  do {                              \
-    cg_status s_ = (call);          \
-    if (s_ != CG_OK) return s_;     \
-  } while (0)
-
-static inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
-
-static inline uint64_t now_ns() {
-  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
-             std::chrono::steady_clock::now().time_since_epoch())
-      .count();
-}
-
-// -------------------------------------------------- device shadow pool
-
-// Device V shadow of every live allocation (R6: all 0xFF on registration).
-// Slabs of device memory are carved best-fit in 256-byte units; free space
-// is kept at 0xFF, so a new allocation's shadow needs no initialisation.
-// Released ranges are refilled with 0xFF (queued, flushed on the next
-// stream operation of the context).
-class ShadowArena {
- public:
-  uint64_t slab_bytes = 1ull << 30;
-  uint64_t budget = 0;
-  uint64_t held = 0;
-
-  ~ShadowArena() { release_all(); }
-
-  void release_all() {
-    for (auto &s : slabs_)
-      if (s.base) cudaFree(s.base);
-    slabs_.clear();
-    by_size_.clear();
-    free_by_off_.clear();
-    slab_index_.clear();
-    held = 0;
-  }
-
-  cg_status alloc(uint64_t size, uint64_t *out) {
-    const uint64_t sz = round_up(size, 256);
-    if (sz > slab_bytes / 2) {  // its own slab
-      if (budget && held + sz > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
-      uint8_t *p = nullptr;
-      cudaError_t e = cudaMalloc(&p, sz);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
-      }
-      e = cudaMemset(p, 0xFF, sz);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
-      add_slab(p, sz, true);
-      held += sz;
-      *out = reinterpret_cast<uint64_t>(p);
-      return CG_OK;
-    }
-    auto it = by_size_.lower_bound(sz);
-    if (it == by_size_.end()) {
-      if (budget && held + slab_bytes > budget) return set_error(CG_E_NOMEM, "shadow budget exceeded");
-      uint8_t *p = nullptr;
-      cudaError_t e = cudaMalloc(&p, slab_bytes);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return set_error(CG_E_NOMEM, std::string("shadow slab: ") + cudaGetErrorString(e));
-      }
-      e = cudaMemset(p, 0xFF, slab_bytes);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(shadow)");
-      const uint32_t si = add_slab(p, slab_bytes, false);
-      held += slab_bytes;
-      insert_free(si, 0, slab_bytes);
-      it = by_size_.lower_bound(sz);
-    }
-    const uint64_t bsize = it->first;
-    const uint32_t si = it->second.first;
-    const uint64_t off = it->second.second;
-    by_size_.erase(it);
-    free_by_off_[si].erase(off);
-    if (bsize > sz) insert_free(si, off + sz, bsize - sz);
-    *out = reinterpret_cast<uint64_t>(slabs_[si].base) + off;
-    return CG_OK;
-  }
-
-  // The caller queues the 0xFF refill of [ptr, ptr+size) before reuse.
-  void release(uint64_t ptr, uint64_t size) {
-    const uint64_t sz = round_up(size, 256);
-    auto it = slab_index_.upper_bound(ptr);
-    --it;
-    const uint32_t si = it->second;
-    Slab &s = slabs_[si];
-    if (s.dedicated) {
-      cudaFree(s.base);  // synchronises the device; dedicated slabs are rare
-      held -= s.size;
-      slab_index_.erase(it);
-      s.base = nullptr;
-      s.size = 0;
-      return;
-    }
-    uint64_t off = ptr - reinterpret_cast<uint64_t>(s.base);
-    uint64_t len = sz;
-    auto &fm = free_by_off_[si];
-    auto nx = fm.lower_bound(off);
-    if (nx != fm.end() && nx->first == off + len) {  // merge with the next block
-      len += nx->second;
-      erase_free(si, nx->first, nx->second);
-      nx = fm.lower_bound(off);
-    }
-    if (nx != fm.begin()) {  // merge with the previous block
-      auto pv = std::prev(nx);
-      if (pv->first + pv->second == off) {
-        off = pv->first;
-        len += pv->second;
-        erase_free(si, pv->first, pv->second);
-      }
-    }
-    insert_free(si, off, len);
-  }
-
- private:
-  struct Slab {
-    uint8_t *base;
-    uint64_t size;
-    bool dedicated;
-  };
-  std::vector<Slab> slabs_;
-  std::multimap<uint64_t, std::pair<uint32_t, uint64_t>> by_size_;  // size -> (slab, off)
-  std::vector<std::map<uint64_t, uint64_t>> free_by_off_;           // per slab: off -> size
-  std::map<uint64_t, uint32_t> slab_index_;                         // base -> slab
-
-  uint32_t add_slab(uint8_t *p, uint64_t size, bool dedicated) {
-    slabs_.push_back({p, size, dedicated});
-    free_by_off_.emplace_back();
-    const uint32_t si = (uint32_t)(slabs_.size() - 1);
-    slab_index_[reinterpret_cast<uint64_t>(p)] = si;
-    return si;
-  }
-  void insert_free(uint32_t si, uint64_t off, uint64_t len) {
-    free_by_off_[si][off] = len;
-    by_size_.insert({len, {si, off}});
-  }
-  void erase_free(uint32_t si, uint64_t off, uint64_t len) {
-    free_by_off_[si].erase(off);
-    auto r = by_size_.equal_range(len);
-    for (auto it = r.first; it != r.second; ++it)
-      if (it->second.first == si && it->second.second == off) {
-        by_size_.erase(it);
-        break;
-      }
-  }
-};
-
-// ---------------------------------------------------- allocation table
-
-// The list of live device allocations (Fig. 2 caption) as a sorted main
-// array (size 0 = tombstone of a freed entry) plus an ordered delta of
-// recent registrations, merged into the main array in bulk.
-class AllocTable {
- public:
-  std::vector<uint64_t> base, size, shadow;  // main, sorted by base
-  std::map<uint64_t, std::pair<uint64_t, uint64_t>> delta;  // base -> (size, shadow)
-  std::set<uint64_t> freed;
-  uint64_t dead = 0;
-  uint64_t live = 0;
-  uint64_t version = 0;
-
-  struct Hit {
-    bool ok;
-    uint64_t base, size, shadow;
-  };
-
-  Hit find(uint64_t addr) const {
-    auto ub = std::upper_bound(base.begin(), base.end(), addr);
-    if (ub != base.begin()) {
-      const size_t j = (size_t)(ub - base.begin()) - 1;
-      if (size[j] && addr - base[j] < size[j]) return {true, base[j], size[j], shadow[j]};
-    }
-    auto it = delta.upper_bound(addr);
-    if (it != delta.begin()) {
-      --it;
-      if (addr - it->first < it->second.first)
-        return {true, it->first, it->second.first, it->second.second};
-    }
-    return {false, 0, 0, 0};
-  }
-
-  bool overlaps(uint64_t b, uint64_t s) const {  // [b, b+s), no wrap
-    auto ub = std::upper_bound(base.begin(), base.end(), b);
-    if (ub != base.begin()) {
-      const size_t j = (size_t)(ub - base.begin()) - 1;
-      if (size[j] && b - base[j] < size[j]) return true;
-    }
-    for (auto k = ub; k != base.end() && *k < b + s; ++k)
-      if (size[(size_t)(k - base.begin())]) return true;
-    auto it = delta.upper_bound(b);
-    if (it != delta.end() && it->first < b + s) return true;
-    if (it != delta.begin()) {
-      --it;
-      if (b - it->first < it->second.first) return true;
-    }
-    return false;
-  }
-
-  void insert(uint64_t b, uint64_t s, uint64_t sh) {
-    delta[b] = {s, sh};
-    live++;
-    version++;
-    freed.erase(freed.lower_bound(b), freed.lower_bound(b + s));  // R13
-    if (delta.size() > std::max<uint64_t>(4096, base.size() / 8)) merge();
-  }
-
-  // Remove the live allocation whose base is exactly b.
-  bool remove_base(uint64_t b, uint64_t *sz, uint64_t *sh) {
-    auto lb = std::lower_bound(base.begin(), base.end(), b);
-    if (lb != base.end() && *lb == b) {
-      const size_t j = (size_t)(lb - base.begin());
-      if (size[j]) {
-        *sz = size[j];
-        *sh = shadow[j];
-        size[j] = 0;
-        dead++;
-        goto removed;
-      }
-    }
-    {
-      auto it = delta.find(b);
-      if (it == delta.end()) return false;
-      *sz = it->second.first;
-      *sh = it->second.second;
-      delta.erase(it);
-    }
-  removed:
-    live--;
-    version++;
-    freed.insert(b);
-    if (dead > 1024 && dead > base.size() / 4) merge();
-    return true;
-  }
-
-  void merge() {
-    if (delta.empty() && dead == 0) return;
-    std::vector<uint64_t> nb, ns, nh;
-    nb.reserve(live);
-    ns.reserve(live);
-    nh.reserve(live);
-    auto it = delta.begin();
-    for (size_t j = 0; j <= base.size(); j++) {
-      const uint64_t limit = j < base.size() ? base[j] : ~0ull;
-      while (it != delta.end() && (j == base.size() || it->first < limit)) {
-        nb.push_back(it->first);
-        ns.push_back(it->second.first);
-        nh.push_back(it->second.second);
-        ++it;
-      }
-      if (j < base.size() && size[j]) {
-        nb.push_back(base[j]);
-        ns.push_back(size[j]);
-        nh.push_back(shadow[j]);
-      }
-    }
-    base.swap(nb);
-    size.swap(ns);
-    shadow.swap(nh);
-    delta.clear();
-    dead = 0;
-  }
-};
-
-// ---------------------------------------------------- batch planner
-
-// Range-chmax / range-max segment tree over the elementary intervals of one
-// address space, holding two values per leaf: the highest level of a copy
-// that wrote it (w) and of one that read it (r).
-class LevelTree {
- public:
-  void init(int n) {
-    n_ = std::max(1, n);
-    size_t m = 1;
-    while (m < (size_t)n_) m <<= 1;
-    nodes_.assign(2 * m, Node{-1, -1, -1, -1});
-  }
-  // max of w (and of r when want_r) over leaves [l, r)
-  int query(int l, int r, bool want_r) const {
-    if (l >= r) return -1;
-    return q(1, 0, n_, l, r, want_r);
-  }
-  void update_w(int l, int r, int v) {
-    if (l < r) u(1, 0, n_, l, r, v, true);
-  }
-  void update_r(int l, int r, int v) {
-    if (l < r) u(1, 0, n_, l, r, v, false);
-  }
-
- private:
-  struct Node {
-    int w, r, tw, tr;  // subtree maxima and pending chmax for the children
-  };
-  int n_ = 1;
-  mutable std::vector<Node> nodes_;
-  void push(int x) const {
-    Node &p = nodes_[x];
-    if (p.tw < 0 && p.tr < 0) return;
-    for (int c = 2 * x; c <= 2 * x + 1; c++) {
-      Node &k = nodes_[c];
-      if (p.tw >= 0) {
-        k.w = std::max(k.w, p.tw);
-        k.tw = std::max(k.tw, p.tw);
-      }
-      if (p.tr >= 0) {
-        k.r = std::max(k.r, p.tr);
-        k.tr = std::max(k.tr, p.tr);
-      }
-    }
-    p.tw = p.tr = -1;
-  }
-  int q(int x, int l, int r, int ql, int qr, bool want_r) const {
-    if (ql <= l && r <= qr) return want_r ? std::max(nodes_[x].w, nodes_[x].r) : nodes_[x].w;
-    push(x);
-    const int m = (l + r) >> 1;
-    int v = -1;
-    if (ql < m) v = q(2 * x, l, m, ql, qr, want_r);
-    if (qr > m) v = std::max(v, q(2 * x + 1, m, r, ql, qr, want_r));
-    return v;
-  }
-  void u(int x, int l, int r, int ql, int qr, int v, bool is_w) {
-    Node &nd = nodes_[x];
-    if (ql <= l && r <= qr) {
-      if (is_w) {
-        nd.w = std::max(nd.w, v);
-        nd.tw = std::max(nd.tw, v);
-      } else {
-        nd.r = std::max(nd.r, v);
-        nd.tr = std::max(nd.tr, v);
-      }
-      return;
-    }
-    push(x);
-    const int m = (l + r) >> 1;
-    if (ql < m) u(2 * x, l, m, ql, qr, v, is_w);
-    if (qr > m) u(2 * x + 1, m, r, ql, qr, v, is_w);
-    nodes_[x].w = std::max(nodes_[2 * x].w, nodes_[2 * x + 1].w);
-    nodes_[x].r = std::max(nodes_[2 * x].r, nodes_[2 * x + 1].r);
-  }
-};
 
 // Dependency levels for sequential semantics (R15): a copy's level is one
 // more than the highest level of any earlier copy it conflicts with (it
@@ -387,8 +29,8 @@ class LevelTree {
 // if that source is valid; without, every copy is taken to read its source
 // and write its destination.  Levels run in order; copies within a level
 // touch disjoint shadow.
-static std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry,
-                                    const uint8_t *modes = nullptr) {
+std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry,
+                                  const uint8_t *modes) {
   std::vector<int> lvl(nreq, 0);
   if (!carry || nreq < 2) return lvl;
   auto end_of = [](uint64_t a, uint64_t n) { return a + n < a ? ~0ull : a + n; };
@@ -469,99 +111,8 @@ static std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool car
   return lvl;
 }
 
-// --------------------------------------------------------------- context
-
-template <typename T>
-struct DevBuf {
-  T *p = nullptr;
-  uint64_t cap = 0;
-  cg_status ensure(uint64_t n) {
-    if (n <= cap) return CG_OK;
-    uint64_t c = std::max<uint64_t>(n, cap * 2);
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    cudaError_t e = cudaMalloc(&p, std::max<uint64_t>(1, c) * sizeof(T));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(CG_E_NOMEM, std::string("device buffer: ") + cudaGetErrorString(e));
-    }
-    cap = c;
-    return CG_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
-
-template <typename T>
-struct PinBuf {
-  T *p = nullptr;
-  uint64_t cap = 0;
-  cg_status ensure(uint64_t n) {
-    if (n <= cap) return CG_OK;
-    uint64_t c = std::max<uint64_t>(n, cap * 2);
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-    cudaError_t e = cudaMallocHost(&p, std::max<uint64_t>(1, c) * sizeof(T));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return set_error(CG_E_NOMEM, std::string("pinned buffer: ") + cudaGetErrorString(e));
-    }
-    cap = c;
-    return CG_OK;
-  }
-  void release() {
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
-
-struct cg_ctx {
-  cg_config cfg{};
-  int device = 0;
-  int sm_count = 1;
-  Image img{nullptr, nullptr, 0};
-  bool img_bound = false;
-  ShadowArena arena;
-  AllocTable table;
-  SingleScratch *d_scratch = nullptr;
-  cg_report *h_result = nullptr;  // mapped pinned
-  cg_report *d_result = nullptr;
-  DevBuf<uint8_t> stage;
-  std::vector<uint64_t> fill_ptr, fill_size;
-  DevBuf<uint64_t> d_fill;
-  PinBuf<uint64_t> h_fill;
-  DevBuf<uint64_t> t_base, t_size, t_shadow;
-  uint64_t t_version = ~0ull;
-  uint64_t t_count = 0;
-  // batch buffers
-  DevBuf<cg_copy> b_reqs;
-  DevBuf<uint32_t> b_order;
-  DevBuf<uint64_t> b_segfirst, b_stage;
-  DevBuf<ScanJob> b_jobs;
-  DevBuf<RangeInfo> b_info;
-  DevBuf<Acc> b_acc;
-  DevBuf<cg_report> b_reps;
-  DevBuf<uint32_t> b_counts;
-  DevBuf<uint64_t> b_blocksums;
-  DevBuf<cg_err_record> b_recs;
-  DevBuf<unsigned int> b_err;
-  DevBuf<uint8_t> b_modes;
-  PinBuf<uint8_t> h_modes;
-  PinBuf<uint8_t> h_stage_in;  // pinned upload staging
-  PinBuf<cg_report> h_reps;
-  PinBuf<cg_err_record> h_recs;
-  PinBuf<uint64_t> h_total;
-  cg_stats stats{};
-};
-
 // Queue 0xFF refills of released shadow ranges on `st`.
-static cg_status flush_fills(cg_ctx *c, cudaStream_t st) {
+cg_status cgi::flush_fills(cg_ctx *c, cudaStream_t st) {
   const uint64_t n = c->fill_ptr.size();
   if (n == 0) return CG_OK;
   if (n <= 8) {
@@ -587,7 +138,7 @@ static cg_status flush_fills(cg_ctx *c, cudaStream_t st) {
   return CG_OK;
 }
 
-static cg_status ensure_device_table(cg_ctx *c, cudaStream_t st) {
+cg_status cgi::ensure_device_table(cg_ctx *c, cudaStream_t st) {
   AllocTable &t = c->table;
   if (!t.delta.empty() || t.dead) t.merge();
   if (c->t_version == t.version && c->t_count == t.base.size()) return CG_OK;
@@ -606,7 +157,7 @@ static cg_status ensure_device_table(cg_ctx *c, cudaStream_t st) {
   return CG_OK;
 }
 
-static cg_status validate(const cg_ctx *c, const cg_copy &q) {
+cg_status cgi::validate(const cg_ctx *c, const cg_copy &q) {
   if (q.kind != CG_HTOD && q.kind != CG_DTOH && q.kind != CG_DTOD)
     return set_error(CG_E_KIND, "copy kind must be CG_HTOD, CG_DTOH or CG_DTOD");
   if (q.reserved != 0) return set_error(CG_E_ARG, "cg_copy.reserved must be 0");
@@ -620,7 +171,7 @@ static cg_status validate(const cg_ctx *c, const cg_copy &q) {
 }
 
 // Host-mirror lookup of one device side (Sec. 2 itemize; R7, R8).
-static bool host_side(const cg_ctx *c, uint64_t p, uint64_t n, uint64_t *found, uint64_t *abase,
+bool cgi::host_side(const cg_ctx *c, uint64_t p, uint64_t n, uint64_t *found, uint64_t *abase,
                       uint64_t *asize, uint64_t *shadow, uint32_t *flags, uint32_t f_unalloc,
                       uint32_t f_overrun) {
   const AllocTable::Hit h = c->table.find(p);
@@ -641,6 +192,13 @@ static bool host_side(const cg_ctx *c, uint64_t p, uint64_t n, uint64_t *found, 
 }
 
 // --------------------------------------------------------------- C ABI
+
+void cgi::count_stats(cg_ctx *c, const cg_report &r) {
+  c->stats.checks++;
+  c->stats.bytes_checked += r.expected;
+  for (int b = 0; b < CG_NFLAGS; b++)
+    if (r.flags & (1u << b)) c->stats.errors[b]++;
+}
 
 extern "C" {
 
@@ -686,6 +244,7 @@ cg_status cg_create(cg_ctx **out, const cg_config *cfg) {
 
 cg_status cg_destroy(cg_ctx *c) {
   if (!c) return CG_OK;
+  if (c->serve) cg_serve_stop(c, nullptr);
   cudaDeviceSynchronize();
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->h_result) cudaFreeHost(c->h_result);
@@ -720,6 +279,7 @@ cg_status cg_destroy(cg_ctx *c) {
 
 cg_status cg_bind_host_shadow(cg_ctx *c, const uint8_t *a_bits_dev, uint8_t *v_dev,
                               uint64_t n_bytes) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c) return set_error(CG_E_ARG, "ctx is NULL");
   if (n_bytes && (!a_bits_dev || !v_dev)) return set_error(CG_E_ARG, "image pointer is NULL");
   if ((reinterpret_cast<uintptr_t>(a_bits_dev) & 15) || (reinterpret_cast<uintptr_t>(v_dev) & 15))
@@ -734,6 +294,7 @@ cg_status cg_bind_host_shadow(cg_ctx *c, const uint8_t *a_bits_dev, uint8_t *v_d
 
 cg_status cg_upload_host_shadow(cg_ctx *c, const uint8_t *a_bits_host, const uint8_t *v_host,
                                 uint64_t off, uint64_t n, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || !a_bits_host || !v_host) return set_error(CG_E_ARG, "NULL argument");
   if (!c->img_bound) return set_error(CG_E_NO_HOST, "no host shadow image bound");
   if ((off | n) & 7) return set_error(CG_E_ALIGN, "off and n must be multiples of 8");
@@ -747,6 +308,7 @@ cg_status cg_upload_host_shadow(cg_ctx *c, const uint8_t *a_bits_host, const uin
 }
 
 cg_status cg_register_alloc(cg_ctx *c, uint64_t dptr, uint64_t size) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c) return set_error(CG_E_ARG, "ctx is NULL");
   if (size == 0) return set_error(CG_E_ZERO_SIZE, "zero-size allocation");
   if (dptr + size < dptr) return set_error(CG_E_WRAP, "allocation wraps 2^64");
@@ -760,6 +322,7 @@ cg_status cg_register_alloc(cg_ctx *c, uint64_t dptr, uint64_t size) {
 
 cg_status cg_register_allocs(cg_ctx *c, const uint64_t *dptr, const uint64_t *size,
                              uint64_t count, cg_status *st_out) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || (count && (!dptr || !size))) return set_error(CG_E_ARG, "NULL argument");
   cg_status first = CG_OK;
   for (uint64_t i = 0; i < count; i++) {
@@ -771,6 +334,7 @@ cg_status cg_register_allocs(cg_ctx *c, const uint64_t *dptr, const uint64_t *si
 }
 
 cg_status cg_free(cg_ctx *c, uint64_t dptr, uint32_t *verdict) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || !verdict) return set_error(CG_E_ARG, "NULL argument");
   uint64_t sz = 0, sh = 0;
   if (c->table.remove_base(dptr, &sz, &sh)) {
@@ -790,6 +354,7 @@ cg_status cg_free(cg_ctx *c, uint64_t dptr, uint32_t *verdict) {
 }
 
 static cg_status mark(cg_ctx *c, uint64_t dptr, uint64_t n, int value, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c) return set_error(CG_E_ARG, "ctx is NULL");
   if (n == 0) return CG_OK;
   const AllocTable::Hit h = c->table.find(dptr);
@@ -810,6 +375,7 @@ cg_status cg_mark_undefined(cg_ctx *c, uint64_t dptr, uint64_t n, void *stream) 
 }
 
 cg_status cg_read_device_shadow(cg_ctx *c, uint64_t dptr, uint64_t n, uint8_t *out) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || (n && !out)) return set_error(CG_E_ARG, "NULL argument");
   if (n == 0) return CG_OK;
   const AllocTable::Hit h = c->table.find(dptr);
@@ -833,12 +399,6 @@ static int single_grid(const cg_ctx *c, const ScanJob &job) {
   return (int)g;
 }
 
-static void count_stats(cg_ctx *c, const cg_report &r) {
-  c->stats.checks++;
-  c->stats.bytes_checked += r.expected;
-  for (int b = 0; b < CG_NFLAGS; b++)
-    if (r.flags & (1u << b)) c->stats.errors[b]++;
-}
 
 // Host part of one check: validation (a1), the device-range lookup on the
 // host mirror (a2) and the scan job.  *trivial is set when no byte needs
@@ -909,6 +469,7 @@ static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, boo
 }
 
 cg_status cg_check_copy(cg_ctx *c, const cg_copy *req, cg_report *rep, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || !req || !rep) return set_error(CG_E_ARG, "NULL argument");
   RangeInfo ri;
   ScanJob job;
@@ -934,6 +495,7 @@ cg_status cg_check_copy(cg_ctx *c, const cg_copy *req, cg_report *rep, void *str
 }
 
 cg_status cg_check_copy_async(cg_ctx *c, const cg_copy *req, cg_report *rep_dev, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || !req || !rep_dev) return set_error(CG_E_ARG, "NULL argument");
   RangeInfo ri;
   ScanJob job;
@@ -950,6 +512,7 @@ cg_status cg_check_copy_async(cg_ctx *c, const cg_copy *req, cg_report *rep_dev,
 cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_report *reps,
                          cg_err_record *recs, uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
     return set_error(CG_E_ARG, "NULL argument");
   for (uint64_t i = 0; i < nreq; i++) {
@@ -1158,6 +721,7 @@ cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, con
 
 cg_status cg_get_stats(const cg_ctx *c, cg_stats *out) {
   if (!c || !out) return set_error(CG_E_ARG, "NULL argument");
+  std::lock_guard<std::mutex> g(const_cast<cg_ctx *>(c)->stats_mu);
   *out = c->stats;
   out->live_allocs = c->table.live;
   out->shadow_bytes = c->arena.held;
