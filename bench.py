@@ -95,6 +95,27 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_max(value: float, device=None) -> float:
+    """The largest of `value` over all ranks (the job's time is its slowest
+    rank's); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(bytes_per_rank: int, elapsed_ms_per_rank: float, device=None) -> tuple[float, float]:
+    """Whole-job throughput (GB/s) from every rank's own work and time:
+    all ranks' bytes over the slowest rank's time."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = reduce_max(elapsed_ms_per_rank, device)
+    return bytes_per_rank * world / (ms / 1e3) / GB, ms
+
+
 def build_workload(sizes):
     w = S.large(0, sizes=sizes)
     return w
@@ -172,12 +193,7 @@ def run_cg(args, world, rank, local):
     # per-kernel durations (the scan kernel is the only launch per check)
     kern_ms = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(len(reqs))]
                         for k in range(args.steps)])
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_bytes = bytes_per_step * args.steps * world
-    value = total_bytes / (elapsed_ms / 1e3) / GB
+    value, elapsed_ms = aggregate(bytes_per_step * args.steps, elapsed_ms, dev)
 
     # roofline of the dominant kernel: the largest transfer's scan+carry
     big = int(np.argmax([int(q["n"]) for q in w.reqs]))
@@ -205,10 +221,8 @@ def run_cg(args, world, rank, local):
         e2e_ms = (time.perf_counter() - s0) * 1e3
         h2d = int(sum(int(q["n"]) + int(q["n"]) // 8 for q in w.reqs))
         d2h = 112 * len(reqs)
-    if world > 1:
-        t = torch.tensor([e2e_ms or 0.0], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    if e2e_ms is not None:
+        e2e_ms = reduce_max(e2e_ms, dev)
 
     out = {
         "metric": "shadow GB/s checked vs HBM peak (single large host->device transfer checks)",
@@ -386,6 +400,19 @@ def run_serving(args):
     }
 
 
+def _summary(key: str, d: dict) -> dict:
+    if key == "batched":
+        return {"workload": d["config"]["workload"], "checks_per_s": d["value"],
+                "gb_per_s": d["batched_gb_per_s"],
+                "one_launch_per_copy_checks_per_s": d["one_launch_per_copy"]["checks_per_s"],
+                "speedup_vs_one_launch_per_copy": d["speedup_vs_one_launch_per_copy"],
+                "levels_per_batch": d["config"]["levels_per_batch"],
+                "ms_per_batch": d["ms_per_step"], "breakdown_ms": d["batch_breakdown_ms"]}
+    return {"workload": d["config"]["workload"], "checks_per_s": d["value"],
+            "latency_us": d["latency_us"], "offered_rate_per_s": d["config"]["offered_rate_per_s"],
+            "all_ok": d["all_ok"], "rounds": d["serve_stats"]["rounds"]}
+
+
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -490,6 +517,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=S.SERVE_RATE)
     ap.add_argument("--serve-image-gib", type=int, default=32)
     ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--extras", type=int, default=1,
+                    help="1: add the batched and serving figures to the default line")
     ap.add_argument("--segment-kib", type=int, default=0)
     ap.add_argument("--single-sample", type=int, default=100_000)
     args = ap.parse_args()
@@ -517,6 +546,19 @@ def main():
             val, sample = cpu_sample(w, args.cpu_budget_s)
             out["cpu_baseline"] = {"value": round(val, 4), "unit": "GB/s", "cores": 1,
                                    "kind": "oracle", "sample": sample}
+        if world == 1 and args.extras:
+            # the metric's other two parts, on their own workloads (batched
+            # checks/s against one launch per copy; serving latency)
+            import torch
+            del w
+            torch.cuda.empty_cache()
+            for key, fn in (("batched", lambda: run_batched_workload(args, "batched")),
+                            ("serving", lambda: run_serving(args))):
+                try:
+                    out[key] = _summary(key, fn())
+                except Exception as exc:  # reported, never hides the headline
+                    out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+                torch.cuda.empty_cache()
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch
