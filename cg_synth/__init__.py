@@ -404,3 +404,14 @@ def serving_image_runs(seed: int, host_n: int, undef_frac: float = 1e-5, mean_ru
     lengths = np.minimum(rng.geometric(1.0 / mean_run, k), 64).astype(np.int64)
     values = rng.integers(1, 256, k).astype(np.uint8)
     return starts, lengths, values
+
+
+def tuning_batch(rng, table: AllocTable, host_n: int) -> np.ndarray:
+    """A batch of random shape for fitting the split cost model: count
+    500-8000, sizes log-uniform in [lo, hi] with lo 16 B-64 KiB and hi up to
+    16 MiB, a random kind mix."""
+    count = int(np.exp(rng.uniform(np.log(500), np.log(8000))))
+    lo = int(2 ** rng.uniform(4, 16))
+    hi = int(min(16 << 20, lo * 2 ** rng.uniform(2, 14)))
+    mix = rng.dirichlet([2.0, 1.0, 0.5])
+    return requests(rng, count, table, host_n, lo, max(lo, hi), mix=tuple(mix), p_wild=0.01)

@@ -156,7 +156,7 @@ typedef struct cg_config {
   uint32_t scan_ctas_per_sm;    /* single-check grid; 0 = automatic */
   uint32_t batch_segment_kib;   /* batched work split, rounded up to whole
                                    engine steps (4 KiB TMA, 2 KiB registers);
-                                   0 = 64 */
+                                   0 = chosen per batch (cg_choose_segment) */
   uint32_t batch_ctas_per_sm;   /* batched grid; 0 = automatic */
   uint32_t scan_engine;         /* scan loads, single and batched checks:
                                    0 auto (= 2), 1 registers, 2 TMA bulk copies */
@@ -270,6 +270,63 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                          cg_report *reps, cg_err_record *recs,
                          uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream);
+
+/* ------------------------------------------------ choosing the batch split */
+
+/* How cg_check_batch cuts copies into segments matters (too small: per-
+ * segment overhead; too large: idle warps at the end of each level), and
+ * the best size depends on the batch.  With batch_segment_kib = 0 the
+ * context picks it per batch: the size cg_tune_batch measured best for a
+ * batch with close features, else the argmin of a learned cost model over
+ * the candidates 4, 8, ..., 1024 KiB, else 64 KiB. */
+
+#define CG_NFEAT 13
+
+/* Features of a batch (host only): [0] log2(1+count), [1] mean and [2]
+ * standard deviation of log2(1+n), [3..8] fraction of all bytes in copies
+ * of at most 4 KiB, 64 KiB, 1 MiB, 4 MiB, 16 MiB, and above, [9..11]
+ * fraction of HtoD, DtoH, DtoD copies, [12] log2(1+total bytes). */
+cg_status cg_batch_features(const cg_copy *reqs, uint64_t nreq, float *feat);
+
+/* Autotuner: time the batch's level kernels for each candidate segment
+ * size (seg_kib[0..ncand), or the default candidates when seg_kib is NULL,
+ * then ms gets ncand or 9 entries) `repeats` times each and keep the
+ * fastest.  With flags & CG_TUNE_REMEMBER the best size is remembered for
+ * batches with these features.  Trial runs are dry (the carry is masked
+ * off: no shadow changes), so tuning may run on the live context.
+ * Synchronous. */
+#define CG_TUNE_REMEMBER 1u
+cg_status cg_tune_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq, const uint32_t *seg_kib,
+                        uint32_t ncand, uint32_t repeats, uint32_t flags, float *ms,
+                        uint32_t *best_kib, void *stream);
+
+/* Install a learned cost model (NULL or hidden = 0 removes it): a
+ * one-hidden-layer ReLU network predicting log2(batch milliseconds) from
+ * x = (features, log2(segment KiB)), D = CG_NFEAT + 1 inputs.  weights (host,
+ * copied): mu[D], sigma[D] (inputs are standardised (x - mu) / sigma),
+ * W1[D][hidden] row-major, b1[hidden], w2[hidden], b2. */
+cg_status cg_set_cost_model(cg_ctx *ctx, const float *weights, uint32_t hidden);
+
+/* Fit the cost model on the GPU (this library's own forward and backward
+ * kernels, full-batch Adam, mean squared error): x[n][D] raw inputs and
+ * t[n] targets (log2 ms), host.  hidden: a multiple of 32, at most 1024.
+ * weights (host) receives the cg_set_cost_model layout, including the
+ * standardisation fitted to x; losses (host, may be NULL) gets the loss
+ * before each of the `epochs` steps.  Synchronous. */
+cg_status cg_mlp_fit(const float *x, const float *t, uint32_t n, uint32_t hidden,
+                     uint32_t epochs, float lr, uint64_t seed, float *weights, float *losses,
+                     void *stream);
+
+/* One forward and backward pass on the GPU with the given weights (the
+ * cg_set_cost_model layout): grads (same layout; zero for mu and sigma)
+ * and the mean squared error *loss.  For checking the kernels. */
+cg_status cg_mlp_grad(const float *x, const float *t, uint32_t n, uint32_t hidden,
+                      const float *weights, float *grads, float *loss, void *stream);
+
+/* The segment size cg_check_batch would use for this batch; *source (may be
+ * NULL): 0 default, 1 tuned entry, 2 learned model, 3 fixed by the config. */
+cg_status cg_choose_segment(const cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
+                            uint32_t *seg_kib, uint32_t *source);
 
 /* --------------------------------------------------------------- serving */
 

@@ -127,6 +127,12 @@ SIGNATURES = [
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
+    ("cg_batch_features", i32, [vp, u64, vp]),
+    ("cg_tune_batch", i32, [vp, vp, u64, vp, u32, u32, u32, vp, ctypes.POINTER(u32), vp]),
+    ("cg_set_cost_model", i32, [vp, vp, u32]),
+    ("cg_mlp_fit", i32, [vp, vp, u32, u32, u32, ctypes.c_float, u64, vp, vp, vp]),
+    ("cg_mlp_grad", i32, [vp, vp, u32, u32, vp, vp, ctypes.POINTER(ctypes.c_float), vp]),
+    ("cg_choose_segment", i32, [vp, vp, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
     ("cg_plan_levels", i32, [vp, u64, u32, vp, vp, ctypes.POINTER(u32)]),
     ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
     ("cg_format_report", i32, [ctypes.POINTER(cg_report), u32, ctypes.c_char_p, ctypes.c_size_t]),
@@ -275,6 +281,35 @@ class Context:
         total = int(n_rec.value)
         return st, reps, recs[:min(total, rec_cap)], total, int(bad.value)
 
+    # ------------------------------------------------------- batch split
+    def tune_batch(self, reqs: np.ndarray, candidates=None, repeats: int = 2,
+                   remember: bool = True, stream=None):
+        """Autotune the segment size on this batch (dry runs).  Returns
+        (best KiB, {candidate KiB: ms})."""
+        reqs = np.ascontiguousarray(reqs)
+        cand = CANDIDATES_KIB if candidates is None else list(candidates)
+        ca = np.ascontiguousarray(cand, dtype=np.uint32)
+        ms = np.zeros(len(cand), dtype=np.float32)
+        best = u32(0)
+        check(cg_tune_batch(self._h, reqs.ctypes.data, len(reqs), ca.ctypes.data, len(cand),
+                            repeats, 1 if remember else 0, ms.ctypes.data, ctypes.byref(best),
+                            _stream_handle(stream)), "cg_tune_batch")
+        return int(best.value), {int(k): float(v) for k, v in zip(cand, ms)}
+
+    def set_cost_model(self, weights: np.ndarray | None, hidden: int = 0) -> None:
+        if weights is None:
+            check(cg_set_cost_model(self._h, None, 0))
+            return
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        check(cg_set_cost_model(self._h, w.ctypes.data, hidden), "cg_set_cost_model")
+
+    def choose_segment(self, reqs: np.ndarray) -> tuple[int, int]:
+        reqs = np.ascontiguousarray(reqs)
+        k, src = u32(0), u32(0)
+        check(cg_choose_segment(self._h, reqs.ctypes.data, len(reqs), ctypes.byref(k),
+                                ctypes.byref(src)))
+        return int(k.value), int(src.value)
+
     # ------------------------------------------------------------ serving
     def serve_start(self, **cfg) -> None:
         c = cg_serve_config()
@@ -333,6 +368,46 @@ def plan_levels(reqs: np.ndarray, carry: bool = True,
                          lv.ctypes.data if len(reqs) else None, ctypes.byref(nl)),
           "cg_plan_levels")
     return lv, int(nl.value)
+
+
+CANDIDATES_KIB = [4, 8, 16, 32, 64, 128, 256, 512, 1024]
+NFEAT = 13
+
+
+def batch_features(reqs: np.ndarray) -> np.ndarray:
+    reqs = np.ascontiguousarray(reqs)
+    f = np.zeros(NFEAT, dtype=np.float32)
+    check(cg_batch_features(reqs.ctypes.data if len(reqs) else None, len(reqs), f.ctypes.data))
+    return f
+
+
+def mlp_nweights(hidden: int) -> int:
+    d = NFEAT + 1
+    return 2 * d + d * hidden + 2 * hidden + 1
+
+
+def mlp_fit(x: np.ndarray, t: np.ndarray, hidden: int = 32, epochs: int = 2000,
+            lr: float = 3e-3, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Train the cost model on the GPU; returns (weights, losses)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    assert x.ndim == 2 and x.shape[1] == NFEAT + 1 and len(t) == len(x)
+    w = np.zeros(mlp_nweights(hidden), dtype=np.float32)
+    losses = np.zeros(epochs, dtype=np.float32)
+    check(cg_mlp_fit(x.ctypes.data, t.ctypes.data, len(t), hidden, epochs, lr, seed,
+                     w.ctypes.data, losses.ctypes.data, None), "cg_mlp_fit")
+    return w, losses
+
+
+def mlp_grad(x: np.ndarray, t: np.ndarray, weights: np.ndarray, hidden: int):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    g = np.zeros_like(w)
+    loss = ctypes.c_float(0)
+    check(cg_mlp_grad(x.ctypes.data, t.ctypes.data, len(t), hidden, w.ctypes.data,
+                      g.ctypes.data, ctypes.byref(loss), None), "cg_mlp_grad")
+    return g, float(loss.value)
 
 
 def format_report(rep: dict, kind: int) -> str:

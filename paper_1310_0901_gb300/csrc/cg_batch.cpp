@@ -1,0 +1,429 @@
+// cg_batch.cpp -- batched checks (cg_check_batch), the batch-split
+// autotuner (cg_tune_batch) and the learned split chooser.
+//
+// A batch runs in phases: prepare (uploads, device lookup, level plan),
+// split (cut every copy of every level into segments of the chosen size),
+// levels (one persistent kernel per dependency level), finish (reports and
+// records).  The tuner repeats split + levels per candidate segment size
+// with the carry masked off, so trials leave the shadow untouched.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "cg_ctx.h"
+
+using namespace cgi;
+
+namespace {
+
+struct StageCopy {
+  int level;
+  uint64_t src, dst, n, req;
+};
+
+struct BatchRun {
+  const cg_copy *reqs = nullptr;
+  uint64_t nreq = 0;
+  BatchPlan plan{};
+  std::vector<int> lvl;
+  int nlev = 0;
+  std::vector<uint64_t> lev_start, lev_segs;
+  std::vector<StageCopy> stages;
+  const uint8_t *modes = nullptr;
+  uint32_t *h_order = nullptr;
+  uint64_t *h_segfirst = nullptr;
+  bool tma = true;
+  int grid = 1;
+};
+
+cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStream_t st,
+                        BatchRun &B) {
+  B.reqs = reqs;
+  B.nreq = nreq;
+  CG_TRY(flush_fills(c, st));
+  CG_TRY(ensure_device_table(c, st));
+  CG_TRY(c->b_reqs.ensure(nreq));
+  CG_TRY(c->b_order.ensure(nreq));
+  CG_TRY(c->b_segfirst.ensure(nreq));
+  CG_TRY(c->b_stage.ensure(nreq));
+  CG_TRY(c->b_jobs.ensure(nreq));
+  CG_TRY(c->b_info.ensure(nreq));
+  CG_TRY(c->b_acc.ensure(nreq));
+  CG_TRY(c->b_reps.ensure(nreq));
+  CG_TRY(c->b_counts.ensure(nreq));
+  CG_TRY(c->b_modes.ensure(nreq));
+  CG_TRY(c->b_err.ensure(1));
+  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8) + 64;
+  CG_TRY(c->h_stage_in.ensure(upload_bytes));
+  CG_TRY(c->h_modes.ensure(nreq));
+  cg_copy *h_reqs = reinterpret_cast<cg_copy *>(c->h_stage_in.p);
+  B.h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
+  B.h_segfirst = reinterpret_cast<uint64_t *>(c->h_stage_in.p +
+                                              round_up(nreq * (sizeof(cg_copy) + 4), 8));
+  uint64_t *h_stagep = B.h_segfirst + nreq;
+  std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
+
+  // overlapping device->device copies are staged (R12); their source and
+  // destination are looked up on the host mirror (they are rare)
+  uint64_t stage_total = 0;
+  std::memset(h_stagep, 0, nreq * sizeof(uint64_t));
+  if (c->cfg.carry) {
+    for (uint64_t i = 0; i < nreq; i++) {
+      const cg_copy &q = reqs[i];
+      if (q.kind != CG_DTOD || q.n == 0) continue;
+      const uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
+      if (dist >= q.n) continue;
+      uint64_t f, b, sz, sh, dsh;
+      uint32_t fl = 0;
+      const bool sok = host_side(c, q.src, q.n, &f, &b, &sz, &sh, &fl, 1, 2);
+      const bool dok = host_side(c, q.dst, q.n, &f, &b, &sz, &dsh, &fl, 1, 2);
+      if (!sok || !dok) continue;
+      B.stages.push_back({0, sh, stage_total, q.n, i});
+      h_stagep[i] = stage_total + 1;  // patched to an address below
+      stage_total += round_up(q.n, 256);
+    }
+    if (stage_total) {
+      CG_TRY(c->stage.ensure(stage_total));
+      const uint64_t base = reinterpret_cast<uint64_t>(c->stage.p);
+      for (uint64_t i = 0; i < nreq; i++)
+        if (h_stagep[i]) h_stagep[i] = base + h_stagep[i] - 1;
+      for (auto &sc : B.stages) sc.dst += base;
+    }
+  }
+  CG_CUDA(cudaMemcpyAsync(c->b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(c->b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, st));
+  BatchPlan &plan = B.plan;
+  plan.reqs = c->b_reqs.p;
+  plan.order = c->b_order.p;
+  plan.seg_first = c->b_segfirst.p;
+  plan.stage = c->b_stage.p;
+  plan.jobs = c->b_jobs.p;
+  plan.info = c->b_info.p;
+  plan.acc = c->b_acc.p;
+  plan.nreq = nreq;
+  plan.mode_mask = ~0u;
+  // device lookup first (a2): it decides which copies carry and read a
+  // device source, which the level plan needs
+  DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
+  const uint64_t t_lookup = now_ns();
+  CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, st));
+  CG_CUDA(launch_job_modes(plan, c->b_modes.p, st));
+  c->stats.kernels += 2;
+  CG_CUDA(cudaMemcpyAsync(c->h_modes.p, c->b_modes.p, nreq, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  B.modes = c->h_modes.p;
+  const uint64_t t_plan = now_ns();
+  c->stats.batch_lookup_ns += t_plan - t_lookup;
+  // dependency levels, exact on validity
+  B.lvl = plan_levels(reqs, nreq, c->cfg.carry != 0, B.modes);
+  B.nlev = 0;
+  for (int l : B.lvl) B.nlev = std::max(B.nlev, l + 1);
+  B.lev_start.assign(B.nlev + 1, 0);
+  for (int l : B.lvl) B.lev_start[l + 1]++;
+  for (int l = 0; l < B.nlev; l++) B.lev_start[l + 1] += B.lev_start[l];
+  {
+    std::vector<uint64_t> fill(B.lev_start.begin(), B.lev_start.end() - 1);
+    for (uint64_t i = 0; i < nreq; i++) B.h_order[fill[B.lvl[i]]++] = (uint32_t)i;
+  }
+  for (auto &sc : B.stages) sc.level = B.lvl[sc.req];
+  std::sort(B.stages.begin(), B.stages.end(),
+            [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
+  c->stats.batch_plan_ns += now_ns() - t_plan;
+  CG_CUDA(cudaMemcpyAsync(c->b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
+  B.tma = c->cfg.scan_engine != 1;
+  int per_sm = (int)c->cfg.batch_ctas_per_sm;
+  if (per_sm <= 0) per_sm = B.tma ? 1 : 8;
+  B.grid = c->sm_count * per_sm;
+  return CG_OK;
+}
+
+// Cut every copy into segments of seg_bytes (rounded to whole engine
+// steps: one tile for the TMA engine, kU rows for register loads).
+cg_status batch_split(cg_ctx *c, BatchRun &B, uint64_t seg_bytes, cudaStream_t st) {
+  const uint64_t quantum = B.tma ? scan_tma_tile_bytes() : 2048;
+  seg_bytes = std::max<uint64_t>(quantum, (seg_bytes + quantum - 1) / quantum * quantum);
+  const uint64_t seg_chunks = seg_bytes / 16;
+  B.plan.seg_chunks = (uint32_t)seg_chunks;
+  B.lev_segs.assign(B.nlev, 0);
+  for (int l = 0; l < B.nlev; l++) {
+    uint64_t acc_segs = 0;
+    for (uint64_t pos = B.lev_start[l]; pos < B.lev_start[l + 1]; pos++) {
+      const uint32_t i = B.h_order[pos];
+      const cg_copy &q = B.reqs[i];
+      B.h_segfirst[pos] = acc_segs;
+      const bool idle = q.kind == CG_DTOD && !(B.modes[i] & (kModeCarry | kModeReadDev));
+      const uint64_t chunks_ub = (q.n && !idle) ? (q.n + 30) >> 4 : 0;
+      acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
+    }
+    B.lev_segs[l] = acc_segs;
+  }
+  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, B.h_segfirst, B.nreq * 8, cudaMemcpyHostToDevice, st));
+  return CG_OK;
+}
+
+cg_status batch_levels(cg_ctx *c, BatchRun &B, uint32_t mode_mask, cudaStream_t st) {
+  B.plan.mode_mask = mode_mask;
+  const bool dry = !(mode_mask & kModeCarry);
+  CG_CUDA(cudaMemsetAsync(c->b_err.p, 0, sizeof(unsigned int), st));
+  size_t sci = 0;
+  for (int l = 0; l < B.nlev; l++) {
+    for (; !dry && sci < B.stages.size() && B.stages[sci].level == l; sci++)
+      CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(B.stages[sci].dst),
+                              reinterpret_cast<const void *>(B.stages[sci].src), B.stages[sci].n,
+                              cudaMemcpyDeviceToDevice, st));
+    if (B.tma)
+      CG_CUDA(launch_scan_level_tma(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1],
+                                    B.lev_segs[l], B.grid, c->b_err.p, st));
+    else
+      CG_CUDA(launch_scan_level(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1], B.lev_segs[l],
+                                B.grid, st));
+    c->stats.kernels++;
+  }
+  return CG_OK;
+}
+
+const uint32_t kCandidatesKib[] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
+constexpr int kNumCandidates = sizeof(kCandidatesKib) / sizeof(kCandidatesKib[0]);
+
+void features(const cg_copy *reqs, uint64_t nreq, float *f) {
+  double s1 = 0, s2 = 0, total = 0;
+  double bins[6] = {0, 0, 0, 0, 0, 0};
+  double kinds[3] = {0, 0, 0};
+  for (uint64_t i = 0; i < nreq; i++) {
+    const double n = (double)reqs[i].n;
+    const double l = std::log2(1.0 + n);
+    s1 += l;
+    s2 += l * l;
+    total += n;
+    const int b = n <= 4096.0 ? 0 : n <= 65536.0 ? 1 : n <= 1048576.0 ? 2
+                  : n <= 4194304.0 ? 3 : n <= 16777216.0 ? 4 : 5;
+    bins[b] += n;
+    if (reqs[i].kind >= 1 && reqs[i].kind <= 3) kinds[reqs[i].kind - 1] += 1.0;
+  }
+  const double m = nreq ? s1 / nreq : 0.0;
+  f[0] = (float)std::log2(1.0 + (double)nreq);
+  f[1] = (float)m;
+  f[2] = (float)std::sqrt(std::max(0.0, nreq ? s2 / nreq - m * m : 0.0));
+  for (int k = 0; k < 6; k++) f[3 + k] = (float)(total > 0 ? bins[k] / total : 0.0);
+  for (int k = 0; k < 3; k++) f[9 + k] = (float)(nreq ? kinds[k] / nreq : 0.0);
+  f[12] = (float)std::log2(1.0 + total);
+}
+
+// The learned cost model: predicted log2(batch ms) for features f and a
+// segment size; see cg_set_cost_model for the weight layout.
+float predict(const cg_ctx *c, const float *f, uint32_t seg_kib) {
+  const int D = CG_NFEAT + 1, H = (int)c->cost_hidden;
+  const float *mu = c->cost_model.data();
+  const float *sd = mu + D;
+  const float *w1 = sd + D;
+  const float *b1 = w1 + D * H;
+  const float *w2 = b1 + H;
+  const float *b2 = w2 + H;
+  float x[CG_NFEAT + 1];
+  for (int k = 0; k < CG_NFEAT; k++) x[k] = f[k];
+  x[CG_NFEAT] = std::log2((float)seg_kib);
+  for (int k = 0; k < D; k++) x[k] = (x[k] - mu[k]) / sd[k];
+  float y = b2[0];
+  for (int j = 0; j < H; j++) {
+    float h = b1[j];
+    for (int k = 0; k < D; k++) h += x[k] * w1[k * H + j];
+    y += (h > 0.f ? h : 0.f) * w2[j];
+  }
+  return y;
+}
+
+// Segment size for a batch when the configuration leaves it open: a tuned
+// entry close to this batch's features, else the learned model's argmin
+// over the candidates, else 64 KiB.
+uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_t *source) {
+  float f[CG_NFEAT];
+  features(reqs, nreq, f);
+  float best_d = 0.5f;  // "close": within 0.5 in every (scaled) feature on average
+  int best = -1;
+  for (size_t e = 0; e < c->tuned_feat.size(); e++) {
+    float d = 0.f;
+    for (int k = 0; k < CG_NFEAT; k++) {
+      const float scale = (k == 0 || k == 12) ? 0.25f : (k == 1 || k == 2) ? 0.5f : 4.0f;
+      d += std::fabs(c->tuned_feat[e][k] - f[k]) * scale;
+    }
+    d /= CG_NFEAT;
+    if (d < best_d) {
+      best_d = d;
+      best = (int)e;
+    }
+  }
+  if (best >= 0) {
+    if (source) *source = 1;
+    return c->tuned_kib[best];
+  }
+  if (!c->cost_model.empty()) {
+    uint32_t arg = 64;
+    float lo = 0.f;
+    for (int k = 0; k < kNumCandidates; k++) {
+      const float y = predict(c, f, kCandidatesKib[k]);
+      if (k == 0 || y < lo) {
+        lo = y;
+        arg = kCandidatesKib[k];
+      }
+    }
+    if (source) *source = 2;
+    return arg;
+  }
+  if (source) *source = 0;
+  return 64;
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_report *reps,
+                         cg_err_record *recs, uint64_t rec_cap, uint64_t *n_rec,
+                         uint64_t *bad_index, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
+  if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
+    return set_error(CG_E_ARG, "NULL argument");
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_status s = validate(c, reqs[i]);
+    if (s != CG_OK) {
+      if (bad_index) *bad_index = i;
+      return s;
+    }
+  }
+  if (nreq == 0) {
+    *n_rec = 0;
+    return CG_OK;
+  }
+  if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
+  const uint64_t t_begin = now_ns();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchRun B;
+  CG_TRY(batch_prepare(c, reqs, nreq, st, B));
+  const uint32_t kib =
+      c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : choose_kib(c, reqs, nreq, nullptr);
+  CG_TRY(batch_split(c, B, (uint64_t)kib * 1024, st));
+  CG_TRY(batch_levels(c, B, ~0u, st));
+  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
+  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
+  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
+  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
+  const int strict = (int)c->cfg.strict_device_undef;
+  CG_CUDA(launch_finalize(B.plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_scan_block_sums(c->b_blocksums.p, nblocks, nullptr, st));
+  CG_CUDA(launch_emit_records(B.plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems,
+                              strict, c->b_recs.p, dev_rec_cap, st));
+  c->stats.kernels += dev_rec_cap ? 3 : 2;
+  CG_TRY(c->h_total.ensure(2));
+  CG_TRY(c->h_reps.ensure(nreq));
+  CG_CUDA(cudaMemcpyAsync(c->h_total.p, c->b_blocksums.p + nblocks, 8, cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(c->h_total.p + 1, c->b_err.p, sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
+                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaStreamSynchronize(st));
+  if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
+    return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
+  const uint64_t total = c->h_total.p[0];
+  const uint64_t take = std::min(total, dev_rec_cap);
+  if (take) {
+    CG_TRY(c->h_recs.ensure(take));
+    CG_CUDA(cudaMemcpyAsync(c->h_recs.p, c->b_recs.p, take * sizeof(cg_err_record),
+                            cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(recs, c->h_recs.p, take * sizeof(cg_err_record));
+  }
+  if (reps) std::memcpy(reps, c->h_reps.p, nreq * sizeof(cg_report));
+  for (uint64_t i = 0; i < nreq; i++) count_stats(c, c->h_reps.p[i]);
+  *n_rec = total;
+  c->stats.batch_ns += now_ns() - t_begin;
+  c->stats.batches++;
+  c->stats.levels += (uint64_t)B.nlev;
+  return CG_OK;
+}
+
+cg_status cg_batch_features(const cg_copy *reqs, uint64_t nreq, float *feat) {
+  if (!feat || (nreq && !reqs)) return set_error(CG_E_ARG, "NULL argument");
+  features(reqs, nreq, feat);
+  return CG_OK;
+}
+
+cg_status cg_tune_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, const uint32_t *seg_kib,
+                        uint32_t ncand, uint32_t repeats, uint32_t flags, float *ms,
+                        uint32_t *best_kib, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
+  if (!c || !reqs || !nreq) return set_error(CG_E_ARG, "NULL argument or empty batch");
+  for (uint64_t i = 0; i < nreq; i++) CG_TRY(validate(c, reqs[i]));
+  const uint32_t *cand = seg_kib ? seg_kib : kCandidatesKib;
+  const uint32_t nc = seg_kib ? ncand : (uint32_t)kNumCandidates;
+  if (nc == 0) return set_error(CG_E_ARG, "no candidates");
+  if (repeats == 0) repeats = 1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchRun B;
+  CG_TRY(batch_prepare(c, reqs, nreq, st, B));
+  cudaEvent_t e0, e1;
+  CG_CUDA(cudaEventCreate(&e0));
+  CG_CUDA(cudaEventCreate(&e1));
+  float best_ms = 0.f;
+  uint32_t best = cand[0];
+  cg_status status = CG_OK;
+  for (uint32_t k = 0; k < nc && status == CG_OK; k++) {
+    status = batch_split(c, B, (uint64_t)cand[k] * 1024, st);
+    float lo = 0.f;
+    for (uint32_t r = 0; r < repeats && status == CG_OK; r++) {
+      cudaEventRecord(e0, st);
+      status = batch_levels(c, B, ~kModeCarry, st);  // dry: the shadow is not written
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) status = set_error(CG_E_CUDA, "tuning run");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r == 0 || t < lo) lo = t;
+    }
+    if (ms) ms[k] = lo;
+    if (k == 0 || lo < best_ms) {
+      best_ms = lo;
+      best = cand[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CG_TRY(status);
+  if (flags & CG_TUNE_REMEMBER) {
+    std::vector<float> f(CG_NFEAT);
+    features(reqs, nreq, f.data());
+    c->tuned_feat.push_back(f);
+    c->tuned_kib.push_back(best);
+  }
+  if (best_kib) *best_kib = best;
+  return CG_OK;
+}
+
+cg_status cg_set_cost_model(cg_ctx *c, const float *weights, uint32_t hidden) {
+  if (!c) return set_error(CG_E_ARG, "ctx is NULL");
+  if (!weights || hidden == 0) {
+    c->cost_model.clear();
+    c->cost_hidden = 0;
+    return CG_OK;
+  }
+  if (hidden > 1024) return set_error(CG_E_TOO_BIG, "hidden layer above 1024 units");
+  const size_t D = CG_NFEAT + 1;
+  const size_t n = 2 * D + D * hidden + hidden + hidden + 1;
+  for (size_t k = D; k < 2 * D; k++)
+    if (!(weights[k] > 0.f)) return set_error(CG_E_ARG, "input scales must be positive");
+  c->cost_model.assign(weights, weights + n);
+  c->cost_hidden = hidden;
+  return CG_OK;
+}
+
+cg_status cg_choose_segment(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq,
+                            uint32_t *seg_kib, uint32_t *source) {
+  if (!c || !seg_kib || (nreq && !reqs)) return set_error(CG_E_ARG, "NULL argument");
+  if (c->cfg.batch_segment_kib) {
+    *seg_kib = c->cfg.batch_segment_kib;
+    if (source) *source = 3;
+    return CG_OK;
+  }
+  *seg_kib = choose_kib(c, reqs, nreq, source);
+  return CG_OK;
+}
+
+}  // extern "C"

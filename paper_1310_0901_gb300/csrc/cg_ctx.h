@@ -467,6 +467,12 @@ struct cg_ctx {
   cgi::PinBuf<cg_report> h_reps;
   cgi::PinBuf<cg_err_record> h_recs;
   cgi::PinBuf<uint64_t> h_total;
+  // batch split choice: tuned entries (features -> segment KiB) and the
+  // learned cost model's weights (empty = none)
+  std::vector<std::vector<float>> tuned_feat;
+  std::vector<uint32_t> tuned_kib;
+  std::vector<float> cost_model;
+  uint32_t cost_hidden = 0;
   cg_stats stats{};
   std::mutex stats_mu;                // guards stats while serving
   cgi::ServeEngine *serve = nullptr;  // non-null while serving

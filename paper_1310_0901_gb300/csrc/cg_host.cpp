@@ -509,203 +509,6 @@ cg_status cg_check_copy_async(cg_ctx *c, const cg_copy *req, cg_report *rep_dev,
   return enqueue_single(c, ri, job, stage, stage_src, rep_dev, static_cast<cudaStream_t>(stream));
 }
 
-cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_report *reps,
-                         cg_err_record *recs, uint64_t rec_cap, uint64_t *n_rec,
-                         uint64_t *bad_index, void *stream) {
-  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
-  if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
-    return set_error(CG_E_ARG, "NULL argument");
-  for (uint64_t i = 0; i < nreq; i++) {
-    const cg_status s = validate(c, reqs[i]);
-    if (s != CG_OK) {
-      if (bad_index) *bad_index = i;
-      return s;
-    }
-  }
-  if (nreq == 0) {
-    *n_rec = 0;
-    return CG_OK;
-  }
-  if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
-  const uint64_t t_begin = now_ns();
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  CG_TRY(flush_fills(c, st));
-  CG_TRY(ensure_device_table(c, st));
-
-  // device lookup first (a2): it decides which copies carry and read a
-  // device source, which the level plan needs
-  CG_TRY(c->b_reqs.ensure(nreq));
-  CG_TRY(c->b_order.ensure(nreq));
-  CG_TRY(c->b_segfirst.ensure(nreq));
-  CG_TRY(c->b_stage.ensure(nreq));
-  CG_TRY(c->b_jobs.ensure(nreq));
-  CG_TRY(c->b_info.ensure(nreq));
-  CG_TRY(c->b_acc.ensure(nreq));
-  CG_TRY(c->b_reps.ensure(nreq));
-  CG_TRY(c->b_counts.ensure(nreq));
-  CG_TRY(c->b_modes.ensure(nreq));
-  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
-  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
-  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
-  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
-
-  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8) + 64;
-  CG_TRY(c->h_stage_in.ensure(upload_bytes));
-  CG_TRY(c->h_modes.ensure(nreq));
-  cg_copy *h_reqs = reinterpret_cast<cg_copy *>(c->h_stage_in.p);
-  uint32_t *h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
-  uint64_t *h_segfirst = reinterpret_cast<uint64_t *>(
-      c->h_stage_in.p + round_up(nreq * (sizeof(cg_copy) + 4), 8));
-  uint64_t *h_stagep = h_segfirst + nreq;
-  std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
-
-  // overlapping device->device copies are staged (R12); their source and
-  // destination are looked up on the host mirror (they are rare)
-  struct StageCopy {
-    int level;
-    uint64_t src, dst, n, req;
-  };
-  std::vector<StageCopy> stage_copies;
-  uint64_t stage_total = 0;
-  std::memset(h_stagep, 0, nreq * sizeof(uint64_t));
-  if (c->cfg.carry) {
-    for (uint64_t i = 0; i < nreq; i++) {
-      const cg_copy &q = reqs[i];
-      if (q.kind != CG_DTOD || q.n == 0) continue;
-      const uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
-      if (dist >= q.n) continue;
-      uint64_t f, b, sz, sh, dsh;
-      uint32_t fl = 0;
-      const bool sok = host_side(c, q.src, q.n, &f, &b, &sz, &sh, &fl, 1, 2);
-      const bool dok = host_side(c, q.dst, q.n, &f, &b, &sz, &dsh, &fl, 1, 2);
-      if (!sok || !dok) continue;
-      stage_copies.push_back({0, sh, stage_total, q.n, i});
-      h_stagep[i] = stage_total + 1;  // patched to an address below
-      stage_total += round_up(q.n, 256);
-    }
-    if (stage_total) {
-      CG_TRY(c->stage.ensure(stage_total));
-      const uint64_t base = reinterpret_cast<uint64_t>(c->stage.p);
-      for (uint64_t i = 0; i < nreq; i++)
-        if (h_stagep[i]) h_stagep[i] = base + h_stagep[i] - 1;
-      for (auto &sc : stage_copies) sc.dst += base;
-    }
-  }
-  CG_CUDA(cudaMemcpyAsync(c->b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, st));
-  BatchPlan plan{};
-  plan.reqs = c->b_reqs.p;
-  plan.order = c->b_order.p;
-  plan.seg_first = c->b_segfirst.p;
-  plan.stage = c->b_stage.p;
-  plan.jobs = c->b_jobs.p;
-  plan.info = c->b_info.p;
-  plan.acc = c->b_acc.p;
-  plan.nreq = nreq;
-  DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
-  const uint64_t t_lookup = now_ns();
-  CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, st));
-  c->stats.kernels++;
-  CG_CUDA(launch_job_modes(plan, c->b_modes.p, st));
-  c->stats.kernels++;
-  CG_CUDA(cudaMemcpyAsync(c->h_modes.p, c->b_modes.p, nreq, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
-  const uint8_t *modes = c->h_modes.p;
-  const uint64_t t_plan = now_ns();
-  c->stats.batch_lookup_ns += t_plan - t_lookup;
-
-  // dependency levels (exact on validity) and the segment split
-  const bool tma = c->cfg.scan_engine != 1;
-  // a segment is a whole number of steps of the engine: kU rows (2 KiB) for
-  // register loads, one tile for the TMA engine
-  const uint64_t quantum = tma ? scan_tma_tile_bytes() : 2048;
-  uint64_t seg_bytes = (uint64_t)(c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : 64) * 1024;
-  seg_bytes = std::max<uint64_t>(quantum, (seg_bytes + quantum - 1) / quantum * quantum);
-  const uint64_t seg_chunks = seg_bytes / 16;
-  plan.seg_chunks = (uint32_t)seg_chunks;
-  const std::vector<int> lvl = plan_levels(reqs, nreq, c->cfg.carry != 0, modes);
-  int nlev = 0;
-  for (int l : lvl) nlev = std::max(nlev, l + 1);
-  std::vector<uint64_t> lev_start(nlev + 1, 0);
-  for (int l : lvl) lev_start[l + 1]++;
-  for (int l = 0; l < nlev; l++) lev_start[l + 1] += lev_start[l];
-  {
-    std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
-    for (uint64_t i = 0; i < nreq; i++) h_order[fill[lvl[i]]++] = (uint32_t)i;
-  }
-  std::vector<uint64_t> lev_segs(nlev, 0);
-  for (int l = 0; l < nlev; l++) {
-    uint64_t acc_segs = 0;
-    for (uint64_t pos = lev_start[l]; pos < lev_start[l + 1]; pos++) {
-      const uint32_t i = h_order[pos];
-      const cg_copy &q = reqs[i];
-      h_segfirst[pos] = acc_segs;
-      const bool idle = q.kind == CG_DTOD && !(modes[i] & (kModeCarry | kModeReadDev));
-      const uint64_t chunks_ub = (q.n && !idle) ? (q.n + 30) >> 4 : 0;
-      acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
-    }
-    lev_segs[l] = acc_segs;
-  }
-  for (auto &sc : stage_copies) sc.level = lvl[sc.req];
-  c->stats.batch_plan_ns += now_ns() - t_plan;
-  CG_CUDA(cudaMemcpyAsync(c->b_order.p, h_order, nreq * 4, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, h_segfirst, nreq * 8, cudaMemcpyHostToDevice, st));
-
-  int per_sm = (int)c->cfg.batch_ctas_per_sm;
-  if (per_sm <= 0) per_sm = tma ? 1 : 8;
-  const int grid = c->sm_count * per_sm;
-  CG_TRY(c->b_err.ensure(1));
-  CG_CUDA(cudaMemsetAsync(c->b_err.p, 0, sizeof(unsigned int), st));
-  size_t sci = 0;
-  std::sort(stage_copies.begin(), stage_copies.end(),
-            [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
-  for (int l = 0; l < nlev; l++) {
-    for (; sci < stage_copies.size() && stage_copies[sci].level == l; sci++)
-      CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(stage_copies[sci].dst),
-                              reinterpret_cast<const void *>(stage_copies[sci].src),
-                              stage_copies[sci].n, cudaMemcpyDeviceToDevice, st));
-    if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
-                                    grid, c->b_err.p, st));
-    else
-      CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l], grid,
-                                st));
-    c->stats.kernels++;
-  }
-  const int strict = (int)c->cfg.strict_device_undef;
-  CG_CUDA(launch_finalize(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems, st));
-  CG_CUDA(launch_scan_block_sums(c->b_blocksums.p, nblocks, nullptr, st));
-  CG_CUDA(launch_emit_records(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems,
-                              strict, c->b_recs.p, dev_rec_cap, st));
-  c->stats.kernels += dev_rec_cap ? 3 : 2;
-  CG_TRY(c->h_total.ensure(2));
-  CG_TRY(c->h_reps.ensure(nreq));
-  CG_CUDA(cudaMemcpyAsync(c->h_total.p, c->b_blocksums.p + nblocks, 8, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(c->h_total.p + 1, c->b_err.p, sizeof(unsigned int),
-                          cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
-                          cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
-  if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
-    return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
-  const uint64_t total = c->h_total.p[0];
-  const uint64_t take = std::min(total, dev_rec_cap);
-  if (take) {
-    CG_TRY(c->h_recs.ensure(take));
-    CG_CUDA(cudaMemcpyAsync(c->h_recs.p, c->b_recs.p, take * sizeof(cg_err_record),
-                            cudaMemcpyDeviceToHost, st));
-    CG_CUDA(cudaStreamSynchronize(st));
-    std::memcpy(recs, c->h_recs.p, take * sizeof(cg_err_record));
-  }
-  if (reps) std::memcpy(reps, c->h_reps.p, nreq * sizeof(cg_report));
-  for (uint64_t i = 0; i < nreq; i++) count_stats(c, c->h_reps.p[i]);
-  *n_rec = total;
-  c->stats.batch_ns += now_ns() - t_begin;
-  c->stats.batches++;
-  c->stats.levels += (uint64_t)nlev;
-  return CG_OK;
-}
-
 cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, const uint8_t *modes,
                          int32_t *level, uint32_t *n_levels) {
   if ((nreq && (!reqs || !level))) return set_error(CG_E_ARG, "NULL argument");

@@ -85,6 +85,7 @@ struct BatchPlan {
   Acc *acc;                   // per request
   uint64_t nreq;
   uint32_t seg_chunks;        // segment length in 16-byte chunks
+  uint32_t mode_mask;         // ANDed into every job's mode (clearing the carry = dry run)
 };
 
 // Build the user-visible report from the range verdict and the scan totals.

@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kThreads) scan_level_kernel(Image img, BatchPl
         hi = mid;
     }
     const uint32_t req = __ldg(p.order + lo);
-    const ScanJob job = p.jobs[req];
+    ScanJob job = p.jobs[req];
+    job.mode &= p.mode_mask;
     const Geo g = make_geo(job, img);
     const int64_t k = (int64_t)(s - __ldg(p.seg_first + lo));
     const int64_t rows = (g.nchunks + 31) >> 5;

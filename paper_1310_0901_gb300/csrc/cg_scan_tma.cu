@@ -259,6 +259,7 @@ __device__ __forceinline__ void seg_load(SegIter &it, const BatchPlan &p, const 
     }
     it.req = __ldg(p.order + lo);
     it.job = p.jobs[it.req];
+    it.job.mode &= p.mode_mask;
     it.g = make_geo(it.job, img);
     const int64_t k = (int64_t)(it.s - __ldg(p.seg_first + lo));
     const int64_t rows = (it.g.nchunks + 31) >> 5;

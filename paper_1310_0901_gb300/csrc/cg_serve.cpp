@@ -505,6 +505,7 @@ struct ServeEngine {
     plan.stage = reinterpret_cast<const uint64_t *>(R.d_up.p + o_stage);
     plan.nreq = n;
     plan.seg_chunks = (uint32_t)seg_chunks;
+    plan.mode_mask = ~0u;
     std::sort(stages.begin(), stages.end(),
               [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
     size_t sci = 0;

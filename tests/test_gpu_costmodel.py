@@ -1,0 +1,77 @@
+"""The learned batch-split cost model: its GPU training kernels against the
+CPU reference (gradients), that training fits, and what the trained model
+gains over choosing the default split, on batches it was not trained on."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import cg_synth as S
+from oracle import mlp as M
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cg():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1310_0901_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("hidden,n", [(32, 7), (32, 300), (64, 1000)])
+def test_gpu_gradients_match_cpu_reference(cg, hidden, n):
+    rng = np.random.default_rng(hidden + n)
+    x = (rng.normal(size=(n, M.D)) * 2 + 1).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    w = np.zeros(cg.mlp_nweights(hidden), np.float32)
+    w[:M.D] = x.mean(axis=0)
+    w[M.D:2 * M.D] = x.std(axis=0) + 0.1
+    w[2 * M.D:] = (rng.normal(size=w.size - 2 * M.D) * 0.3).astype(np.float32)
+    g_gpu, l_gpu = cg.mlp_grad(x, t, w, hidden)
+    g_cpu, l_cpu = M.grad(x.astype(np.float64), t.astype(np.float64), w.astype(np.float64),
+                          hidden)
+    assert abs(l_gpu - l_cpu) <= 1e-4 * max(1.0, abs(l_cpu))
+    scale = np.abs(g_cpu).max()
+    assert np.max(np.abs(g_gpu - g_cpu)) <= 2e-4 * scale, np.max(np.abs(g_gpu - g_cpu)) / scale
+
+
+def test_fit_reduces_loss(cg):
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(400, M.D)).astype(np.float32)
+    t = (np.sin(x[:, 0]) + 0.5 * x[:, 1] ** 2 - x[:, 13]).astype(np.float32)
+    w, losses = cg.mlp_fit(x, t, 32, 1500, 3e-3, 0)
+    assert losses[-1] < 0.1 * losses[0]
+    assert abs(M.loss(x, t, w, 32) - losses[-1]) < 0.05 * losses[0]
+
+
+def test_learned_split_gains_over_default(cg):
+    from paper_1310_0901_gb300 import costmodel as CM
+    rng = S.rng_for(31)
+    table = S.alloc_table(rng, 20000, 256, 1 << 20, log_sizes=True)
+    img = S.host_image_runs(rng, 256 << 20, 1e-4, 8.0, 0.5, 1e-5)
+    ctx, _, _ = U.make_pair(img, table)
+    batches = [S.tuning_batch(rng, table, img.n) for _ in range(150)]
+    measured = CM.measure(ctx, batches, repeats=2)
+    train, held = measured[:120], measured[120:]
+    w, losses = CM.fit(train, hidden=32, epochs=4000)
+    assert losses[-1] < losses[0]
+    ctx.set_cost_model(w, 32)
+    t_default = t_model = t_best = 0.0
+    for b, m in zip(batches[120:], held):
+        kib, source = ctx.choose_segment(b)
+        assert source == 2
+        preds = {k: CM.predict(w, m["features"], k, 32) for k in cg.CANDIDATES_KIB}
+        assert kib == min(preds, key=preds.get)
+        t_default += m["ms"][64]
+        t_model += m["ms"][kib]
+        t_best += min(m["ms"].values())
+    gain = t_default / t_model
+    print(f"held-out level time: default 64 KiB {t_default:.2f} ms, learned {t_model:.2f} ms, "
+          f"grid-search best {t_best:.2f} ms; gain {gain:.3f}x")
+    assert t_model <= t_default * 1.02
+    # a tuned entry for a batch takes precedence over the model
+    best, _ = ctx.tune_batch(batches[121], repeats=1)
+    assert ctx.choose_segment(batches[121]) == (best, 1)
