@@ -280,7 +280,7 @@ def run_batched_workload(args, which: str):
     n_img = w.image.n
     a_dev = torch.from_numpy(w.image.a_bits[: n_img // 8].copy()).to(dev)
     v_dev = torch.from_numpy(w.image.v).to(dev)
-    ctx = cg.Context(batch_segment_kib=args.segment_kib)
+    ctx = cg.Context(batch_segment_kib=args.segment_kib, batch_autotune=1)
     ctx.bind_host_shadow(a_dev, v_dev)
     order = np.argsort(w.table.base)
     t_reg = time.perf_counter()
@@ -291,7 +291,9 @@ def run_batched_workload(args, which: str):
     nreq = len(reqs)
     bytes_per_batch = int(reqs["n"].sum())
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
+    # the split is autotuned online: the warm-up batches try the candidates
+    # (real runs, timed), the timed batches use the fastest
+    for _ in range(max(args.warmup, 5 if not args.segment_kib else 0)):
         stt, reps, recs, total, _ = ctx.check_batch(reqs, rec_cap=8 * nreq)
         cg.check(stt, "check_batch")
     s0 = ctx.stats()
@@ -326,13 +328,16 @@ def run_batched_workload(args, which: str):
         "data": "synthetic (seeded cg_synth." + which + ")",
         "config": {"workload": w.name, "requests": nreq, "allocations": int(len(w.table.base)),
                    "bytes_checked_per_batch": bytes_per_batch,
-                   "segment_kib": args.segment_kib or 64, "levels_per_batch": levels,
+                   "levels_per_batch": levels,
                    "l2": "working set larger than L2", "carry": True},
         "batched_gb_per_s": round(bytes_per_batch * args.steps / dt / GB, 1),
         "one_launch_per_copy": {"checks_per_s": round(single_cps, 1), "sample": m,
                                 "gb_per_s": round(int(reqs["n"][:m].sum()) / dt1 / GB, 1)},
         "speedup_vs_one_launch_per_copy": round(batch_cps / single_cps, 2),
         "records_per_batch": int(total),
+        "split": {"segment_kib": ctx.choose_segment(reqs)[0],
+                  "source": ["default", "autotuned", "learned", "fixed", "trial"][
+                      ctx.choose_segment(reqs)[1]]},
         "batch_breakdown_ms": {"total": per_batch_ms["batch_ns"],
                                "host_plan": per_batch_ms["batch_plan_ns"],
                                "lookup_and_readback": per_batch_ms["batch_lookup_ns"]},

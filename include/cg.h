@@ -160,7 +160,11 @@ typedef struct cg_config {
   uint32_t batch_ctas_per_sm;   /* batched grid; 0 = automatic */
   uint32_t scan_engine;         /* scan loads, single and batched checks:
                                    0 auto (= 2), 1 registers, 2 TMA bulk copies */
-  uint32_t reserved[8];
+  uint32_t batch_autotune;      /* 1: with batch_segment_kib = 0, batches of a
+                                   new shape first try the split candidates
+                                   16..256 KiB in turn (real runs, timed), then
+                                   keep the fastest (see cg_choose_segment) */
+  uint32_t reserved[7];
 } cg_config;
 
 typedef struct cg_ctx cg_ctx;
@@ -276,9 +280,11 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
 /* How cg_check_batch cuts copies into segments matters (too small: per-
  * segment overhead; too large: idle warps at the end of each level), and
  * the best size depends on the batch.  With batch_segment_kib = 0 the
- * context picks it per batch: the size cg_tune_batch measured best for a
- * batch with close features, else the argmin of a learned cost model over
- * the candidates 4, 8, ..., 1024 KiB, else 64 KiB. */
+ * context picks it per batch, in this order: the size measured best for a
+ * batch with close features (by cg_tune_batch, or by the online tuner);
+ * with batch_autotune on, the next candidate the online tuner wants to
+ * try for this shape; the argmin of a learned cost model over the
+ * candidates 4, 8, ..., 1024 KiB; else 64 KiB. */
 
 #define CG_NFEAT 13
 
@@ -324,7 +330,8 @@ cg_status cg_mlp_grad(const float *x, const float *t, uint32_t n, uint32_t hidde
                       const float *weights, float *grads, float *loss, void *stream);
 
 /* The segment size cg_check_batch would use for this batch; *source (may be
- * NULL): 0 default, 1 tuned entry, 2 learned model, 3 fixed by the config. */
+ * NULL): 0 default, 1 tuned entry, 2 learned model, 3 fixed by the config,
+ * 4 an online-tuning trial. */
 cg_status cg_choose_segment(const cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                             uint32_t *seg_kib, uint32_t *source);
 

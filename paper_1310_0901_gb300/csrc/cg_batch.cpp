@@ -184,6 +184,8 @@ cg_status batch_levels(cg_ctx *c, BatchRun &B, uint32_t mode_mask, cudaStream_t 
 
 const uint32_t kCandidatesKib[] = {4, 8, 16, 32, 64, 128, 256, 512, 1024};
 constexpr int kNumCandidates = sizeof(kCandidatesKib) / sizeof(kCandidatesKib[0]);
+const uint32_t kOnlineKib[] = {16, 32, 64, 128, 256};
+constexpr uint32_t kNumOnline = sizeof(kOnlineKib) / sizeof(kOnlineKib[0]);
 
 void features(const cg_copy *reqs, uint64_t nreq, float *f) {
   double s1 = 0, s2 = 0, total = 0;
@@ -232,21 +234,30 @@ float predict(const cg_ctx *c, const float *f, uint32_t seg_kib) {
   return y;
 }
 
+// mean scaled distance between two feature vectors
+float feature_distance(const float *a, const float *b) {
+  float d = 0.f;
+  for (int k = 0; k < CG_NFEAT; k++) {
+    const float scale = (k == 0 || k == 12) ? 0.25f : (k == 1 || k == 2) ? 0.5f : 4.0f;
+    d += std::fabs(a[k] - b[k]) * scale;
+  }
+  return d / CG_NFEAT;
+}
+constexpr float kClose = 0.5f;
+
 // Segment size for a batch when the configuration leaves it open: a tuned
-// entry close to this batch's features, else the learned model's argmin
-// over the candidates, else 64 KiB.
-uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_t *source) {
+// entry close to this batch's features; else, with online tuning on, the
+// next trial for this shape (*online_slot set); else the learned model's
+// argmin over the candidates; else 64 KiB.
+uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_t *source,
+                    int *online_slot) {
   float f[CG_NFEAT];
   features(reqs, nreq, f);
-  float best_d = 0.5f;  // "close": within 0.5 in every (scaled) feature on average
+  if (online_slot) *online_slot = -1;
+  float best_d = kClose;
   int best = -1;
   for (size_t e = 0; e < c->tuned_feat.size(); e++) {
-    float d = 0.f;
-    for (int k = 0; k < CG_NFEAT; k++) {
-      const float scale = (k == 0 || k == 12) ? 0.25f : (k == 1 || k == 2) ? 0.5f : 4.0f;
-      d += std::fabs(c->tuned_feat[e][k] - f[k]) * scale;
-    }
-    d /= CG_NFEAT;
+    const float d = feature_distance(c->tuned_feat[e].data(), f);
     if (d < best_d) {
       best_d = d;
       best = (int)e;
@@ -255,6 +266,21 @@ uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_
   if (best >= 0) {
     if (source) *source = 1;
     return c->tuned_kib[best];
+  }
+  if (c->cfg.batch_autotune) {
+    int slot = -1;
+    best_d = kClose;
+    for (size_t e = 0; e < c->online.size(); e++) {
+      const float d = feature_distance(c->online[e].feat.data(), f);
+      if (d < best_d) {
+        best_d = d;
+        slot = (int)e;
+      }
+    }
+    const uint32_t next = slot >= 0 ? c->online[slot].next : 0;
+    if (online_slot) *online_slot = slot;  // -1: a new shape (an entry is made on use)
+    if (source) *source = 4;
+    return kOnlineKib[next < kNumOnline ? next : 0];
   }
   if (!c->cost_model.empty()) {
     uint32_t arg = 64;
@@ -271,6 +297,29 @@ uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_
   }
   if (source) *source = 0;
   return 64;
+}
+
+// Record an online trial; once every candidate has run, the fastest
+// becomes a tuned entry for this shape.
+void online_record(cg_ctx *c, int slot, const cg_copy *reqs, uint64_t nreq, uint32_t kib,
+                   float ms) {
+  if (slot < 0) {
+    cg_ctx::OnlineTune t;
+    t.feat.resize(CG_NFEAT);
+    features(reqs, nreq, t.feat.data());
+    c->online.push_back(t);
+    slot = (int)c->online.size() - 1;
+  }
+  cg_ctx::OnlineTune &t = c->online[slot];
+  if (t.next == 0 || ms < t.best_ms) {
+    t.best_ms = ms;
+    t.best_kib = kib;
+  }
+  if (++t.next >= kNumOnline) {
+    c->tuned_feat.push_back(t.feat);
+    c->tuned_kib.push_back(t.best_kib);
+    c->online.erase(c->online.begin() + slot);
+  }
 }
 
 }  // namespace
@@ -299,10 +348,19 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   BatchRun B;
   CG_TRY(batch_prepare(c, reqs, nreq, st, B));
-  const uint32_t kib =
-      c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : choose_kib(c, reqs, nreq, nullptr);
+  uint32_t source = 3;
+  int online_slot = -1;
+  const uint32_t kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib
+                                                : choose_kib(c, reqs, nreq, &source, &online_slot);
   CG_TRY(batch_split(c, B, (uint64_t)kib * 1024, st));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (source == 4) {  // an online trial: time the level kernels
+    CG_CUDA(cudaEventCreate(&e0));
+    CG_CUDA(cudaEventCreate(&e1));
+    CG_CUDA(cudaEventRecord(e0, st));
+  }
   CG_TRY(batch_levels(c, B, ~0u, st));
+  if (source == 4) CG_CUDA(cudaEventRecord(e1, st));
   const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
   CG_TRY(c->b_blocksums.ensure(nblocks + 1));
   const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
@@ -321,6 +379,13 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
                           cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
+  if (source == 4) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    online_record(c, online_slot, reqs, nreq, kib, ms);
+  }
   if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
     return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
   const uint64_t total = c->h_total.p[0];
@@ -422,7 +487,7 @@ cg_status cg_choose_segment(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq,
     if (source) *source = 3;
     return CG_OK;
   }
-  *seg_kib = choose_kib(c, reqs, nreq, source);
+  *seg_kib = choose_kib(c, reqs, nreq, source, nullptr);
   return CG_OK;
 }
 

@@ -473,6 +473,13 @@ struct cg_ctx {
   std::vector<uint32_t> tuned_kib;
   std::vector<float> cost_model;
   uint32_t cost_hidden = 0;
+  struct OnlineTune {
+    std::vector<float> feat;
+    uint32_t next = 0;  // index of the next candidate to try
+    uint32_t best_kib = 0;
+    float best_ms = 0.f;
+  };
+  std::vector<OnlineTune> online;
   cg_stats stats{};
   std::mutex stats_mu;                // guards stats while serving
   cgi::ServeEngine *serve = nullptr;  // non-null while serving

@@ -232,11 +232,19 @@ __global__ void __launch_bounds__(kTW * 32, 1)
 
 // ------------------------------------------------ batched: one level
 
-// The tiles a warp processes in one level, in order: segments w, w + W, ...
-// of the level's segment list, each segment's tiles in turn.  Producer and
-// consumer walk identical iterators, the producer kNS tiles ahead.
+// The tiles a warp processes in one level, in order: segments w, w + W,
+// w + 2W, ... of the level's segment list (warps interleave, so the bytes
+// streamed at any moment are close together), each segment's tiles in
+// turn.  The copy owning a segment is found by one binary search per warp,
+// then by galloping forward from the previous copy (segments of a copy are
+// consecutive, so a step of W segments usually stays in the same copy).
+// Producer and consumer walk identical iterators, the producer kNS tiles
+// ahead.
 struct SegIter {
   uint64_t s;      // current segment id
+  uint64_t pos;    // order position of the current copy
+  uint64_t first;  // its first segment id
+  uint64_t next;   // first segment id of the next position (or ~0)
   uint32_t req;    // its request
   ScanJob job;
   Geo g;
@@ -244,24 +252,47 @@ struct SegIter {
   bool valid;
 };
 
-__device__ __forceinline__ void seg_load(SegIter &it, const BatchPlan &p, const Image &img,
-                                         uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
-                                         uint64_t step) {
+__device__ __forceinline__ void seg_set_pos(SegIter &it, const BatchPlan &p, const Image &img,
+                                            uint64_t pos, uint64_t pos_end) {
+  it.pos = pos;
+  it.first = __ldg(p.seg_first + pos);
+  it.next = pos + 1 < pos_end ? __ldg(p.seg_first + pos + 1) : ~0ull;
+  it.req = __ldg(p.order + pos);
+  it.job = p.jobs[it.req];
+  it.job.mode &= p.mode_mask;
+  it.g = make_geo(it.job, img);
+}
+
+// last position in [lo, hi) whose first segment is <= s, given that
+// position lo qualifies
+__device__ __forceinline__ uint64_t seg_search(const BatchPlan &p, uint64_t lo, uint64_t hi,
+                                               uint64_t s) {
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(p.seg_first + mid) <= s)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Settle on segment it.s (or the first non-empty one among s, s+W, ...).
+__device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, const Image &img,
+                                           uint64_t pos_end, uint64_t n_segs, uint64_t step) {
   const int64_t seg_rows = p.seg_chunks >> 5;
   while (it.s < n_segs) {
-    uint64_t lo = pos_begin, hi = pos_end;  // last position whose first segment <= s
-    while (hi - lo > 1) {
-      const uint64_t mid = (lo + hi) >> 1;
-      if (__ldg(p.seg_first + mid) <= it.s)
-        lo = mid;
-      else
-        hi = mid;
+    if (it.s >= it.next) {  // gallop forward from the next position
+      uint64_t lo = it.pos + 1, span = 1, hi = lo + 1;
+      while (hi < pos_end && __ldg(p.seg_first + hi) <= it.s) {
+        lo = hi;
+        span <<= 1;
+        hi = lo + span;
+      }
+      if (hi > pos_end) hi = pos_end;
+      seg_set_pos(it, p, img, seg_search(p, lo, hi, it.s), pos_end);
     }
-    it.req = __ldg(p.order + lo);
-    it.job = p.jobs[it.req];
-    it.job.mode &= p.mode_mask;
-    it.g = make_geo(it.job, img);
-    const int64_t k = (int64_t)(it.s - __ldg(p.seg_first + lo));
+    const int64_t k = (int64_t)(it.s - it.first);
     const int64_t rows = (it.g.nchunks + 31) >> 5;
     const int64_t r0 = k * seg_rows;
     const int64_t r1 = r0 + seg_rows < rows ? r0 + seg_rows : rows;
@@ -271,9 +302,26 @@ __device__ __forceinline__ void seg_load(SegIter &it, const BatchPlan &p, const 
       it.valid = true;
       return;
     }
-    it.s += step;
+    it.s += step;  // an empty trailing segment (the count was an upper bound)
   }
   it.valid = false;
+}
+
+__device__ __forceinline__ void seg_begin(SegIter &it, const BatchPlan &p, const Image &img,
+                                          uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
+                                          uint64_t s, uint64_t step) {
+  it.s = s;
+  it.valid = false;
+  if (s >= n_segs) return;
+  seg_set_pos(it, p, img, seg_search(p, pos_begin, pos_end, s), pos_end);
+  seg_settle(it, p, img, pos_end, n_segs, step);
+}
+
+__device__ __forceinline__ void seg_advance(SegIter &it, const BatchPlan &p, const Image &img,
+                                            uint64_t pos_end, uint64_t n_segs, uint64_t step) {
+  if (++it.t < it.t_end) return;
+  it.s += step;
+  seg_settle(it, p, img, pos_end, n_segs, step);
 }
 
 __device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bits, uint32_t st,
@@ -336,17 +384,13 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   }
   __syncwarp();
   SegIter prod, cons;
-  prod.s = gw;
-  seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
+  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, nw);
   cons = prod;
   int issued = 0;
   for (int s = 0; s < kNS && prod.valid; s++) {
     if (lane == 0) seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
     issued++;
-    if (++prod.t >= prod.t_end) {
-      prod.s += nw;
-      seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
-    }
+    seg_advance(prod, p, img, pos_end, n_segs, nw);
   }
   LaneAcc la;
   lane_acc_reset(la);
@@ -369,16 +413,12 @@ __global__ void __launch_bounds__(kTW * 32, 1)
         seg_issue(prod, img.a_bits, smem_addr(wbase + stage * kStage), smem_addr(&bars[stage]));
       }
       issued++;
-      if (++prod.t >= prod.t_end) {
-        prod.s += nw;
-        seg_load(prod, p, img, pos_begin, pos_end, n_segs, nw);
-      }
+      seg_advance(prod, p, img, pos_end, n_segs, nw);
     }
-    if (++cons.t >= cons.t_end) {  // segment done: its counts go to its request
-      warp_flush(la, &p.acc[cons.req], lane);
-      cons.s += nw;
-      seg_load(cons, p, img, pos_begin, pos_end, n_segs, nw);
-    }
+    const uint32_t req = cons.req;
+    const uint64_t seg = cons.s;
+    seg_advance(cons, p, img, pos_end, n_segs, nw);
+    if (!cons.valid || cons.s != seg) warp_flush(la, &p.acc[req], lane);  // segment done
     stage = stage + 1 == kNS ? 0 : stage + 1;
   }
   if (failed) {  // drain the copies still in flight, bounded

@@ -75,3 +75,26 @@ def test_learned_split_gains_over_default(cg):
     # a tuned entry for a batch takes precedence over the model
     best, _ = ctx.tune_batch(batches[121], repeats=1)
     assert ctx.choose_segment(batches[121]) == (best, 1)
+
+
+def test_online_autotune_tries_then_keeps_fastest(cg):
+    """With batch_autotune on, batches of one shape try the candidates in
+    turn (real runs) and then keep the fastest; every batch's reports stay
+    equal to the oracle's whatever the split."""
+    import oracle as O
+    w = S.small(5)
+    ctx, orc, (a, v) = U.make_pair(w.image, w.table, batch_autotune=1)
+    seen = []
+    for rep in range(7):
+        kib, source = ctx.choose_segment(w.reqs)
+        seen.append((kib, source))
+        st, reps, recs, total, _ = ctx.check_batch(w.reqs)
+        assert st == 0
+        st_o, oreps, _ = orc.check_batch(w.reqs)
+        for i, (g, o) in enumerate(zip(U.reports_from_array(reps), oreps)):
+            U.assert_same_report(g, o, f"batch {rep} request {i}")
+        assert U.reports_from_array(recs) == O.emit_records(oreps, w.reqs)
+    trials = [k for k, s in seen if s == 4]
+    assert trials == [16, 32, 64, 128, 256]
+    assert seen[5][1] == 1 and seen[6] == seen[5] and seen[5][0] in trials
+    U.assert_same_state(ctx, orc, v, w.table)
