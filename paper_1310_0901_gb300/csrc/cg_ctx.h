@@ -299,76 +299,78 @@ class AllocTable {
 
 // Range-chmax / range-max segment tree over the elementary intervals of one
 // address space, holding two values per leaf: the highest level of a copy
-// that wrote it (w) and of one that read it (r).
+// that wrote it (w) and of one that read it (r).  Values only grow, so a
+// chmax never has to be pushed down: each node keeps the max of its
+// subtree (sub) and the chmax applied to its whole subtree (tag); a range
+// max is the max of `sub` over the covering nodes and of `tag` over the
+// ancestors of the range's two end leaves.  Iterative, bottom-up.
 class LevelTree {
  public:
   void init(int n) {
-    n_ = std::max(1, n);
     size_t m = 1;
-    while (m < (size_t)n_) m <<= 1;
+    while (m < (size_t)std::max(1, n)) m <<= 1;
+    m_ = m;
     nodes_.assign(2 * m, Node{-1, -1, -1, -1});
   }
   // max of w (and of r when want_r) over leaves [l, r)
   int query(int l, int r, bool want_r) const {
     if (l >= r) return -1;
-    return q(1, 0, n_, l, r, want_r);
+    int v = -1;
+    size_t a = l + m_, b = r + m_;
+    const size_t a0 = a, b0 = b - 1;
+    while (a < b) {
+      if (a & 1) v = std::max(v, sub(nodes_[a++], want_r));
+      if (b & 1) v = std::max(v, sub(nodes_[--b], want_r));
+      a >>= 1;
+      b >>= 1;
+    }
+    for (size_t i = a0 >> 1; i; i >>= 1) v = std::max(v, tag(nodes_[i], want_r));
+    for (size_t i = b0 >> 1; i; i >>= 1) v = std::max(v, tag(nodes_[i], want_r));
+    return v;
   }
-  void update_w(int l, int r, int v) {
-    if (l < r) u(1, 0, n_, l, r, v, true);
-  }
-  void update_r(int l, int r, int v) {
-    if (l < r) u(1, 0, n_, l, r, v, false);
-  }
+  void update_w(int l, int r, int v) { update(l, r, v, true); }
+  void update_r(int l, int r, int v) { update(l, r, v, false); }
 
  private:
   struct Node {
-    int w, r, tw, tr;  // subtree maxima and pending chmax for the children
+    int sw, sr, tw, tr;  // subtree maxima, whole-subtree chmax tags
   };
-  int n_ = 1;
-  mutable std::vector<Node> nodes_;
-  void push(int x) const {
-    Node &p = nodes_[x];
-    if (p.tw < 0 && p.tr < 0) return;
-    for (int c = 2 * x; c <= 2 * x + 1; c++) {
-      Node &k = nodes_[c];
-      if (p.tw >= 0) {
-        k.w = std::max(k.w, p.tw);
-        k.tw = std::max(k.tw, p.tw);
-      }
-      if (p.tr >= 0) {
-        k.r = std::max(k.r, p.tr);
-        k.tr = std::max(k.tr, p.tr);
-      }
-    }
-    p.tw = p.tr = -1;
-  }
-  int q(int x, int l, int r, int ql, int qr, bool want_r) const {
-    if (ql <= l && r <= qr) return want_r ? std::max(nodes_[x].w, nodes_[x].r) : nodes_[x].w;
-    push(x);
-    const int m = (l + r) >> 1;
-    int v = -1;
-    if (ql < m) v = q(2 * x, l, m, ql, qr, want_r);
-    if (qr > m) v = std::max(v, q(2 * x + 1, m, r, ql, qr, want_r));
-    return v;
-  }
-  void u(int x, int l, int r, int ql, int qr, int v, bool is_w) {
-    Node &nd = nodes_[x];
-    if (ql <= l && r <= qr) {
+  size_t m_ = 1;
+  std::vector<Node> nodes_;
+  static int sub(const Node &n, bool want_r) { return want_r ? std::max(n.sw, n.sr) : n.sw; }
+  static int tag(const Node &n, bool want_r) { return want_r ? std::max(n.tw, n.tr) : n.tw; }
+  void update(int l, int r, int v, bool is_w) {
+    if (l >= r) return;
+    size_t a = l + m_, b = r + m_;
+    const size_t a0 = a, b0 = b - 1;
+    auto apply = [&](Node &n) {
       if (is_w) {
-        nd.w = std::max(nd.w, v);
-        nd.tw = std::max(nd.tw, v);
+        n.sw = std::max(n.sw, v);
+        n.tw = std::max(n.tw, v);
       } else {
-        nd.r = std::max(nd.r, v);
-        nd.tr = std::max(nd.tr, v);
+        n.sr = std::max(n.sr, v);
+        n.tr = std::max(n.tr, v);
       }
-      return;
+    };
+    while (a < b) {
+      if (a & 1) apply(nodes_[a++]);
+      if (b & 1) apply(nodes_[--b]);
+      a >>= 1;
+      b >>= 1;
     }
-    push(x);
-    const int m = (l + r) >> 1;
-    if (ql < m) u(2 * x, l, m, ql, qr, v, is_w);
-    if (qr > m) u(2 * x + 1, m, r, ql, qr, v, is_w);
-    nodes_[x].w = std::max(nodes_[2 * x].w, nodes_[2 * x + 1].w);
-    nodes_[x].r = std::max(nodes_[2 * x].r, nodes_[2 * x + 1].r);
+    // ancestors of the end leaves: subtree max = max(own tag, children's)
+    auto rebuild = [&](size_t i) {
+      for (i >>= 1; i; i >>= 1) {
+        Node &n = nodes_[i];
+        const Node &c0 = nodes_[2 * i], &c1 = nodes_[2 * i + 1];
+        if (is_w)
+          n.sw = std::max(n.tw, std::max(c0.sw, c1.sw));
+        else
+          n.sr = std::max(n.tr, std::max(c0.sr, c1.sr));
+      }
+    };
+    rebuild(a0);
+    rebuild(b0);
   }
 };
 

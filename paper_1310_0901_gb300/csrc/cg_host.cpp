@@ -79,8 +79,28 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
   }
   // compress: each endpoint gets the rank of its value among distinct values
   std::vector<int32_t> idx(8 * nreq, -1);
+  std::vector<Ep> tmp;
+  auto radix_sort = [&](std::vector<Ep> &e) {  // LSD, 11-bit digits, skipping flat ones
+    tmp.resize(e.size());
+    for (int shift = 0; shift < 64; shift += 11) {
+      uint32_t cnt[2048] = {0};
+      for (const Ep &x : e) cnt[(x.v >> shift) & 2047]++;
+      bool flat = false;
+      for (int d = 0; d < 2048; d++)
+        if (cnt[d] == e.size()) flat = true;
+      if (flat) continue;
+      uint32_t sum = 0;
+      for (int d = 0; d < 2048; d++) {
+        const uint32_t c = cnt[d];
+        cnt[d] = sum;
+        sum += c;
+      }
+      for (const Ep &x : e) tmp[cnt[(x.v >> shift) & 2047]++] = x;
+      e.swap(tmp);
+    }
+  };
   auto compress = [&](std::vector<Ep> &e) -> int {
-    std::sort(e.begin(), e.end(), [](const Ep &a, const Ep &b) { return a.v < b.v; });
+    radix_sort(e);
     int rank = -1;
     uint64_t prev = 0;
     for (size_t k = 0; k < e.size(); k++) {
