@@ -223,6 +223,28 @@ def run_cg(args, world, rank, local):
         d2h = 112 * len(reqs)
     if e2e_ms is not None:
         e2e_ms = reduce_max(e2e_ms, dev)
+    # end to end, in place: the kernel reads the pinned host shadow over the
+    # host link (no staging copy); the carry still lands in HBM
+    zc_ms = None
+    if args.e2e_steps > 0:
+        ctx_h = cg.Context()
+        ctx_h.bind_host_shadow(a_host, v_host)
+        for b, s_ in zip(w.table.base[order], w.table.size[order]):
+            cg.check(ctx_h.register_alloc(int(b), int(s_)), "register")
+        for q in w.reqs:  # untimed pass (first-touch of the device shadow)
+            cg.check(ctx_h.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]), int(q["n"]),
+                                      stream)[0], "check_copy")
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for i, q in enumerate(w.reqs):
+                st, rep = ctx_h.check_copy(int(q["kind"]), int(q["dst"]), int(q["src"]),
+                                           int(q["n"]), stream)
+                cg.check(st, "check_copy")
+                assert rep["n_undef"] == int(reps[i]["n_undef"])
+        torch.cuda.synchronize()
+        zc_ms = reduce_max((time.perf_counter() - s0) * 1e3, dev)
+        ctx_h.close()
 
     out = {
         "metric": "shadow GB/s checked vs HBM peak (single large host->device transfer checks)",
@@ -254,8 +276,13 @@ def run_cg(args, world, rank, local):
         "gpu_launches": int(launches),
     }
     if e2e_ms is not None:
-        out["e2e"] = {"value": round(bytes_per_step * args.e2e_steps * world / (e2e_ms / 1e3) / GB, 2),
-                      "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        up = bytes_per_step * args.e2e_steps * world / (e2e_ms / 1e3) / GB
+        inplace = bytes_per_step * args.e2e_steps * world / (zc_ms / 1e3) / GB if zc_ms else 0.0
+        out["e2e"] = {"value": round(max(up, inplace), 2), "unit": "GB/s",
+                      "mode": "in place over the host link" if inplace > up else
+                              "upload then check",
+                      "upload_then_check": round(up, 2), "in_place": round(inplace, 2),
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "steps": args.e2e_steps}
     if clk is not None:
         out["clocks"] = clk

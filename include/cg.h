@@ -197,11 +197,14 @@ cg_status cg_create(cg_ctx **out, const cg_config *cfg);
 cg_status cg_destroy(cg_ctx *ctx);
 
 /* Bind the host shadow image (Memcheck's A and V bits of host memory,
- * Sec. 1.1).  a_bits_dev: device, n_bytes/8 bytes; v_dev: device, n_bytes
- * bytes.  Both 16-byte aligned; n_bytes a multiple of 128 (so both arrays
- * are whole 16-byte vectors).  The caller keeps ownership and must keep them
- * alive while bound; DtoH checks write v_dev (the carry).  Rebinding
- * replaces the previous image.  CG_E_ALIGN on a broken rule. */
+ * Sec. 1.1).  a_bits_dev: n_bytes/8 bytes; v_dev: n_bytes bytes; each in
+ * device memory, managed memory, or pinned host memory mapped into the
+ * device (then read in place over the host link, with register loads).
+ * Both 16-byte aligned; n_bytes a multiple of 128 (so both arrays are whole
+ * 16-byte vectors).  The caller keeps ownership and must keep them alive
+ * while bound; DtoH checks write v_dev (the carry).  Rebinding replaces the
+ * previous image.  CG_E_ALIGN on a broken rule, CG_E_ARG for memory the
+ * device cannot read. */
 cg_status cg_bind_host_shadow(cg_ctx *ctx, const uint8_t *a_bits_dev,
                               uint8_t *v_dev, uint64_t n_bytes);
 

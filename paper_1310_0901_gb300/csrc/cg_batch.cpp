@@ -130,7 +130,7 @@ cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStrea
             [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
   c->stats.batch_plan_ns += now_ns() - t_plan;
   CG_CUDA(cudaMemcpyAsync(c->b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
-  B.tma = c->cfg.scan_engine != 1;
+  B.tma = c->cfg.scan_engine != 1 && !c->img_on_host;
   int per_sm = (int)c->cfg.batch_ctas_per_sm;
   if (per_sm <= 0) per_sm = B.tma ? 1 : 8;
   B.grid = c->sm_count * per_sm;

@@ -439,6 +439,7 @@ struct cg_ctx {
   int sm_count = 1;
   cgi::Image img{nullptr, nullptr, 0};
   bool img_bound = false;
+  bool img_on_host = false;  // image in mapped pinned host memory: register engine
   cgi::ShadowArena arena;
   cgi::AllocTable table;
   cgi::SingleScratch *d_scratch = nullptr;

@@ -297,6 +297,29 @@ cg_status cg_destroy(cg_ctx *c) {
   return CG_OK;
 }
 
+// The device's view of a pointer: device and managed memory as is, mapped
+// pinned host memory through its device pointer; anything else (pageable
+// host memory) is refused.
+static cg_status device_view(const void *p, const void **out, bool *on_host) {
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(CG_E_ARG, "pointer unknown to CUDA");
+  }
+  if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+    *out = p;
+    *on_host = false;
+    return CG_OK;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+    *out = at.devicePointer;
+    *on_host = true;
+    return CG_OK;
+  }
+  return set_error(CG_E_ARG, "host memory the device cannot read (pin and map it)");
+}
+
 cg_status cg_bind_host_shadow(cg_ctx *c, const uint8_t *a_bits_dev, uint8_t *v_dev,
                               uint64_t n_bytes) {
   if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
@@ -305,10 +328,19 @@ cg_status cg_bind_host_shadow(cg_ctx *c, const uint8_t *a_bits_dev, uint8_t *v_d
   if ((reinterpret_cast<uintptr_t>(a_bits_dev) & 15) || (reinterpret_cast<uintptr_t>(v_dev) & 15))
     return set_error(CG_E_ALIGN, "host shadow arrays must be 16-byte aligned");
   if (n_bytes % 128) return set_error(CG_E_ALIGN, "host image size must be a multiple of 128");
-  c->img.a_bits = a_bits_dev;
-  c->img.v = v_dev;
+  const void *a = a_bits_dev, *v = v_dev;
+  bool a_host = false, v_host = false;
+  if (n_bytes) {
+    CG_TRY(device_view(a_bits_dev, &a, &a_host));
+    CG_TRY(device_view(v_dev, &v, &v_host));
+    if ((reinterpret_cast<uintptr_t>(a) & 15) || (reinterpret_cast<uintptr_t>(v) & 15))
+      return set_error(CG_E_ALIGN, "host shadow arrays must be 16-byte aligned");
+  }
+  c->img.a_bits = static_cast<const uint8_t *>(a);
+  c->img.v = const_cast<uint8_t *>(static_cast<const uint8_t *>(v));
   c->img.n = n_bytes;
   c->img_bound = true;
+  c->img_on_host = a_host || v_host;
   return CG_OK;
 }
 
@@ -477,7 +509,7 @@ static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, boo
                             cudaMemcpyDeviceToDevice, st));
     job.dev_src = reinterpret_cast<uint64_t>(c->stage.p);
   }
-  if (c->cfg.scan_engine == 1)
+  if (c->cfg.scan_engine == 1 || c->img_on_host)  // bulk copies read device memory only
     CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
   else
     CG_CUDA(launch_scan_single_tma(c->img, job, ri, c->d_scratch, out,

@@ -77,6 +77,15 @@ extern "C" cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, u
     if (host_n % 128) return fail(CG_E_ALIGN, "host image size must be a multiple of 128");
     if (host_off > host_n || n > host_n - host_off)
       return fail(CG_E_HOST_RANGE, "host range outside the host image");
+    for (const void *p : {static_cast<const void *>(a_bits_dev), static_cast<const void *>(host_v_dev)}) {
+      cudaPointerAttributes at{};
+      if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CG_E_ARG, "host image pointer unknown to CUDA");
+      }
+      if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(CG_E_ARG, "the host image must be in device memory for cg_scan_noalloc");
+    }
   }
   const bool has_src = kind != CG_HTOD && dev_src_shadow != nullptr;
   const bool has_dst = kind != CG_DTOH && dev_dst_shadow != nullptr;

@@ -446,7 +446,8 @@ struct ServeEngine {
       std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
       for (uint64_t i = 0; i < n; i++) ho[fill[lvl[i]]++] = (uint32_t)i;
     }
-    const uint64_t quantum = scan_tma_tile_bytes();
+    const uint64_t quantum =
+        (c->img_on_host || c->cfg.scan_engine == 1) ? 2048 : scan_tma_tile_bytes();
     uint64_t seg_bytes = (uint64_t)(c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib : 64) * 1024;
     seg_bytes = std::max<uint64_t>(quantum, (seg_bytes + quantum - 1) / quantum * quantum);
     const uint64_t seg_chunks = seg_bytes / 16;
@@ -515,8 +516,12 @@ struct ServeEngine {
         CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(stages[sci].off),
                                 reinterpret_cast<const void *>(stages[sci].src), stages[sci].n,
                                 cudaMemcpyDeviceToDevice, s));
-      CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
-                                    c->sm_count, R.err.p, s));
+      if (c->img_on_host || c->cfg.scan_engine == 1)
+        CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
+                                  c->sm_count * 8, s));
+      else
+        CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
+                                      c->sm_count, R.err.p, s));
       kernels++;
     }
     CG_CUDA(launch_finalize(plan, R.reps.p, R.counts.p, R.blocksums.p, kFinalizeItems, s));

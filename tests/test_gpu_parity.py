@@ -245,3 +245,31 @@ def test_large_table_batch(cg):
     assert total == len(orecs) and U.reports_from_array(recs) == orecs
     gv = v.cpu().numpy()
     assert np.array_equal(gv, orc.read_host_v())
+
+
+def test_host_resident_image(cg):
+    """An image in pinned host memory is read in place (register engine);
+    results equal the oracle's.  Pageable host memory is refused."""
+    import torch
+    w = S.small(6)
+    n = w.image.n
+    a_h = torch.from_numpy(w.image.a_bits[: n // 8].copy()).pin_memory()
+    v_h = torch.from_numpy(w.image.v.copy()).pin_memory()
+    ctx = cg.Context()
+    ctx.bind_host_shadow(a_h, v_h)
+    orc = O.Oracle(w.image.a_bits, w.image.v)
+    bases, sizes = U.sorted_table(w.table)
+    assert not ctx.register_allocs(bases, sizes).any()
+    for b, s_ in zip(bases, sizes):
+        assert orc.register_alloc(int(b), int(s_)) == 0
+    _run_single(ctx, orc, w.reqs[:400], "host image/single")
+    st, reps, _, _, _ = ctx.check_batch(w.reqs[400:])
+    st_o, oreps, _ = orc.check_batch(w.reqs[400:])
+    assert st == st_o == 0
+    for i, (g, o) in enumerate(zip(U.reports_from_array(reps), oreps)):
+        U.assert_same_report(g, o, f"host image/batch {i}")
+    torch.cuda.synchronize()
+    assert np.array_equal(v_h.numpy(), orc.read_host_v())
+    pageable = torch.zeros(n, dtype=torch.uint8)
+    st = cg.cg_bind_host_shadow(ctx.handle, a_h.data_ptr(), pageable.data_ptr(), n)
+    assert st == -1
