@@ -1,6 +1,8 @@
 // cg_scan_tma.cu -- the single-copy scan with its loads on the TMA engine.
 //
-// Every warp runs its own pipeline of kNS shared-memory stages.  Lane 0
+// Every warp runs its own pipeline of kNS shared-memory stages (16 warps
+// per CTA, 2 stages of 4 KiB tiles: 16 warps hide the classification
+// latency on error-dense data, 2 stages keep enough bytes in flight).  Lane 0
 // issues 1-D bulk copies (cp.async.bulk, completion counted on an mbarrier)
 // of the next tiles' V and A bytes; all 32 lanes wait on the stage's
 // mbarrier, classify and carry the tile out of shared memory, and hand the
@@ -21,10 +23,10 @@
 #define CG_TMA_R 8
 #endif
 #ifndef CG_TMA_NS
-#define CG_TMA_NS 4
+#define CG_TMA_NS 2
 #endif
 #ifndef CG_TMA_WARPS
-#define CG_TMA_WARPS 8
+#define CG_TMA_WARPS 16
 #endif
 
 namespace cgi {
@@ -228,6 +230,18 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     }
   }
   single_epilogue(la, scr, ri, out, err);
+}
+
+// CTAs of a TMA kernel that fit on one SM (shared memory bound).
+template <typename K>
+static int tma_ctas_per_sm(K kernel) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kTW * 32, kSmemBytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
 }
 
 // ------------------------------------------------ batched: one level
@@ -435,16 +449,17 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
                                   unsigned int *err_flag, cudaStream_t st) {
   if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int per_sm = 0;
+  if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(scan_level_tma_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    per_sm = tma_ctas_per_sm(scan_level_tma_kernel);
   }
+  const uint64_t cap = (uint64_t)max_ctas * (uint64_t)per_sm;  // max_ctas counts SMs
   const uint64_t ctas = (n_segs + kTW - 1) / kTW;
-  const unsigned g = (unsigned)(ctas < (uint64_t)max_ctas ? ctas : (uint64_t)max_ctas);
+  const unsigned g = (unsigned)(ctas < cap ? ctas : cap);
   scan_level_tma_kernel<<<g, kTW * 32, kSmemBytes, st>>>(img, p, pos_begin, pos_end, n_segs,
                                                          err_flag);
   return cudaGetLastError();
@@ -453,15 +468,17 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
 template <uint32_t KIND, bool CARRY>
 static cudaError_t launch_tma_t(const Image &img, const ScanJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int grid, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static int per_sm = 0;
+  if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(scan_single_tma_kernel<KIND, CARRY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    per_sm = tma_ctas_per_sm(scan_single_tma_kernel<KIND, CARRY>);
   }
-  scan_single_tma_kernel<KIND, CARRY><<<grid, kTW * 32, kSmemBytes, st>>>(img, job, ri, scr, out);
+  // `grid` counts SM-sized units of work; fill every resident CTA slot
+  scan_single_tma_kernel<KIND, CARRY><<<grid * per_sm, kTW * 32, kSmemBytes, st>>>(img, job, ri,
+                                                                                scr, out);
   return cudaGetLastError();
 }
 
@@ -485,7 +502,8 @@ cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const R
 uint32_t scan_tma_tile_bytes() { return 512u * kR; }
 
 int scan_single_tma_grid(int sm_count, uint64_t n) {
-  // tiles of kR rows; one CTA (kTW warps) per SM at most
+  // tiles of kR rows over kTW-warp CTAs, in SM units (the launch multiplies
+  // by the CTAs resident per SM)
   const uint64_t tiles = ((n + 30) / 16 / 32 + kR) / kR + 1;
   const uint64_t ctas = (tiles + kTW - 1) / kTW;
   return (int)(ctas < (uint64_t)sm_count ? (ctas ? ctas : 1) : (uint64_t)sm_count);
