@@ -54,13 +54,14 @@ __device__ __forceinline__ uint4 funnel16(uint4 a, uint4 b, int r) {
   return o;
 }
 
-// 4-bit mask of the nonzero bytes of x (bit k <-> byte k)
+// 4-bit mask of the nonzero bytes of x (bit k <-> byte k).  Bit 7 of each
+// byte of t is set iff the byte is nonzero: adding 0x7F to its low 7 bits
+// carries into bit 7 unless they are all zero (and never past it), OR-ing
+// x adds the byte's own bit 7.  The multiply then moves bits 7, 15, 23 and
+// 31 to bits 28..31 (partial products land on distinct bits: no carries).
 __device__ __forceinline__ uint32_t nz4(uint32_t x) {
-  uint32_t t = x | (x >> 4);
-  t |= t >> 2;
-  t |= t >> 1;
-  t &= 0x01010101u;                       // bit 0 of each byte = OR of its bits
-  return ((t * 0x00204081u) >> 21) & 0xFu;  // gather bits 0, 8, 16, 24
+  const uint32_t t = (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+  return (t * 0x00204081u) >> 28;
 }
 __device__ __forceinline__ uint32_t nz16(uint4 v) {
   return nz4(v.x) | (nz4(v.y) << 4) | (nz4(v.z) << 8) | (nz4(v.w) << 12);
@@ -187,17 +188,19 @@ __device__ __forceinline__ void lane_acc_reset(LaneAcc &la) {
 // V = the input V window, a16 = its A bits (all ones for device->device).
 template <uint32_t KIND, bool CARRY>
 __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uint32_t a16,
-                                           LaneAcc &la) {
-  const int64_t i0 = 16 * c - g.ax;
-  const uint32_t vm = valid_mask(i0, g.n);
+                                           uint32_t vm, LaneAcc &la) {
+  // vm: bytes of this chunk inside the copy (0xFFFF for interior tiles)
   const bool clean = ((V.x | V.y | V.z | V.w) == 0u) && (((a16 | ~vm) & 0xFFFFu) == 0xFFFFu);
   if (!clean && vm) {
     const uint32_t un = vm & ~a16 & 0xFFFFu;
     const uint32_t ud = vm & a16 & nz16(V);
     la.un += __popc(un);
     la.ud += __popc(ud);
-    if (un && la.fun == kNone) la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
-    if (ud && la.fud == kNone) la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
+    if ((un && la.fun == kNone) || (ud && la.fud == kNone)) {
+      const int64_t i0 = 16 * c - g.ax;
+      if (un && la.fun == kNone) la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
+      if (ud && la.fud == kNone) la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
+    }
   }
   if (CARRY && vm) {
     uint8_t *p = g.out_al + 16 * c;

@@ -45,7 +45,8 @@ __device__ __forceinline__ void do_rows(const Geo &g, const uint32_t *A32, int64
 #pragma unroll
   for (int u = 0; u < kU; u++) {
     if (u >= nrows) break;
-    chunk_step<KIND, CARRY>(g, (row0 + u) * 32 + lane, v[u], a[u], la);
+    const int64_t c = (row0 + u) * 32 + lane;
+    chunk_step<KIND, CARRY>(g, c, v[u], a[u], valid_mask(16 * c - g.ax, g.n), la);
   }
 }
 

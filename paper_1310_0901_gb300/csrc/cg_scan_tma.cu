@@ -147,6 +147,8 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   const uint4 *vs = reinterpret_cast<const uint4 *>(sp);
   const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
   const int64_t aorig = floor16((g.hb0 + 16 * c0) >> 3);
+  const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
+  const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
 #pragma unroll 4
   for (int u = 0; u < kR; u++) {
     const int k = 32 * u + lane;
@@ -165,7 +167,8 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
       const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
       a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
     }
-    chunk_step<KIND, CARRY>(g, c, V, a16, la);
+    const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * c - g.ax, g.n);
+    chunk_step<KIND, CARRY>(g, c, V, a16, vm, la);
   }
 }
 
