@@ -145,7 +145,7 @@ def run_cg(args, world, rank, local):
     bytes_per_step = sum(int(q["n"]) for q in w.reqs)
     stream = torch.cuda.current_stream(dev)
     sh = stream.cuda_stream
-    rep_dev = torch.zeros((len(reqs), 112), dtype=torch.uint8, device=dev)
+    rep_dev = torch.zeros((len(reqs), cg.REPORT_DTYPE.itemsize), dtype=torch.uint8, device=dev)
     import ctypes
 
     def step_async(events=None):
@@ -220,7 +220,7 @@ def run_cg(args, world, rank, local):
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - s0) * 1e3
         h2d = int(sum(int(q["n"]) + int(q["n"]) // 8 for q in w.reqs))
-        d2h = 112 * len(reqs)
+        d2h = cg.REPORT_DTYPE.itemsize * len(reqs)
     if e2e_ms is not None:
         e2e_ms = reduce_max(e2e_ms, dev)
     # end to end, in place: the kernel reads the pinned host shadow over the
@@ -427,6 +427,7 @@ def run_serving(args):
         "latency_us_checks_le_4KiB": {f"p{p}": round(float(np.percentile(lat_us[small], p)), 1)
                                       for p in (50, 99)},
         "all_ok": bool(ok.all()), "span_s": round(span_s, 3),
+        "concurrent_access_findings": int(((res["report"]["flags"] & (1 << 8)) != 0).sum()),
         "offered_gb_per_s": round(float(sizes.sum()) / (args.serve_seconds * 1e9), 1),
         "serve_stats": stats,
     }

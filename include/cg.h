@@ -81,7 +81,8 @@ typedef int32_t cg_status;
 #define CG_F_HOST_UNDEF (1u << 5)    /* HtoD: undefined host bytes sent */
 #define CG_F_DEV_UNDEF_SRC (1u << 6) /* DtoH/DtoD: undefined device bytes (warning) */
 #define CG_F_DTOD_OVERLAP (1u << 7)  /* DtoD src and dst overlap (warning) */
-#define CG_NFLAGS 8
+#define CG_F_CONCURRENT (1u << 8)    /* served: races a copy of another client (warning) */
+#define CG_NFLAGS 9
 /* Not a finding: set when a kernel's bounded wait for its own data ran out;
  * the counts of such a report are not valid (cg_check_copy then returns
  * CG_E_TIMEOUT).  Never produces a record. */
@@ -129,7 +130,8 @@ typedef struct cg_report {
   uint64_t alloc_size_dst;
   uint64_t alloc_base_src;
   uint64_t alloc_size_src;
-} cg_report; /* 112 bytes */
+  int64_t race_seq; /* CONCURRENT: seq of the copy it races with, else -1 */
+} cg_report; /* 120 bytes */
 
 /* One error or warning, emitted per set report flag in (req, cls) order.
  *   UNALLOC_*:     off 0,            count n,             found 0
@@ -137,7 +139,9 @@ typedef struct cg_report {
  *   HOST_UNADDR:   off first unaddr, count n_unaddr,      found n - n_unaddr
  *   HOST_UNDEF / DEV_UNDEF_SRC: off first undef, count n_undef, found n_good
  *   DTOD_OVERLAP:  off dst - src,    count overlap bytes, found 0
- * severity: 0 error, 1 warning (DEV_UNDEF_SRC unless strict; DTOD_OVERLAP). */
+ *   CONCURRENT:    off race_seq,     count n,             found 0
+ * severity: 0 error, 1 warning (DEV_UNDEF_SRC unless strict; DTOD_OVERLAP;
+ * CONCURRENT). */
 typedef struct cg_err_record {
   uint64_t req;
   uint32_t cls;
@@ -351,8 +355,16 @@ cg_status cg_choose_segment(const cg_ctx *ctx, const cg_copy *reqs, uint64_t nre
  * Admission stops while the bytes of admitted, unfinished checks would
  * exceed budget_bytes.  Every result equals the one the same request gets
  * when all requests are applied one by one in seq order (cg_check_copy,
- * cg_register_alloc, cg_free, cg_mark_*).  Sec. 2's wrappers check each
- * call as it happens; serving keeps that order while batching the work. */
+ * cg_register_alloc, cg_free, cg_mark_*), except for one finding only
+ * serving can make: the paper's concurrent accesses of several threads
+ * (Sec. 2 itemize).  A check r gets CG_F_CONCURRENT (a warning; race_seq =
+ * the smallest such seq) when a copy q of another client, admitted before
+ * r, had not yet returned its result when r was submitted (q.done_ns >
+ * r.submit_ns), and one of them writes data the other reads or writes:
+ * the data ranges [dst, dst+n) written and [src, src+n) read, host offsets
+ * and device addresses apart, of copies whose device ranges are valid.
+ * Sec. 2's wrappers check each call as it happens; serving keeps that
+ * order while batching the work. */
 
 #define CG_OP_CHECK 1u
 #define CG_OP_ALLOC 2u          /* dst = base, n = size */
@@ -377,7 +389,7 @@ typedef struct cg_result {
   uint64_t submit_ns; /* steady clock at cg_submit */
   uint64_t done_ns;   /* steady clock when the result became visible */
   cg_report report;   /* CG_OP_CHECK */
-} cg_result; /* 144 bytes */
+} cg_result; /* 152 bytes */
 
 typedef struct cg_serve_config {
   uint32_t clients;       /* client rings, 1..64 (0 = 8) */

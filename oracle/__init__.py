@@ -27,7 +27,7 @@ HTOD, DTOH, DTOD = 1, 2, 3
 BYTE_GOOD, BYTE_UNADDR, BYTE_UNDEF = 0, 1, 2
 FLAG_NAMES = [
     "UNALLOC_DST", "UNALLOC_SRC", "OVERRUN_DST", "OVERRUN_SRC",
-    "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP",
+    "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP", "CONCURRENT",
 ]
 FLAGS = {name: 1 << i for i, name in enumerate(FLAG_NAMES)}
 FREE_NAMES = {0: "OK", 1: "UNKNOWN", 2: "DOUBLE", 3: "INTERIOR"}
@@ -45,7 +45,7 @@ class OrReport(ctypes.Structure):
         ("expected", ctypes.c_uint64), ("found_dst", ctypes.c_uint64),
         ("found_src", ctypes.c_uint64), ("alloc_base_dst", ctypes.c_uint64),
         ("alloc_size_dst", ctypes.c_uint64), ("alloc_base_src", ctypes.c_uint64),
-        ("alloc_size_src", ctypes.c_uint64),
+        ("alloc_size_src", ctypes.c_uint64), ("race_seq", ctypes.c_int64),
     ]
 
 
@@ -109,6 +109,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.or_read_dev_v.restype = i32
     lib.or_live_count.argtypes = [vp]
     lib.or_live_count.restype = u64
+    lib.or_races.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, vp]
+    lib.or_races.restype = u64
     return lib
 
 
@@ -225,3 +227,22 @@ def emit_records(reports: list[dict], reqs: np.ndarray, strict: bool = False,
     lib.or_emit_records(ctypes.addressof(reps), k.ctypes.data, d.ctypes.data, s.ctypes.data,
                         n.ctypes.data, nreq, int(strict), ctypes.addressof(out), total)
     return [{f: getattr(out[i], f) for f in RECORD_FIELDS} for i in range(total)]
+
+
+def races(reqs: np.ndarray, client: np.ndarray, submit_ns: np.ndarray, done_ns: np.ndarray,
+          moved: np.ndarray, lib: ctypes.CDLL | None = None) -> np.ndarray:
+    """race_seq per request of a served trace given in seq order (see or_races)."""
+    lib = lib if lib is not None else load()
+    n = len(reqs)
+    k = np.ascontiguousarray(reqs["kind"], dtype=np.uint32)
+    d = np.ascontiguousarray(reqs["dst"], dtype=np.uint64)
+    s = np.ascontiguousarray(reqs["src"], dtype=np.uint64)
+    nn = np.ascontiguousarray(reqs["n"], dtype=np.uint64)
+    c = np.ascontiguousarray(client, dtype=np.uint32)
+    sub = np.ascontiguousarray(submit_ns, dtype=np.uint64)
+    done = np.ascontiguousarray(done_ns, dtype=np.uint64)
+    mv = np.ascontiguousarray(moved, dtype=np.uint8)
+    out = np.full(max(1, n), -1, dtype=np.int64)
+    lib.or_races(k.ctypes.data, d.ctypes.data, s.ctypes.data, nn.ctypes.data, c.ctypes.data,
+                 sub.ctypes.data, done.ctypes.data, mv.ctypes.data, n, out.ctypes.data)
+    return out[:n]

@@ -279,6 +279,7 @@ static int check_one(or_state *s, uint32_t kind, uint64_t dst, uint64_t src,
   r->first_bad_off = -1;
   r->first_unaddr_off = -1;
   r->first_undef_off = -1;
+  r->race_seq = -1;
   r->expected = n;
   if (n == 0) return OR_OK; /* R9 */
 
@@ -422,17 +423,59 @@ uint64_t or_emit_records(const or_report *reps, const uint32_t *kind,
         rec.count = r->n_undef;
         rec.found = r->n_good;
         if (f == OR_F_DEV_UNDEF_SRC && !strict) rec.severity = 1;
-      } else { /* OR_F_DTOD_OVERLAP */
+      } else if (f == OR_F_DTOD_OVERLAP) {
         uint64_t dist = src[i] <= dst[i] ? dst[i] - src[i] : src[i] - dst[i];
         rec.off = (int64_t)(dst[i] - src[i]);
         rec.count = n[i] - dist;
         rec.found = 0;
         rec.severity = 1;
         (void)kind;
+      } else { /* OR_F_CONCURRENT */
+        rec.off = r->race_seq;
+        rec.count = n[i];
+        rec.found = 0;
+        rec.severity = 1;
       }
       if (k < cap) out[k] = rec;
       k++;
     }
   }
   return k;
+}
+
+/* ------------------------------------------------------------- races */
+
+/* [a, a+na) and [b, b+nb) share a byte */
+static int meets(uint64_t a, uint64_t na, uint64_t b, uint64_t nb) {
+  return a < b + nb && b < a + na;
+}
+
+/* Which address space each side of a copy lives in: 0 host, 1 device. */
+static int dst_space(uint32_t kind) { return kind == OR_DTOH ? 0 : 1; }
+static int src_space(uint32_t kind) { return kind == OR_HTOD ? 0 : 1; }
+
+uint64_t or_races(const uint32_t *kind, const uint64_t *dst, const uint64_t *src,
+                  const uint64_t *n, const uint32_t *client, const uint64_t *submit_ns,
+                  const uint64_t *done_ns, const uint8_t *moved, uint64_t count,
+                  int64_t *race_seq) {
+  uint64_t flagged = 0;
+  for (uint64_t r = 0; r < count; r++) {
+    race_seq[r] = -1;
+    if (!moved[r] || n[r] == 0) continue;
+    for (uint64_t q = 0; q < r; q++) {
+      if (!moved[q] || n[q] == 0 || client[q] == client[r]) continue;
+      if (!(done_ns[q] > submit_ns[r])) continue; /* q finished before r was sent */
+      /* q writes what r reads, q writes what r writes, q reads what r writes */
+      int hit = 0;
+      if (dst_space(kind[q]) == src_space(kind[r]) && meets(dst[q], n[q], src[r], n[r])) hit = 1;
+      if (dst_space(kind[q]) == dst_space(kind[r]) && meets(dst[q], n[q], dst[r], n[r])) hit = 1;
+      if (src_space(kind[q]) == dst_space(kind[r]) && meets(src[q], n[q], dst[r], n[r])) hit = 1;
+      if (hit) {
+        race_seq[r] = (int64_t)q;
+        flagged++;
+        break;
+      }
+    }
+  }
+  return flagged;
 }

@@ -44,7 +44,8 @@ extern "C" {
 #define OR_F_HOST_UNDEF   (1u << 5)
 #define OR_F_DEV_UNDEF_SRC (1u << 6)
 #define OR_F_DTOD_OVERLAP (1u << 7)
-#define OR_NFLAGS 8
+#define OR_F_CONCURRENT (1u << 8)
+#define OR_NFLAGS 9
 
 /* free verdicts */
 #define OR_FREE_OK       0u
@@ -79,6 +80,7 @@ typedef struct or_report {
   uint64_t alloc_size_dst;
   uint64_t alloc_base_src;
   uint64_t alloc_size_src;
+  int64_t race_seq;
 } or_report;
 
 typedef struct or_record {
@@ -114,6 +116,17 @@ uint64_t or_emit_records(const or_report *reps, const uint32_t *kind,
                          const uint64_t *dst, const uint64_t *src,
                          const uint64_t *n, uint64_t nreq, int strict,
                          or_record *out, uint64_t cap);
+
+/* Concurrent-access races of a served trace (Sec. 2 itemize: concurrent
+ * accesses when several threads are used), requests given in seq order:
+ * race_seq[r] = the smallest q < r such that client[q] != client[r],
+ * done_ns[q] > submit_ns[r], both copies moved data (moved[q], moved[r]:
+ * their device ranges were valid) and one writes what the other reads or
+ * writes; -1 if none.  Returns the number of flagged requests. */
+uint64_t or_races(const uint32_t *kind, const uint64_t *dst, const uint64_t *src,
+                  const uint64_t *n, const uint32_t *client, const uint64_t *submit_ns,
+                  const uint64_t *done_ns, const uint8_t *moved, uint64_t count,
+                  int64_t *race_seq);
 
 /* state read-back */
 int or_read_host_v(const or_state *s, uint64_t off, uint64_t n, uint8_t *out);

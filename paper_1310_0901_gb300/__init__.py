@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(PKG, "libcg.so")
 HTOD, DTOH, DTOD = 1, 2, 3
 BYTE_GOOD, BYTE_UNADDR, BYTE_UNDEF = 0, 1, 2
 FLAG_NAMES = ["UNALLOC_DST", "UNALLOC_SRC", "OVERRUN_DST", "OVERRUN_SRC",
-              "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP"]
+              "HOST_UNADDR", "HOST_UNDEF", "DEV_UNDEF_SRC", "DTOD_OVERLAP", "CONCURRENT"]
 FLAGS = {n: 1 << i for i, n in enumerate(FLAG_NAMES)}
 FREE_NAMES = {0: "OK", 1: "UNKNOWN", 2: "DOUBLE", 3: "INTERIOR"}
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_KIND", -3: "E_HOST_RANGE", -4: "E_ZERO_SIZE",
@@ -43,7 +43,7 @@ class cg_report(ctypes.Structure):
                 ("first_unaddr_off", i64), ("first_undef_off", i64), ("n_good", u64),
                 ("n_unaddr", u64), ("n_undef", u64), ("expected", u64), ("found_dst", u64),
                 ("found_src", u64), ("alloc_base_dst", u64), ("alloc_size_dst", u64),
-                ("alloc_base_src", u64), ("alloc_size_src", u64)]
+                ("alloc_base_src", u64), ("alloc_size_src", u64), ("race_seq", i64)]
 
 
 class cg_err_record(ctypes.Structure):
@@ -60,7 +60,7 @@ class cg_config(ctypes.Structure):
 
 class cg_stats(ctypes.Structure):
     _fields_ = [("checks", u64), ("bytes_checked", u64), ("batches", u64), ("levels", u64),
-                ("kernels", u64), ("errors", u64 * 8), ("live_allocs", u64),
+                ("kernels", u64), ("errors", u64 * 9), ("live_allocs", u64),
                 ("shadow_bytes", u64), ("batch_ns", u64), ("batch_plan_ns", u64),
                 ("batch_lookup_ns", u64)]
 
@@ -98,10 +98,10 @@ RECORD_DTYPE = np.dtype([(f, "<i8" if t is i64 else ("<u4" if t is u32 else "<u8
                          for f, t in cg_err_record._fields_])
 RESULT_DTYPE = np.dtype([("seq", "<u8"), ("status", "<i4"), ("verdict", "<u4"),
                          ("submit_ns", "<u8"), ("done_ns", "<u8"), ("report", REPORT_DTYPE)])
-assert ctypes.sizeof(cg_copy) == 32 and ctypes.sizeof(cg_report) == 112
+assert ctypes.sizeof(cg_copy) == 32 and ctypes.sizeof(cg_report) == 120
 assert ctypes.sizeof(cg_err_record) == 48
-assert ctypes.sizeof(cg_request) == 32 and ctypes.sizeof(cg_result) == 144
-assert REPORT_DTYPE.itemsize == 112 and RECORD_DTYPE.itemsize == 48
+assert ctypes.sizeof(cg_request) == 32 and ctypes.sizeof(cg_result) == 152
+assert REPORT_DTYPE.itemsize == 120 and RECORD_DTYPE.itemsize == 48
 
 # (name, restype, argtypes) of every entry point declared in include/cg.h
 SIGNATURES = [

@@ -98,6 +98,7 @@ CG_HD void assemble_report(cg_report *r, const RangeInfo &ri, const Acc &a) {
   r->alloc_size_dst = ri.size_dst;
   r->alloc_base_src = ri.base_src;
   r->alloc_size_src = ri.size_src;
+  r->race_seq = -1;
   r->n_unaddr = a.n_unaddr;
   r->n_undef = a.n_undef;
   r->n_good = ri.n - a.n_unaddr - a.n_undef;
@@ -153,10 +154,15 @@ CG_HD uint32_t write_records(const cg_report &r, const cg_copy &q, uint64_t req,
       e.count = r.n_undef;
       e.found = r.n_good;
       if (f == CG_F_DEV_UNDEF_SRC && !strict) e.severity = 1;
-    } else {  // CG_F_DTOD_OVERLAP
+    } else if (f == CG_F_DTOD_OVERLAP) {
       uint64_t dist = q.src <= q.dst ? q.dst - q.src : q.src - q.dst;
       e.off = (int64_t)(q.dst - q.src);
       e.count = q.n - dist;
+      e.found = 0;
+      e.severity = 1;
+    } else {  // CG_F_CONCURRENT
+      e.off = r.race_seq;
+      e.count = q.n;
       e.found = 0;
       e.severity = 1;
     }

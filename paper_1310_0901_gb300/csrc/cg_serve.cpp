@@ -36,7 +36,35 @@ struct ClientRing {
   alignas(64) std::atomic<uint64_t> head{0};       // next index to submit (client)
   alignas(64) std::atomic<uint64_t> taken{0};      // next index to admit (scheduler)
   alignas(64) std::atomic<uint64_t> collected{0};  // all below collected (client)
+  // 0: not inside cg_submit; 1: inside, timestamp not taken yet; else the
+  // submit timestamp being published (lower bound for the race window)
+  alignas(64) std::atomic<uint64_t> submitting{0};
 };
+
+// An admitted copy that moved data (valid device ranges), kept while a
+// later copy of another client may still race with it.
+struct RaceEntry {
+  uint64_t seq;
+  uint32_t client;
+  uint32_t kind;
+  uint64_t dst, src, n;
+  uint64_t done_ns;  // 0 while in flight
+};
+
+static bool meets(uint64_t a, uint64_t na, uint64_t b, uint64_t nb) {
+  return a < b + nb && b < a + na;
+}
+
+// q writes what r reads or writes, or reads what r writes (host offsets and
+// device addresses are separate spaces)
+static bool races_with(const RaceEntry &q, uint32_t kind, uint64_t dst, uint64_t src,
+                       uint64_t n) {
+  auto dsp = [](uint32_t k) { return k == CG_DTOH ? 0 : 1; };
+  auto ssp = [](uint32_t k) { return k == CG_HTOD ? 0 : 1; };
+  return (dsp(q.kind) == ssp(kind) && meets(q.dst, q.n, src, n)) ||
+         (dsp(q.kind) == dsp(kind) && meets(q.dst, q.n, dst, n)) ||
+         (ssp(q.kind) == dsp(kind) && meets(q.src, q.n, dst, n));
+}
 
 struct Iv {
   uint64_t a, b;
@@ -130,6 +158,7 @@ struct ServeEngine {
   uint64_t rr = 0;
   uint64_t inflight_bytes = 0;
   std::vector<Deferred> deferred;
+  std::deque<RaceEntry> window;  // seq order
   cg_status fatal = CG_OK;
 
   ServeEngine(cg_ctx *ctx, size_t nclients) : c(ctx), stats_mu(ctx->stats_mu), rings(nclients) {}
@@ -160,11 +189,19 @@ struct ServeEngine {
         std::lock_guard<std::mutex> g(stats_mu);
         for (size_t i = 0; i < r.members.size(); i++) {
           RingSlot *sl = r.members[i];
+          const int64_t race = sl->res.report.race_seq;  // set at admission
           sl->res.report = r.h_reps.p[i];
+          if (race >= 0) {
+            sl->res.report.flags |= CG_F_CONCURRENT;
+            sl->res.report.race_seq = race;
+          }
           if (ok) count_stats(c, sl->res.report);
         }
       }
-      for (RingSlot *sl : r.members) finish(sl, ok ? CG_OK : (e == cudaSuccess ? CG_E_TIMEOUT : CG_E_CUDA));
+      for (RingSlot *sl : r.members) {
+        finish(sl, ok ? CG_OK : (e == cudaSuccess ? CG_E_TIMEOUT : CG_E_CUDA));
+        mark_done(sl->res.seq, sl->res.done_ns);
+      }
       inflight_bytes -= r.bytes;
       r.busy = false;
       r.members.clear();
@@ -172,6 +209,32 @@ struct ServeEngine {
     }
     if (progress) release_deferred(done_upto());
     return progress;
+  }
+
+  // the window entry of copy `seq` (if it moved data) finished at done
+  void mark_done(uint64_t seq, uint64_t done) {
+    auto it = std::lower_bound(window.begin(), window.end(), seq,
+                               [](const RaceEntry &e, uint64_t v) { return e.seq < v; });
+    if (it != window.end() && it->seq == seq) it->done_ns = done;
+  }
+
+  // Drop finished copies that no request submitted from now on can race
+  // with (those that finished no later than every future submit time).
+  void prune_window() {
+    if (window.empty()) return;
+    uint64_t bound = now_ns();  // read before the clients' words
+    for (auto &g : rings) {
+      const uint64_t v = g.submitting.load(std::memory_order_seq_cst);
+      if (v == 1) return;  // a timestamp is being taken: keep everything
+      if (v) bound = std::min(bound, v);
+      const uint64_t t = g.taken.load(std::memory_order_relaxed);
+      if (t != g.head.load(std::memory_order_acquire))
+        bound = std::min(bound, g.slots[t & g.mask].submit_ns);
+    }
+    size_t k = 0;
+    for (size_t i = 0; i < window.size(); i++)
+      if (!(window[i].done_ns && window[i].done_ns <= bound)) window[k++] = window[i];
+    window.resize(k);
   }
 
   void release_deferred(uint64_t upto) {
@@ -263,6 +326,7 @@ struct ServeEngine {
   // whether anything was admitted.
   bool build_round(RoundSlot &R) {
     const uint64_t round_id = next_round;
+    prune_window();
     std::vector<RingSlot *> members;
     std::vector<cg_copy> copies;
     std::vector<ScanJob> jobs;
@@ -301,8 +365,8 @@ struct ServeEngine {
             cg_status s = validate(c, cq);
             if (s != CG_OK) {
               finish(sl, s);
-            } else if (!admit_check(sl, cq, members, copies, jobs, infos, modes, stages, stage_ptr,
-                                    stage_bytes, bytes)) {
+            } else if (!admit_check(sl, (uint32_t)((rr + k) % nc), cq, members, copies, jobs, infos,
+                                    modes, stages, stage_ptr, stage_bytes, bytes)) {
               // finished on the host (n == 0 or nothing readable)
             }
           } else if (q.op == CG_OP_MARK_DEFINED || q.op == CG_OP_MARK_UNDEFINED) {
@@ -335,7 +399,8 @@ struct ServeEngine {
   }
 
   // Host part of one admitted check.  Returns true if it joins the round.
-  bool admit_check(RingSlot *sl, const cg_copy &q, std::vector<RingSlot *> &members,
+  bool admit_check(RingSlot *sl, uint32_t client, const cg_copy &q,
+                   std::vector<RingSlot *> &members,
                    std::vector<cg_copy> &copies, std::vector<ScanJob> &jobs,
                    std::vector<RangeInfo> &infos, std::vector<uint8_t> &modes,
                    std::vector<StageCopy> &stages, std::vector<uint64_t> &stage_ptr,
@@ -375,11 +440,26 @@ struct ServeEngine {
       job.mode |= kModeCarry;
       if (q.kind != CG_DTOH) job.dev_dst = dsh;
     }
+    // concurrent accesses (Sec. 2 itemize): an earlier copy of another
+    // client still outstanding when this one was submitted, touching the
+    // same data
+    int64_t race = -1;
+    const bool moved = dst_ok && src_ok;
+    if (moved) {
+      for (const RaceEntry &e : window)
+        if (e.client != client && (e.done_ns == 0 || e.done_ns > sl->submit_ns) &&
+            races_with(e, q.kind, q.dst, q.src, q.n)) {
+          race = (int64_t)e.seq;
+          break;
+        }
+      window.push_back({sl->res.seq, client, q.kind, q.dst, q.src, q.n, 0});
+    }
     if (q.kind == CG_DTOD && !(job.mode & (kModeCarry | kModeReadDev))) {
       assemble_report(&sl->res.report, ri, none);
       finish(sl, CG_OK);
       return false;
     }
+    sl->res.report.race_seq = race;
     uint64_t sp = 0;
     if (overlap && (job.mode & kModeCarry)) {  // staged through the round's buffer
       stages.push_back({0, ssh, stage_bytes, q.n});
@@ -627,9 +707,14 @@ cg_status cg_submit(cg_ctx *c, uint32_t client, const cg_request *req, uint64_t 
   if (h - r.collected.load(std::memory_order_relaxed) > r.mask) return CG_E_FULL;
   RingSlot &sl = r.slots[h & r.mask];
   sl.req = *req;
-  sl.submit_ns = now_ns();
+  // the race window relies on this order: announce, then take the time
+  r.submitting.store(1, std::memory_order_seq_cst);
+  const uint64_t t = now_ns();
+  r.submitting.store(t, std::memory_order_seq_cst);
+  sl.submit_ns = t;
   sl.state.store(1, std::memory_order_relaxed);
   r.head.store(h + 1, std::memory_order_release);
+  r.submitting.store(0, std::memory_order_release);
   *ticket = ((uint64_t)client << 56) | h;
   return CG_OK;
 }

@@ -449,11 +449,47 @@ def pin_host_range_errors(lib):
     o.close()
 
 
+def pin_races(lib):
+    """Concurrent accesses (Sec. 2 itemize), scripted traces whose races are
+    known by construction: another client's copy still outstanding when
+    this one was submitted, one writing what the other reads or writes."""
+    R = np.zeros(9, S.REQ_DTYPE)
+    # q0 client 0: HtoD writes device [1000, 1100); r1 client 1 DtoH reads
+    # device [1050, 1060) while q0 is outstanding -> race with 0
+    R[0] = (HTOD, 0, 1000, 0, 100)
+    R[1] = (DTOH, 0, 0, 1050, 10)
+    # r2 client 1 reads the same device bytes after q0's result -> no race
+    R[2] = (DTOH, 0, 0, 1050, 10)
+    # r3 client 0 reads device [1020, 1030), which q0 is writing -- but q0
+    # is its own client's copy: no race with 0; it writes host [0, 10),
+    # which r1 (client 1, still outstanding) also writes -> race with 1
+    R[3] = (DTOH, 0, 0, 1020, 10)
+    # r4 client 2: HtoD reads host [500, 600), r5 client 3: HtoD reads host
+    # [550, 650): two reads -> no race; r5 writes device [7000, 7100), r4
+    # writes device [6000, 6100) -> disjoint
+    R[4] = (HTOD, 0, 6000, 500, 100)
+    R[5] = (HTOD, 0, 7000, 550, 100)
+    # r6 client 2: DtoD writes device [7050, 7060) while r5 (client 3)
+    # writes [7000, 7100) -> race with 5; its source [1000, 1010) was
+    # written by q0 long ago
+    R[6] = (DTOD, 0, 7050, 1000, 10)
+    # r7 client 1 writes host [0, 10) but did not move data -> never races
+    R[7] = (DTOH, 0, 0, 1050, 10)
+    # r8 client 3: device [1000, 1100) vs host [1000, 1100): different spaces
+    R[8] = (DTOH, 0, 1000, 99999, 10)
+    client = np.array([0, 1, 1, 0, 2, 3, 2, 1, 3], np.uint32)
+    submit = np.array([10, 20, 200, 30, 300, 310, 320, 330, 340], np.uint64)
+    done = np.array([100, 60, 250, 70, 400, 400, 420, 420, 420], np.uint64)
+    moved = np.array([1, 1, 1, 1, 1, 1, 1, 0, 1], np.uint8)
+    got = O.races(R, client, submit, done, moved, lib=lib)
+    assert got.tolist() == [-1, 0, -1, 1, -1, -1, 5, -1, -1], got.tolist()
+
+
 ALL_PINS = [
     pin_listing5, pin_htod_bytes_by_construction, pin_dtoh_bytes_by_construction,
     pin_range_bruteforce, pin_free_sequences, pin_free_sequences_reuse, pin_generator_truth,
     pin_invariants, pin_carry_roundtrip, pin_dtod_memmove, pin_records,
-    pin_host_range_errors,
+    pin_host_range_errors, pin_races,
 ]
 
 

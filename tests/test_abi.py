@@ -44,7 +44,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_struct_sizes_match_header_comments():
     assert ctypes.sizeof(cg.cg_copy) == 32
-    assert ctypes.sizeof(cg.cg_report) == 112
+    assert ctypes.sizeof(cg.cg_report) == 120
     assert ctypes.sizeof(cg.cg_err_record) == 48
     assert S.REQ_DTYPE.itemsize == 32
 

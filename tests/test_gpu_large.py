@@ -53,7 +53,7 @@ def test_large_transfer(large, idx):
     q = w.reqs[idx]
     n, dst = int(q["n"]), int(q["dst"])
     # the benchmark's call: asynchronous check, report in device memory
-    rep = torch.zeros(112, dtype=torch.uint8, device="cuda")
+    rep = torch.zeros(cg.REPORT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
     req = cg.cg_copy(int(q["kind"]), 0, dst, int(q["src"]), n)
     st = cg.cg_check_copy_async(ctx.handle, ctypes.byref(req), rep.data_ptr(),
                                 torch.cuda.current_stream().cuda_stream)

@@ -9,7 +9,10 @@ import numpy as np
 import pytest
 
 import cg_synth as S
+import oracle as O
 from tests import gpu_util as U
+
+races_found = []
 
 pytestmark = pytest.mark.gpu
 
@@ -76,15 +79,34 @@ def test_served_results_equal_alone(cg, streams, budget, max_round):
     # replay alone, in seq order, on a fresh context and in the oracle
     ctx2, orc, (a2, v2) = U.make_pair(w.image, w.table)
     names = cg.REPORT_DTYPE.names
-    for i in np.argsort(res["seq"]):
+    order = np.argsort(res["seq"])
+    alone = {}
+    for i in order:
         q = tr.reqs[i]
         st, verdict, rep = _apply_alone(cg, ctx2, orc, q)
         assert int(res["status"][i]) == st, (i, q, int(res["status"][i]), st)
         if verdict is not None:
             assert cg.FREE_NAMES[int(res["verdict"][i])] == verdict, (i, q)
         if rep is not None and st == 0:
-            got = {k: int(res["report"][i][k]) for k in names}
-            U.assert_same_report(got, rep, f"served request {i} (seq {int(res['seq'][i])})")
+            alone[i] = rep
+    # the concurrent-access class: the oracle's definition over the recorded
+    # submit and result times (copies that moved data: valid device ranges)
+    dev_fail = sum(O.FLAGS[k] for k in ("UNALLOC_DST", "UNALLOC_SRC", "OVERRUN_DST",
+                                        "OVERRUN_SRC"))
+    moved = np.array([i in alone and alone[i]["expected"] > 0 and not alone[i]["flags"] & dev_fail
+                      for i in order], dtype=np.uint8)
+    race = O.races(tr.reqs[order], tr.client[order], res["submit_ns"][order],
+                   res["done_ns"][order], moved)
+    for k, i in enumerate(order):
+        if i not in alone:
+            continue
+        want = dict(alone[i])
+        if race[k] >= 0:
+            want["flags"] |= O.FLAGS["CONCURRENT"]
+            want["race_seq"] = int(race[k])
+        got = {f: int(res["report"][i][f]) for f in names}
+        U.assert_same_report(got, want, f"served request {i} (seq {int(res['seq'][i])})")
+    races_found.append(int((race >= 0).sum()))
     assert np.array_equal(v.cpu().numpy(), v2.cpu().numpy())
     assert np.array_equal(v.cpu().numpy(), orc.read_host_v())
 
@@ -113,3 +135,12 @@ def test_serving_api_edges(cg):
     assert st == 0 and r.status == -1
     ctx.serve_stop()
     assert ctx.check_copy(S.HTOD, int(w.table.base[0]), 0, 8)[0] == 0  # usable again
+
+
+def test_some_races_were_exercised():
+    """The mixes above (4 clients arriving at 4M req/s over a 1 MiB image)
+    must have produced concurrent-access findings, or the class went
+    untested."""
+    if not races_found:
+        pytest.skip("serving tests did not run")
+    assert sum(races_found) > 0, races_found

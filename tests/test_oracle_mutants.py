@@ -66,6 +66,12 @@ MUTANTS = {
         "if (ub < s->n_live && s->live[ub].base < base + size) return OR_E_OVERLAP;", ""),
     "overrun_record_count": ("rec.count = n[i] - found;", "rec.count = found;"),
     "warning_severity_lost": ("if (f == OR_F_DEV_UNDEF_SRC && !strict) rec.severity = 1;", ""),
+    "race_same_client_counts": ("if (!moved[q] || n[q] == 0 || client[q] == client[r]) continue;",
+                                "if (!moved[q] || n[q] == 0) continue;"),
+    "race_ignores_done_time": ("if (!(done_ns[q] > submit_ns[r])) continue; /* q finished before r was sent */",
+                               ""),
+    "race_reads_conflict": ("if (src_space(kind[q]) == dst_space(kind[r]) && meets(src[q], n[q], dst[r], n[r])) hit = 1;",
+                            "if (src_space(kind[q]) == src_space(kind[r]) && meets(src[q], n[q], src[r], n[r])) hit = 1;"),
     "batch_not_validated_first": (
         "    int st = validate(s, kind[i], dst[i], src[i], n[i]);\n    if (st) {",
         "    int st = 0;\n    if (st) {"),

@@ -45,7 +45,7 @@ def test_noalloc_matches_check_copy():
     a_na = torch.from_numpy(img.a_bits[: n_img // 8].copy()).cuda()
     v_na = torch.from_numpy(img.v.copy()).cuda()
     shadow = torch.full((size,), 0xFF, dtype=torch.uint8, device="cuda")  # a fresh allocation
-    reps = torch.zeros((3, 112), dtype=torch.uint8, device="cuda")
+    reps = torch.zeros((3, cg.REPORT_DTYPE.itemsize), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     sp = shadow.data_ptr()
 
