@@ -34,6 +34,7 @@ FREE_NAMES = {0: "OK", 1: "UNKNOWN", 2: "DOUBLE", 3: "INTERIOR"}
 STATUS = {0: "OK", -1: "E_ARG", -2: "E_KIND", -3: "E_HOST_RANGE",
           -4: "E_ZERO_SIZE", -5: "E_WRAP", -6: "E_OVERLAP", -7: "E_NOMEM",
           -8: "E_RANGE"}
+STATUS_CODES = {name: code for code, name in STATUS.items()}
 
 
 class OrReport(ctypes.Structure):
@@ -47,6 +48,28 @@ class OrReport(ctypes.Structure):
         ("alloc_size_dst", ctypes.c_uint64), ("alloc_base_src", ctypes.c_uint64),
         ("alloc_size_src", ctypes.c_uint64), ("race_seq", ctypes.c_int64),
     ]
+
+
+class OrSide3d(ctypes.Structure):
+    _fields_ = [
+        ("ptr", ctypes.c_uint64), ("pitch", ctypes.c_uint64), ("rows", ctypes.c_uint64),
+        ("x", ctypes.c_uint64), ("y", ctypes.c_uint64), ("z", ctypes.c_uint64),
+        ("is_array", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    ]
+
+
+class OrCopy3d(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("dst", OrSide3d), ("src", OrSide3d),
+        ("width", ctypes.c_uint64), ("height", ctypes.c_uint64), ("depth", ctypes.c_uint64),
+    ]
+
+
+def side(ptr: int, pitch: int = 0, rows: int = 0, x: int = 0, y: int = 0, z: int = 0,
+         array: bool = False) -> dict:
+    """One side of a pitched copy (see or_check_copy3d)."""
+    return dict(ptr=ptr, pitch=pitch, rows=rows, x=x, y=y, z=z, is_array=int(array))
 
 
 class OrRecord(ctypes.Structure):
@@ -109,6 +132,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.or_read_dev_v.restype = i32
     lib.or_live_count.argtypes = [vp]
     lib.or_live_count.restype = u64
+    lib.or_check_copy3d.argtypes = [vp, ctypes.POINTER(OrCopy3d), ctypes.POINTER(OrReport)]
+    lib.or_check_copy3d.restype = i32
+    lib.or_register_array.argtypes = [vp, u64, u64, u64, u64]
+    lib.or_register_array.restype = i32
+    lib.or_free_array.argtypes = [vp, u64, ctypes.POINTER(u32)]
+    lib.or_free_array.restype = i32
+    lib.or_read_array_v.argtypes = [vp, u64, u64, u64, vp]
+    lib.or_read_array_v.restype = i32
     lib.or_races.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, u64, vp]
     lib.or_races.restype = u64
     return lib
@@ -178,6 +209,29 @@ class Oracle:
         r = OrReport()
         st = self.lib.or_check_copy(self._h, kind, dst, src, n, ctypes.byref(r))
         return st, report_dict(r)
+
+    def check_copy3d(self, kind: int, dst: dict, src: dict, width: int, height: int,
+                     depth: int = 1):
+        q = OrCopy3d(kind=kind, reserved=0, dst=OrSide3d(reserved=0, **dst),
+                     src=OrSide3d(reserved=0, **src), width=width, height=height, depth=depth)
+        r = OrReport()
+        st = self.lib.or_check_copy3d(self._h, ctypes.byref(q), ctypes.byref(r))
+        return st, report_dict(r)
+
+    def register_array(self, handle: int, w: int, h: int, d: int = 1) -> int:
+        return self.lib.or_register_array(self._h, handle, w, h, d)
+
+    def free_array(self, handle: int) -> str:
+        v = ctypes.c_uint32(99)
+        st = self.lib.or_free_array(self._h, handle, ctypes.byref(v))
+        assert st == 0, st
+        return FREE_NAMES[v.value]
+
+    def read_array_v(self, handle: int, off: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint8)
+        st = self.lib.or_read_array_v(self._h, handle, off, n, out.ctypes.data if n else None)
+        assert st == 0, st
+        return out
 
     def check_batch(self, reqs: np.ndarray):
         """reqs: structured array with fields kind, dst, src, n."""

@@ -35,6 +35,15 @@
  *   R13 free: live base -> ok; inside a live allocation -> interior; a freed
  *       base not reused since -> double free; anything else -> unknown.
  *   R14 registering an allocation that overlaps a live one is refused.
+ *   R20 concurrent access (or_races): see cg_oracle.h.
+ *   R21 pitched copies: only the copied bytes are classified, in the copy's
+ *       row-major order; a linear device side must hold the whole extent
+ *       (first to one past the last copied byte) in one allocation; a device
+ *       array is keyed by its handle, bounded per dimension, and shadowed
+ *       densely in (z, y, x) order.
+ *   R22 the overlap warning of a pitched device->device copy is raised when
+ *       the two spans intersect (for arrays: the same array, spans in its
+ *       dense layout); the carry reads every source byte before writing.
  */
 #include "cg_oracle.h"
 
@@ -47,6 +56,14 @@ typedef struct {
   uint8_t *shadow; /* NULL: never written, every byte reads 0xFF (R6) */
 } live_alloc;
 
+/* Device arrays (Fig. 2: the context's second list) are keyed by handle, a
+ * namespace of their own.  Their shadow is dense and row-major (R21): byte
+ * (x, y, z) of a W x H x D array (x in bytes) is shadow[(z*H + y)*W + x]. */
+typedef struct live_array_s {
+  uint64_t handle, w, h, d;
+  uint8_t *shadow; /* NULL: never written, reads 0xFF (R6) */
+} live_array;
+
 struct or_state {
   uint64_t host_n;
   uint8_t *a_bits;
@@ -57,6 +74,10 @@ struct or_state {
   uint64_t n_live, cap_live;
   uint64_t *freed; /* sorted freed bases */
   uint64_t n_freed, cap_freed;
+  live_array *arrays; /* device arrays, unordered */
+  uint64_t n_arrays, cap_arrays;
+  uint64_t *freed_arrays; /* handles of destroyed arrays */
+  uint64_t n_freed_arrays, cap_freed_arrays;
 };
 
 /* ---------------------------------------------------------------- state */
@@ -84,6 +105,9 @@ void or_destroy(or_state *s) {
   if (!s) return;
   for (uint64_t j = 0; j < s->n_live; j++) free(s->live[j].shadow);
   free(s->live);
+  for (uint64_t j = 0; j < s->n_arrays; j++) free(s->arrays[j].shadow);
+  free(s->arrays);
+  free(s->freed_arrays);
   free(s->freed);
   free(s->a_bits);
   free(s->host_v);
@@ -384,6 +408,323 @@ int or_check_batch(or_state *s, const uint32_t *kind, const uint64_t *dst,
       if (bad_index) *bad_index = i;
       return st;
     }
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------------- pitched copies, arrays */
+
+static live_array *find_array(const or_state *s, uint64_t handle) {
+  for (uint64_t j = 0; j < s->n_arrays; j++)
+    if (s->arrays[j].handle == handle) return &s->arrays[j];
+  return NULL;
+}
+
+static int handle_freed(const or_state *s, uint64_t handle) {
+  for (uint64_t j = 0; j < s->n_freed_arrays; j++)
+    if (s->freed_arrays[j] == handle) return 1;
+  return 0;
+}
+
+int or_register_array(or_state *s, uint64_t handle, uint64_t w, uint64_t h, uint64_t d) {
+  if (!s) return OR_E_ARG;
+  if (w == 0 || h == 0 || d == 0) return OR_E_ZERO_SIZE;
+  if (h > UINT64_MAX / w || d > UINT64_MAX / (w * h)) return OR_E_WRAP;
+  if (find_array(s, handle)) return OR_E_OVERLAP;
+  if (s->n_arrays == s->cap_arrays) {
+    uint64_t cap = s->cap_arrays ? 2 * s->cap_arrays : 8;
+    live_array *p = (live_array *)realloc(s->arrays, cap * sizeof *p);
+    if (!p) return OR_E_NOMEM;
+    s->arrays = p;
+    s->cap_arrays = cap;
+  }
+  live_array *a = &s->arrays[s->n_arrays++];
+  a->handle = handle;
+  a->w = w;
+  a->h = h;
+  a->d = d;
+  a->shadow = NULL;
+  /* a re-used handle is no longer "freed" */
+  for (uint64_t j = 0; j < s->n_freed_arrays; j++)
+    if (s->freed_arrays[j] == handle) s->freed_arrays[j] = s->freed_arrays[--s->n_freed_arrays];
+  return OR_OK;
+}
+
+int or_free_array(or_state *s, uint64_t handle, uint32_t *verdict) {
+  if (!s || !verdict) return OR_E_ARG;
+  live_array *a = find_array(s, handle);
+  if (a) {
+    free(a->shadow);
+    *a = s->arrays[--s->n_arrays];
+    if (s->n_freed_arrays == s->cap_freed_arrays) {
+      uint64_t cap = s->cap_freed_arrays ? 2 * s->cap_freed_arrays : 8;
+      uint64_t *p = (uint64_t *)realloc(s->freed_arrays, cap * sizeof *p);
+      if (!p) return OR_E_NOMEM;
+      s->freed_arrays = p;
+      s->cap_freed_arrays = cap;
+    }
+    s->freed_arrays[s->n_freed_arrays++] = handle;
+    *verdict = OR_FREE_OK;
+  } else {
+    *verdict = handle_freed(s, handle) ? OR_FREE_DOUBLE : OR_FREE_UNKNOWN;
+  }
+  return OR_OK;
+}
+
+int or_read_array_v(const or_state *s, uint64_t handle, uint64_t off, uint64_t n, uint8_t *out) {
+  live_array *a = find_array(s, handle);
+  if (!a) return OR_E_RANGE;
+  const uint64_t total = a->w * a->h * a->d;
+  if (off > total || n > total - off) return OR_E_RANGE;
+  for (uint64_t i = 0; i < n; i++) out[i] = a->shadow ? a->shadow[off + i] : 0xFF;
+  return OR_OK;
+}
+
+/* One side of a 3-D copy as the checks see it. */
+typedef struct {
+  int array;          /* 1: a device array, 0: linear memory / host image */
+  live_alloc *alloc;  /* linear device side, valid range: its allocation */
+  live_array *arr;    /* array side, valid range: the array */
+  uint64_t start;     /* linear: address (host offset) of copy byte (0,0,0) */
+  uint64_t pitch;     /* bytes between rows */
+  uint64_t slice;     /* bytes between slices */
+  int ok;             /* the range check passed */
+} side3d;
+
+/* Byte (i, y, z) of the copy (x-in-bytes, row, slice, all relative to the
+ * copy's origin) on one side: a host offset, a device address, or an index
+ * into an array's dense shadow. */
+static uint64_t side_pos(const side3d *sd, uint64_t i, uint64_t y, uint64_t z) {
+  return sd->start + z * sd->slice + y * sd->pitch + i;
+}
+
+static uint8_t side_dev_v(const side3d *sd, uint64_t pos) {
+  if (sd->array) return sd->arr->shadow ? sd->arr->shadow[pos] : 0xFF;
+  return dev_v(sd->alloc, pos - sd->alloc->base);
+}
+
+static int side_materialise(side3d *sd) {
+  if (!sd->array) return materialise(sd->alloc);
+  if (sd->arr->shadow) return OR_OK;
+  const uint64_t total = sd->arr->w * sd->arr->h * sd->arr->d;
+  sd->arr->shadow = (uint8_t *)malloc(total);
+  if (!sd->arr->shadow) return OR_E_NOMEM;
+  memset(sd->arr->shadow, 0xFF, total);
+  return OR_OK;
+}
+
+static uint8_t *side_dev_byte(side3d *sd, uint64_t pos) {
+  if (sd->array) return &sd->arr->shadow[pos];
+  return &sd->alloc->shadow[pos - sd->alloc->base];
+}
+
+/* start = origin address, extent = bytes from the first to one past the last
+ * copied byte; returns OR_E_WRAP if either does not fit in 64 bits. */
+static int linear_geometry(const or_side3d *q, uint64_t w, uint64_t h, uint64_t d,
+                           uint64_t *start, uint64_t *extent, uint64_t *pitch, uint64_t *slice) {
+  const uint64_t p = q->pitch, rows = q->rows;
+  if (rows && p > UINT64_MAX / rows) return OR_E_WRAP;
+  const uint64_t sl = p * rows;
+  if ((q->z && sl && q->z > UINT64_MAX / sl) || (q->y && p && q->y > UINT64_MAX / p))
+    return OR_E_WRAP;
+  const uint64_t o1 = q->z * sl, o2 = q->y * p;
+  if (o1 > UINT64_MAX - o2 || o1 + o2 > UINT64_MAX - q->x) return OR_E_WRAP;
+  const uint64_t off = o1 + o2 + q->x;
+  if (q->ptr > UINT64_MAX - off) return OR_E_WRAP;
+  if ((d - 1) && sl && d - 1 > UINT64_MAX / sl) return OR_E_WRAP;
+  if ((h - 1) && p && h - 1 > UINT64_MAX / p) return OR_E_WRAP;
+  const uint64_t e1 = (d - 1) * sl, e2 = (h - 1) * p;
+  if (e1 > UINT64_MAX - e2 || e1 + e2 > UINT64_MAX - w) return OR_E_WRAP;
+  *start = q->ptr + off;
+  *extent = e1 + e2 + w;
+  *pitch = p;
+  *slice = sl;
+  return OR_OK;
+}
+
+static int check_side_args(const or_side3d *q, uint64_t w, uint64_t h, uint64_t d) {
+  if (q->reserved) return OR_E_ARG;
+  if (q->is_array) return OR_OK;
+  if ((h > 1 || d > 1) && q->pitch < w) return OR_E_ARG;
+  if (d > 1 && q->rows < h) return OR_E_ARG;
+  return OR_OK;
+}
+
+/* The device side of a 3-D copy: array lookup by handle with a bound per
+ * dimension, or the linear range check over the extent. */
+static int device_side3d(or_state *s, const or_side3d *q, uint64_t w, uint64_t h, uint64_t d,
+                         side3d *sd, uint64_t *found, uint64_t *abase, uint64_t *asize,
+                         uint32_t *flags, uint32_t f_unalloc, uint32_t f_overrun) {
+  memset(sd, 0, sizeof *sd);
+  if (q->is_array) {
+    sd->array = 1;
+    live_array *a = find_array(s, q->ptr);
+    *found = *abase = *asize = 0;
+    if (!a) {
+      *flags |= f_unalloc;
+      return OR_OK;
+    }
+    sd->arr = a;
+    *abase = a->handle;
+    *asize = a->w * a->h * a->d;
+    const int inside = q->x < a->w && q->y < a->h && q->z < a->d;
+    if (inside) *found = *asize - ((q->z * a->h + q->y) * a->w + q->x);
+    /* per dimension: origin + extent within the array's box (no overflow:
+     * each origin is compared before adding) */
+    const int fits = q->x <= a->w && w <= a->w - q->x && q->y <= a->h && h <= a->h - q->y &&
+                     q->z <= a->d && d <= a->d - q->z;
+    if (!fits) {
+      *flags |= f_overrun;
+      return OR_OK;
+    }
+    sd->start = (q->z * a->h + q->y) * a->w + q->x;
+    sd->pitch = a->w;
+    sd->slice = a->w * a->h;
+    sd->ok = 1;
+    return OR_OK;
+  }
+  uint64_t start, ext;
+  int st = linear_geometry(q, w, h, d, &start, &ext, &sd->pitch, &sd->slice);
+  if (st) return st;
+  sd->start = start;
+  sd->alloc = device_side(s, start, ext, found, abase, asize, flags, f_unalloc, f_overrun);
+  sd->ok = sd->alloc != NULL;
+  return OR_OK;
+}
+
+int or_check_copy3d(or_state *s, const or_copy3d *q, or_report *r) {
+  if (!s || !q || !r) return OR_E_ARG;
+  const uint32_t kind = q->kind;
+  if (kind != OR_HTOD && kind != OR_DTOH && kind != OR_DTOD) return OR_E_KIND;
+  if (q->reserved) return OR_E_ARG;
+  const uint64_t w = q->width, h = q->height, d = q->depth;
+  if (w && h && (h > UINT64_MAX / w || (d && d > UINT64_MAX / (w * h)))) return OR_E_WRAP;
+  const uint64_t n = w * h * d;
+  /* the host side is the bound image, never an array */
+  if ((kind == OR_HTOD && q->src.is_array) || (kind == OR_DTOH && q->dst.is_array))
+    return OR_E_ARG;
+  memset(r, 0, sizeof *r);
+  r->first_bad_off = -1;
+  r->first_unaddr_off = -1;
+  r->first_undef_off = -1;
+  r->race_seq = -1;
+  r->expected = n;
+  if (n == 0) return OR_OK; /* R9 */
+  int st = check_side_args(&q->dst, w, h, d);
+  if (!st) st = check_side_args(&q->src, w, h, d);
+  if (st) return st;
+  side3d host, ds, ss;
+  memset(&host, 0, sizeof host);
+  memset(&ds, 0, sizeof ds);
+  memset(&ss, 0, sizeof ss);
+  if (kind == OR_HTOD || kind == OR_DTOH) {
+    const or_side3d *hq = kind == OR_HTOD ? &q->src : &q->dst;
+    uint64_t ext;
+    st = linear_geometry(hq, w, h, d, &host.start, &ext, &host.pitch, &host.slice);
+    if (st) return st;
+    if (host.start > s->host_n || ext > s->host_n - host.start) return OR_E_HOST_RANGE;
+  }
+  if (kind == OR_HTOD || kind == OR_DTOD) {
+    st = device_side3d(s, &q->dst, w, h, d, &ds, &r->found_dst, &r->alloc_base_dst,
+                       &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_DST, OR_F_OVERRUN_DST);
+    if (st) return st;
+  }
+  if (kind == OR_DTOH || kind == OR_DTOD) {
+    st = device_side3d(s, &q->src, w, h, d, &ss, &r->found_src, &r->alloc_base_src,
+                       &r->alloc_size_src, &r->flags, OR_F_UNALLOC_SRC, OR_F_OVERRUN_SRC);
+    if (st) return st;
+  }
+  /* classification in the copy's own row-major order */
+  for (uint64_t z = 0; z < d; z++)
+    for (uint64_t y = 0; y < h; y++)
+      for (uint64_t i = 0; i < w; i++) {
+        const uint64_t o = (z * h + y) * w + i; /* linear offset */
+        uint32_t cls = OR_BYTE_GOOD;
+        if (kind == OR_HTOD) {
+          const uint64_t hp = side_pos(&host, i, y, z);
+          if (!host_a_bit(s, hp))
+            cls = OR_BYTE_UNADDR;
+          else if (s->host_v[hp] != 0)
+            cls = OR_BYTE_UNDEF;
+        } else if (kind == OR_DTOH) {
+          if (!host_a_bit(s, side_pos(&host, i, y, z)))
+            cls = OR_BYTE_UNADDR;
+          else if (ss.ok && side_dev_v(&ss, side_pos(&ss, i, y, z)) != 0)
+            cls = OR_BYTE_UNDEF;
+        } else if (ss.ok && side_dev_v(&ss, side_pos(&ss, i, y, z)) != 0) {
+          cls = OR_BYTE_UNDEF;
+        }
+        if (cls == OR_BYTE_GOOD) {
+          r->n_good++;
+          continue;
+        }
+        if (cls == OR_BYTE_UNADDR) {
+          r->n_unaddr++;
+          if (r->first_unaddr_off < 0) r->first_unaddr_off = (int64_t)o;
+        } else {
+          r->n_undef++;
+          if (r->first_undef_off < 0) r->first_undef_off = (int64_t)o;
+        }
+        if (r->first_bad_off < 0) {
+          r->first_bad_off = (int64_t)o;
+          r->first_bad_kind = cls;
+        }
+      }
+  if (r->n_unaddr) r->flags |= OR_F_HOST_UNADDR;
+  if (r->n_undef) r->flags |= kind == OR_HTOD ? OR_F_HOST_UNDEF : OR_F_DEV_UNDEF_SRC;
+  /* overlap warning (R22): the two spans, first to one past the last copied
+   * byte, intersect (arrays: the same array, spans in its dense layout) */
+  if (kind == OR_DTOD && q->dst.is_array == q->src.is_array) {
+    const int same = q->dst.is_array ? q->dst.ptr == q->src.ptr : 1;
+    if (same) {
+      uint64_t dstart, dext, sstart, sext, p0, s0;
+      if (q->dst.is_array) {
+        live_array *a = find_array(s, q->dst.ptr);
+        if (a) {
+          dstart = (q->dst.z * a->h + q->dst.y) * a->w + q->dst.x;
+          sstart = (q->src.z * a->h + q->src.y) * a->w + q->src.x;
+          dext = sext = ((d - 1) * a->h + (h - 1)) * a->w + w;
+          if (dstart < sstart + sext && sstart < dstart + dext) r->flags |= OR_F_DTOD_OVERLAP;
+        }
+      } else if (!linear_geometry(&q->dst, w, h, d, &dstart, &dext, &p0, &s0) &&
+                 !linear_geometry(&q->src, w, h, d, &sstart, &sext, &p0, &s0)) {
+        if (dstart - sstart < sext || sstart - dstart < dext) r->flags |= OR_F_DTOD_OVERLAP;
+      }
+    }
+  }
+  if (!s->carry) return OR_OK;
+  /* R11: no carry unless every device side passed its range check */
+  if (kind == OR_HTOD && ds.ok) {
+    if ((st = side_materialise(&ds))) return st;
+    for (uint64_t z = 0; z < d; z++)
+      for (uint64_t y = 0; y < h; y++)
+        for (uint64_t i = 0; i < w; i++) {
+          const uint64_t hp = side_pos(&host, i, y, z);
+          *side_dev_byte(&ds, side_pos(&ds, i, y, z)) = host_a_bit(s, hp) ? s->host_v[hp] : 0xFF;
+        }
+  } else if (kind == OR_DTOH && ss.ok) {
+    for (uint64_t z = 0; z < d; z++)
+      for (uint64_t y = 0; y < h; y++)
+        for (uint64_t i = 0; i < w; i++) {
+          const uint64_t hp = side_pos(&host, i, y, z);
+          if (host_a_bit(s, hp)) s->host_v[hp] = side_dev_v(&ss, side_pos(&ss, i, y, z));
+        }
+  } else if (kind == OR_DTOD && ss.ok && ds.ok) {
+    uint8_t *tmp = (uint8_t *)malloc(n); /* every source byte before any write */
+    if (!tmp) return OR_E_NOMEM;
+    for (uint64_t z = 0; z < d; z++)
+      for (uint64_t y = 0; y < h; y++)
+        for (uint64_t i = 0; i < w; i++)
+          tmp[(z * h + y) * w + i] = side_dev_v(&ss, side_pos(&ss, i, y, z));
+    if ((st = side_materialise(&ds))) {
+      free(tmp);
+      return st;
+    }
+    for (uint64_t z = 0; z < d; z++)
+      for (uint64_t y = 0; y < h; y++)
+        for (uint64_t i = 0; i < w; i++)
+          *side_dev_byte(&ds, side_pos(&ds, i, y, z)) = tmp[(z * h + y) * w + i];
+    free(tmp);
   }
   return OR_OK;
 }

@@ -112,6 +112,49 @@ int or_check_batch(or_state *s, const uint32_t *kind, const uint64_t *dst,
                    const uint64_t *src, const uint64_t *n, uint64_t nreq,
                    or_report *reps, uint64_t *bad_index);
 
+/* Pitched 2-D / 3-D copies and device arrays (Sec. 2: the context keeps a
+ * list of linear allocations and one of device arrays, Fig. 2; the footnote
+ * to the error list: strided host access is not an error).
+ *
+ * A copy moves depth slices of height rows of width bytes.  On each side,
+ * byte (i, y, z) of the copy (i < width, y < height, z < depth) lives at
+ *   linear memory / host image:  ptr + (z0+z)*pitch*rows + (y0+y)*pitch + x0+i
+ *   device array (ptr = handle): shadow[((z0+z)*H + y0+y)*W + x0+i]
+ * where (x0, y0, z0) = (x, y, z) of the side (x in bytes), pitch = bytes per
+ * row, rows = rows per slice, and W x H x D the array's dimensions.
+ * pitch >= width when height > 1 or depth > 1, rows >= height when depth > 1
+ * (OR_E_ARG otherwise); both still place the origin when they are not
+ * needed for the rows themselves.
+ * Linear device sides: the extent from the first to one past the last
+ * copied byte lies in one live allocation.  Array sides: the handle is a
+ * live array and x0+width <= W, y0+height <= H, z0+depth <= D; found = the
+ * array bytes from the origin's dense position to the end (0 if the origin
+ * is outside).  Only copied bytes are classified (a pitch gap never is), at
+ * offsets (z*height + y)*width + i; expected = width*height*depth.  The host
+ * side is never an array (OR_E_ARG). */
+typedef struct or_side3d {
+  uint64_t ptr; /* device address, host image offset, or array handle */
+  uint64_t pitch;
+  uint64_t rows;
+  uint64_t x, y, z;
+  uint32_t is_array;
+  uint32_t reserved;
+} or_side3d;
+
+typedef struct or_copy3d {
+  uint32_t kind;
+  uint32_t reserved;
+  or_side3d dst, src;
+  uint64_t width, height, depth;
+} or_copy3d;
+
+int or_check_copy3d(or_state *s, const or_copy3d *q, or_report *rep);
+int or_register_array(or_state *s, uint64_t handle, uint64_t w, uint64_t h, uint64_t d);
+/* verdict: OR_FREE_OK, OR_FREE_DOUBLE (destroyed before) or OR_FREE_UNKNOWN */
+int or_free_array(or_state *s, uint64_t handle, uint32_t *verdict);
+/* bytes [off, off+n) of an array's dense shadow */
+int or_read_array_v(const or_state *s, uint64_t handle, uint64_t off, uint64_t n, uint8_t *out);
+
 uint64_t or_emit_records(const or_report *reps, const uint32_t *kind,
                          const uint64_t *dst, const uint64_t *src,
                          const uint64_t *n, uint64_t nreq, int strict,

@@ -485,11 +485,384 @@ def pin_races(lib):
     assert got.tolist() == [-1, 0, -1, 1, -1, -1, 5, -1, -1], got.tolist()
 
 
+# ------------------------------------------------ pitched copies, arrays
+
+
+def _coords(w, h, d):
+    """(i, y, z) of every copied byte in the copy's row-major order."""
+    z, y, i = np.meshgrid(np.arange(d), np.arange(h), np.arange(w), indexing="ij")
+    return i.ravel(), y.ravel(), z.ravel()
+
+
+def _positions(sd, w, h, d, dims=None):
+    """Positions of every copied byte on one side, computed with numpy
+    broadcasting: linear memory / host image by pitch and rows, an array by
+    its dense (z, y, x) layout."""
+    i, y, z = _coords(w, h, d)
+    if sd["is_array"]:
+        W, H, _ = dims
+        return ((sd["z"] + z) * H + sd["y"] + y) * W + sd["x"] + i
+    return sd["ptr"] + (sd["z"] + z) * sd["pitch"] * sd["rows"] + (sd["y"] + y) * sd["pitch"] \
+        + sd["x"] + i
+
+
+def pin_strided_footnote(lib):
+    """The footnote to Sec. 2's error list: host memory read with a stride is
+    not an error.  An array of 24-byte records whose last 8 bytes are
+    padding (never written: undefined, some unaddressable) is copied as a
+    pitched copy of the 16 payload bytes per record: only the payload is
+    classified, with counts and first offsets equal to the payload's class
+    list in row-major order; a plain copy of the same span reports the
+    padding.  Host->device and device->host (destination A bits)."""
+    rng = np.random.default_rng(31)
+    rec, pay, nrec = 24, 16, 40
+    n_img = rec * nrec + 64
+    states = rng.integers(0, len(BYTE_STATES), n_img)
+    states[rng.random(n_img) < 0.85] = 4   # mostly (A=1, V=0): good payload
+    addr = np.array([BYTE_STATES[k][0] for k in states], bool)
+    v = np.array([BYTE_STATES[k][1] for k in states], np.uint8)
+    cls = np.array([BYTE_STATES[k][2] for k in states])
+    for r_ in range(nrec):  # padding: undefined, every third record unaddressable
+        pad = slice(r_ * rec + pay, (r_ + 1) * rec)
+        addr[pad] = r_ % 3 != 0
+        v[pad] = 0xFF
+        cls[pad] = O.BYTE_UNADDR if r_ % 3 == 0 else O.BYTE_UNDEF
+    a_bits, vv = _image(addr, v)
+    dev = 1 << 40
+    for h0 in (0, 5):  # record phase within the image
+        for kind in (HTOD, DTOH):
+            o = O.Oracle(a_bits, vv, lib=lib)
+            assert o.register_alloc(dev, 1 << 16) == 0
+            if kind == DTOH:  # a fully defined device source
+                assert o.mark(dev, 1 << 16, 0) == 0
+            rows = nrec - 1
+            hs = O.side(h0, pitch=rec)
+            ds = O.side(dev + 100, pitch=pay)
+            dst, src = (ds, hs) if kind == HTOD else (hs, ds)
+            st, r = o.check_copy3d(kind, dst, src, pay, rows)
+            assert st == 0
+            payload = [int(cls[h0 + y * rec + i]) for y in range(rows) for i in range(pay)]
+            if kind == DTOH:  # the device source is defined: only A matters
+                payload = [O.BYTE_UNADDR if c == O.BYTE_UNADDR else O.BYTE_GOOD for c in payload]
+            assert _sub(r, SCAN_KEYS) == _expect_from_classes(payload), (h0, kind)
+            assert r["expected"] == pay * rows
+            # the plain copy of the whole span sees the padding
+            span = (rows - 1) * rec + pay
+            if kind == HTOD:
+                st, r1 = o.check_copy(HTOD, dev + 5000, h0, span)
+            else:
+                st, r1 = o.check_copy(DTOH, h0, dev, span)
+            assert st == 0
+            whole = [int(cls[h0 + k]) for k in range(span)]
+            if kind == DTOH:
+                whole = [O.BYTE_UNADDR if c == O.BYTE_UNADDR else O.BYTE_GOOD for c in whole]
+            assert _sub(r1, SCAN_KEYS) == _expect_from_classes(whole)
+            assert r1["n_unaddr"] + r1["n_undef"] > r["n_unaddr"] + r["n_undef"]
+            o.close()
+
+
+def pin_pitched_reduces_to_1d(lib, trials: int = 120):
+    """Two special cases that are plain copies: contiguous rows and slices
+    (pitch = width, rows = height), and a single row (height = depth = 1,
+    placed at (z*rows + y)*pitch + x).  Each must give the plain copy's
+    report and leave the same shadow state, for every kind."""
+    rng = S.rng_for(37)
+    n_img = 1 << 13
+    v = rng.integers(0, 256, n_img).astype(np.uint8)
+    v[rng.random(n_img) < 0.6] = 0
+    addr = rng.random(n_img) > 0.1
+    a_bits, vv = _image(addr, v)
+    d0, d1 = 1 << 36, 1 << 37
+    for t in range(trials):
+        kind = int(rng.choice([HTOD, DTOH, DTOD]))
+        o3, o1 = O.Oracle(a_bits, vv, lib=lib), O.Oracle(a_bits, vv, lib=lib)
+        for o in (o3, o1):
+            assert o.register_alloc(d0, 4096) == 0 and o.register_alloc(d1, 4096) == 0
+            assert o.check_copy(HTOD, d0, 1000, 4096)[0] == 0  # some device state
+        if t % 2:
+            w, h, d = int(rng.integers(1, 40)), int(rng.integers(1, 6)), int(rng.integers(1, 4))
+            n = w * h * d
+            sides = [O.side(p, pitch=w, rows=h) for p in (0, 0)]
+            offs = []
+            for k in range(2):
+                dev_side = (k == 0 and kind != DTOH) or (k == 1 and kind != HTOD)
+                base = (d0 if k else d1) if dev_side else 0
+                lim = 4096 + 64 if dev_side else n_img
+                p = base + int(rng.integers(0, lim - n))
+                if kind == DTOD and k == 1 and t % 4 == 1:  # overlapping the destination
+                    p = int(np.clip(offs[0] + rng.integers(-n, n + 1), d1, d1 + 4096))
+                sides[k]["ptr"] = p
+                offs.append(p)
+        else:
+            w, h, d = int(rng.integers(1, 300)), 1, 1
+            n = w
+            sides, offs = [], []
+            for k in range(2):
+                dev_side = (k == 0 and kind != DTOH) or (k == 1 and kind != HTOD)
+                base = (d0 if k else d1) if dev_side else 0
+                pitch, rows = int(rng.integers(0, 50)), int(rng.integers(0, 5))
+                x, y, z = int(rng.integers(0, 20)), int(rng.integers(0, 4)), int(rng.integers(0, 3))
+                place = (z * rows + y) * pitch + x
+                lim = 4096 + 64 if dev_side else n_img - 64
+                p = base + int(rng.integers(0, max(1, lim - n - place)))
+                sides.append(O.side(p, pitch=pitch, rows=rows, x=x, y=y, z=z))
+                offs.append(p + place)
+        st3, r3 = o3.check_copy3d(kind, sides[0], sides[1], w, h, d)
+        st1, r1 = o1.check_copy(kind, offs[0], offs[1], n)
+        assert st3 == st1, (t, st3, st1)
+        if st1 == 0:
+            assert r3 == r1, (t, kind, r3, r1)
+            assert np.array_equal(o3.read_host_v(), o1.read_host_v())
+            for b in (d0, d1):
+                assert np.array_equal(o3.read_dev_v(b, 4096), o1.read_dev_v(b, 4096))
+        o3.close()
+        o1.close()
+
+
+def pin_pitched_bruteforce(lib, trials: int = 150):
+    """Random pitched geometry (pitch >= width, rows >= height, origins)
+    against formulations that share nothing with the oracle's loops:
+    - range: every copied byte's address belongs to the allocation of the
+      first one, set membership over the whole extent (R21 asks for the
+      extent, first to last copied byte, in one allocation);
+    - counts and first offsets: the class of each byte at its numpy-computed
+      position, in row-major order;
+    - carry: numpy fancy-index assignment (device->device reads the whole
+      source first, like memmove);
+    - overlap warning: the two spans intersect."""
+    rng = S.rng_for(41)
+    n_img = 1 << 14
+    v = rng.integers(1, 256, n_img).astype(np.uint8)
+    v[rng.random(n_img) < 0.7] = 0
+    addr = rng.random(n_img) > 0.08
+    a_bits, vv = _image(addr, v)
+    host_cls = np.where(~addr, O.BYTE_UNADDR, np.where(v != 0, O.BYTE_UNDEF, O.BYTE_GOOD))
+    base0 = 1 << 38
+    layout = [(0, 3000), (3000, 1000), (5000, 4000)]   # two touching, then a gap
+    for t in range(trials):
+        kind = int(rng.choice([HTOD, DTOH, DTOD]))
+        o = O.Oracle(a_bits, vv, lib=lib)
+        dev = np.full(9000, 0xFF, np.uint8)   # model of the modelled device space
+        for b, sz in layout:
+            assert o.register_alloc(base0 + b, sz) == 0
+        o.check_copy(HTOD, base0 + 5000, 2000, 4000)
+        dev[5000:9000] = np.where(addr[2000:6000], v[2000:6000], 0xFF)
+        w, h, d = int(rng.integers(1, 24)), int(rng.integers(1, 7)), int(rng.integers(1, 4))
+        sides = []
+        for k in range(2):
+            pitch = w + int(rng.integers(0, 20))
+            rows = h + int(rng.integers(0, 3))
+            x, y, z = (int(rng.integers(0, 8)), int(rng.integers(0, 3)), int(rng.integers(0, 2)))
+            dev_side = (k == 0 and kind != DTOH) or (k == 1 and kind != HTOD)
+            if dev_side and k == 1 and kind == DTOD and t % 2:  # near the destination
+                ptr = int(np.clip(sides[0]["ptr"] + rng.integers(-300, 300), base0, base0 + 8800))
+            elif dev_side:
+                ptr = base0 + int(rng.integers(0, 8800))
+            else:
+                ptr = int(rng.integers(0, n_img // 2))
+            sides.append(O.side(ptr, pitch=pitch, rows=rows, x=x, y=y, z=z))
+        st, r = o.check_copy3d(kind, sides[0], sides[1], w, h, d)
+        assert st == 0, (t, st)
+        pos = [_positions(sd, w, h, d) for sd in sides]
+        ok = {}
+        for k, name in ((0, "DST"), (1, "SRC")):
+            dev_side = (k == 0 and kind != DTOH) or (k == 1 and kind != HTOD)
+            if not dev_side:
+                continue
+            rel = pos[k] - base0
+            first = int(rel[0])
+            own = _owner(layout, first)
+            lo, hi = first, first + int(rel.max() - rel.min()) + 1  # the extent
+            if own is None:
+                want = "UNALLOC"
+            else:
+                want = "OK" if all(_owner(layout, a) == own for a in range(lo, hi)) else "OVERRUN"
+            got = "UNALLOC" if r["flags"] & F["UNALLOC_" + name] else \
+                "OVERRUN" if r["flags"] & F["OVERRUN_" + name] else "OK"
+            assert got == want, (t, name, got, want)
+            ok[k] = want == "OK"
+        # classes
+        if kind == HTOD:
+            c = host_cls[pos[1]]
+        elif kind == DTOH:
+            c = np.where(~addr[pos[0]], O.BYTE_UNADDR, O.BYTE_GOOD)
+            if ok[1]:
+                c = np.where((c == O.BYTE_GOOD) & (dev[pos[1] - base0] != 0), O.BYTE_UNDEF, c)
+        else:
+            c = np.full(w * h * d, O.BYTE_GOOD)
+            if ok[1]:
+                c = np.where(dev[pos[1] - base0] != 0, O.BYTE_UNDEF, O.BYTE_GOOD)
+        assert _sub(r, SCAN_KEYS) == _expect_from_classes([int(x) for x in c]), (t, kind)
+        if kind == DTOD:
+            sp = [(int(p.min()), int(p.max()) + 1) for p in pos]
+            inter = sp[0][0] < sp[1][1] and sp[1][0] < sp[0][1]
+            assert bool(r["flags"] & F["DTOD_OVERLAP"]) == inter, t
+        # carry
+        hv = v.copy()
+        if kind == HTOD and ok[0]:
+            dev[pos[0] - base0] = np.where(addr[pos[1]], v[pos[1]], 0xFF)
+        elif kind == DTOH and ok[1]:
+            src_v = dev[pos[1] - base0]
+            m = addr[pos[0]]
+            hv[pos[0][m]] = src_v[m]
+        elif kind == DTOD and ok[0] and ok[1]:
+            tmp = dev[pos[1] - base0].copy()
+            dev[pos[0] - base0] = tmp
+        assert np.array_equal(o.read_host_v(), hv), (t, kind)
+        for b, sz in layout:
+            got = o.read_dev_v(base0 + b, sz)
+            assert np.array_equal(got, dev[b:b + sz]), (t, kind, b)
+        o.close()
+
+
+def pin_arrays(lib):
+    """Device arrays (Fig. 2's second list): keyed by handle, bounds checked
+    per dimension, dense row-major shadow.  Checked against numpy block
+    assignment on a (D, H, W) array and enumeration of the copied box."""
+    rng = S.rng_for(43)
+    n_img = 1 << 13
+    v = rng.integers(0, 256, n_img).astype(np.uint8)
+    v[rng.random(n_img) < 0.5] = 0
+    addr = rng.random(n_img) > 0.05
+    a_bits, vv = _image(addr, v)
+    W, H, D = 40, 12, 5
+    A1, A2 = 0x1000, 0x2000           # handles: a namespace of their own
+    o = O.Oracle(a_bits, vv, lib=lib)
+    assert o.register_array(A1, W, H, D) == 0
+    assert o.register_array(A2, 16, 16, 1) == 0
+    assert o.register_array(A1, 4, 4, 1) == O.STATUS_CODES["E_OVERLAP"]
+    assert o.register_array(0x3000, 0, 4, 1) == O.STATUS_CODES["E_ZERO_SIZE"]
+    assert o.register_alloc(A1, 64) == 0   # the same number as an address: no clash
+    model = np.full((D, H, W), 0xFF, np.uint8)
+    assert np.array_equal(o.read_array_v(A1, 0, W * H * D), model.ravel())
+    for t in range(150):
+        x, y, z = int(rng.integers(0, W)), int(rng.integers(0, H)), int(rng.integers(0, D))
+        if t % 4:  # mostly boxes that fit, some reaching the far faces exactly
+            w, h, d = (int(rng.integers(1, W - x + 1)), int(rng.integers(1, H - y + 1)),
+                       int(rng.integers(1, D - z + 1)))
+        else:
+            w, h, d = (int(rng.integers(1, W + 4)), int(rng.integers(1, H + 3)),
+                       int(rng.integers(1, D + 2)))
+        fits = all(0 <= c < lim for (c, lim) in
+                   [(x + w - 1, W), (y + h - 1, H), (z + d - 1, D)])
+        kind = int(rng.choice([HTOD, DTOH, DTOD]))
+        arr = O.side(A1, x=x, y=y, z=z, array=True)
+        hp = int(rng.integers(w, w + 30))
+        hrows = h + int(rng.integers(0, 3))
+        host = O.side(int(rng.integers(0, 2000)), pitch=hp, rows=hrows)
+        hv = o.read_host_v()   # device->host copies change it
+        if kind == HTOD:
+            st, r = o.check_copy3d(HTOD, arr, host, w, h, d)
+            flag = "DST"
+        elif kind == DTOH:
+            st, r = o.check_copy3d(DTOH, host, arr, w, h, d)
+            flag = "SRC"
+        else:  # array -> itself at another origin
+            x2, y2, z2 = (int(rng.integers(0, W - w + 1)) if w <= W else 0,
+                          int(rng.integers(0, H - h + 1)) if h <= H else 0,
+                          int(rng.integers(0, D - d + 1)) if d <= D else 0)
+            fits2 = x2 + w <= W and y2 + h <= H and z2 + d <= D
+            st, r = o.check_copy3d(DTOD, O.side(A1, x=x2, y=y2, z=z2, array=True), arr, w, h, d)
+            flag = "SRC"
+        assert st == 0, (t, st)
+        assert bool(r["flags"] & F["OVERRUN_" + flag]) == (not fits), (t, x, y, z, w, h, d)
+        assert r["alloc_base_" + flag.lower()] == A1 and r["alloc_size_" + flag.lower()] == W * H * D
+        assert r["found_" + flag.lower()] == W * H * D - ((z * H + y) * W + x)
+        hpos = _positions(host, w, h, d)
+        if kind == HTOD and fits:
+            blk = np.where(addr[hpos], hv[hpos], 0xFF).reshape(d, h, w)
+            model[z:z + d, y:y + h, x:x + w] = blk
+            assert r["n_unaddr"] == int((~addr[hpos]).sum())
+        elif kind == DTOH:
+            exp_undef = int(((model[z:z + d, y:y + h, x:x + w].ravel() != 0) & addr[hpos]).sum()) \
+                if fits else 0
+            assert r["n_undef"] == exp_undef, t
+            if fits:
+                src = model[z:z + d, y:y + h, x:x + w].ravel()
+                cur = o.read_host_v()
+                assert np.array_equal(cur[hpos[addr[hpos]]], src[addr[hpos]])
+        elif kind == DTOD:
+            assert bool(r["flags"] & F["OVERRUN_DST"]) == (not fits2)
+            if fits and fits2:
+                tmp = model[z:z + d, y:y + h, x:x + w].copy()
+                model[z2:z2 + d, y2:y2 + h, x2:x2 + w] = tmp
+                a0 = (z * H + y) * W + x
+                b0 = (z2 * H + y2) * W + x2
+                span = ((d - 1) * H + (h - 1)) * W + w
+                assert bool(r["flags"] & F["DTOD_OVERLAP"]) == (a0 < b0 + span and b0 < a0 + span)
+        assert np.array_equal(o.read_array_v(A1, 0, W * H * D), model.ravel()), (t, kind)
+    # array <-> linear memory, both ways
+    assert o.check_copy3d(DTOD, O.side(A1 + 0, pitch=8, rows=2), O.side(A2, x=3, y=1, array=True),
+                          8, 2, 1)[0] == 0
+    # an unknown handle is unallocated; the host side is never an array
+    st, r = o.check_copy3d(HTOD, O.side(0x9999, array=True), O.side(0, pitch=4), 4, 1)
+    assert st == 0 and r["flags"] & F["UNALLOC_DST"] and r["found_dst"] == 0
+    assert o.check_copy3d(HTOD, O.side(A2, array=True), O.side(A1, array=True), 4, 1)[0] == \
+        O.STATUS_CODES["E_ARG"]
+    # destroy: ok, then double; unknown; re-creation clears the freed mark
+    assert o.free_array(A2) == "OK" and o.free_array(A2) == "DOUBLE"
+    assert o.free_array(0x7777) == "UNKNOWN"
+    st, r = o.check_copy3d(HTOD, O.side(A2, array=True), O.side(0, pitch=4), 4, 1)
+    assert r["flags"] & F["UNALLOC_DST"]
+    assert o.register_array(A2, 8, 8, 1) == 0 and o.free_array(A2) == "OK"
+    o.close()
+
+
+def pin_pitched_args(lib):
+    """Argument rules of pitched copies: rows closer than the width, slices
+    closer than the rows, a host span outside the image, an empty copy (no
+    range check at all, R9) and 64-bit overflow of the geometry."""
+    a_bits, vv = _image(np.ones(256, bool), np.zeros(256, np.uint8))
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev = 1 << 30
+    assert o.register_alloc(dev, 4096) == 0
+    E = O.STATUS_CODES
+    ok = lambda st: st == 0  # noqa: E731
+    assert o.check_copy3d(HTOD, O.side(dev, pitch=7), O.side(0, pitch=8), 8, 2)[0] == E["E_ARG"]
+    assert o.check_copy3d(HTOD, O.side(dev, pitch=8), O.side(0, pitch=7), 8, 2)[0] == E["E_ARG"]
+    assert ok(o.check_copy3d(HTOD, O.side(dev, pitch=0), O.side(0, pitch=0), 8, 1)[0])
+    assert o.check_copy3d(HTOD, O.side(dev, pitch=8, rows=1), O.side(0, pitch=8, rows=2),
+                          8, 2, 2)[0] == E["E_ARG"]
+    assert ok(o.check_copy3d(HTOD, O.side(dev, pitch=8, rows=2), O.side(0, pitch=8, rows=2),
+                             8, 2, 2)[0])
+    # host span: rows 0..3 of pitch 64 end at 3*64+16 = 208 <= 256; one more row does not
+    assert ok(o.check_copy3d(HTOD, O.side(dev, pitch=16), O.side(0, pitch=64), 16, 4)[0])
+    assert o.check_copy3d(HTOD, O.side(dev, pitch=16), O.side(0, pitch=64), 16, 5)[0] == \
+        E["E_HOST_RANGE"]
+    assert o.check_copy3d(DTOH, O.side(200, pitch=64), O.side(dev, pitch=16), 16, 1)[0] == 0
+    assert o.check_copy3d(DTOH, O.side(0, pitch=64, y=3), O.side(dev, pitch=16), 65, 1)[0] == \
+        E["E_HOST_RANGE"]
+    # empty copies: nothing is checked
+    for whd in ((0, 5, 5), (5, 0, 5), (5, 5, 0)):
+        st, r = o.check_copy3d(HTOD, O.side(12345, array=True), O.side(10**12), *whd)
+        assert st == 0 and r["flags"] == 0 and r["expected"] == 0 and r["first_bad_off"] == -1
+    # the extent of the last row ends exactly at the allocation's end
+    st, r = o.check_copy3d(HTOD, O.side(dev + 4096 - (3 * 100 + 10), pitch=100), O.side(0, pitch=10),
+                           10, 4)
+    assert st == 0 and r["flags"] == 0 and r["found_dst"] == 3 * 100 + 10
+    st, r = o.check_copy3d(HTOD, O.side(dev + 4096 - (3 * 100 + 9), pitch=100), O.side(0, pitch=10),
+                           10, 4)
+    assert r["flags"] & F["OVERRUN_DST"] and r["found_dst"] == 3 * 100 + 9
+    # slices: the extent uses rows per slice, not height
+    st, r = o.check_copy3d(HTOD, O.side(dev, pitch=10, rows=100), O.side(0, pitch=10, rows=3),
+                           10, 3, 5)
+    assert st == 0 and r["flags"] == 0
+    st, r = o.check_copy3d(HTOD, O.side(dev, pitch=10, rows=100), O.side(0, pitch=10, rows=3),
+                           10, 3, 6)
+    assert r["flags"] & F["OVERRUN_DST"] and r["found_dst"] == 4096
+    # geometry beyond 64 bits
+    big = 1 << 62
+    assert o.check_copy3d(HTOD, O.side(dev, pitch=big, rows=8), O.side(0, pitch=8, rows=8),
+                          8, 2, 2)[0] == E["E_WRAP"]
+    o.close()
+
+
 ALL_PINS = [
     pin_listing5, pin_htod_bytes_by_construction, pin_dtoh_bytes_by_construction,
     pin_range_bruteforce, pin_free_sequences, pin_free_sequences_reuse, pin_generator_truth,
     pin_invariants, pin_carry_roundtrip, pin_dtod_memmove, pin_records,
-    pin_host_range_errors, pin_races,
+    pin_host_range_errors, pin_races, pin_strided_footnote, pin_pitched_reduces_to_1d,
+    pin_pitched_bruteforce, pin_arrays, pin_pitched_args,
 ]
 
 

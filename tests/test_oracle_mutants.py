@@ -38,8 +38,12 @@ MUTANTS = {
                             "if (0)\n        cls = OR_BYTE_UNADDR;"),
     "last_unaddr_not_first": ("if (r->first_unaddr_off < 0) r->first_unaddr_off = (int64_t)i;",
                               "r->first_unaddr_off = (int64_t)i;"),
-    "first_bad_kind_unset": ("r->first_bad_kind = cls;", "r->first_bad_kind = OR_BYTE_UNDEF;"),
-    "good_count_dropped": ("      r->n_good++;", "      ;"),
+    "first_bad_kind_unset": ("r->first_bad_off = (int64_t)i;\n      r->first_bad_kind = cls;",
+                             "r->first_bad_off = (int64_t)i;\n      r->first_bad_kind = OR_BYTE_UNDEF;"),
+    "p3_first_bad_kind_unset": ("r->first_bad_off = (int64_t)o;\n          r->first_bad_kind = cls;",
+                                "r->first_bad_off = (int64_t)o;\n          r->first_bad_kind = OR_BYTE_UNDEF;"),
+    "good_count_dropped": ("      r->n_good++;\n    } else", "      ;\n    } else"),
+    "p3_good_count_dropped": ("          r->n_good++;\n          continue;", "          continue;"),
     "overrun_off_by_one": ("if (n > *found) {", "if (n >= *found) {"),
     "found_off_by_one": ("*found = a->base + a->size - p;", "*found = a->base + a->size - p - 1;"),
     "containment_inclusive": ("if (addr - a->base < a->size) return a;",
@@ -72,6 +76,32 @@ MUTANTS = {
                                ""),
     "race_reads_conflict": ("if (src_space(kind[q]) == dst_space(kind[r]) && meets(src[q], n[q], dst[r], n[r])) hit = 1;",
                             "if (src_space(kind[q]) == src_space(kind[r]) && meets(src[q], n[q], src[r], n[r])) hit = 1;"),
+    # pitched copies and arrays
+    "p3_offset_transposed": ("const uint64_t o = (z * h + y) * w + i; /* linear offset */",
+                             "const uint64_t o = (y * d + z) * w + i; /* linear offset */"),
+    "p3_extent_whole_last_row": ("*extent = e1 + e2 + w;", "*extent = e1 + e2 + p;"),
+    "p3_slice_uses_height": ("const uint64_t p = q->pitch, rows = q->rows;",
+                             "const uint64_t p = q->pitch, rows = h;"),
+    "p3_pitch_check_dropped": ("if ((h > 1 || d > 1) && q->pitch < w) return OR_E_ARG;", ""),
+    "p3_array_bound_exclusive": ("w <= a->w - q->x", "w < a->w - q->x"),
+    "p3_array_pitch_is_height": ("    sd->pitch = a->w;\n", "    sd->pitch = a->h;\n"),
+    "p3_array_found_whole": ("if (inside) *found = *asize - ((q->z * a->h + q->y) * a->w + q->x);",
+                             "if (inside) *found = *asize;"),
+    "p3_dtod_no_staging": ("*side_dev_byte(&ds, side_pos(&ds, i, y, z)) = tmp[(z * h + y) * w + i];",
+                           "*side_dev_byte(&ds, side_pos(&ds, i, y, z)) = side_dev_v(&ss, side_pos(&ss, i, y, z));"),
+    "p3_overlap_by_count": ("if (dstart - sstart < sext || sstart - dstart < dext)",
+                            "if (dstart - sstart < n || sstart - dstart < n)"),
+    "p3_htod_carry_ignores_a": (
+        "*side_dev_byte(&ds, side_pos(&ds, i, y, z)) = host_a_bit(s, hp) ? s->host_v[hp] : 0xFF;",
+        "*side_dev_byte(&ds, side_pos(&ds, i, y, z)) = s->host_v[hp];"),
+    "p3_array_double_destroy_unknown": (
+        "*verdict = handle_freed(s, handle) ? OR_FREE_DOUBLE : OR_FREE_UNKNOWN;",
+        "*verdict = OR_FREE_UNKNOWN;"),
+    "p3_dtoh_carry_ignores_a": (
+        "if (host_a_bit(s, hp)) s->host_v[hp] = side_dev_v(&ss, side_pos(&ss, i, y, z));",
+        "s->host_v[hp] = side_dev_v(&ss, side_pos(&ss, i, y, z));"),
+    "p3_origin_ignores_y": ("const uint64_t o1 = q->z * sl, o2 = q->y * p;",
+                            "const uint64_t o1 = q->z * sl, o2 = 0;"),
     "batch_not_validated_first": (
         "    int st = validate(s, kind[i], dst[i], src[i], n[i]);\n    if (st) {",
         "    int st = 0;\n    if (st) {"),
