@@ -415,3 +415,169 @@ def tuning_batch(rng, table: AllocTable, host_n: int) -> np.ndarray:
     hi = int(min(16 << 20, lo * 2 ** rng.uniform(2, 14)))
     mix = rng.dirichlet([2.0, 1.0, 0.5])
     return requests(rng, count, table, host_n, lo, max(lo, hi), mix=tuple(mix), p_wild=0.01)
+
+
+# ------------------------------------------------ pitched copies, arrays
+
+@dataclass
+class PitchedWorkload:
+    image: HostImage
+    table: AllocTable
+    arrays: list  # (handle, width_bytes, height, depth)
+    copies: list  # dicts: kind, dst, src (side dicts), width, height, depth
+    name: str = ""
+
+
+def side3d(ptr: int, pitch: int = 0, rows: int = 0, x: int = 0, y: int = 0, z: int = 0,
+           array: bool = False) -> dict:
+    return dict(ptr=int(ptr), pitch=int(pitch), rows=int(rows), x=int(x), y=int(y), z=int(z),
+                is_array=int(array))
+
+
+def _pitched_shape(rng, max_bytes: int):
+    """Row width, rows and slices: narrow (record-like), medium and wide rows."""
+    u = rng.random()
+    if u < 0.35:
+        w = int(rng.integers(1, 65))
+    elif u < 0.7:
+        w = int(rng.integers(65, 2049))
+    else:
+        w = int(rng.integers(2049, 24 * 1024))
+    h = int(rng.integers(1, 65))
+    d = int(rng.integers(1, 5)) if rng.random() < 0.3 else 1
+    while w * h * d > max_bytes and h > 1:
+        h = max(1, h // 2)
+    if w * h * d > max_bytes:
+        d = 1
+    return w, h, d
+
+
+def _pitch_for(rng, w: int) -> int:
+    """A pitch >= w: tight, a small ragged gap, or rounded up to 512 B (the
+    kind a pitched allocator returns)."""
+    u = rng.random()
+    if u < 0.2:
+        return w
+    if u < 0.6:
+        return w + int(rng.integers(1, 80))
+    return ((w + 511) // 512) * 512 + (512 if rng.random() < 0.3 else 0)
+
+
+def _linear_side(rng, w, h, d, lo: int, room: int, p_over: float = 0.0):
+    """A linear side whose extent starts in [lo, lo+room) and fits, or (with
+    probability p_over) runs past lo+room."""
+    pitch = _pitch_for(rng, w)
+    rows = h + (int(rng.integers(0, 4)) if d > 1 else 0)
+    x, y, z = int(rng.integers(0, 33)), int(rng.integers(0, 3)), int(rng.integers(0, 2))
+    place = (z * rows + y) * pitch + x
+    ext = ((d - 1) * rows + (h - 1)) * pitch + w
+    if ext + place > room:
+        x = y = z = 0
+        place = 0
+    if ext > room:
+        return None
+    if rng.random() < p_over:
+        first = room - ext + int(rng.integers(1, min(ext, 4096) + 1))
+    else:
+        first = int(rng.integers(0, room - ext + 1))
+    ptr = lo + max(first - place, 0)
+    if first < place:  # keep the origin arithmetic inside [lo, ...)
+        x = y = z = 0
+        ptr = lo + first
+    return side3d(ptr, pitch, rows, x, y, z)
+
+
+def pitched(seed: int = 0, n_copies: int = 300, host_n: int = 8 << 20, max_bytes: int = 256 << 10,
+            n_alloc: int = 48, n_arrays: int = 6) -> PitchedWorkload:
+    """Pitched 2-D / 3-D copies over linear allocations (4 KiB - 4 MiB,
+    log-uniform) and device arrays: kind mix 60/30/10, row widths from
+    1 B (record fields) to 24 KiB, pitches tight, ragged or 512-rounded;
+    10 % of linear device sides overrun, 3 % aim at a freed allocation,
+    20 % of device sides are arrays (15 % of those boxes do not fit)."""
+    rng = rng_for(7000 + seed)
+    image = host_image_runs(rng, host_n, undef_frac=2e-3, mean_run=8.0, unaddr_p=5e-4)
+    table = alloc_table(rng, n_alloc, 4096, 4 << 20, True, n_freed=3, round_to=256)
+    live = np.setdiff1d(np.arange(n_alloc), table.freed)
+    arrays = []
+    for k in range(n_arrays):
+        W = int(rng.integers(16, 4097))
+        H = int(rng.integers(1, 129))
+        D = int(rng.integers(1, 9)) if k % 2 else 1
+        arrays.append((0x5000_0000 + 0x100 * k, W, H, D))
+    copies = []
+    while len(copies) < n_copies:
+        kind = int(rng.choice([HTOD, DTOH, DTOD], p=[0.6, 0.3, 0.1]))
+        w, h, d = _pitched_shape(rng, max_bytes)
+        sides = {}
+        ok = True
+        for role in ("dst", "src"):
+            host_side = (role == "src" and kind == HTOD) or (role == "dst" and kind == DTOH)
+            if host_side:
+                s = _linear_side(rng, w, h, d, 0, host_n)
+            elif rng.random() < 0.2:
+                handle, W, H, D = arrays[int(rng.integers(0, len(arrays)))]
+                if rng.random() < 0.85 and w <= W and h <= H and d <= D:
+                    x, y, z = (int(rng.integers(0, W - w + 1)), int(rng.integers(0, H - h + 1)),
+                               int(rng.integers(0, D - d + 1)))
+                else:
+                    x, y, z = (int(rng.integers(0, W)), int(rng.integers(0, H)),
+                               int(rng.integers(0, D)))
+                s = side3d(handle, 0, 0, x, y, z, array=True)
+            else:
+                u = rng.random()
+                j = int(rng.choice(table.freed)) if u < 0.03 and len(table.freed) else \
+                    int(rng.choice(live))
+                s = _linear_side(rng, w, h, d, int(table.base[j]), int(table.size[j]),
+                                 p_over=0.1)
+            if s is None:
+                ok = False
+                break
+            sides[role] = s
+        if not ok:
+            continue
+        if kind == DTOD and rng.random() < 0.3 and not sides["dst"]["is_array"]:
+            # overlapping: the source shifted a little from the destination
+            s = dict(sides["dst"])
+            s["ptr"] = max(0, s["ptr"] + int(rng.integers(-300, 300)))
+            sides["src"] = s
+        copies.append(dict(kind=kind, dst=sides["dst"], src=sides["src"], width=w, height=h,
+                           depth=d))
+    return PitchedWorkload(image, table, arrays, copies, f"pitched/seed{seed}")
+
+
+# Full-size pitched transfers (host->device with carry), 256 MiB of payload each:
+#   wide:   16384 rows of 16 KiB, host and device pitch 16.5 KiB (512 B of
+#           never-written padding per host row), as an image or matrix with a
+#           padded leading dimension;
+#   narrow: one 16-byte field of 16M 24-byte host records (8 B of never-written
+#           padding each) into a dense device array: the strided host read of
+#           the paper's footnote.
+PITCHED_LARGE = {
+    "wide": dict(width=16 << 10, height=16384, host_pitch=(16 << 10) + 512,
+                 dev_pitch=(16 << 10) + 512),
+    "narrow": dict(width=16, height=16 << 20, host_pitch=24, dev_pitch=16),
+}
+
+
+def pitched_large(which: str = "wide", seed: int = 0) -> PitchedWorkload:
+    cfg = PITCHED_LARGE[which]
+    w, h, hp, dp = cfg["width"], cfg["height"], cfg["host_pitch"], cfg["dev_pitch"]
+    rng = rng_for(8000 + seed)
+    host_ext = (h - 1) * hp + w
+    host_n = (host_ext + 4095) // 4096 * 4096
+    image = host_image_runs(rng, host_n, undef_frac=1e-6, mean_run=8.0)
+    # the padding between rows was never written: undefined
+    pad = np.ones(hp, bool)
+    pad[:w] = False
+    rows_in_image = host_n // hp
+    view = image.v[: rows_in_image * hp].reshape(rows_in_image, hp)
+    view[:, pad] = 0xFF
+    image.v[rows_in_image * hp:] = 0xFF
+    dev_size = (h - 1) * dp + w
+    dev_size = (dev_size + 255) // 256 * 256
+    sizes = np.array([dev_size] + [1 << 20] * 15, dtype=np.uint64)
+    bases = disjoint_bases(rng, sizes)
+    table = AllocTable(bases, sizes, np.zeros(0, np.int64))
+    copy = dict(kind=HTOD, dst=side3d(int(bases[0]), dp, h), src=side3d(0, hp, h), width=w,
+                height=h, depth=1)
+    return PitchedWorkload(image, table, [], [copy], f"pitched_{which}")

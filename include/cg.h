@@ -282,6 +282,89 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                          uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream);
 
+/* ------------------------------------------- pitched copies and arrays */
+
+/* One side of a pitched 2-D / 3-D copy (cuMemcpy2D / cuMemcpy3D).  ptr is a
+ * device address, a host offset into the bound image (the host side of
+ * CG_HTOD / CG_DTOH), or, with is_array = 1, the handle of a device array
+ * registered with cg_register_array.  pitch = bytes between rows, rows =
+ * rows per slice, (x, y, z) = the origin, x in bytes.  For an array side,
+ * pitch and rows are ignored: the array's own width and height apply.
+ * reserved must be 0.  56 bytes. */
+typedef struct cg_side3d {
+  uint64_t ptr;
+  uint64_t pitch;
+  uint64_t rows;
+  uint64_t x, y, z;
+  uint32_t is_array;
+  uint32_t reserved;
+} cg_side3d;
+
+/* A pitched copy of depth slices of height rows of width bytes.  Byte
+ * (i, y, z) of the copy (i < width, y < height, z < depth) lives at
+ *   ptr + (z0+z)*pitch*rows + (y0+y)*pitch + x0+i   (linear memory, host)
+ *   dense position ((z0+z)*H + y0+y)*W + x0+i        (a W x H x D array)
+ * on each side, (x0, y0, z0) being that side's origin.  Rules (Sec. 2, its
+ * footnote on strided host access, Fig. 2):
+ *   - only the copied bytes are classified, never a pitch gap; report
+ *     offsets are linear in the copy, (z*height + y)*width + i, and
+ *     expected = width*height*depth;
+ *   - a linear device side must hold its whole extent, first to one past
+ *     the last copied byte, in one live allocation (found and alloc_* as
+ *     for a plain copy, measured from the first copied byte);
+ *   - an array side must name a live array and fit per dimension
+ *     (x0+width <= W, y0+height <= H, z0+depth <= D), else OVERRUN; found =
+ *     W*H*D minus the origin's dense position (0 if the origin lies
+ *     outside), alloc_base = the handle, alloc_size = W*H*D;
+ *   - device->device: the overlap warning is raised when the two spans
+ *     intersect (arrays: the same array); the carry reads the whole source
+ *     first.
+ * reserved must be 0.  144 bytes. */
+typedef struct cg_copy3d {
+  uint32_t kind;
+  uint32_t reserved;
+  cg_side3d dst;
+  cg_side3d src;
+  uint64_t width;
+  uint64_t height;
+  uint64_t depth;
+} cg_copy3d;
+
+/* Register a device array (Fig. 2's second list: the cuArrayCreate /
+ * cuArray3DCreate wrapper): handle = the array's handle, width in bytes,
+ * height and depth >= 1.  Its shadow is dense, row-major, all undefined.
+ * Handles are a namespace of their own (no clash with device addresses).
+ * CG_E_ZERO_SIZE, CG_E_WRAP (W*H*D beyond 64 bits), CG_E_OVERLAP (handle
+ * already live), CG_E_NOMEM. */
+cg_status cg_register_array(cg_ctx *ctx, uint64_t handle, uint64_t width, uint64_t height,
+                            uint64_t depth);
+
+/* The cuArrayDestroy wrapper's check: *verdict = CG_FREE_OK (removed,
+ * shadow released), CG_FREE_DOUBLE (destroyed before and not re-created)
+ * or CG_FREE_UNKNOWN. */
+cg_status cg_free_array(cg_ctx *ctx, uint64_t handle, uint32_t *verdict);
+
+/* Copy bytes [off, off+n) of an array's dense shadow to host memory `out`.
+ * Synchronous.  CG_E_RANGE if the handle is not live or the span is
+ * outside the array. */
+cg_status cg_read_array_shadow(cg_ctx *ctx, uint64_t handle, uint64_t off, uint64_t n,
+                               uint8_t *out);
+
+/* Check one pitched copy and carry its V shadow.  req, rep: host.
+ * Synchronous.  API errors, checked in this order (nothing runs then):
+ * CG_E_KIND; CG_E_ARG (reserved fields, an array as the host side);
+ * CG_E_WRAP (width*height*depth beyond 64 bits); then, for a non-empty
+ * copy, CG_E_ARG (pitch < width with height or depth > 1, rows < height
+ * with depth > 1), CG_E_NO_HOST, CG_E_WRAP (a position or extent beyond
+ * 64 bits), CG_E_HOST_RANGE (the host extent outside the image).  An
+ * empty copy is a no-op (expected 0, no range check). */
+cg_status cg_check_copy3d(cg_ctx *ctx, const cg_copy3d *req, cg_report *rep, void *stream);
+
+/* Asynchronous form (as cg_check_copy_async): the report is written to
+ * rep_dev when `stream` reaches it. */
+cg_status cg_check_copy3d_async(cg_ctx *ctx, const cg_copy3d *req, cg_report *rep_dev,
+                                void *stream);
+
 /* ------------------------------------------------ choosing the batch split */
 
 /* How cg_check_batch cuts copies into segments matters (too small: per-

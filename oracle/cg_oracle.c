@@ -596,7 +596,7 @@ int or_check_copy3d(or_state *s, const or_copy3d *q, or_report *r) {
   if (!s || !q || !r) return OR_E_ARG;
   const uint32_t kind = q->kind;
   if (kind != OR_HTOD && kind != OR_DTOH && kind != OR_DTOD) return OR_E_KIND;
-  if (q->reserved) return OR_E_ARG;
+  if (q->reserved || q->dst.reserved || q->src.reserved) return OR_E_ARG;
   const uint64_t w = q->width, h = q->height, d = q->depth;
   if (w && h && (h > UINT64_MAX / w || (d && d > UINT64_MAX / (w * h)))) return OR_E_WRAP;
   const uint64_t n = w * h * d;

@@ -38,6 +38,29 @@ class cg_copy(ctypes.Structure):
     _fields_ = [("kind", u32), ("reserved", u32), ("dst", u64), ("src", u64), ("n", u64)]
 
 
+class cg_side3d(ctypes.Structure):
+    _fields_ = [("ptr", u64), ("pitch", u64), ("rows", u64), ("x", u64), ("y", u64),
+                ("z", u64), ("is_array", u32), ("reserved", u32)]
+
+
+class cg_copy3d(ctypes.Structure):
+    _fields_ = [("kind", u32), ("reserved", u32), ("dst", cg_side3d), ("src", cg_side3d),
+                ("width", u64), ("height", u64), ("depth", u64)]
+
+
+def side(ptr: int, pitch: int = 0, rows: int = 0, x: int = 0, y: int = 0, z: int = 0,
+         array: bool = False) -> dict:
+    """One side of a pitched copy: a device address, a host offset, or (with
+    array=True) a device array's handle; pitch = bytes between rows, rows =
+    rows per slice, (x, y, z) = origin with x in bytes."""
+    return dict(ptr=ptr, pitch=pitch, rows=rows, x=x, y=y, z=z, is_array=int(array))
+
+
+def copy3d(kind: int, dst: dict, src: dict, width: int, height: int, depth: int = 1) -> cg_copy3d:
+    return cg_copy3d(kind=kind, reserved=0, dst=cg_side3d(reserved=0, **dst),
+                     src=cg_side3d(reserved=0, **src), width=width, height=height, depth=depth)
+
+
 class cg_report(ctypes.Structure):
     _fields_ = [("flags", u32), ("first_bad_kind", u32), ("first_bad_off", i64),
                 ("first_unaddr_off", i64), ("first_undef_off", i64), ("n_good", u64),
@@ -127,6 +150,11 @@ SIGNATURES = [
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
+    ("cg_register_array", i32, [vp, u64, u64, u64, u64]),
+    ("cg_free_array", i32, [vp, u64, ctypes.POINTER(u32)]),
+    ("cg_read_array_shadow", i32, [vp, u64, u64, u64, vp]),
+    ("cg_check_copy3d", i32, [vp, ctypes.POINTER(cg_copy3d), vp, vp]),
+    ("cg_check_copy3d_async", i32, [vp, ctypes.POINTER(cg_copy3d), vp, vp]),
     ("cg_batch_features", i32, [vp, u64, vp]),
     ("cg_tune_batch", i32, [vp, vp, u64, vp, u32, u32, u32, vp, ctypes.POINTER(u32), vp]),
     ("cg_set_cost_model", i32, [vp, vp, u32]),
@@ -260,6 +288,28 @@ class Context:
         r = cg_report()
         st = cg_check_copy(self._h, ctypes.byref(q), ctypes.byref(r), _stream_handle(stream))
         return st, report_to_dict(r)
+
+    def check_copy3d(self, kind: int, dst: dict, src: dict, width: int, height: int,
+                     depth: int = 1, stream=None):
+        """A pitched copy (see side()); returns (status, report dict)."""
+        q = copy3d(kind, dst, src, width, height, depth)
+        r = cg_report()
+        st = cg_check_copy3d(self._h, ctypes.byref(q), ctypes.byref(r), _stream_handle(stream))
+        return st, report_to_dict(r)
+
+    def register_array(self, handle: int, width: int, height: int, depth: int = 1) -> int:
+        return cg_register_array(self._h, handle, width, height, depth)
+
+    def free_array(self, handle: int) -> str:
+        v = u32(99)
+        check(cg_free_array(self._h, handle, ctypes.byref(v)), "cg_free_array")
+        return FREE_NAMES[v.value]
+
+    def read_array_shadow(self, handle: int, off: int, n: int) -> np.ndarray:
+        out = np.empty(n, dtype=np.uint8)
+        check(cg_read_array_shadow(self._h, handle, off, n, out.ctypes.data if n else None),
+              "cg_read_array_shadow")
+        return out
 
     def check_batch(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None):
         """reqs: structured array with the layout of cg_copy (cg_synth.REQ_DTYPE).

@@ -12,6 +12,8 @@
 #include <mutex>
 #include <set>
 #include <string>
+#include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "cg_internal.h"
@@ -483,6 +485,13 @@ struct cg_ctx {
     float best_ms = 0.f;
   };
   std::vector<OnlineTune> online;
+  // device arrays (Fig. 2's second list): handle -> dimensions and shadow
+  struct ArrayInfo {
+    uint64_t w, h, d;
+    uint64_t shadow;  // dense, row-major
+  };
+  std::unordered_map<uint64_t, ArrayInfo> arrays;
+  std::unordered_set<uint64_t> freed_arrays;
   cg_stats stats{};
   std::mutex stats_mu;                // guards stats while serving
   cgi::ServeEngine *serve = nullptr;  // non-null while serving

@@ -105,6 +105,7 @@ struct Geo {
   bool has_vin;
   int64_t hb0;  // host position of chunk 0 byte 0 (may be negative)
   int64_t hlo, hhi;
+  int64_t obase;  // report offset of copy byte 0 (a row of a pitched copy)
 };
 
 __device__ __forceinline__ Geo make_geo(const ScanJob &j, const Image &img) {
@@ -134,6 +135,7 @@ __device__ __forceinline__ Geo make_geo(const ScanJob &j, const Image &img) {
   g.hb0 = (int64_t)j.host_off - g.ax;
   g.hlo = (int64_t)j.host_off;
   g.hhi = (int64_t)(j.host_off + j.n);
+  g.obase = 0;
   return g;
 }
 
@@ -197,7 +199,7 @@ __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uin
     la.un += __popc(un);
     la.ud += __popc(ud);
     if ((un && la.fun == kNone) || (ud && la.fud == kNone)) {
-      const int64_t i0 = 16 * c - g.ax;
+      const int64_t i0 = g.obase + 16 * c - g.ax;
       if (un && la.fun == kNone) la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
       if (ud && la.fud == kNone) la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
     }

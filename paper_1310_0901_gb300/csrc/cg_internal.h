@@ -31,6 +31,19 @@ struct ScanJob {
   uint64_t dev_dst;   // shadow address of dst byte 0 (HtoD/DtoD with kModeCarry)
 };
 
+// One pitched copy as the pitched scan kernel sees it: rows = height*depth
+// rows of `width` bytes; row (y, z) of side s starts at
+// s_start + z*s_slice + y*s_pitch (host side: offsets into the image; device
+// sides: shadow addresses).
+struct PitchedJob {
+  uint32_t kind;
+  uint32_t mode;
+  uint64_t width, height, depth;
+  uint64_t host_start, host_pitch, host_slice;
+  uint64_t src_start, src_pitch, src_slice;  // kModeReadDev
+  uint64_t dst_start, dst_pitch, dst_slice;  // kModeCarry (device destination)
+};
+
 // Bound host shadow image.
 struct Image {
   const uint8_t *a_bits;
@@ -200,6 +213,15 @@ cudaError_t launch_emit_records(const BatchPlan &p, const cg_report *reps, const
                                 cg_err_record *recs, uint64_t rec_cap, cudaStream_t st);
 cudaError_t launch_fill(const uint64_t *ptrs, const uint64_t *sizes, uint64_t count,
                         uint8_t value, cudaStream_t st);
+
+// Pitched copies (cg_scan_pitched.cu).
+cudaError_t launch_scan_pitched(const Image &img, const PitchedJob &job, const RangeInfo &ri,
+                                SingleScratch *scr, cg_report *out, int sm_count,
+                                cudaStream_t st);
+// Gather the rows of a pitched device span into dense `out` (row-major).
+cudaError_t launch_gather_rows(const uint8_t *src, uint64_t pitch, uint64_t slice,
+                               uint64_t width, uint64_t height, uint64_t depth, uint8_t *out,
+                               int sm_count, cudaStream_t st);
 
 constexpr int kFinalizeItems = 1024;  // requests per finalize/emit block
 
