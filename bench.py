@@ -433,7 +433,88 @@ def run_serving(args):
     }
 
 
+def run_pitched(args):
+    """Full-size pitched host->device checks with carry (cg_check_copy3d_async,
+    one launch each): 256 MiB of 16 KiB rows at a 16.5 KiB pitch, and a
+    16-byte field of 16M 24-byte records (the strided host read of the
+    paper's footnote).  Kernel time by CUDA events around each launch."""
+    import ctypes
+
+    import torch
+
+    import paper_1310_0901_gb300 as cg
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+    peak, peak_kind = _peaks()
+    lines = {}
+    launches = 0
+    clocks = Clocks(dev.index)
+    clocks.start()
+    for which in sorted(S.PITCHED_LARGE):
+        w = S.pitched_large(which)
+        q = w.copies[0]
+        n = q["width"] * q["height"] * q["depth"]
+        a_dev = torch.from_numpy(w.image.a_bits[: w.image.n // 8].copy()).to(dev)
+        v_dev = torch.from_numpy(w.image.v).to(dev)
+        ctx = cg.Context()
+        ctx.bind_host_shadow(a_dev, v_dev)
+        for b, s_ in sorted(zip(w.table.base.tolist(), w.table.size.tolist())):
+            cg.check(ctx.register_alloc(int(b), int(s_)), "register")
+        qq = cg.copy3d(q["kind"], q["dst"], q["src"], q["width"], q["height"], q["depth"])
+        rep = torch.zeros(cg.REPORT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        for _ in range(max(3, args.warmup)):
+            cg.check(cg.cg_check_copy3d_async(ctx.handle, ctypes.byref(qq), rep.data_ptr(), sh),
+                     "check3d")
+        torch.cuda.synchronize()
+        r = np.frombuffer(rep.cpu().numpy().tobytes(), dtype=cg.REPORT_DTYPE)[0]
+        payload = np.lib.stride_tricks.as_strided(w.image.v, shape=(q["height"], q["width"]),
+                                                  strides=(q["src"]["pitch"], 1))
+        assert int(r["n_undef"]) == int((payload != 0).sum()), "report mismatch"
+        k0 = ctx.stats()["kernels"]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for e0, e1 in ev:
+            e0.record(stream)
+            cg.check(cg.cg_check_copy3d_async(ctx.handle, ctypes.byref(qq), rep.data_ptr(), sh),
+                     "check3d")
+            e1.record(stream)
+        torch.cuda.synchronize()
+        launches += ctx.stats()["kernels"] - k0
+        ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+        achieved = BYTES_PER_BYTE_CARRY * n / (ms / 1e3) / GB
+        span = (q["height"] - 1) * q["src"]["pitch"] + q["width"]
+        lines[which] = {
+            "checked_gb_per_s": round(n / (ms / 1e3) / GB, 2), "kernel_ms_mean": round(ms, 4),
+            "payload_bytes": n, "host_span_bytes": span,
+            "rows": q["height"], "row_bytes": q["width"], "host_pitch": q["src"]["pitch"],
+            "dev_pitch": q["dst"]["pitch"], "n_undef_payload": int(r["n_undef"]),
+            "roofline": {"bound": "hbm", "kernel": "scan_pitched_kernel<HTOD,carry>",
+                         "bytes_per_checked_byte": BYTES_PER_BYTE_CARRY,
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_source": peak_kind}}
+        ctx.close()
+        del a_dev, v_dev
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    out = {"metric": "pitched host->device checks: payload GB/s checked vs HBM peak",
+           "unit": "GB/s", "value": min(d["checked_gb_per_s"] for d in lines.values()),
+           "steps": args.steps, "warmup": max(3, args.warmup), "gpu_launches": int(launches),
+           "config": {"workload": "pitched_large (wide 16 KiB rows, narrow 16 B of 24 B records)",
+                      "l2": "inputs larger than L2 (>= 256 MiB each); no flush"},
+           "lines": lines}
+    if clk is not None:
+        out["clocks"] = clk
+    return out
+
+
 def _summary(key: str, d: dict) -> dict:
+    if key == "pitched":
+        return {"workload": d["config"]["workload"],
+                **{k: {"checked_gb_per_s": v["checked_gb_per_s"],
+                       "roofline_frac": v["roofline"]["frac"],
+                       "kernel_ms_mean": v["kernel_ms_mean"]} for k, v in d["lines"].items()}}
     if key == "batched":
         return {"workload": d["config"]["workload"], "checks_per_s": d["value"],
                 "gb_per_s": d["batched_gb_per_s"],
@@ -449,7 +530,7 @@ def _summary(key: str, d: dict) -> dict:
 def _kernel_hash() -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("cg_scan_tma.cu", "cg_device.cuh", "cg_internal.h"):
+    for f in ("cg_scan_tma.cu", "cg_tma.cuh", "cg_device.cuh", "cg_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -545,7 +626,7 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 register loads, 2 TMA bulk")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batched", "adversarial", "serving"])
+                    choices=["large", "batched", "adversarial", "serving", "pitched"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=S.SERVE_RATE)
     ap.add_argument("--serve-image-gib", type=int, default=32)
@@ -565,6 +646,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "pitched":
+        if rank == 0:
+            print(json.dumps(run_pitched(args)), flush=True)
         return
     if args.workload != "large":
         if rank == 0:
@@ -586,7 +671,8 @@ def main():
             del w
             torch.cuda.empty_cache()
             for key, fn in (("batched", lambda: run_batched_workload(args, "batched")),
-                            ("serving", lambda: run_serving(args))):
+                            ("serving", lambda: run_serving(args)),
+                            ("pitched", lambda: run_pitched(args))):
                 try:
                     out[key] = _summary(key, fn())
                 except Exception as exc:  # reported, never hides the headline

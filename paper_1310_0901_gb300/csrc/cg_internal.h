@@ -215,9 +215,11 @@ cudaError_t launch_fill(const uint64_t *ptrs, const uint64_t *sizes, uint64_t co
                         uint8_t value, cudaStream_t st);
 
 // Pitched copies (cg_scan_pitched.cu).
+// row_chunks = 16-byte chunks of the longest row on its anchor grid;
+// tma_ok = bulk copies may read the image (it is in device memory).
 cudaError_t launch_scan_pitched(const Image &img, const PitchedJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int sm_count,
-                                cudaStream_t st);
+                                uint64_t row_chunks, bool tma_ok, cudaStream_t st);
 // Gather the rows of a pitched device span into dense `out` (row-major).
 cudaError_t launch_gather_rows(const uint8_t *src, uint64_t pitch, uint64_t slice,
                                uint64_t width, uint64_t height, uint64_t depth, uint8_t *out,

@@ -172,6 +172,24 @@ cg_status prepare3d(cg_ctx *c, const cg_copy3d &q, Prepared *P) {
   return CG_OK;
 }
 
+// 16-byte chunks of a row on the grid of the buffer the scan writes (the
+// kernels' anchor): exact when every row starts at the same address mod 16,
+// else the bound for any alignment.
+uint64_t row_chunks(const cg_ctx *c, const PitchedJob &j) {
+  const bool carry = j.mode & kModeCarry;
+  const uint64_t host = reinterpret_cast<uint64_t>(c->img.v) + j.host_start;
+  uint64_t a = 0, pitch = 0, slice = 0;
+  if (j.kind == CG_DTOH || (j.kind == CG_HTOD && !carry)) {
+    a = host, pitch = j.host_pitch, slice = j.host_slice;
+  } else if (carry) {
+    a = j.dst_start, pitch = j.dst_pitch, slice = j.dst_slice;
+  } else {
+    a = j.src_start, pitch = j.src_pitch, slice = j.src_slice;
+  }
+  const bool uniform = (j.height == 1 || pitch % 16 == 0) && (j.depth == 1 || slice % 16 == 0);
+  return uniform ? ((a & 15) + j.width + 15) >> 4 : (j.width + 30) >> 4;
+}
+
 cg_status enqueue3d(cg_ctx *c, Prepared &P, cg_report *out, cudaStream_t st) {
   CG_TRY(flush_fills(c, st));
   if (P.trivial) {  // no byte to read: the report alone
@@ -193,7 +211,8 @@ cg_status enqueue3d(cg_ctx *c, Prepared &P, cg_report *out, cudaStream_t st) {
     job.src_slice = job.width * job.height;
     c->stats.kernels++;
   }
-  CG_CUDA(launch_scan_pitched(c->img, job, P.ri, c->d_scratch, out, c->sm_count, st));
+  CG_CUDA(launch_scan_pitched(c->img, job, P.ri, c->d_scratch, out, c->sm_count,
+                              row_chunks(c, job), !c->img_on_host || job.kind == CG_DTOD, st));
   c->stats.kernels++;
   return CG_OK;
 }

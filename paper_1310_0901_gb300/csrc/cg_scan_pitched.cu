@@ -6,157 +6,326 @@
 // Sec. 2's error list: strided host access is not an error), and the carry
 // writes only the copied bytes of each destination row.
 //
-// Work split: a row is cut into groups of P*U 16-byte chunks of its anchor
-// grid; a subgroup of P lanes takes one group (U chunks per lane).  Wide
-// rows use whole warps (P = 32) with U = 4 loads in flight per lane; rows of
-// at most 32 chunks use P = the next power of two of their chunk count and
-// U = 1, so one warp covers 32/P rows at once.  Warps walk the (row, group)
-// items in grid-stride order, advancing (group, y, z) incrementally.  The
-// last CTA to finish publishes the report, as for a plain copy.
+// Three launch shapes, by the row's length in 16-byte chunks of its anchor
+// grid (the buffer the copy writes):
+//   - rows of at most 32 chunks: a group of P lanes (P = the next power of
+//     two of the chunk count) takes one row, and every group U rows at once
+//     (all loads first, then the classification), so one warp covers
+//     32/P * U rows per step;
+//   - rows of up to kTmaRowChunks chunks: whole warps take groups of 128
+//     chunks of a row, 4 loads in flight per lane;
+//   - longer rows: the TMA tile pipeline of the plain copy (per-warp
+//     shared-memory stages filled by bulk copies), one 4 KiB tile of one row
+//     at a time, rows taken in order.
+// The last CTA to finish publishes the report, as for a plain copy.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "cg_device.cuh"
+#include "cg_tma.cuh"
 
 namespace cgi {
 
-constexpr int kPThreads = 256;
-constexpr int kPWide = 4;  // chunks in flight per lane on wide rows
+// Short rows are latency-bound: measured on the 16-byte-field workload,
+// one row per lane group and 8 CTAs per SM (64 warps, a few spilled
+// registers) beat more rows in flight per lane at lower occupancy
+// (0.159 ms vs 0.17-0.30 ms for 2-8 rows at 2-6 CTAs per SM).
+#ifndef CG_PN_U
+#define CG_PN_U 1
+#endif
+#ifndef CG_PN_MINB
+#define CG_PN_MINB 8
+#endif
 
-// Grid-stride bookkeeping computed on the host for the chosen grid.
-struct PitchedGrid {
-  uint64_t groups;  // chunk groups per row (G)
-  uint64_t tg;      // per-iteration advance of the group index: T mod G
-  uint64_t ty, tz;  // ... and of the row: (T div G) as (y, z) steps
-  uint32_t lp;      // log2 of the lanes per group (P)
-};
+constexpr int kPThreads = 256;
+constexpr int kPWide = 4;          // chunks in flight per lane on medium rows
+constexpr int kPNarrow = CG_PN_U;  // rows in flight per lane group on short rows
+constexpr uint64_t kTmaRowChunks = 256;  // rows this long go to the TMA pipeline
+
+// Row r of the copy as a plain one-row job; obase = its first byte's offset
+// in the copy.  Rows past the end become empty jobs (nothing is read).
+__device__ __forceinline__ Geo row_geo(const PitchedJob &pj, const Image &img, uint32_t kind,
+                                       uint64_t r) {
+  uint64_t y = r, z = 0;
+  if (pj.depth > 1) {
+    z = r / pj.height;
+    y = r - z * pj.height;
+  }
+  ScanJob j;
+  j.kind = kind;
+  j.mode = pj.mode;
+  j.n = z < pj.depth && y < pj.height ? pj.width : 0;
+  j.host_off = pj.host_start + z * pj.host_slice + y * pj.host_pitch;
+  j.dev_src = pj.src_start + z * pj.src_slice + y * pj.src_pitch;
+  j.dev_dst = pj.dst_start + z * pj.dst_slice + y * pj.dst_pitch;
+  Geo g = make_geo(j, img);
+  g.obase = (int64_t)(r * pj.width);
+  return g;
+}
 
 // The input V window of chunk c when the warp is split into groups of P
 // lanes: the lane after this one (same group) holds chunk c+1's first
 // vector; the last lane of a group fetches it itself.  Every lane calls it.
+// Both of the last lane's loads are issued before the shuffle waits on the
+// first, so a group of one lane has its two loads in flight together.
 __device__ __forceinline__ uint4 load_window_group(const Geo &g, int64_t c, bool last_in_group) {
   const uintptr_t a0 = g.vin_al + 16 * (uintptr_t)c;
+  const uintptr_t a1 = a0 + 16;
   const bool in0 = a0 < g.vin_hi && a0 + 16 > g.vin_lo;
+  const bool in1 = last_in_group && g.vin_r != 0 && a1 < g.vin_hi && a1 + 16 > g.vin_lo;
   const uint4 l0 = in0 ? ld_stream((const void *)a0) : make_uint4(0, 0, 0, 0);
+  const uint4 own1 = in1 ? ld_stream((const void *)a1) : make_uint4(0, 0, 0, 0);
   uint4 l1;
   l1.x = __shfl_down_sync(CG_FULL, l0.x, 1);
   l1.y = __shfl_down_sync(CG_FULL, l0.y, 1);
   l1.z = __shfl_down_sync(CG_FULL, l0.z, 1);
   l1.w = __shfl_down_sync(CG_FULL, l0.w, 1);
-  if (last_in_group) {
-    const uintptr_t a1 = a0 + 16;
-    const bool in1 = a1 < g.vin_hi && a1 + 16 > g.vin_lo;
-    l1 = in1 ? ld_stream((const void *)a1) : make_uint4(0, 0, 0, 0);
-  }
+  if (last_in_group) l1 = own1;
   return g.vin_r == 0 ? l0 : funnel16(l0, l1, g.vin_r);
 }
 
-template <uint32_t KIND, bool CARRY, int U>
-__global__ void __launch_bounds__(kPThreads) scan_pitched_kernel(Image img, PitchedJob pj,
-                                                                 RangeInfo ri, SingleScratch *scr,
-                                                                 cg_report *out, PitchedGrid pg) {
+// ------------------------------------------------------------ short rows
+
+// Groups of P = 2^lp lanes; each group takes U rows per step: rows
+// base + k*(32/P) + group, k < U.
+template <uint32_t KIND, bool CARRY>
+__global__ void __launch_bounds__(kPThreads, CG_PN_MINB) scan_pitched_narrow_kernel(Image img, PitchedJob pj,
+                                                                        RangeInfo ri,
+                                                                        SingleScratch *scr,
+                                                                        cg_report *out,
+                                                                        uint32_t lp) {
+  constexpr int U = kPNarrow;
   const int lane = threadIdx.x & 31;
-  const uint32_t P = 1u << pg.lp;
+  const uint32_t P = 1u << lp;
   const uint32_t ls = lane & (P - 1);
-  const uint64_t per_unit = 32u >> pg.lp;  // groups one warp takes at once
+  const uint64_t groups = 32u >> lp;
+  const uint64_t per_step = groups * U;
+  const uint64_t rows = pj.height * pj.depth;
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const uint32_t *A32 = reinterpret_cast<const uint32_t *>(img.a_bits);
-  const uint64_t t0 = warp * per_unit + (lane >> pg.lp);
-  uint64_t grp = t0 % pg.groups;
-  const uint64_t r0 = t0 / pg.groups;
-  uint64_t y = r0 % pj.height, z = r0 / pj.height;
   LaneAcc la;
   lane_acc_reset(la);
-  while (__any_sync(CG_FULL, z < pj.depth)) {
-    ScanJob j;
-    j.kind = KIND;
-    j.mode = pj.mode;
-    j.n = z < pj.depth ? pj.width : 0;  // past the last row: an empty row
-    j.host_off = pj.host_start + z * pj.host_slice + y * pj.host_pitch;
-    j.dev_src = pj.src_start + z * pj.src_slice + y * pj.src_pitch;
-    j.dev_dst = pj.dst_start + z * pj.dst_slice + y * pj.dst_pitch;
-    Geo g = make_geo(j, img);
-    g.obase = (int64_t)((z * pj.height + y) * pj.width);
-    const int64_t c0 = (int64_t)(grp * P * U) + ls;
+  for (uint64_t base = warp * per_step; base < rows; base += nwarps * per_step) {
+    Geo g[U];
     uint4 v[U];
     uint32_t a[U];
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      const int64_t c = c0 + (int64_t)k * P;
+      g[k] = row_geo(pj, img, KIND, base + (uint64_t)k * groups + (lane >> lp));
       v[k] = make_uint4(0, 0, 0, 0);
       a[k] = 0xFFFFu;
-      if (KIND == CG_HTOD || g.has_vin) v[k] = load_window_group(g, c, ls == P - 1);
+      if (KIND == CG_HTOD || g[k].has_vin) v[k] = load_window_group(g[k], ls, ls == P - 1);
+      if (KIND != CG_DTOD) a[k] = load_a16(A32, g[k].hb0 + 16 * (int64_t)ls, g[k].hlo, g[k].hhi);
+    }
+#pragma unroll
+    for (int k = 0; k < U; k++)
+      chunk_step<KIND, CARRY>(g[k], ls, v[k], a[k], valid_mask(16 * (int64_t)ls - g[k].ax, g[k].n),
+                              la);
+  }
+  single_epilogue(la, scr, ri, out, 0u);
+}
+
+// ----------------------------------------------------------- medium rows
+
+// Whole warps; item = (row, group of 32*U chunks), items in grid-stride
+// order, (group, row) advanced incrementally by the grid's step.
+struct WideStep {
+  uint64_t groups;  // chunk groups per row
+  uint64_t tg, tr;  // grid step: group advance, row advance
+};
+
+template <uint32_t KIND, bool CARRY>
+__global__ void __launch_bounds__(kPThreads) scan_pitched_wide_kernel(Image img, PitchedJob pj,
+                                                                      RangeInfo ri,
+                                                                      SingleScratch *scr,
+                                                                      cg_report *out, WideStep ws) {
+  constexpr int U = kPWide;
+  const int lane = threadIdx.x & 31;
+  const uint64_t rows = pj.height * pj.depth;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t *A32 = reinterpret_cast<const uint32_t *>(img.a_bits);
+  uint64_t grp = warp % ws.groups;
+  uint64_t r = warp / ws.groups;
+  LaneAcc la;
+  lane_acc_reset(la);
+  while (r < rows) {  // warp-uniform
+    const Geo g = row_geo(pj, img, KIND, r);
+    const int64_t c0 = (int64_t)(grp * 32 * U) + lane;
+    uint4 v[U];
+    uint32_t a[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const int64_t c = c0 + 32 * k;
+      v[k] = make_uint4(0, 0, 0, 0);
+      a[k] = 0xFFFFu;
+      if (KIND == CG_HTOD || g.has_vin) v[k] = load_window_group(g, c, lane == 31);
       if (KIND != CG_DTOD) a[k] = load_a16(A32, g.hb0 + 16 * c, g.hlo, g.hhi);
     }
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      const int64_t c = c0 + (int64_t)k * P;
+      const int64_t c = c0 + 32 * k;
       chunk_step<KIND, CARRY>(g, c, v[k], a[k], valid_mask(16 * c - g.ax, g.n), la);
     }
-    grp += pg.tg;
-    uint64_t next_row = 0;
-    if (grp >= pg.groups) {
-      grp -= pg.groups;
-      next_row = 1;
-    }
-    y += pg.ty + next_row;
-    z += pg.tz;
-    if (y >= pj.height) {
-      y -= pj.height;
-      z++;
+    grp += ws.tg;
+    r += ws.tr;
+    if (grp >= ws.groups) {
+      grp -= ws.groups;
+      r++;
     }
   }
   single_epilogue(la, scr, ri, out, 0u);
 }
 
+// ------------------------------------------------------------- long rows
+
+// The plain copy's TMA pipeline over tiles t = (row, tile in row), tiles in
+// grid-stride order per warp; lane 0 keeps kNS tiles in flight.
 template <uint32_t KIND, bool CARRY>
-static void *pitched_fn(bool wide) {
-  return wide ? reinterpret_cast<void *>(&scan_pitched_kernel<KIND, CARRY, kPWide>)
-              : reinterpret_cast<void *>(&scan_pitched_kernel<KIND, CARRY, 1>);
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_pitched_tma_kernel(Image img, PitchedJob pj, RangeInfo ri, SingleScratch *scr,
+                            cg_report *out, uint64_t tiles_per_row, uint64_t ntiles) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
+  const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t err = 0;
+  if (lane == 0)
+    for (int s = 0; s < kNS; s++) {
+      const uint64_t t = gw + (uint64_t)s * nw;
+      if (t < ntiles) {
+        const uint64_t r = t / tiles_per_row;
+        const Geo g = row_geo(pj, img, KIND, r);
+        issue_tile<KIND>(g, img.a_bits, (int64_t)(t - r * tiles_per_row) * kR * 32,
+                         smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+      }
+    }
+  uint32_t parity = 0;
+  int s = 0;
+  uint64_t t = gw;
+  for (; t < ntiles; t += nw) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      err = 1;
+      break;
+    }
+    parity ^= 1u << s;
+    {
+      const uint64_t r = t / tiles_per_row;
+      const Geo g = row_geo(pj, img, KIND, r);
+      consume_tile<KIND, CARRY>(g, (int64_t)(t - r * tiles_per_row) * kR * 32, wbase + s * kStage,
+                                lane, la);
+    }
+    __syncwarp();
+    const uint64_t tn = t + (uint64_t)kNS * nw;
+    if (lane == 0 && tn < ntiles) {
+      fence_proxy_async();
+      const uint64_t r = tn / tiles_per_row;
+      const Geo g = row_geo(pj, img, KIND, r);
+      issue_tile<KIND>(g, img.a_bits, (int64_t)(tn - r * tiles_per_row) * kR * 32,
+                       smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    }
+    s = s + 1 == kNS ? 0 : s + 1;
+  }
+  if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
+    for (int d = 0; d < kNS; d++) {
+      const uint64_t td = t + (uint64_t)d * nw;
+      if (td >= ntiles) break;
+      const int sd = (s + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+  }
+  single_epilogue(la, scr, ri, out, err);
 }
 
-static void *pick_pitched(uint32_t kind, bool carry, bool wide) {
-  switch (kind) {
-    case CG_HTOD:
-      return carry ? pitched_fn<CG_HTOD, true>(wide) : pitched_fn<CG_HTOD, false>(wide);
-    case CG_DTOH:
-      return carry ? pitched_fn<CG_DTOH, true>(wide) : pitched_fn<CG_DTOH, false>(wide);
-    default:
-      return carry ? pitched_fn<CG_DTOD, true>(wide) : pitched_fn<CG_DTOD, false>(wide);
+// --------------------------------------------------------------- launch
+
+template <uint32_t KIND, bool CARRY>
+static cudaError_t launch_t(const Image &img, const PitchedJob &job, const RangeInfo &ri,
+                            SingleScratch *scr, cg_report *out, int sm_count, uint64_t kmax,
+                            bool tma_ok, cudaStream_t st) {
+  const uint64_t rows = job.height * job.depth;
+  const uint64_t wpc = kPThreads / 32;
+  if (kmax >= kTmaRowChunks && tma_ok) {
+    static int per_sm = 0;
+    if (!per_sm) {
+      cudaError_t e = cudaFuncSetAttribute(scan_pitched_tma_kernel<KIND, CARRY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmemBytes);
+      if (e != cudaSuccess) return e;
+      per_sm = tma_ctas_per_sm(scan_pitched_tma_kernel<KIND, CARRY>);
+    }
+    const uint64_t tpr = (kmax + 32 * kR - 1) / (32 * kR);
+    const uint64_t ntiles = rows * tpr;
+    const uint64_t need = (ntiles + kTW - 1) / kTW;
+    const uint64_t cap = (uint64_t)sm_count * per_sm;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    scan_pitched_tma_kernel<KIND, CARRY><<<grid, kTW * 32, kSmemBytes, st>>>(img, job, ri, scr, out,
+                                                                             tpr, ntiles);
+    return cudaGetLastError();
   }
+  if (kmax > 32) {
+    static int per_sm = 0;
+    if (!per_sm &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+             &per_sm, scan_pitched_wide_kernel<KIND, CARRY>, kPThreads, 0) != cudaSuccess ||
+         per_sm < 1))
+      per_sm = 1;
+    WideStep ws;
+    ws.groups = (kmax + 32 * kPWide - 1) / (32 * kPWide);
+    const uint64_t items = rows * ws.groups;
+    const uint64_t need = (items + wpc - 1) / wpc;
+    const uint64_t cap = (uint64_t)sm_count * per_sm;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    const uint64_t T = (uint64_t)grid * wpc;
+    ws.tg = T % ws.groups;
+    ws.tr = T / ws.groups;
+    scan_pitched_wide_kernel<KIND, CARRY><<<grid, kPThreads, 0, st>>>(img, job, ri, scr, out, ws);
+    return cudaGetLastError();
+  }
+  static int per_sm = 0;
+  if (!per_sm &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+           &per_sm, scan_pitched_narrow_kernel<KIND, CARRY>, kPThreads, 0) != cudaSuccess ||
+       per_sm < 1))
+    per_sm = 1;
+  uint32_t lp = 0;
+  while ((1ull << lp) < kmax) lp++;
+  const uint64_t per_warp = (32ull >> lp) * kPNarrow;
+  const uint64_t need = (rows + per_warp * wpc - 1) / (per_warp * wpc);
+  const uint64_t cap = (uint64_t)sm_count * per_sm;
+  const unsigned grid = (unsigned)(need < cap ? need : cap);
+  scan_pitched_narrow_kernel<KIND, CARRY><<<grid, kPThreads, 0, st>>>(img, job, ri, scr, out, lp);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_scan_pitched(const Image &img, const PitchedJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int sm_count,
-                                cudaStream_t st) {
-  const uint64_t kmax = (job.width + 30) >> 4;  // anchor chunks of a row, any alignment
-  const bool wide = kmax > 32;
-  uint32_t lp = 0;
-  while ((1ull << lp) < kmax && lp < 5) lp++;
-  PitchedGrid pg;
-  pg.lp = wide ? 5 : lp;
-  const uint64_t per_group = wide ? 32ull * kPWide : 1ull << pg.lp;
-  pg.groups = (kmax + per_group - 1) / per_group;
-  const uint64_t per_unit = 32ull >> pg.lp;
-  const uint64_t rows = job.height * job.depth;
-  const uint64_t units = (rows * pg.groups + per_unit - 1) / per_unit;
-  void *fn = pick_pitched(job.kind, job.mode & kModeCarry, wide);
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  const uint64_t warps_per_cta = kPThreads / 32;
-  const uint64_t need = (units + warps_per_cta - 1) / warps_per_cta;
-  const uint64_t cap = (uint64_t)sm_count * (uint64_t)per_sm;
-  const unsigned grid = (unsigned)(need < 1 ? 1 : (need < cap ? need : cap));
-  const uint64_t T = (uint64_t)grid * warps_per_cta * per_unit;  // groups per grid step
-  pg.tg = T % pg.groups;
-  const uint64_t tr = T / pg.groups;
-  pg.ty = tr % job.height;
-  pg.tz = tr / job.height;
-  void *args[] = {const_cast<Image *>(&img), const_cast<PitchedJob *>(&job),
-                  const_cast<RangeInfo *>(&ri), &scr, &out, &pg};
-  return cudaLaunchKernel(fn, dim3(grid), dim3(kPThreads), args, 0, st);
+                                uint64_t row_chunks, bool tma_ok, cudaStream_t st) {
+  const bool carry = job.mode & kModeCarry;
+  switch (job.kind) {
+    case CG_HTOD:
+      return carry ? launch_t<CG_HTOD, true>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st)
+                   : launch_t<CG_HTOD, false>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st);
+    case CG_DTOH:
+      return carry ? launch_t<CG_DTOH, true>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st)
+                   : launch_t<CG_DTOH, false>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st);
+    default:
+      return carry ? launch_t<CG_DTOD, true>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st)
+                   : launch_t<CG_DTOD, false>(img, job, ri, scr, out, sm_count, row_chunks, tma_ok, st);
+  }
 }
 
 // ------------------------------------------------- staging an overlap

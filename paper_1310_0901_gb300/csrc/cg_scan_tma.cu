@@ -17,160 +17,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "cg_device.cuh"
-
-#ifndef CG_TMA_R
-#define CG_TMA_R 8
-#endif
-#ifndef CG_TMA_NS
-#define CG_TMA_NS 2
-#endif
-#ifndef CG_TMA_WARPS
-#define CG_TMA_WARPS 16
-#endif
+#include "cg_tma.cuh"
 
 namespace cgi {
-
-constexpr int kR = CG_TMA_R;       // warp rows per tile
-constexpr int kNS = CG_TMA_NS;     // stages per warp
-constexpr int kTW = CG_TMA_WARPS;  // warps per CTA
-constexpr uint32_t kVBytes = 16u * (32u * kR + 1u);                 // V window of a tile
-constexpr uint32_t kABytes = 64u * kR + 64u;                        // A window of a tile
-constexpr uint32_t kStage = ((kVBytes + kABytes) + 127u) & ~127u;  // one stage
-constexpr uint32_t kWarpSmem = kNS * kStage;
-constexpr size_t kSmemBytes = (size_t)kTW * kWarpSmem + (size_t)kTW * kNS * 8 + 128;
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
-
-// ------------------------------------------------------------------ PTX
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait for a stage; false if about one second passes first.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
-  }
-}
-
-__device__ __forceinline__ int64_t floor16(int64_t x) { return x & ~(int64_t)15; }
-__device__ __forceinline__ int64_t ceil16(int64_t x) { return (x + 15) & ~(int64_t)15; }
-
-// Lane 0: queue the V and A bytes of the tile starting at anchor chunk c0
-// into the stage at `st` (shared address), completion on `bar`.
-template <uint32_t KIND>
-__device__ __forceinline__ void issue_tile(const Geo &g, const uint8_t *a_bytes, int64_t c0,
-                                           uint32_t st, uint32_t bar) {
-  uint32_t tx = 0, vbytes = 0, abytes = 0, voff = 0, aoff = 0;
-  uintptr_t vsrc = 0;
-  int64_t asrc = 0;
-  if (KIND == CG_HTOD || g.has_vin) {
-    // aligned V chunks of the tile, clipped to the chunks the copy touches
-    const uintptr_t vbeg = g.vin_al + 16 * (uintptr_t)c0;
-    const uintptr_t vend = vbeg + kVBytes;
-    const uintptr_t lo_lim = g.vin_lo & ~(uintptr_t)15;
-    const uintptr_t hi_lim = (g.vin_hi + 15) & ~(uintptr_t)15;
-    const uintptr_t lo = vbeg > lo_lim ? vbeg : lo_lim;
-    const uintptr_t hi = vend < hi_lim ? vend : hi_lim;
-    if (hi > lo) {
-      vbytes = (uint32_t)(hi - lo);
-      voff = (uint32_t)(lo - vbeg);
-      vsrc = lo;
-      tx += vbytes;
-    }
-  }
-  if (KIND != CG_DTOD) {
-    // A bytes holding bits [p0, p1 + 32), clipped to the copy's host bits
-    const int64_t p0 = g.hb0 + 16 * c0;
-    const int64_t p1 = p0 + 512 * kR;
-    const int64_t aorig = floor16(p0 >> 3);
-    const int64_t q0 = p0 > g.hlo ? p0 : g.hlo;
-    const int64_t q1 = (p1 + 32) < g.hhi ? (p1 + 32) : g.hhi;
-    if (q1 > q0) {
-      const int64_t b0 = floor16(q0 >> 3);
-      const int64_t b1 = ceil16((q1 + 7) >> 3);
-      abytes = (uint32_t)(b1 - b0);
-      aoff = (uint32_t)(b0 - aorig);
-      asrc = b0;
-      tx += abytes;
-    }
-  }
-  mbar_arrive_expect_tx(bar, tx);
-  if (vbytes) bulk_g2s(st + voff, reinterpret_cast<const void *>(vsrc), vbytes, bar);
-  if (abytes) bulk_g2s(st + kVBytes + aoff, a_bytes + asrc, abytes, bar);
-}
-
-// All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
-template <uint32_t KIND, bool CARRY>
-__device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uint8_t *sp,
-                                             int lane, LaneAcc &la) {
-  const uint4 *vs = reinterpret_cast<const uint4 *>(sp);
-  const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
-  const int64_t aorig = floor16((g.hb0 + 16 * c0) >> 3);
-  const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
-  const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
-#pragma unroll 4
-  for (int u = 0; u < kR; u++) {
-    const int k = 32 * u + lane;
-    const int64_t c = c0 + k;
-    uint4 V = make_uint4(0, 0, 0, 0);
-    if (KIND == CG_HTOD || g.has_vin) {
-      V = vs[k];
-      if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
-    }
-    uint32_t a16 = 0xFFFFu;
-    if (KIND != CG_DTOD) {
-      const int64_t q = g.hb0 + 16 * c;
-      const int sh = (int)(q & 31);
-      const int64_t wi = (((q >> 5) << 2) - aorig) >> 2;
-      const uint32_t w0 = as[wi];
-      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
-      a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
-    }
-    const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * c - g.ax, g.n);
-    chunk_step<KIND, CARRY>(g, c, V, a16, vm, la);
-  }
-}
 
 template <uint32_t KIND, bool CARRY>
 __global__ void __launch_bounds__(kTW * 32, 1)
@@ -235,17 +84,6 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   single_epilogue(la, scr, ri, out, err);
 }
 
-// CTAs of a TMA kernel that fit on one SM (shared memory bound).
-template <typename K>
-static int tma_ctas_per_sm(K kernel) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kTW * 32, kSmemBytes) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  return n > 0 ? n : 1;
-}
 
 // ------------------------------------------------ batched: one level
 

@@ -230,3 +230,34 @@ def test_pitched_large_matches_oracle(cg, which):
     U.assert_same_report(got, o, which)
     b, s = int(w.table.base[0]), int(w.table.size[0])
     assert np.array_equal(ctx.read_device_shadow(b, s), orc.read_dev_v(b, s))
+
+
+def test_pitched_host_resident_image(cg):
+    """An image in pinned host memory (read in place, register kernels for
+    every row length): the mixed workload still equals the oracle."""
+    import torch
+    w = S.pitched(6, n_copies=150)
+    n = w.image.n
+    a_h = torch.from_numpy(w.image.a_bits[: n // 8].copy()).pin_memory()
+    v_h = torch.from_numpy(w.image.v.copy()).pin_memory()
+    ctx = cg.Context()
+    ctx.bind_host_shadow(a_h, v_h)
+    orc = O.Oracle(w.image.a_bits, w.image.v)
+    bases, sizes = U.sorted_table(w.table)
+    assert not ctx.register_allocs(bases, sizes).any()
+    for b, s_ in zip(bases, sizes):
+        assert orc.register_alloc(int(b), int(s_)) == 0
+    for j in w.table.freed:
+        assert ctx.free(int(w.table.base[j])) == orc.free(int(w.table.base[j])) == "OK"
+    for h, W, H, D in w.arrays:
+        assert ctx.register_array(h, W, H, D) == orc.register_array(h, W, H, D) == 0
+    wide = 0
+    for i, q in enumerate(w.copies):
+        st_g, g, st_o, o = _both(ctx, orc, q)
+        assert st_g == st_o, (i, st_g, st_o)
+        if st_o == 0:
+            U.assert_same_report(g, o, f"host image copy {i}")
+            wide += q["width"] >= 4096
+    assert wide > 0
+    torch.cuda.synchronize()
+    assert np.array_equal(v_h.numpy(), orc.read_host_v())
