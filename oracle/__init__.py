@@ -35,6 +35,7 @@ STATUS = {0: "OK", -1: "E_ARG", -2: "E_KIND", -3: "E_HOST_RANGE",
           -4: "E_ZERO_SIZE", -5: "E_WRAP", -6: "E_OVERLAP", -7: "E_NOMEM",
           -8: "E_RANGE"}
 STATUS_CODES = {name: code for code, name in STATUS.items()}
+ARG_READ, ARG_WRITE = 1, 2
 
 
 class OrReport(ctypes.Structure):
@@ -132,6 +133,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.or_read_dev_v.restype = i32
     lib.or_live_count.argtypes = [vp]
     lib.or_live_count.restype = u64
+    lib.or_memset.argtypes = [vp, u64, u64, u64, u64, ctypes.POINTER(OrReport)]
+    lib.or_memset.restype = i32
+    lib.or_check_kernel_args.argtypes = [vp, vp, vp, vp, u64, vp]
+    lib.or_check_kernel_args.restype = i32
     lib.or_check_copy3d.argtypes = [vp, ctypes.POINTER(OrCopy3d), ctypes.POINTER(OrReport)]
     lib.or_check_copy3d.restype = i32
     lib.or_register_array.argtypes = [vp, u64, u64, u64, u64]
@@ -217,6 +222,22 @@ class Oracle:
         r = OrReport()
         st = self.lib.or_check_copy3d(self._h, ctypes.byref(q), ctypes.byref(r))
         return st, report_dict(r)
+
+    def memset(self, dptr: int, width: int, height: int = 1, pitch: int = 0):
+        r = OrReport()
+        st = self.lib.or_memset(self._h, dptr, pitch, width, height, ctypes.byref(r))
+        return st, report_dict(r)
+
+    def check_kernel_args(self, ptr, nbytes, access):
+        """Arguments as three sequences; returns (status, list of report dicts)."""
+        p = np.ascontiguousarray(ptr, dtype=np.uint64)
+        b = np.ascontiguousarray(nbytes, dtype=np.uint64)
+        a = np.ascontiguousarray(access, dtype=np.uint32)
+        n = len(p)
+        reps = (OrReport * max(1, n))()
+        st = self.lib.or_check_kernel_args(self._h, p.ctypes.data, b.ctypes.data, a.ctypes.data,
+                                           n, reps)
+        return st, [report_dict(reps[i]) for i in range(n)]
 
     def register_array(self, handle: int, w: int, h: int, d: int = 1) -> int:
         return self.lib.or_register_array(self._h, handle, w, h, d)

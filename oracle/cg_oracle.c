@@ -44,6 +44,13 @@
  *   R22 the overlap warning of a pitched device->device copy is raised when
  *       the two spans intersect (for arrays: the same array, spans in its
  *       dense layout); the carry reads every source byte before writing.
+ *   R23 memset: the extent must lie in one allocation; the written bytes
+ *       become defined.  Kernel arguments: a read argument's range is
+ *       checked as a copy source and its undefined bytes counted (a warning
+ *       class); a write argument's as a destination, and the whole range
+ *       becomes defined after the launch; every read sees the state before
+ *       the launch; a zero extent checks only that the pointer lies in a
+ *       live allocation.
  */
 #include "cg_oracle.h"
 
@@ -725,6 +732,79 @@ int or_check_copy3d(or_state *s, const or_copy3d *q, or_report *r) {
         for (uint64_t i = 0; i < w; i++)
           *side_dev_byte(&ds, side_pos(&ds, i, y, z)) = tmp[(z * h + y) * w + i];
     free(tmp);
+  }
+  return OR_OK;
+}
+
+/* ------------------------------------- memset and kernel arguments */
+
+static void blank_report(or_report *r, uint64_t n) {
+  memset(r, 0, sizeof *r);
+  r->first_bad_off = -1;
+  r->first_unaddr_off = -1;
+  r->first_undef_off = -1;
+  r->race_seq = -1;
+  r->expected = n;
+}
+
+int or_memset(or_state *s, uint64_t dptr, uint64_t pitch, uint64_t width, uint64_t height,
+              or_report *r) {
+  if (!s || !r) return OR_E_ARG;
+  if (height > 1 && pitch < width) return OR_E_ARG;
+  if (width && height > UINT64_MAX / width) return OR_E_WRAP;
+  const uint64_t n = width * height;
+  blank_report(r, n);
+  if (n == 0) return OR_OK; /* R9 */
+  if (height - 1 > (UINT64_MAX - width) / (pitch ? pitch : 1)) return OR_E_WRAP;
+  const uint64_t ext = (height - 1) * pitch + width;
+  live_alloc *a = device_side(s, dptr, ext, &r->found_dst, &r->alloc_base_dst,
+                              &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_DST, OR_F_OVERRUN_DST);
+  r->n_good = n; /* nothing is read: no byte can be bad */
+  if (!a || !s->carry) return OR_OK;
+  int st = materialise(a);
+  if (st) return st;
+  for (uint64_t y = 0; y < height; y++)
+    for (uint64_t i = 0; i < width; i++) a->shadow[dptr + y * pitch + i - a->base] = 0x00;
+  return OR_OK;
+}
+
+int or_check_kernel_args(or_state *s, const uint64_t *ptr, const uint64_t *bytes,
+                         const uint32_t *access, uint64_t nargs, or_report *reps) {
+  if (!s || (nargs && (!ptr || !bytes || !access || !reps))) return OR_E_ARG;
+  for (uint64_t i = 0; i < nargs; i++)
+    if (access[i] == 0 || (access[i] & ~(OR_ARG_READ | OR_ARG_WRITE))) return OR_E_ARG;
+  /* every read sees the state before the launch */
+  for (uint64_t i = 0; i < nargs; i++) {
+    or_report *r = &reps[i];
+    blank_report(r, bytes[i]);
+    live_alloc *ra = NULL;
+    if (access[i] & OR_ARG_READ)
+      ra = device_side(s, ptr[i], bytes[i], &r->found_src, &r->alloc_base_src,
+                       &r->alloc_size_src, &r->flags, OR_F_UNALLOC_SRC, OR_F_OVERRUN_SRC);
+    if (access[i] & OR_ARG_WRITE)
+      (void)device_side(s, ptr[i], bytes[i], &r->found_dst, &r->alloc_base_dst,
+                        &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_DST, OR_F_OVERRUN_DST);
+    for (uint64_t k = 0; ra && k < bytes[i]; k++) {
+      if (dev_v(ra, ptr[i] + k - ra->base) == 0) continue;
+      r->n_undef++;
+      if (r->first_undef_off < 0) {
+        r->first_undef_off = (int64_t)k;
+        r->first_bad_off = (int64_t)k;
+        r->first_bad_kind = OR_BYTE_UNDEF;
+      }
+    }
+    r->n_good = bytes[i] - r->n_undef;
+    if (r->n_undef) r->flags |= OR_F_DEV_UNDEF_SRC;
+  }
+  if (!s->carry) return OR_OK;
+  /* then every written argument whose range is valid becomes defined */
+  for (uint64_t i = 0; i < nargs; i++) {
+    if (!(access[i] & OR_ARG_WRITE) || bytes[i] == 0) continue;
+    if (reps[i].flags & (OR_F_UNALLOC_DST | OR_F_OVERRUN_DST)) continue;
+    live_alloc *a = find_alloc(s, ptr[i]);
+    int st = materialise(a);
+    if (st) return st;
+    memset(a->shadow + (ptr[i] - a->base), 0x00, bytes[i]);
   }
   return OR_OK;
 }

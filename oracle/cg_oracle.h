@@ -155,6 +155,33 @@ int or_free_array(or_state *s, uint64_t handle, uint32_t *verdict);
 /* bytes [off, off+n) of an array's dense shadow */
 int or_read_array_v(const or_state *s, uint64_t handle, uint64_t off, uint64_t n, uint8_t *out);
 
+/* The memset wrappers (cuMemsetD8/16/32 and their 2-D forms; Sec. 2 wraps
+ * every driver call that touches device memory): height rows of width bytes
+ * at dptr + y*pitch (pitch >= width when height > 1, else OR_E_ARG).  The
+ * extent (height-1)*pitch + width must lie in one live allocation
+ * (UNALLOC_DST / OVERRUN_DST, found_dst as for a copy); then, with carry on,
+ * every written byte becomes defined.  expected = n_good = width*height
+ * (nothing is read).  width*height == 0 is a no-op. */
+int or_memset(or_state *s, uint64_t dptr, uint64_t pitch, uint64_t width, uint64_t height,
+              or_report *rep);
+
+/* Kernel launch arguments (Sec. 6 outlook: a cuLaunchKernel wrapper that
+ * checks the pointers a kernel is given).  Argument i: device pointer
+ * ptr[i], the bytes[i] the kernel may touch from there, access[i] = a
+ * nonzero subset of OR_ARG_READ | OR_ARG_WRITE (else OR_E_ARG, nothing
+ * done).  A read argument is checked as a copy source (UNALLOC_SRC /
+ * OVERRUN_SRC, found_src, alloc_*_src) and, when in range, its undefined
+ * device bytes are counted (n_undef, first_undef_off, DEV_UNDEF_SRC); a
+ * write argument as a destination (UNALLOC_DST / OVERRUN_DST).  bytes[i] ==
+ * 0 checks only that the pointer lies in a live allocation.  Every read
+ * sees the state before the launch; then (carry on) each write argument
+ * with a valid range becomes defined over its whole range.
+ * expected = bytes[i], n_good = bytes[i] - n_undef. */
+#define OR_ARG_READ 1u
+#define OR_ARG_WRITE 2u
+int or_check_kernel_args(or_state *s, const uint64_t *ptr, const uint64_t *bytes,
+                         const uint32_t *access, uint64_t nargs, or_report *reps);
+
 uint64_t or_emit_records(const or_report *reps, const uint32_t *kind,
                          const uint64_t *dst, const uint64_t *src,
                          const uint64_t *n, uint64_t nreq, int strict,

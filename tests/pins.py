@@ -857,12 +857,143 @@ def pin_pitched_args(lib):
     o.close()
 
 
+# ------------------------------------------------ memset, kernel arguments
+
+
+def pin_memset(lib, trials: int = 200):
+    """Memset wrappers: the range verdict equals set membership over the
+    extent; with a valid range exactly the written bytes become defined
+    (numpy model of the device space), nothing else changes; a failed range
+    changes nothing; a later device->host copy of the written bytes finds
+    them defined.  Argument rules: rows closer than the width, overflow,
+    empty memsets."""
+    rng = S.rng_for(53)
+    n_img = 1 << 14
+    a_bits, vv = _image(np.ones(n_img, bool), rng.integers(0, 256, n_img).astype(np.uint8))
+    base0 = 1 << 39
+    layout = [(0, 3000), (3000, 1000), (5000, 4000)]
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev = np.full(9000, 0xFF, np.uint8)
+    for b, sz in layout:
+        assert o.register_alloc(base0 + b, sz) == 0
+    o.check_copy(HTOD, base0 + 5000, 100, 4000)
+    dev[5000:9000] = vv[100:4100]
+    for t in range(trials):
+        w, h = int(rng.integers(1, 200)), int(rng.integers(1, 8))
+        pitch = w + int(rng.integers(0, 100)) if h > 1 else int(rng.integers(0, 300))
+        d = int(rng.integers(0, 9000))
+        st, r = o.memset(base0 + d, w, h, pitch)
+        assert st == 0
+        ext = (h - 1) * pitch + w
+        own = _owner(layout, d)
+        want = "UNALLOC" if own is None else \
+            "OK" if all(_owner(layout, a) == own for a in range(d, d + ext)) else "OVERRUN"
+        got = "UNALLOC" if r["flags"] & F["UNALLOC_DST"] else \
+            "OVERRUN" if r["flags"] & F["OVERRUN_DST"] else "OK"
+        assert got == want, (t, d, w, h, pitch, got, want)
+        assert r["expected"] == r["n_good"] == w * h and r["n_undef"] == r["n_unaddr"] == 0
+        if want == "OK":
+            rows = (d + np.arange(h)[:, None] * pitch + np.arange(w)[None, :]).ravel()
+            dev[rows] = 0
+        for b, sz in layout:
+            assert np.array_equal(o.read_dev_v(base0 + b, sz), dev[b:b + sz]), (t, b)
+    # a memset region copied back to the host is defined
+    st, _ = o.memset(base0 + 100, 64, 1)
+    st, r = o.check_copy(DTOH, 0, base0 + 100, 64)
+    assert st == 0 and r["n_undef"] == 0
+    E = O.STATUS_CODES
+    assert o.memset(base0, 10, 2, 9)[0] == E["E_ARG"]
+    assert o.memset(base0, 10, 1, 0)[0] == 0
+    assert o.memset(base0, 1 << 40, 1 << 30, 1 << 40)[0] == E["E_WRAP"]
+    st, r = o.memset(12345, 0, 7)
+    assert st == 0 and r["flags"] == 0 and r["expected"] == 0
+    o.close()
+    # carry off: verdicts only
+    o = O.Oracle(a_bits, vv, carry=False, lib=lib)
+    assert o.register_alloc(base0, 100) == 0
+    st, r = o.memset(base0, 100)
+    assert st == 0 and r["flags"] == 0
+    assert np.all(o.read_dev_v(base0, 100) == 0xFF)
+    o.close()
+
+
+def pin_kernel_args(lib, trials: int = 120):
+    """Kernel arguments: range verdicts by set membership (a zero extent:
+    containment of the pointer alone); undefined bytes of a read argument
+    counted against the device model, first offset relative to the
+    pointer; every read sees the state before the launch (an argument
+    written and read in the same launch still reports what was undefined);
+    afterwards exactly the valid write ranges are defined.  Access values
+    outside read/write are refused with nothing changed."""
+    rng = S.rng_for(59)
+    n_img = 1 << 14
+    v = rng.integers(0, 256, n_img).astype(np.uint8)
+    v[rng.random(n_img) < 0.6] = 0
+    a_bits, vv = _image(np.ones(n_img, bool), v)
+    base0 = 1 << 41
+    layout = [(0, 3000), (3000, 1000), (5000, 4000)]
+    R, W = O.ARG_READ, O.ARG_WRITE
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev = np.full(9000, 0xFF, np.uint8)
+    for b, sz in layout:
+        assert o.register_alloc(base0 + b, sz) == 0
+    o.check_copy(HTOD, base0 + 200, 0, 2800)
+    dev[200:3000] = v[:2800]
+    o.check_copy(HTOD, base0 + 5000, 4000, 4000)
+    dev[5000:9000] = v[4000:8000]
+    for t in range(trials):
+        k = int(rng.integers(1, 6))
+        ptr = [int(rng.integers(0, 9100)) for _ in range(k)]
+        if t % 3 == 0 and k > 1:
+            ptr[1] = ptr[0]     # aliasing arguments
+        nb = [int(rng.integers(0, 800)) if rng.random() > 0.1 else 0 for _ in range(k)]
+        acc = [int(rng.choice([R, W, R | W])) for _ in range(k)]
+        st, reps = o.check_kernel_args([base0 + p for p in ptr], nb, acc)
+        assert st == 0
+        after = dev.copy()
+        for i in range(k):
+            r = reps[i]
+            own = _owner(layout, ptr[i])
+            if own is None:
+                want = "UNALLOC"
+            elif all(_owner(layout, a) == own for a in range(ptr[i], ptr[i] + nb[i])):
+                want = "OK"
+            else:
+                want = "OVERRUN"
+            for side, bit in (("SRC", R), ("DST", W)):
+                got = "UNALLOC" if r["flags"] & F["UNALLOC_" + side] else \
+                    "OVERRUN" if r["flags"] & F["OVERRUN_" + side] else "OK"
+                assert got == (want if acc[i] & bit else "OK"), (t, i, side, got, want)
+            assert r["expected"] == nb[i]
+            if acc[i] & R and want == "OK":
+                seg = dev[ptr[i]:ptr[i] + nb[i]]          # the state before the launch
+                bad = np.nonzero(seg != 0)[0]
+                assert r["n_undef"] == bad.size and r["n_good"] == nb[i] - bad.size
+                assert r["first_undef_off"] == (int(bad[0]) if bad.size else -1)
+                assert bool(r["flags"] & F["DEV_UNDEF_SRC"]) == bool(bad.size)
+            else:
+                assert r["n_undef"] == 0 and not r["flags"] & F["DEV_UNDEF_SRC"]
+            if acc[i] & W and want == "OK":
+                after[ptr[i]:ptr[i] + nb[i]] = 0
+        dev = after
+        for b, sz in layout:
+            assert np.array_equal(o.read_dev_v(base0 + b, sz), dev[b:b + sz]), (t, b)
+    # refused as a whole: nothing changes
+    before = o.read_dev_v(base0, 3000).copy()
+    st, _ = o.check_kernel_args([base0, base0], [100, 100], [W, 4])
+    assert st == O.STATUS_CODES["E_ARG"]
+    st, _ = o.check_kernel_args([base0], [100], [0])
+    assert st == O.STATUS_CODES["E_ARG"]
+    assert np.array_equal(o.read_dev_v(base0, 3000), before)
+    o.close()
+
+
 ALL_PINS = [
     pin_listing5, pin_htod_bytes_by_construction, pin_dtoh_bytes_by_construction,
     pin_range_bruteforce, pin_free_sequences, pin_free_sequences_reuse, pin_generator_truth,
     pin_invariants, pin_carry_roundtrip, pin_dtod_memmove, pin_records,
     pin_host_range_errors, pin_races, pin_strided_footnote, pin_pitched_reduces_to_1d,
-    pin_pitched_bruteforce, pin_arrays, pin_pitched_args,
+    pin_pitched_bruteforce, pin_arrays, pin_pitched_args, pin_memset, pin_kernel_args,
 ]
 
 

@@ -102,6 +102,25 @@ MUTANTS = {
         "s->host_v[hp] = side_dev_v(&ss, side_pos(&ss, i, y, z));"),
     "p3_origin_ignores_y": ("const uint64_t o1 = q->z * sl, o2 = q->y * p;",
                             "const uint64_t o1 = q->z * sl, o2 = 0;"),
+    # memset and kernel arguments
+    "ms_carry_ignores_pitch": ("a->shadow[dptr + y * pitch + i - a->base] = 0x00;",
+                               "a->shadow[dptr + y * width + i - a->base] = 0x00;"),
+    "ms_extent_whole_pitch": ("const uint64_t ext = (height - 1) * pitch + width;",
+                              "const uint64_t ext = height * pitch;"),
+    "ms_pitch_check_dropped": ("if (height > 1 && pitch < width) return OR_E_ARG;", ""),
+    "ka_counts_full_masks_only": ("if (dev_v(ra, ptr[i] + k - ra->base) == 0) continue;",
+                                  "if (dev_v(ra, ptr[i] + k - ra->base) != 0xFF) continue;"),
+    "ka_write_short_by_one": ("memset(a->shadow + (ptr[i] - a->base), 0x00, bytes[i]);",
+                              "memset(a->shadow + (ptr[i] - a->base), 0x00, bytes[i] - 1);"),
+    "ka_write_as_src_flags": (
+        "(void)device_side(s, ptr[i], bytes[i], &r->found_dst, &r->alloc_base_dst,\n"
+        "                        &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_DST, OR_F_OVERRUN_DST);",
+        "(void)device_side(s, ptr[i], bytes[i], &r->found_dst, &r->alloc_base_dst,\n"
+        "                        &r->alloc_size_dst, &r->flags, OR_F_UNALLOC_SRC, OR_F_OVERRUN_SRC);"),
+    "ka_invalid_write_defines": ("if (reps[i].flags & (OR_F_UNALLOC_DST | OR_F_OVERRUN_DST)) continue;",
+                                 "if (reps[i].flags & OR_F_UNALLOC_DST) continue;"),
+    "ka_access_unchecked": ("if (access[i] == 0 || (access[i] & ~(OR_ARG_READ | OR_ARG_WRITE))) return OR_E_ARG;",
+                            "if (access[i] == 0) return OR_E_ARG;"),
     "batch_not_validated_first": (
         "    int st = validate(s, kind[i], dst[i], src[i], n[i]);\n    if (st) {",
         "    int st = 0;\n    if (st) {"),
