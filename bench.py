@@ -509,7 +509,118 @@ def run_pitched(args):
     return out
 
 
+def run_devops(args):
+    """Memset and kernel-argument checks, timed with CUDA events: a 1 GiB
+    memset (its shadow fill is 1 B written per byte), one launch with four
+    256 MiB arguments (read scans 1 B read per byte, write fills 1 B written
+    per byte), and the per-launch latency of checking the arguments of many
+    small launches (1-6 arguments of 16 B - 64 KiB) against a table of
+    100,000 allocations."""
+    import torch
+
+    import paper_1310_0901_gb300 as cg
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = _peaks()
+    wl = S.devops_large()
+    ctx = cg.Context()
+    a_dev = torch.from_numpy(wl.image.a_bits[: wl.image.n // 8].copy()).to(dev)
+    v_dev = torch.from_numpy(wl.image.v).to(dev)
+    ctx.bind_host_shadow(a_dev, v_dev)
+    for b, s_ in sorted(zip(wl.table.base.tolist(), wl.table.size.tolist())):
+        cg.check(ctx.register_alloc(int(b), int(s_)), "register")
+    for q in wl.setup:
+        cg.check(ctx.check_copy(*q)[0], "setup")
+    k0 = ctx.stats()["kernels"]
+    clocks = Clocks(dev.index)
+    clocks.start()
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    d, pitch, wd, h = wl.memset
+    ms_memset = timed(lambda: cg.check(ctx.check_memset(d, wd, h, pitch, stream)[0], "memset"),
+                      args.steps)
+    n_set = wd * h
+    ms_launch = timed(lambda: cg.check(ctx.check_kernel_args(wl.args, stream)[0], "args"),
+                      args.steps)
+    st, reps, _ = ctx.check_kernel_args(wl.args, stream)
+    launches = ctx.stats()["kernels"] - k0
+    moved = int(sum(int(x["bytes"]) for x in wl.args if x["access"] & S.ARG_READ)) + \
+        int(sum(int(x["bytes"]) for x in wl.args if x["access"] & S.ARG_WRITE))
+    ctx.close()
+    del a_dev, v_dev
+    torch.cuda.empty_cache()
+    # many small launches over a 100k-entry table: host-timed latency per call
+    rng = S.rng_for(77)
+    table = S.alloc_table(rng, 100_000, 256, 1 << 20, True)
+    small = S.kernel_launches(rng, 2000, table)
+    ctx = cg.Context()
+    order = np.argsort(table.base)
+    st_ = ctx.register_allocs(table.base[order], table.size[order])
+    assert not st_.any()
+    for x in small[:50]:
+        cg.check(ctx.check_kernel_args(x, stream)[0], "args")
+    torch.cuda.synchronize()
+    lat = []
+    for x in small:
+        t0 = time.perf_counter()
+        cg.check(ctx.check_kernel_args(x, stream)[0], "args")
+        lat.append((time.perf_counter() - t0) * 1e6)
+    lat = np.array(lat)
+    launches += ctx.stats()["kernels"]
+    ctx.close()
+    clk = clocks.stop()
+    fill_gbs = n_set / (ms_memset / 1e3) / GB
+    launch_gbs = moved / (ms_launch / 1e3) / GB
+    out = {
+        "metric": "memset / kernel-argument checks: shadow GB/s vs HBM peak; per-launch latency",
+        "unit": "GB/s", "value": round(fill_gbs, 1), "steps": args.steps,
+        "warmup": max(3, args.warmup), "gpu_launches": int(launches),
+        "config": {"workload": "devops_large (1 GiB memset; 4 x 256 MiB arguments) + 2000 small "
+                               "launches over 100k allocations",
+                   "l2": "inputs larger than L2; no flush"},
+        "memset": {"bytes": n_set, "ms": round(ms_memset, 4), "gb_per_s": round(fill_gbs, 1),
+                   "roofline": {"bound": "hbm", "kernel": "fill_rows_kernel",
+                                "bytes_per_byte": 1.0, "achieved": round(fill_gbs, 1),
+                                "peak": peak, "unit": "GB/s",
+                                "frac": round(fill_gbs / peak, 4), "peak_source": peak_kind}},
+        "large_launch": {"args": len(wl.args), "bytes_read_plus_written": moved,
+                         "ms": round(ms_launch, 4), "gb_per_s": round(launch_gbs, 1),
+                         "roofline": {"bound": "hbm", "bytes_per_byte": 1.0,
+                                      "achieved": round(launch_gbs, 1), "peak": peak,
+                                      "unit": "GB/s", "frac": round(launch_gbs / peak, 4),
+                                      "peak_source": peak_kind},
+                         "n_undef": [int(r["n_undef"]) for r in reps]},
+        "small_launches": {"launches": len(small), "table": 100_000,
+                           "args_per_launch_mean": round(float(np.mean([len(x) for x in small])), 2),
+                           "latency_us": {"p50": round(float(np.percentile(lat, 50)), 1),
+                                          "p99": round(float(np.percentile(lat, 99)), 1)},
+                           "launches_per_s": round(len(small) / (lat.sum() / 1e6), 1)},
+    }
+    if clk is not None:
+        out["clocks"] = clk
+    return out
+
+
 def _summary(key: str, d: dict) -> dict:
+    if key == "devops":
+        return {"workload": d["config"]["workload"],
+                "memset_gb_per_s": d["memset"]["gb_per_s"],
+                "memset_roofline_frac": d["memset"]["roofline"]["frac"],
+                "large_launch_gb_per_s": d["large_launch"]["gb_per_s"],
+                "large_launch_roofline_frac": d["large_launch"]["roofline"]["frac"],
+                "small_launch_latency_us": d["small_launches"]["latency_us"]}
     if key == "pitched":
         return {"workload": d["config"]["workload"],
                 **{k: {"checked_gb_per_s": v["checked_gb_per_s"],
@@ -626,7 +737,7 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--engine", type=int, default=0, help="0 auto, 1 register loads, 2 TMA bulk")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "batched", "adversarial", "serving", "pitched"])
+                    choices=["large", "batched", "adversarial", "serving", "pitched", "devops"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=S.SERVE_RATE)
     ap.add_argument("--serve-image-gib", type=int, default=32)
@@ -647,9 +758,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_serving(args)), flush=True)
         return
-    if args.workload == "pitched":
+    if args.workload in ("pitched", "devops"):
         if rank == 0:
-            print(json.dumps(run_pitched(args)), flush=True)
+            fn = run_pitched if args.workload == "pitched" else run_devops
+            print(json.dumps(fn(args)), flush=True)
         return
     if args.workload != "large":
         if rank == 0:
@@ -672,7 +784,8 @@ def main():
             torch.cuda.empty_cache()
             for key, fn in (("batched", lambda: run_batched_workload(args, "batched")),
                             ("serving", lambda: run_serving(args)),
-                            ("pitched", lambda: run_pitched(args))):
+                            ("pitched", lambda: run_pitched(args)),
+                            ("devops", lambda: run_devops(args))):
                 try:
                     out[key] = _summary(key, fn())
                 except Exception as exc:  # reported, never hides the headline

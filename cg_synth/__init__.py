@@ -581,3 +581,95 @@ def pitched_large(which: str = "wide", seed: int = 0) -> PitchedWorkload:
     copy = dict(kind=HTOD, dst=side3d(int(bases[0]), dp, h), src=side3d(0, hp, h), width=w,
                 height=h, depth=1)
     return PitchedWorkload(image, table, [], [copy], f"pitched_{which}")
+
+
+# ------------------------------------------- memsets and kernel launches
+
+KARG_DTYPE = np.dtype([("ptr", "<u8"), ("bytes", "<u8"), ("access", "<u4"), ("reserved", "<u4")])
+ARG_READ, ARG_WRITE = 1, 2
+
+
+def kernel_launches(rng, n_launch: int, table: AllocTable, max_args: int = 6,
+                    bytes_lo: int = 16, bytes_hi: int = 64 << 10, p_bad: float = 0.08,
+                    p_zero: float = 0.05) -> list:
+    """Pointer arguments of n_launch kernel launches: 1..max_args each, read,
+    write or both (40/35/25), extents log-uniform in [bytes_lo, bytes_hi]
+    placed inside a live allocation; p_bad of them overrun it or point at a
+    freed one, p_zero have no extent (pointer check only); some launches
+    pass the same buffer twice."""
+    live = np.setdiff1d(np.arange(len(table.base)), table.freed)
+    out = []
+    for _ in range(n_launch):
+        k = int(rng.integers(1, max_args + 1))
+        a = np.zeros(k, KARG_DTYPE)
+        for i in range(k):
+            acc = int(rng.choice([ARG_READ, ARG_WRITE, ARG_READ | ARG_WRITE], p=[0.4, 0.35, 0.25]))
+            n = 0 if rng.random() < p_zero else int(log_uniform_int(rng, bytes_lo, bytes_hi, 1)[0])
+            u = rng.random()
+            if u < p_bad / 3 and len(table.freed):
+                j = int(rng.choice(table.freed))
+                ptr = int(table.base[j]) + int(rng.integers(0, int(table.size[j])))
+            else:
+                j = int(rng.choice(live))
+                b, s = int(table.base[j]), int(table.size[j])
+                if u < p_bad:      # runs past the end
+                    ptr = b + max(0, s - max(1, n // 2))
+                else:
+                    ptr = b + int(rng.integers(0, max(1, s - n + 1)))
+            a[i] = (ptr, n, acc, 0)
+        if k > 1 and rng.random() < 0.15:
+            a[1]["ptr"] = a[0]["ptr"]
+        out.append(a)
+    return out
+
+
+def memsets(rng, count: int, table: AllocTable, p_bad: float = 0.1) -> list:
+    """(dptr, pitch, width, height) of cuMemsetD8/D2D-style calls inside
+    live allocations; p_bad of them run past the allocation's end."""
+    live = np.setdiff1d(np.arange(len(table.base)), table.freed)
+    out = []
+    for _ in range(count):
+        j = int(rng.choice(live))
+        b, s = int(table.base[j]), int(table.size[j])
+        if rng.random() < 0.5:
+            h, w = 1, int(rng.integers(1, s + 1))
+            pitch = 0
+        else:
+            h = int(rng.integers(2, 33))
+            w = int(rng.integers(1, max(2, s // h)))
+            pitch = w + int(rng.integers(0, 64))
+        ext = (h - 1) * pitch + w
+        if rng.random() < p_bad:
+            d = b + max(0, s - ext + int(rng.integers(1, 64)))
+        else:
+            d = b + int(rng.integers(0, max(1, s - ext + 1)))
+        out.append((d, pitch, w, h))
+    return out
+
+
+@dataclass
+class DevopsWorkload:
+    image: HostImage
+    table: AllocTable
+    setup: list      # (kind, dst, src, n) copies run first
+    memset: tuple    # (dptr, pitch, width, height)
+    args: np.ndarray  # KARG_DTYPE: one launch
+    name: str = "devops"
+
+
+def devops_large(seed: int = 0) -> DevopsWorkload:
+    """A 1 GiB memset and one launch with four 256 MiB pointer arguments:
+    read (a buffer copied from a host image with undefined runs, density
+    1e-6), read+write (another such buffer), write (a fresh buffer), read
+    (the memset buffer).  16 allocations in all."""
+    rng = rng_for(9000 + seed)
+    n = 256 << 20
+    image = host_image_runs(rng, n, undef_frac=1e-6, mean_run=8.0)
+    sizes = np.array([1 << 30, n, n, n] + [1 << 20] * 12, dtype=np.uint64)
+    bases = disjoint_bases(rng, sizes)
+    table = AllocTable(bases, sizes, np.zeros(0, np.int64))
+    A, B, C, D = (int(x) for x in bases[:4])
+    setup = [(HTOD, B, 0, n), (HTOD, C, 0, n)]
+    args = np.array([(B, n, ARG_READ, 0), (C, n, ARG_READ | ARG_WRITE, 0), (D, n, ARG_WRITE, 0),
+                     (A + (64 << 20), n, ARG_READ, 0)], KARG_DTYPE)
+    return DevopsWorkload(image, table, setup, (A, 0, 1 << 30, 1), args)

@@ -365,6 +365,53 @@ cg_status cg_check_copy3d(cg_ctx *ctx, const cg_copy3d *req, cg_report *rep, voi
 cg_status cg_check_copy3d_async(cg_ctx *ctx, const cg_copy3d *req, cg_report *rep_dev,
                                 void *stream);
 
+/* --------------------------------------- memset and kernel arguments */
+
+/* The memset wrappers' check (cuMemsetD8/D16/D32 and cuMemsetD2D8/16/32:
+ * every driver call that writes device memory is wrapped, Sec. 2): height
+ * rows of width BYTES (elements x element size) at dptr + y*pitch.  The
+ * extent (height-1)*pitch + width must lie in one live allocation
+ * (UNALLOC_DST / OVERRUN_DST, found_dst and alloc_*_dst as for a copy);
+ * with carry on, the written bytes then become defined (V = 0).  expected =
+ * n_good = width*height (nothing is read).  width*height == 0 is a no-op.
+ * API errors: CG_E_ARG (pitch < width with height > 1), CG_E_WRAP.  *rep
+ * (host) is final at return; the shadow update is enqueued on `stream`. */
+cg_status cg_check_memset(cg_ctx *ctx, uint64_t dptr, uint64_t pitch, uint64_t width,
+                          uint64_t height, cg_report *rep, void *stream);
+
+/* The same, with the report written to rep_dev (device or mapped pinned
+ * memory) when `stream` reaches it. */
+cg_status cg_check_memset_async(cg_ctx *ctx, uint64_t dptr, uint64_t pitch, uint64_t width,
+                                uint64_t height, cg_report *rep_dev, void *stream);
+
+/* One pointer argument of a kernel launch (the cuLaunchKernel wrapper of
+ * the paper's outlook, Sec. 6): the device pointer, the bytes the kernel
+ * may touch from it, and how (CG_ARG_READ, CG_ARG_WRITE or both).
+ * reserved must be 0.  24 bytes. */
+#define CG_ARG_READ 1u  /* reads [ptr, ptr+bytes): undefined bytes are reported */
+#define CG_ARG_WRITE 2u /* writes all of [ptr, ptr+bytes): it becomes defined */
+typedef struct cg_karg {
+  uint64_t ptr;
+  uint64_t bytes;
+  uint32_t access;
+  uint32_t reserved;
+} cg_karg;
+
+/* Check the pointer arguments args[0..nargs) of one launch, one report
+ * each (reps: host, may be NULL).  A read argument is checked as a copy
+ * source (UNALLOC_SRC / OVERRUN_SRC, found_src, alloc_*_src) and, in range,
+ * its undefined device bytes are counted (n_undef, first_undef_off, the
+ * DEV_UNDEF_SRC warning, an error in strict mode); a write argument as a
+ * destination (UNALLOC_DST / OVERRUN_DST).  bytes == 0: only that the
+ * pointer lies in a live allocation.  Every read sees the state before the
+ * launch; then, with carry on, every write argument in range becomes
+ * defined over its whole range.  expected = bytes, n_good = bytes -
+ * n_undef.  Synchronous.  CG_E_ARG (an access outside READ|WRITE, or 0;
+ * reserved != 0) refuses the whole call, *bad_index (may be NULL) = the
+ * argument. */
+cg_status cg_check_kernel_args(cg_ctx *ctx, const cg_karg *args, uint64_t nargs,
+                               cg_report *reps, uint64_t *bad_index, void *stream);
+
 /* ------------------------------------------------ choosing the batch split */
 
 /* How cg_check_batch cuts copies into segments matters (too small: per-

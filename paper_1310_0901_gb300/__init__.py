@@ -38,6 +38,14 @@ class cg_copy(ctypes.Structure):
     _fields_ = [("kind", u32), ("reserved", u32), ("dst", u64), ("src", u64), ("n", u64)]
 
 
+class cg_karg(ctypes.Structure):
+    _fields_ = [("ptr", u64), ("bytes", u64), ("access", u32), ("reserved", u32)]
+
+
+ARG_READ, ARG_WRITE = 1, 2
+KARG_DTYPE = np.dtype([("ptr", "<u8"), ("bytes", "<u8"), ("access", "<u4"), ("reserved", "<u4")])
+
+
 class cg_side3d(ctypes.Structure):
     _fields_ = [("ptr", u64), ("pitch", u64), ("rows", u64), ("x", u64), ("y", u64),
                 ("z", u64), ("is_array", u32), ("reserved", u32)]
@@ -150,6 +158,9 @@ SIGNATURES = [
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
+    ("cg_check_memset", i32, [vp, u64, u64, u64, u64, vp, vp]),
+    ("cg_check_memset_async", i32, [vp, u64, u64, u64, u64, vp, vp]),
+    ("cg_check_kernel_args", i32, [vp, vp, u64, vp, ctypes.POINTER(u64), vp]),
     ("cg_register_array", i32, [vp, u64, u64, u64, u64]),
     ("cg_free_array", i32, [vp, u64, ctypes.POINTER(u32)]),
     ("cg_read_array_shadow", i32, [vp, u64, u64, u64, vp]),
@@ -296,6 +307,24 @@ class Context:
         r = cg_report()
         st = cg_check_copy3d(self._h, ctypes.byref(q), ctypes.byref(r), _stream_handle(stream))
         return st, report_to_dict(r)
+
+    def check_memset(self, dptr: int, width: int, height: int = 1, pitch: int = 0, stream=None):
+        """A memset of height rows of width bytes at dptr + y*pitch."""
+        r = cg_report()
+        st = cg_check_memset(self._h, dptr, pitch, width, height, ctypes.byref(r),
+                             _stream_handle(stream))
+        return st, report_to_dict(r)
+
+    def check_kernel_args(self, args: np.ndarray, stream=None):
+        """args: structured array of KARG_DTYPE.  Returns (status, reports as
+        a structured array, bad index)."""
+        args = np.ascontiguousarray(args, dtype=KARG_DTYPE)
+        n = len(args)
+        reps = np.zeros(max(1, n), dtype=REPORT_DTYPE)
+        bad = u64(0)
+        st = cg_check_kernel_args(self._h, args.ctypes.data if n else None, n, reps.ctypes.data,
+                                  ctypes.byref(bad), _stream_handle(stream))
+        return st, reps[:n], int(bad.value)
 
     def register_array(self, handle: int, width: int, height: int, depth: int = 1) -> int:
         return cg_register_array(self._h, handle, width, height, depth)

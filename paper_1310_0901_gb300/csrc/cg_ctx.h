@@ -485,6 +485,9 @@ struct cg_ctx {
     float best_ms = 0.f;
   };
   std::vector<OnlineTune> online;
+  // kernel-argument checks: the arguments, fill spans and their groups
+  cgi::DevBuf<cg_karg> k_args;
+  cgi::DevBuf<uint64_t> k_fill;  // ptr[n], bytes[n], first group[n]
   // device arrays (Fig. 2's second list): handle -> dimensions and shadow
   struct ArrayInfo {
     uint64_t w, h, d;

@@ -225,6 +225,17 @@ cudaError_t launch_gather_rows(const uint8_t *src, uint64_t pitch, uint64_t slic
                                uint64_t width, uint64_t height, uint64_t depth, uint8_t *out,
                                int sm_count, cudaStream_t st);
 
+// Memset and kernel arguments (cg_devops_kernels.cu).
+cudaError_t launch_fill_rows(uint8_t *base, uint64_t pitch, uint64_t width, uint64_t rows,
+                             uint8_t value, const RangeInfo &ri, cg_report *out, int sm_count,
+                             cudaStream_t st);
+uint64_t fill_span_groups(uint64_t n);  // fill groups of a span of n bytes
+cudaError_t launch_fill_spans(const uint64_t *ptr, const uint64_t *n, const uint64_t *seg_first,
+                              uint64_t count, uint64_t nsegs, uint8_t value, int sm_count,
+                              cudaStream_t st);
+cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_karg *args,
+                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, cudaStream_t st);
+
 constexpr int kFinalizeItems = 1024;  // requests per finalize/emit block
 
 // Set the text cg_last_error() returns on this thread (cg_host.cpp).

@@ -46,6 +46,7 @@ def test_struct_sizes_match_header_comments():
     assert ctypes.sizeof(cg.cg_copy) == 32
     assert ctypes.sizeof(cg.cg_report) == 120
     assert ctypes.sizeof(cg.cg_err_record) == 48
+    assert ctypes.sizeof(cg.cg_karg) == 24 == cg.KARG_DTYPE.itemsize
     assert ctypes.sizeof(cg.cg_side3d) == 56 == ctypes.sizeof(O.OrSide3d)
     assert ctypes.sizeof(cg.cg_copy3d) == 144 == ctypes.sizeof(O.OrCopy3d)
     assert S.REQ_DTYPE.itemsize == 32
