@@ -385,7 +385,7 @@ cg_status cg_check_memset_async(cg_ctx *ctx, uint64_t dptr, uint64_t pitch, uint
                                 uint64_t height, cg_report *rep_dev, void *stream);
 
 /* One pointer argument of a kernel launch (the cuLaunchKernel wrapper of
- * the paper's outlook, Sec. 6): the device pointer, the bytes the kernel
+ * the paper's outlook, Sec. 5.1): the device pointer, the bytes the kernel
  * may touch from it, and how (CG_ARG_READ, CG_ARG_WRITE or both).
  * reserved must be 0.  24 bytes. */
 #define CG_ARG_READ 1u  /* reads [ptr, ptr+bytes): undefined bytes are reported */

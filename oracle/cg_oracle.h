@@ -165,7 +165,7 @@ int or_read_array_v(const or_state *s, uint64_t handle, uint64_t off, uint64_t n
 int or_memset(or_state *s, uint64_t dptr, uint64_t pitch, uint64_t width, uint64_t height,
               or_report *rep);
 
-/* Kernel launch arguments (Sec. 6 outlook: a cuLaunchKernel wrapper that
+/* Kernel launch arguments (Sec. 5.1, Outlook: a cuLaunchKernel wrapper that
  * checks the pointers a kernel is given).  Argument i: device pointer
  * ptr[i], the bytes[i] the kernel may touch from there, access[i] = a
  * nonzero subset of OR_ARG_READ | OR_ARG_WRITE (else OR_E_ARG, nothing
