@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "cg_internal.h"
+#include "cg_launch.h"
 
 namespace cgi {
 

@@ -12,6 +12,7 @@
 
 #include "cg_device.cuh"
 #include "cg_table.cuh"
+#include "cg_launch.h"
 
 namespace cgi {
 

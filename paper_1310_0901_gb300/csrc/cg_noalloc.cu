@@ -18,6 +18,7 @@
 #include <string>
 
 #include "cg_internal.h"
+#include "cg_launch.h"
 
 namespace cgi {
 

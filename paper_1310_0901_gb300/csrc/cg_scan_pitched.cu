@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "cg_tma.cuh"
+#include "cg_launch.h"
 
 namespace cgi {
 

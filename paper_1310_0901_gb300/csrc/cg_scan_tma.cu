@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "cg_tma.cuh"
+#include "cg_launch.h"
 
 namespace cgi {
 
