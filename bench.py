@@ -29,6 +29,7 @@ import cg_synth as S  # noqa: E402
 
 GB = 1e9
 BYTES_PER_BYTE_CARRY = 2.125  # V read 1 + A read 1/8 + device V write 1
+BYTES_PER_BYTE_SCAN = 1.125  # V read 1 + A read 1/8 (what crosses the host link)
 
 
 def _peaks():
@@ -275,6 +276,21 @@ def run_cg(args, world, rank, local):
                                             for i, q in enumerate(w.reqs)}},
         "gpu_launches": int(launches),
     }
+    # the host link's rate for a plain pinned host->device copy (1 GiB of the
+    # image copied onto itself): the ceiling of both e2e modes
+    link_gbs = None
+    if args.e2e_steps > 0:
+        m = min(1 << 30, n_img)
+        for _ in range(2):
+            v_dev[:m].copy_(v_host[:m], non_blocking=True)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(4):
+            v_dev[:m].copy_(v_host[:m], non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = 4 * m / (c0.elapsed_time(c1) / 1e3) / GB
     if e2e_ms is not None:
         up = bytes_per_step * args.e2e_steps * world / (e2e_ms / 1e3) / GB
         inplace = bytes_per_step * args.e2e_steps * world / (zc_ms / 1e3) / GB if zc_ms else 0.0
@@ -284,6 +300,11 @@ def run_cg(args, world, rank, local):
                       "upload_then_check": round(up, 2), "in_place": round(inplace, 2),
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                       "steps": args.e2e_steps}
+        if link_gbs:
+            # a check reads 1.125 B of host shadow per checked byte
+            out["e2e"]["host_link_gbs"] = round(link_gbs, 1)
+            out["e2e"]["frac_of_host_link"] = round(max(up, inplace) * BYTES_PER_BYTE_SCAN
+                                                    / link_gbs, 4)
     if clk is not None:
         out["clocks"] = clk
     ctx.close()

@@ -619,6 +619,24 @@ cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, uint8_t *hos
                           uint8_t *dev_dst_shadow, uint64_t n, uint32_t carry,
                           cg_report *rep_dev, void *stream);
 
+/* ------------------------------------------------------- fault injection */
+
+/* Host-side hooks that make one failure happen on purpose, so that the
+ * error paths can be tested without faulting a GPU.  One-shot: the fault
+ * applies to the next operation that can take it, then is cleared.
+ *   CG_FAULT_STALL_COPY: the next single check that runs on the TMA engine
+ *     never issues one of its bulk copies, so the wait for that tile runs
+ *     out (about one second, %globaltimer): the report carries
+ *     CG_F_INCOMPLETE and cg_check_copy returns CG_E_TIMEOUT.  No copy is
+ *     left in flight; the context stays usable.
+ *   CG_FAULT_SHADOW_ALLOC: the next shadow allocation fails:
+ *     cg_register_alloc / cg_register_array return CG_E_NOMEM and the table
+ *     is unchanged. */
+#define CG_FAULT_NONE 0u
+#define CG_FAULT_STALL_COPY 1u
+#define CG_FAULT_SHADOW_ALLOC 2u
+cg_status cg_inject_fault(cg_ctx *ctx, uint32_t fault);
+
 /* ----------------------------------------------------------- diagnostics */
 
 /* The dependency levels cg_check_batch runs reqs[0..nreq) in (host only,

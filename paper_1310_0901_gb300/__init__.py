@@ -43,6 +43,7 @@ class cg_karg(ctypes.Structure):
 
 
 ARG_READ, ARG_WRITE = 1, 2
+FAULT_STALL_COPY, FAULT_SHADOW_ALLOC = 1, 2
 KARG_DTYPE = np.dtype([("ptr", "<u8"), ("bytes", "<u8"), ("access", "<u4"), ("reserved", "<u4")])
 
 
@@ -158,6 +159,7 @@ SIGNATURES = [
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
+    ("cg_inject_fault", i32, [vp, u32]),
     ("cg_check_memset", i32, [vp, u64, u64, u64, u64, vp, vp]),
     ("cg_check_memset_async", i32, [vp, u64, u64, u64, u64, vp, vp]),
     ("cg_check_kernel_args", i32, [vp, vp, u64, vp, ctypes.POINTER(u64), vp]),

@@ -496,6 +496,7 @@ struct cg_ctx {
   };
   std::unordered_map<uint64_t, ArrayInfo> arrays;
   std::unordered_set<uint64_t> freed_arrays;
+  uint32_t fault_pending = 0;  // CG_FAULT_* bits injected for the next operation
   cg_stats stats{};
   std::mutex stats_mu;                // guards stats while serving
   cgi::ServeEngine *serve = nullptr;  // non-null while serving

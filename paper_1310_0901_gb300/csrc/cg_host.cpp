@@ -366,9 +366,21 @@ cg_status cg_register_alloc(cg_ctx *c, uint64_t dptr, uint64_t size) {
   if (dptr + size < dptr) return set_error(CG_E_WRAP, "allocation wraps 2^64");
   if (c->table.overlaps(dptr, size))
     return set_error(CG_E_OVERLAP, "allocation overlaps a live allocation");
+  if (c->fault_pending & CG_FAULT_SHADOW_ALLOC) {
+    c->fault_pending &= ~CG_FAULT_SHADOW_ALLOC;
+    return set_error(CG_E_NOMEM, "shadow allocation failed (injected fault)");
+  }
   uint64_t sh = 0;
   CG_TRY(c->arena.alloc(size, &sh));
   c->table.insert(dptr, size, sh);
+  return CG_OK;
+}
+
+cg_status cg_inject_fault(cg_ctx *c, uint32_t fault) {
+  if (!c) return set_error(CG_E_ARG, "ctx is NULL");
+  if (fault & ~(CG_FAULT_STALL_COPY | CG_FAULT_SHADOW_ALLOC))
+    return set_error(CG_E_ARG, "unknown fault");
+  c->fault_pending |= fault;
   return CG_OK;
 }
 
@@ -509,11 +521,16 @@ static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, boo
                             cudaMemcpyDeviceToDevice, st));
     job.dev_src = reinterpret_cast<uint64_t>(c->stage.p);
   }
-  if (c->cfg.scan_engine == 1 || c->img_on_host)  // bulk copies read device memory only
+  if (c->cfg.scan_engine == 1 || c->img_on_host) {  // bulk copies read device memory only
     CG_CUDA(launch_scan_single(c->img, job, ri, c->d_scratch, out, single_grid(c, job), st));
-  else
+  } else {
+    if ((c->fault_pending & CG_FAULT_STALL_COPY) && job.n) {
+      job.mode |= kModeStall;
+      c->fault_pending &= ~CG_FAULT_STALL_COPY;
+    }
     CG_CUDA(launch_scan_single_tma(c->img, job, ri, c->d_scratch, out,
                                    scan_single_tma_grid(c->sm_count, job.n), st));
+  }
   c->stats.kernels++;
   c->stats.checks++;
   c->stats.bytes_checked += job.n;

@@ -19,6 +19,7 @@ constexpr unsigned long long kNone = ~0ull;  // "no offset" inside the kernels
 // job mode bits
 constexpr uint32_t kModeCarry = 1u;    // perform the V-shadow carry
 constexpr uint32_t kModeReadDev = 2u;  // device-source V is readable (valid src)
+constexpr uint32_t kModeStall = 4u;    // injected fault: one tile's copy is never issued
 
 // One copy as the scan kernels see it.  Addresses are absolute device
 // addresses of copy byte 0 (host V: host_v + host_off).

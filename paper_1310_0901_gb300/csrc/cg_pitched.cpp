@@ -231,6 +231,10 @@ cg_status cg_register_array(cg_ctx *c, uint64_t handle, uint64_t width, uint64_t
   if (mul_over(width, height, &wh) || mul_over(wh, depth, &bytes))
     return set_error(CG_E_WRAP, "array size exceeds 64 bits");
   if (c->arrays.count(handle)) return set_error(CG_E_OVERLAP, "array handle already live");
+  if (c->fault_pending & CG_FAULT_SHADOW_ALLOC) {
+    c->fault_pending &= ~CG_FAULT_SHADOW_ALLOC;
+    return set_error(CG_E_NOMEM, "shadow allocation failed (injected fault)");
+  }
   uint64_t sh = 0;
   CG_TRY(c->arena.alloc(bytes, &sh));
   c->arrays[handle] = cg_ctx::ArrayInfo{width, height, depth, sh};

@@ -49,7 +49,10 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   if (lane == 0)
     for (int s = 0; s < kNS; s++) {
       const int64_t t = gw + (int64_t)s * nw;
-      if (t < ntiles)
+      if (t >= ntiles) continue;
+      if ((job.mode & kModeStall) && gw == 0 && s == 0)  // injected: expect bytes, copy none
+        mbar_arrive_expect_tx(smem_addr(&bars[s]), 16);
+      else
         issue_tile<KIND>(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
                          smem_addr(&bars[s]));
     }
