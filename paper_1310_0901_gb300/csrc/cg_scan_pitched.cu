@@ -251,6 +251,275 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   single_epilogue(la, scr, ri, out, err);
 }
 
+// ------------------------------------------------ short, close rows: TMA
+
+// Short rows that lie close together (a field of an array of records, the
+// footnote's strided host read) are read as whole spans: a tile is R_T
+// consecutive rows of one slice, and lane 0 bulk-copies the input V bytes
+// and the host A bytes spanning them (gaps included: DRAM moves whole
+// sectors anyway) into the warp's stage; groups of P lanes then classify
+// and carry row after row out of shared memory.  The host picks R_T so
+// both spans fit the stage's windows.
+struct SpanTiles {
+  uint64_t rows_per_tile;    // R_T
+  uint64_t tiles_per_slice;  // ceil(height / R_T)
+  uint64_t ntiles;
+  uint32_t lp;               // log2 of the lanes per row
+};
+
+template <uint32_t KIND>
+__device__ __forceinline__ void span_rows(const PitchedJob &pj, const SpanTiles &sp, uint64_t t,
+                                          uint64_t *r_first, uint64_t *r_end) {
+  const uint64_t z = t / sp.tiles_per_slice;
+  const uint64_t y0 = (t - z * sp.tiles_per_slice) * sp.rows_per_tile;
+  const uint64_t y1 = y0 + sp.rows_per_tile < pj.height ? y0 + sp.rows_per_tile : pj.height;
+  *r_first = z * pj.height + y0;
+  *r_end = z * pj.height + y1;
+}
+
+// Lane 0: queue tile t's V span and A span.
+template <uint32_t KIND>
+__device__ __forceinline__ void issue_span(const PitchedJob &pj, const Image &img,
+                                           const SpanTiles &sp, uint64_t t, uint32_t st,
+                                           uint32_t bar) {
+  uint64_t r0, r1;
+  span_rows<KIND>(pj, sp, t, &r0, &r1);
+  const Geo g0 = row_geo(pj, img, KIND, r0);
+  const Geo g1 = row_geo(pj, img, KIND, r1 - 1);
+  uint32_t tx = 0, vbytes = 0, abytes = 0, voff = 0, aoff = 0;
+  uintptr_t vsrc = 0;
+  int64_t asrc = 0;
+  if (KIND == CG_HTOD || g0.has_vin) {
+    const uintptr_t vbeg = g0.vin_al;
+    const uintptr_t lo = g0.vin_lo & ~(uintptr_t)15;
+    uintptr_t hi = (g1.vin_hi + 15) & ~(uintptr_t)15;
+    if (hi > vbeg + kVBytes) hi = vbeg + kVBytes;
+    if (hi > lo) {
+      vbytes = (uint32_t)(hi - lo);
+      voff = (uint32_t)(lo - vbeg);
+      vsrc = lo;
+      tx += vbytes;
+    }
+  }
+  if (KIND != CG_DTOD) {
+    const int64_t aorig = floor16(g0.hb0 >> 3);
+    const int64_t q0 = g0.hb0 > g0.hlo ? g0.hb0 : g0.hlo;
+    const int64_t q1 = g1.hhi;
+    if (q1 > q0) {
+      const int64_t b0 = floor16(q0 >> 3);
+      int64_t b1 = ceil16((q1 + 7) >> 3);
+      if (b1 > aorig + (int64_t)kABytes) b1 = aorig + (int64_t)kABytes;
+      abytes = (uint32_t)(b1 - b0);
+      aoff = (uint32_t)(b0 - aorig);
+      asrc = b0;
+      tx += abytes;
+    }
+  }
+  mbar_arrive_expect_tx(bar, tx);
+  if (vbytes) bulk_g2s(st + voff, reinterpret_cast<const void *>(vsrc), vbytes, bar);
+  if (abytes) bulk_g2s(st + kVBytes + aoff, img.a_bits + asrc, abytes, bar);
+}
+
+// A lane's walk over the rows of one tile: the row's anchor (the buffer the
+// scan writes), input V and host positions advance by fixed steps (a tile
+// lies in one slice), so each row's geometry is a few adds instead of a
+// full row_geo.
+struct RowCursor {
+  uintptr_t anchor, vin;
+  int64_t host;
+  int64_t obase;
+  uintptr_t d_anchor, d_vin;
+  int64_t d_host, d_obase;
+};
+
+template <uint32_t KIND>
+__device__ __forceinline__ RowCursor row_cursor(const PitchedJob &pj, const Image &img,
+                                                uint64_t r, uint64_t step) {
+  uint64_t y = r, z = 0;
+  if (pj.depth > 1) {
+    z = r / pj.height;
+    y = r - z * pj.height;
+  }
+  const bool carry = pj.mode & kModeCarry;
+  const uint64_t host_off = pj.host_start + z * pj.host_slice + y * pj.host_pitch;
+  const uintptr_t host_v = reinterpret_cast<uintptr_t>(img.v) + host_off;
+  const uintptr_t src = pj.src_start + z * pj.src_slice + y * pj.src_pitch;
+  const uintptr_t dst = pj.dst_start + z * pj.dst_slice + y * pj.dst_pitch;
+  RowCursor c;
+  c.host = (int64_t)host_off;
+  c.d_host = (int64_t)(step * pj.host_pitch);
+  c.obase = (int64_t)(r * pj.width);
+  c.d_obase = (int64_t)(step * pj.width);
+  if (KIND == CG_HTOD) {
+    c.vin = host_v;
+    c.d_vin = step * pj.host_pitch;
+  } else {
+    c.vin = src;
+    c.d_vin = step * pj.src_pitch;
+  }
+  if (KIND == CG_DTOH || (KIND == CG_HTOD && !carry)) {
+    c.anchor = host_v;
+    c.d_anchor = step * pj.host_pitch;
+  } else if (carry) {
+    c.anchor = dst;
+    c.d_anchor = step * pj.dst_pitch;
+  } else {
+    c.anchor = src;
+    c.d_anchor = step * pj.src_pitch;
+  }
+  return c;
+}
+
+// The fields of a row's Geo that classification, carry and the shared-
+// memory reads use (make_geo's rules, for one row of `n` bytes).
+__device__ __forceinline__ Geo cursor_geo(const RowCursor &c, uint64_t n, bool has_vin) {
+  Geo g;
+  g.n = n;
+  g.ax = (int64_t)(c.anchor & 15);
+  g.nchunks = 0;  // not used by the span kernel
+  g.out_al = reinterpret_cast<uint8_t *>(c.anchor - (uintptr_t)g.ax);
+  const uintptr_t vw = c.vin - (uintptr_t)g.ax;
+  g.vin_r = (int)(vw & 15);
+  g.vin_al = vw - (uintptr_t)g.vin_r;
+  g.vin_lo = c.vin;
+  g.vin_hi = c.vin + n;
+  g.has_vin = has_vin;
+  g.hb0 = c.host - g.ax;
+  g.hlo = c.host;
+  g.hhi = c.host + (int64_t)n;
+  g.obase = c.obase;
+  return g;
+}
+
+// All lanes: the rows of tile t out of stage `sp_mem`.
+template <uint32_t KIND, bool CARRY>
+__device__ __forceinline__ void consume_span(const PitchedJob &pj, const Image &img,
+                                             const SpanTiles &sp, uint64_t t,
+                                             const uint8_t *sp_mem, int lane, LaneAcc &la) {
+  uint64_t r0, r1;
+  span_rows<KIND>(pj, sp, t, &r0, &r1);
+  const Geo g0 = row_geo(pj, img, KIND, r0);
+  const uintptr_t vbeg = g0.vin_al;
+  const int64_t aorig = floor16(g0.hb0 >> 3);
+  const uint4 *vs = reinterpret_cast<const uint4 *>(sp_mem);
+  const uint32_t *as = reinterpret_cast<const uint32_t *>(sp_mem + kVBytes);
+  const uint32_t P = 1u << sp.lp;
+  const uint64_t step = 32u >> sp.lp;
+  const int64_t c = lane & (P - 1);
+  uint64_t r = r0 + (lane >> sp.lp);
+  if (r >= r1) return;
+  RowCursor cur = row_cursor<KIND>(pj, img, r, step);
+  const bool has_vin = g0.has_vin;
+  for (; r < r1; r += step) {
+    const Geo g = cursor_geo(cur, pj.width, has_vin);
+    uint4 V = make_uint4(0, 0, 0, 0);
+    if (KIND == CG_HTOD || has_vin) {
+      const uint64_t k = (g.vin_al + 16 * (uintptr_t)c - vbeg) >> 4;
+      V = vs[k];
+      if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
+    }
+    uint32_t a16 = 0xFFFFu;
+    if (KIND != CG_DTOD) {
+      const int64_t q = g.hb0 + 16 * c;
+      const int sh = (int)(q & 31);
+      const int64_t wi = (((q >> 5) << 2) - aorig) >> 2;
+      const uint32_t w0 = as[wi];
+      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
+      a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
+    }
+    chunk_step<KIND, CARRY>(g, c, V, a16, valid_mask(16 * c - g.ax, g.n), la);
+    cur.anchor += cur.d_anchor;
+    cur.vin += cur.d_vin;
+    cur.host += cur.d_host;
+    cur.obase += cur.d_obase;
+  }
+}
+
+template <uint32_t KIND, bool CARRY>
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_pitched_span_kernel(Image img, PitchedJob pj, RangeInfo ri, SingleScratch *scr,
+                             cg_report *out, SpanTiles sp) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
+  const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t err = 0;
+  if (lane == 0)
+    for (int s = 0; s < kNS; s++) {
+      const uint64_t t = gw + (uint64_t)s * nw;
+      if (t < sp.ntiles)
+        issue_span<KIND>(pj, img, sp, t, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    }
+  uint32_t parity = 0;
+  int s = 0;
+  uint64_t t = gw;
+  for (; t < sp.ntiles; t += nw) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      err = 1;
+      break;
+    }
+    parity ^= 1u << s;
+    consume_span<KIND, CARRY>(pj, img, sp, t, wbase + s * kStage, lane, la);
+    __syncwarp();
+    const uint64_t tn = t + (uint64_t)kNS * nw;
+    if (lane == 0 && tn < sp.ntiles) {
+      fence_proxy_async();
+      issue_span<KIND>(pj, img, sp, tn, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    }
+    s = s + 1 == kNS ? 0 : s + 1;
+  }
+  if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
+    for (int d = 0; d < kNS; d++) {
+      const uint64_t td = t + (uint64_t)d * nw;
+      if (td >= sp.ntiles) break;
+      const int sd = (s + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+  }
+  single_epilogue(la, scr, ri, out, err);
+}
+
+// Rows per span tile when every row is read by `lanes` lanes (one chunk
+// each), or 0 when fewer than two rows fit (then the register kernel reads
+// row by row).  Bounds: every row's V window (its aligned start, one chunk
+// per lane and one more vector) stays inside
+// the stage's V window from the first row's aligned start, with 62 bytes of
+// alignment slack; every row's A words (two per chunk position) inside the
+// A window from the first row's aligned A byte, with slack.
+static uint64_t span_rows_per_tile(const PitchedJob &job, uint64_t lanes) {
+  if (job.height < 2) return 0;
+  uint64_t rt = job.height;
+  const bool reads_v = job.kind == CG_HTOD || (job.mode & kModeReadDev);
+  if (reads_v) {
+    const uint64_t pv = job.kind == CG_HTOD ? job.host_pitch : job.src_pitch;
+    const int64_t room = (int64_t)kVBytes - 62 - 16 * (int64_t)lanes;
+    if (room < 0 || pv == 0) return 0;
+    const uint64_t r = (uint64_t)room / pv + 1;
+    rt = r < rt ? r : rt;
+  }
+  if (job.kind != CG_DTOD) {
+    const int64_t room = ((int64_t)kABytes - 32) * 8 - 15 - 16 * (int64_t)lanes;
+    if (room < 0 || job.host_pitch == 0) return 0;
+    const uint64_t r = (uint64_t)room / job.host_pitch + 1;
+    rt = r < rt ? r : rt;
+  }
+  return rt >= 2 ? rt : 0;
+}
+
 // --------------------------------------------------------------- launch
 
 template <uint32_t KIND, bool CARRY>
@@ -296,14 +565,36 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
     scan_pitched_wide_kernel<KIND, CARRY><<<grid, kPThreads, 0, st>>>(img, job, ri, scr, out, ws);
     return cudaGetLastError();
   }
+  uint32_t lp = 0;
+  while ((1ull << lp) < kmax) lp++;
+  const uint64_t rt = tma_ok ? span_rows_per_tile(job, 1ull << lp) : 0;
+  if (rt) {
+    static int span_per_sm = 0;
+    if (!span_per_sm) {
+      cudaError_t e = cudaFuncSetAttribute(scan_pitched_span_kernel<KIND, CARRY>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kSmemBytes);
+      if (e != cudaSuccess) return e;
+      span_per_sm = tma_ctas_per_sm(scan_pitched_span_kernel<KIND, CARRY>);
+    }
+    SpanTiles sp;
+    sp.rows_per_tile = rt;
+    sp.tiles_per_slice = (job.height + rt - 1) / rt;
+    sp.ntiles = sp.tiles_per_slice * job.depth;
+    sp.lp = lp;
+    const uint64_t need = (sp.ntiles + kTW - 1) / kTW;
+    const uint64_t cap = (uint64_t)sm_count * span_per_sm;
+    const unsigned grid = (unsigned)(need < cap ? need : cap);
+    scan_pitched_span_kernel<KIND, CARRY><<<grid, kTW * 32, kSmemBytes, st>>>(img, job, ri, scr,
+                                                                              out, sp);
+    return cudaGetLastError();
+  }
   static int per_sm = 0;
   if (!per_sm &&
       (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
            &per_sm, scan_pitched_narrow_kernel<KIND, CARRY>, kPThreads, 0) != cudaSuccess ||
        per_sm < 1))
     per_sm = 1;
-  uint32_t lp = 0;
-  while ((1ull << lp) < kmax) lp++;
   const uint64_t per_warp = (32ull >> lp) * kPNarrow;
   const uint64_t need = (rows + per_warp * wpc - 1) / (per_warp * wpc);
   const uint64_t cap = (uint64_t)sm_count * per_sm;
