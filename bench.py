@@ -368,6 +368,26 @@ def run_batched_workload(args, which: str):
     dt1 = time.perf_counter() - t1
     batch_cps = nreq * args.steps / dt
     single_cps = m / dt1
+    # algorithmic HBM bytes of one batch, from its verdicts: the host scan
+    # always runs (V + A of host bytes), device V is read only from a valid
+    # source and written only when every device range is valid
+    f = reps["flags"].astype(np.int64)
+    n = reqs["n"].astype(np.float64)
+    kind = reqs["kind"]
+    dst_ok = (f & (cg.FLAGS["UNALLOC_DST"] | cg.FLAGS["OVERRUN_DST"])) == 0
+    src_ok = (f & (cg.FLAGS["UNALLOC_SRC"] | cg.FLAGS["OVERRUN_SRC"])) == 0
+    alg = np.where(kind == S.HTOD, 1.125 * n + n * dst_ok,
+                   np.where(kind == S.DTOH, 0.125 * n + 2 * n * src_ok,
+                            n * src_ok + n * (src_ok & dst_ok)))
+    alg_bytes = float(alg.sum())
+    peak, peak_kind = _peaks()
+    gpu_ms = per_batch_ms["batch_ns"] - per_batch_ms["batch_plan_ns"] - per_batch_ms["batch_lookup_ns"]
+    roof = {"bound": "hbm", "algorithmic_bytes_per_batch": int(alg_bytes),
+            "achieved": round(alg_bytes / (dt / args.steps) / GB, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(alg_bytes / (dt / args.steps) / GB / peak, 4),
+            "frac_during_level_kernels": round(alg_bytes / (gpu_ms / 1e3) / GB / peak, 4)
+            if gpu_ms > 0 else None,
+            "peak_source": peak_kind}
     out = {
         "metric": "batched checks/sec",
         "value": round(batch_cps, 1), "unit": "checks/s", "n_gpus": 1, "steps": args.steps,
@@ -379,6 +399,7 @@ def run_batched_workload(args, which: str):
                    "levels_per_batch": levels,
                    "l2": "working set larger than L2", "carry": True},
         "batched_gb_per_s": round(bytes_per_batch * args.steps / dt / GB, 1),
+        "roofline": roof,
         "one_launch_per_copy": {"checks_per_s": round(single_cps, 1), "sample": m,
                                 "gb_per_s": round(int(reqs["n"][:m].sum()) / dt1 / GB, 1)},
         "speedup_vs_one_launch_per_copy": round(batch_cps / single_cps, 2),
@@ -653,6 +674,8 @@ def _summary(key: str, d: dict) -> dict:
                 "one_launch_per_copy_checks_per_s": d["one_launch_per_copy"]["checks_per_s"],
                 "speedup_vs_one_launch_per_copy": d["speedup_vs_one_launch_per_copy"],
                 "levels_per_batch": d["config"]["levels_per_batch"],
+                "roofline_frac": d["roofline"]["frac"],
+                "roofline_frac_during_level_kernels": d["roofline"]["frac_during_level_kernels"],
                 "ms_per_batch": d["ms_per_step"], "breakdown_ms": d["batch_breakdown_ms"]}
     return {"workload": d["config"]["workload"], "checks_per_s": d["value"],
             "latency_us": d["latency_us"], "offered_rate_per_s": d["config"]["offered_rate_per_s"],

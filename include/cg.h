@@ -619,6 +619,23 @@ cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, uint8_t *hos
                           uint8_t *dev_dst_shadow, uint64_t n, uint32_t carry,
                           cg_report *rep_dev, void *stream);
 
+/* ------------------------------------------------------ checkpoint / resume */
+
+/* Save the context's checking state to the file `path`: every live
+ * allocation with its device V shadow, the freed bases (so double frees are
+ * still recognised), the device arrays with their shadows and the destroyed
+ * array handles.  The host shadow image is the caller's and is not saved.
+ * Synchronous; CG_E_ARG with text in cg_last_error() when the file cannot
+ * be written. */
+cg_status cg_snapshot(cg_ctx *ctx, const char *path);
+
+/* Load a snapshot into a context that has no allocations, freed bases or
+ * arrays yet (CG_E_STATE otherwise); its configuration is the context's own.
+ * After it, checks give the results they would have given in the saved
+ * context.  CG_E_ARG for a file that is not a complete snapshot (the
+ * context may then hold part of it). */
+cg_status cg_restore(cg_ctx *ctx, const char *path);
+
 /* ------------------------------------------------------- fault injection */
 
 /* Host-side hooks that make one failure happen on purpose, so that the

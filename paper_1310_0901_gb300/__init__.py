@@ -160,6 +160,8 @@ SIGNATURES = [
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
     ("cg_inject_fault", i32, [vp, u32]),
+    ("cg_snapshot", i32, [vp, ctypes.c_char_p]),
+    ("cg_restore", i32, [vp, ctypes.c_char_p]),
     ("cg_check_memset", i32, [vp, u64, u64, u64, u64, vp, vp]),
     ("cg_check_memset_async", i32, [vp, u64, u64, u64, u64, vp, vp]),
     ("cg_check_kernel_args", i32, [vp, vp, u64, vp, ctypes.POINTER(u64), vp]),
@@ -309,6 +311,12 @@ class Context:
         r = cg_report()
         st = cg_check_copy3d(self._h, ctypes.byref(q), ctypes.byref(r), _stream_handle(stream))
         return st, report_to_dict(r)
+
+    def snapshot(self, path: str) -> int:
+        return cg_snapshot(self._h, os.fsencode(path))
+
+    def restore(self, path: str) -> int:
+        return cg_restore(self._h, os.fsencode(path))
 
     def check_memset(self, dptr: int, width: int, height: int = 1, pitch: int = 0, stream=None):
         """A memset of height rows of width bytes at dptr + y*pitch."""

@@ -15,7 +15,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 
 SOURCES = ["cg_kernels.cu", "cg_scan_tma.cu", "cg_noalloc.cu", "cg_mlp.cu", "cg_scan_pitched.cu",
            "cg_devops_kernels.cu", "cg_host.cpp", "cg_batch.cpp", "cg_serve.cpp", "cg_pitched.cpp",
-           "cg_devops.cpp"]
+           "cg_devops.cpp", "cg_snapshot.cpp"]
 
 
 def _cmd_compile(src: str, obj: str) -> list[str]:

@@ -129,10 +129,47 @@ __device__ __forceinline__ void issue_tile(const Geo &g, const uint8_t *a_bytes,
   if (abytes) bulk_g2s(st + kVBytes + aoff, a_bytes + asrc, abytes, bar);
 }
 
+// A device->host copy whose source range is invalid reads no V and carries
+// nothing: its bytes are classified by the destination's A bits alone
+// (unaddressable or good).  Lane L takes 128 copy bytes, i.e. four A words,
+// of the tile instead of walking 16-byte chunks: zeros are counted with
+// popc, the first one found with ffs.
+__device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, const uint8_t *sp,
+                                                    int lane, LaneAcc &la) {
+  const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
+  const int64_t p0 = g.hb0 + 16 * c0;   // host position of the tile's first byte
+  const int64_t aorig = floor16(p0 >> 3);
+  const int64_t i0 = 16 * c0 - g.ax + 128 * (int64_t)lane;  // copy offset of this lane's bytes
+  const int64_t rel = p0 + 128 * (int64_t)lane - 8 * aorig;  // bit offset in the A window
+  const int64_t w = rel >> 5;
+  const int sh = (int)(rel & 31);
+  uint32_t un = 0;
+  unsigned long long first = kNone;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int64_t b0 = i0 + 32 * k;  // copy offset of bit 0 of this word
+    const int64_t lo = b0 < 0 ? -b0 : 0;
+    const int64_t rem = (int64_t)g.n - b0;
+    const int64_t hi = rem < 32 ? rem : 32;
+    if (hi <= lo) continue;
+    const uint32_t valid = (hi == 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+    const uint32_t bits = __funnelshift_r(as[w + k], as[w + k + 1], sh);
+    const uint32_t zero = ~bits & valid;
+    un += __popc(zero);
+    if (zero && first == kNone) first = (unsigned long long)(g.obase + b0 + __ffs(zero) - 1);
+  }
+  la.un += un;
+  if (first != kNone && la.fun == kNone) la.fun = first;
+}
+
 // All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
 template <uint32_t KIND, bool CARRY>
 __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uint8_t *sp,
                                              int lane, LaneAcc &la) {
+  if (KIND == CG_DTOH && !CARRY && !g.has_vin) {  // nothing but the destination's A bits
+    consume_tile_a_only(g, c0, sp, lane, la);
+    return;
+  }
   const uint4 *vs = reinterpret_cast<const uint4 *>(sp);
   const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
   const int64_t aorig = floor16((g.hb0 + 16 * c0) >> 3);
