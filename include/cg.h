@@ -282,6 +282,26 @@ cg_status cg_check_batch(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                          uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream);
 
+/* The same batch check, returned from as soon as it is enqueued: *ticket
+ * identifies it for cg_batch_wait.  Two batches may be in flight per
+ * context (CG_E_FULL for a third).  A batch's device lookup runs on a
+ * stream of the context's own and its level plan on the host while the
+ * batch before it still runs on `stream`; its kernels follow that batch's
+ * on `stream`, so batches take effect in submission order, with exactly
+ * the results of cg_check_batch called in that order.  The request array
+ * is copied before return.  rec_cap bounds the records kept on the device
+ * for this batch.  Errors as cg_check_batch (nothing is enqueued then). */
+cg_status cg_check_batch_async(cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
+                               uint64_t rec_cap, uint64_t *ticket, uint64_t *bad_index,
+                               void *stream);
+
+/* Wait for the batch `ticket` and write its reports (reps, may be NULL), up
+ * to rec_cap records (recs) and the total record count (*n_rec, may be
+ * NULL); host buffers.  CG_E_ARG for an unknown or already collected
+ * ticket; CG_E_TIMEOUT as cg_check_batch. */
+cg_status cg_batch_wait(cg_ctx *ctx, uint64_t ticket, cg_report *reps, cg_err_record *recs,
+                        uint64_t rec_cap, uint64_t *n_rec);
+
 /* ------------------------------------------- pitched copies and arrays */
 
 /* One side of a pitched 2-D / 3-D copy (cuMemcpy2D / cuMemcpy3D).  ptr is a

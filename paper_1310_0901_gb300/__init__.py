@@ -159,6 +159,9 @@ SIGNATURES = [
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
+    ("cg_check_batch_async", i32, [vp, vp, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                   vp]),
+    ("cg_batch_wait", i32, [vp, u64, vp, vp, u64, ctypes.POINTER(u64)]),
     ("cg_inject_fault", i32, [vp, u32]),
     ("cg_snapshot", i32, [vp, ctypes.c_char_p]),
     ("cg_restore", i32, [vp, ctypes.c_char_p]),
@@ -349,6 +352,30 @@ class Context:
         check(cg_read_array_shadow(self._h, handle, off, n, out.ctypes.data if n else None),
               "cg_read_array_shadow")
         return out
+
+    def check_batch_async(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None):
+        """Enqueue a batch; returns (status, ticket, bad index).  The request
+        array is copied before return."""
+        reqs = np.ascontiguousarray(reqs)
+        assert reqs.dtype.itemsize == 32
+        n = len(reqs)
+        t = u64(0)
+        bad = u64(0)
+        st = cg_check_batch_async(self._h, reqs.ctypes.data, n, 8 * n if rec_cap is None else rec_cap,
+                                  ctypes.byref(t), ctypes.byref(bad), _stream_handle(stream))
+        return st, int(t.value), int(bad.value)
+
+    def batch_wait(self, ticket: int, nreq: int, rec_cap: int | None = None):
+        """Results of an enqueued batch: (status, reports, records, total)."""
+        if rec_cap is None:
+            rec_cap = 8 * nreq
+        reps = np.zeros(max(1, nreq), dtype=REPORT_DTYPE)
+        recs = np.zeros(max(1, rec_cap), dtype=RECORD_DTYPE)
+        n_rec = u64(0)
+        st = cg_batch_wait(self._h, ticket, reps.ctypes.data, recs.ctypes.data, rec_cap,
+                           ctypes.byref(n_rec))
+        total = int(n_rec.value)
+        return st, reps[:nreq], recs[:min(total, rec_cap)], total
 
     def check_batch(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None):
         """reqs: structured array with the layout of cg_copy (cg_synth.REQ_DTYPE).

@@ -36,29 +36,32 @@ struct BatchRun {
   int grid = 1;
 };
 
-cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStream_t st,
-                        BatchRun &B) {
+// `st` runs the batch; `look` runs its lookup (the same stream, or the side
+// stream of an asynchronous submission so that the lookup does not queue
+// behind the batch before it).
+cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t nreq,
+                        cudaStream_t st, cudaStream_t look, BatchRun &B) {
   B.reqs = reqs;
   B.nreq = nreq;
   CG_TRY(flush_fills(c, st));
-  CG_TRY(ensure_device_table(c, st));
-  CG_TRY(c->b_reqs.ensure(nreq));
-  CG_TRY(c->b_order.ensure(nreq));
-  CG_TRY(c->b_segfirst.ensure(nreq));
-  CG_TRY(c->b_stage.ensure(nreq));
-  CG_TRY(c->b_jobs.ensure(nreq));
-  CG_TRY(c->b_info.ensure(nreq));
-  CG_TRY(c->b_acc.ensure(nreq));
-  CG_TRY(c->b_reps.ensure(nreq));
-  CG_TRY(c->b_counts.ensure(nreq));
-  CG_TRY(c->b_modes.ensure(nreq));
-  CG_TRY(c->b_err.ensure(1));
+  CG_TRY(ensure_device_table(c, look));  // only lookups read the device table
+  CG_TRY(K.b_reqs.ensure(nreq));
+  CG_TRY(K.b_order.ensure(nreq));
+  CG_TRY(K.b_segfirst.ensure(nreq));
+  CG_TRY(K.b_stage.ensure(nreq));
+  CG_TRY(K.b_jobs.ensure(nreq));
+  CG_TRY(K.b_info.ensure(nreq));
+  CG_TRY(K.b_acc.ensure(nreq));
+  CG_TRY(K.b_reps.ensure(nreq));
+  CG_TRY(K.b_counts.ensure(nreq));
+  CG_TRY(K.b_modes.ensure(nreq));
+  CG_TRY(K.b_err.ensure(1));
   const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8) + 64;
-  CG_TRY(c->h_stage_in.ensure(upload_bytes));
-  CG_TRY(c->h_modes.ensure(nreq));
-  cg_copy *h_reqs = reinterpret_cast<cg_copy *>(c->h_stage_in.p);
+  CG_TRY(K.h_stage_in.ensure(upload_bytes));
+  CG_TRY(K.h_modes.ensure(nreq));
+  cg_copy *h_reqs = reinterpret_cast<cg_copy *>(K.h_stage_in.p);
   B.h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
-  B.h_segfirst = reinterpret_cast<uint64_t *>(c->h_stage_in.p +
+  B.h_segfirst = reinterpret_cast<uint64_t *>(K.h_stage_in.p +
                                               round_up(nreq * (sizeof(cg_copy) + 4), 8));
   uint64_t *h_stagep = B.h_segfirst + nreq;
   std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
@@ -83,35 +86,36 @@ cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStrea
       stage_total += round_up(q.n, 256);
     }
     if (stage_total) {
-      CG_TRY(c->stage.ensure(stage_total));
-      const uint64_t base = reinterpret_cast<uint64_t>(c->stage.p);
+      CG_TRY(K.stage.ensure(stage_total));
+      const uint64_t base = reinterpret_cast<uint64_t>(K.stage.p);
       for (uint64_t i = 0; i < nreq; i++)
         if (h_stagep[i]) h_stagep[i] = base + h_stagep[i] - 1;
       for (auto &sc : B.stages) sc.dst += base;
     }
   }
-  CG_CUDA(cudaMemcpyAsync(c->b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_reqs.p, h_reqs, nreq * sizeof(cg_copy), cudaMemcpyHostToDevice,
+                          look));
+  CG_CUDA(cudaMemcpyAsync(K.b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, look));
   BatchPlan &plan = B.plan;
-  plan.reqs = c->b_reqs.p;
-  plan.order = c->b_order.p;
-  plan.seg_first = c->b_segfirst.p;
-  plan.stage = c->b_stage.p;
-  plan.jobs = c->b_jobs.p;
-  plan.info = c->b_info.p;
-  plan.acc = c->b_acc.p;
+  plan.reqs = K.b_reqs.p;
+  plan.order = K.b_order.p;
+  plan.seg_first = K.b_segfirst.p;
+  plan.stage = K.b_stage.p;
+  plan.jobs = K.b_jobs.p;
+  plan.info = K.b_info.p;
+  plan.acc = K.b_acc.p;
   plan.nreq = nreq;
   plan.mode_mask = ~0u;
   // device lookup first (a2): it decides which copies carry and read a
   // device source, which the level plan needs
   DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
   const uint64_t t_lookup = now_ns();
-  CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, st));
-  CG_CUDA(launch_job_modes(plan, c->b_modes.p, st));
+  CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, look));
+  CG_CUDA(launch_job_modes(plan, K.b_modes.p, look));
   c->stats.kernels += 2;
-  CG_CUDA(cudaMemcpyAsync(c->h_modes.p, c->b_modes.p, nreq, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
-  B.modes = c->h_modes.p;
+  CG_CUDA(cudaMemcpyAsync(K.h_modes.p, K.b_modes.p, nreq, cudaMemcpyDeviceToHost, look));
+  CG_CUDA(cudaStreamSynchronize(look));  // the level kernels on st are issued after this
+  B.modes = K.h_modes.p;
   const uint64_t t_plan = now_ns();
   c->stats.batch_lookup_ns += t_plan - t_lookup;
   // dependency levels, exact on validity
@@ -129,7 +133,7 @@ cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStrea
   std::sort(B.stages.begin(), B.stages.end(),
             [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
   c->stats.batch_plan_ns += now_ns() - t_plan;
-  CG_CUDA(cudaMemcpyAsync(c->b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
   B.tma = c->cfg.scan_engine != 1 && !c->img_on_host;
   int per_sm = (int)c->cfg.batch_ctas_per_sm;
   if (per_sm <= 0) per_sm = B.tma ? 1 : 8;
@@ -139,7 +143,8 @@ cg_status batch_prepare(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cudaStrea
 
 // Cut every copy into segments of seg_bytes (rounded to whole engine
 // steps: one tile for the TMA engine, kU rows for register loads).
-cg_status batch_split(cg_ctx *c, BatchRun &B, uint64_t seg_bytes, cudaStream_t st) {
+cg_status batch_split(cg_ctx *c, BatchBufs &K, BatchRun &B, uint64_t seg_bytes,
+                      cudaStream_t st) {
   const uint64_t quantum = B.tma ? scan_tma_tile_bytes() : 2048;
   seg_bytes = std::max<uint64_t>(quantum, (seg_bytes + quantum - 1) / quantum * quantum);
   const uint64_t seg_chunks = seg_bytes / 16;
@@ -157,14 +162,15 @@ cg_status batch_split(cg_ctx *c, BatchRun &B, uint64_t seg_bytes, cudaStream_t s
     }
     B.lev_segs[l] = acc_segs;
   }
-  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, B.h_segfirst, B.nreq * 8, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_segfirst.p, B.h_segfirst, B.nreq * 8, cudaMemcpyHostToDevice, st));
   return CG_OK;
 }
 
-cg_status batch_levels(cg_ctx *c, BatchRun &B, uint32_t mode_mask, cudaStream_t st) {
+cg_status batch_levels(cg_ctx *c, BatchBufs &K, BatchRun &B, uint32_t mode_mask,
+                       cudaStream_t st) {
   B.plan.mode_mask = mode_mask;
   const bool dry = !(mode_mask & kModeCarry);
-  CG_CUDA(cudaMemsetAsync(c->b_err.p, 0, sizeof(unsigned int), st));
+  CG_CUDA(cudaMemsetAsync(K.b_err.p, 0, sizeof(unsigned int), st));
   size_t sci = 0;
   for (int l = 0; l < B.nlev; l++) {
     for (; !dry && sci < B.stages.size() && B.stages[sci].level == l; sci++)
@@ -173,7 +179,7 @@ cg_status batch_levels(cg_ctx *c, BatchRun &B, uint32_t mode_mask, cudaStream_t 
                               cudaMemcpyDeviceToDevice, st));
     if (B.tma)
       CG_CUDA(launch_scan_level_tma(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1],
-                                    B.lev_segs[l], B.grid, c->b_err.p, st));
+                                    B.lev_segs[l], B.grid, K.b_err.p, st));
     else
       CG_CUDA(launch_scan_level(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1], B.lev_segs[l],
                                 B.grid, st));
@@ -299,27 +305,143 @@ uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_
   return 64;
 }
 
-// Record an online trial; once every candidate has run, the fastest
-// becomes a tuned entry for this shape.
-void online_record(cg_ctx *c, int slot, const cg_copy *reqs, uint64_t nreq, uint32_t kib,
-                   float ms) {
+// Record an online trial of segment size kib for the batch shape `f`; once
+// every candidate has run, the fastest becomes a tuned entry.  The shape's
+// entry is found again by its features (another batch may have finished
+// in between), and a candidate timed twice does not skip one.
+void online_record(cg_ctx *c, const float *f, uint32_t kib, float ms) {
+  int slot = -1;
+  float best_d = kClose;
+  for (size_t e = 0; e < c->online.size(); e++) {
+    const float d = feature_distance(c->online[e].feat.data(), f);
+    if (d < best_d) {
+      best_d = d;
+      slot = (int)e;
+    }
+  }
   if (slot < 0) {
+    for (size_t e = 0; e < c->tuned_feat.size(); e++)  // already settled
+      if (feature_distance(c->tuned_feat[e].data(), f) < kClose) return;
     cg_ctx::OnlineTune t;
-    t.feat.resize(CG_NFEAT);
-    features(reqs, nreq, t.feat.data());
+    t.feat.assign(f, f + CG_NFEAT);
     c->online.push_back(t);
     slot = (int)c->online.size() - 1;
   }
   cg_ctx::OnlineTune &t = c->online[slot];
-  if (t.next == 0 || ms < t.best_ms) {
+  uint32_t idx = 0;
+  while (idx < kNumOnline && kOnlineKib[idx] != kib) idx++;
+  if (t.best_kib == 0 || ms < t.best_ms) {
     t.best_ms = ms;
     t.best_kib = kib;
   }
-  if (++t.next >= kNumOnline) {
+  t.next = std::max(t.next, idx + 1);
+  if (t.next >= kNumOnline) {
     c->tuned_feat.push_back(t.feat);
     c->tuned_kib.push_back(t.best_kib);
     c->online.erase(c->online.begin() + slot);
   }
+}
+
+// Enqueue a batch into a free slot: host validation, the lookup (on `look`)
+// and the level plan on the host, then the level kernels, reports, records
+// and the copies of the results on `st`; K.done is recorded after them.
+cg_status batch_submit(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t rec_cap,
+                       uint64_t *bad_index, cudaStream_t st, cudaStream_t look, int *slot_out) {
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_status s = validate(c, reqs[i]);
+    if (s != CG_OK) {
+      if (bad_index) *bad_index = i;
+      return s;
+    }
+  }
+  if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
+  int slot = -1;
+  for (int k = 0; k < 2 && slot < 0; k++)
+    if (!c->bb[k].ticket) slot = k;
+  if (slot < 0) return set_error(CG_E_FULL, "two batches in flight: cg_batch_wait first");
+  BatchBufs &K = c->bb[slot];
+  K.t_begin = now_ns();
+  BatchRun B;
+  CG_TRY(batch_prepare(c, K, reqs, nreq, st, look, B));
+  K.source = 3;
+  K.online_slot = -1;
+  K.kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib
+                                   : choose_kib(c, reqs, nreq, &K.source, &K.online_slot);
+  if (K.source == 4) {
+    K.feat.resize(CG_NFEAT);
+    features(reqs, nreq, K.feat.data());
+  }
+  CG_TRY(batch_split(c, K, B, (uint64_t)K.kib * 1024, st));
+  if (!K.done) CG_CUDA(cudaEventCreateWithFlags(&K.done, cudaEventDisableTiming));
+  if (!K.t0) CG_CUDA(cudaEventCreate(&K.t0));
+  if (!K.t1) CG_CUDA(cudaEventCreate(&K.t1));
+  CG_CUDA(cudaEventRecord(K.t0, st));
+  CG_TRY(batch_levels(c, K, B, ~0u, st));
+  CG_CUDA(cudaEventRecord(K.t1, st));
+  K.nreq = nreq;
+  K.nlev = B.nlev;
+  K.nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
+  CG_TRY(K.b_blocksums.ensure(K.nblocks + 1));
+  K.dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
+  CG_TRY(K.b_recs.ensure(std::max<uint64_t>(K.dev_rec_cap, 1)));
+  const int strict = (int)c->cfg.strict_device_undef;
+  CG_CUDA(launch_finalize(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_scan_block_sums(K.b_blocksums.p, K.nblocks, nullptr, st));
+  CG_CUDA(launch_emit_records(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems,
+                              strict, K.b_recs.p, K.dev_rec_cap, st));
+  c->stats.kernels += K.dev_rec_cap ? 3 : 2;
+  CG_TRY(K.h_total.ensure(2));
+  CG_TRY(K.h_reps.ensure(nreq));
+  CG_CUDA(cudaMemcpyAsync(K.h_total.p, K.b_blocksums.p + K.nblocks, 8, cudaMemcpyDeviceToHost,
+                          st));
+  CG_CUDA(cudaMemcpyAsync(K.h_total.p + 1, K.b_err.p, sizeof(unsigned int),
+                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(K.h_reps.p, K.b_reps.p, nreq * sizeof(cg_report),
+                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaEventRecord(K.done, st));
+  K.ticket = c->next_ticket++;
+  *slot_out = slot;
+  return CG_OK;
+}
+
+// Wait for the batch in `slot` and hand its results out; frees the slot.
+cg_status batch_finish(cg_ctx *c, int slot, cg_report *reps, cg_err_record *recs,
+                       uint64_t rec_cap, uint64_t *n_rec) {
+  BatchBufs &K = c->bb[slot];
+  struct Free {
+    BatchBufs &k;
+    ~Free() { k.ticket = 0; }
+  } release_slot{K};
+  CG_CUDA(cudaEventSynchronize(K.done));
+  if (K.source == 4) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, K.t0, K.t1);
+    online_record(c, K.feat.data(), K.kib, ms);
+  }
+  if (reinterpret_cast<const unsigned int *>(K.h_total.p + 1)[0])
+    return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
+  const uint64_t total = K.h_total.p[0];
+  const uint64_t take = std::min(std::min(total, K.dev_rec_cap), rec_cap);
+  if (take && recs) {
+    // on the context's own non-blocking stream: a synchronous copy on the
+    // legacy stream would also wait for the next batch's kernels
+    if (!c->side) CG_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+    CG_TRY(K.h_recs.ensure(take));
+    CG_CUDA(cudaMemcpyAsync(K.h_recs.p, K.b_recs.p, take * sizeof(cg_err_record),
+                            cudaMemcpyDeviceToHost, c->side));
+    CG_CUDA(cudaStreamSynchronize(c->side));
+    std::memcpy(recs, K.h_recs.p, take * sizeof(cg_err_record));
+  }
+  if (reps) std::memcpy(reps, K.h_reps.p, K.nreq * sizeof(cg_report));
+  {
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    for (uint64_t i = 0; i < K.nreq; i++) count_stats(c, K.h_reps.p[i]);
+    c->stats.batch_ns += now_ns() - K.t_begin;
+    c->stats.batches++;
+    c->stats.levels += (uint64_t)K.nlev;
+  }
+  if (n_rec) *n_rec = total;
+  return CG_OK;
 }
 
 }  // namespace
@@ -332,78 +454,35 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
   if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
     return set_error(CG_E_ARG, "NULL argument");
-  for (uint64_t i = 0; i < nreq; i++) {
-    const cg_status s = validate(c, reqs[i]);
-    if (s != CG_OK) {
-      if (bad_index) *bad_index = i;
-      return s;
-    }
-  }
   if (nreq == 0) {
+    for (uint64_t i = 0; i < nreq; i++) CG_TRY(validate(c, reqs[i]));
     *n_rec = 0;
     return CG_OK;
   }
-  if (nreq > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 requests per batch");
-  const uint64_t t_begin = now_ns();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  BatchRun B;
-  CG_TRY(batch_prepare(c, reqs, nreq, st, B));
-  uint32_t source = 3;
-  int online_slot = -1;
-  const uint32_t kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib
-                                                : choose_kib(c, reqs, nreq, &source, &online_slot);
-  CG_TRY(batch_split(c, B, (uint64_t)kib * 1024, st));
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (source == 4) {  // an online trial: time the level kernels
-    CG_CUDA(cudaEventCreate(&e0));
-    CG_CUDA(cudaEventCreate(&e1));
-    CG_CUDA(cudaEventRecord(e0, st));
-  }
-  CG_TRY(batch_levels(c, B, ~0u, st));
-  if (source == 4) CG_CUDA(cudaEventRecord(e1, st));
-  const uint64_t nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
-  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
-  const uint64_t dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
-  CG_TRY(c->b_recs.ensure(std::max<uint64_t>(dev_rec_cap, 1)));
-  const int strict = (int)c->cfg.strict_device_undef;
-  CG_CUDA(launch_finalize(B.plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems, st));
-  CG_CUDA(launch_scan_block_sums(c->b_blocksums.p, nblocks, nullptr, st));
-  CG_CUDA(launch_emit_records(B.plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems,
-                              strict, c->b_recs.p, dev_rec_cap, st));
-  c->stats.kernels += dev_rec_cap ? 3 : 2;
-  CG_TRY(c->h_total.ensure(2));
-  CG_TRY(c->h_reps.ensure(nreq));
-  CG_CUDA(cudaMemcpyAsync(c->h_total.p, c->b_blocksums.p + nblocks, 8, cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(c->h_total.p + 1, c->b_err.p, sizeof(unsigned int),
-                          cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nreq * sizeof(cg_report),
-                          cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaStreamSynchronize(st));
-  if (source == 4) {
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    online_record(c, online_slot, reqs, nreq, kib, ms);
-  }
-  if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
-    return set_error(CG_E_TIMEOUT, "a bounded wait in the batched scan kernel ran out");
-  const uint64_t total = c->h_total.p[0];
-  const uint64_t take = std::min(total, dev_rec_cap);
-  if (take) {
-    CG_TRY(c->h_recs.ensure(take));
-    CG_CUDA(cudaMemcpyAsync(c->h_recs.p, c->b_recs.p, take * sizeof(cg_err_record),
-                            cudaMemcpyDeviceToHost, st));
-    CG_CUDA(cudaStreamSynchronize(st));
-    std::memcpy(recs, c->h_recs.p, take * sizeof(cg_err_record));
-  }
-  if (reps) std::memcpy(reps, c->h_reps.p, nreq * sizeof(cg_report));
-  for (uint64_t i = 0; i < nreq; i++) count_stats(c, c->h_reps.p[i]);
-  *n_rec = total;
-  c->stats.batch_ns += now_ns() - t_begin;
-  c->stats.batches++;
-  c->stats.levels += (uint64_t)B.nlev;
+  int slot = -1;
+  CG_TRY(batch_submit(c, reqs, nreq, rec_cap, bad_index, st, st, &slot));
+  return batch_finish(c, slot, reps, recs, rec_cap, n_rec);
+}
+
+cg_status cg_check_batch_async(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t rec_cap,
+                               uint64_t *ticket, uint64_t *bad_index, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
+  if (!c || !nreq || !reqs || !ticket) return set_error(CG_E_ARG, "NULL argument or empty batch");
+  if (!c->side) CG_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  int slot = -1;
+  CG_TRY(batch_submit(c, reqs, nreq, rec_cap, bad_index, static_cast<cudaStream_t>(stream),
+                      c->side, &slot));
+  *ticket = c->bb[slot].ticket;
   return CG_OK;
+}
+
+cg_status cg_batch_wait(cg_ctx *c, uint64_t ticket, cg_report *reps, cg_err_record *recs,
+                        uint64_t rec_cap, uint64_t *n_rec) {
+  if (!c || (rec_cap && !recs)) return set_error(CG_E_ARG, "NULL argument");
+  for (int k = 0; k < 2; k++)
+    if (ticket && c->bb[k].ticket == ticket) return batch_finish(c, k, reps, recs, rec_cap, n_rec);
+  return set_error(CG_E_ARG, "no batch in flight with this ticket");
 }
 
 cg_status cg_batch_features(const cg_copy *reqs, uint64_t nreq, float *feat) {
@@ -422,9 +501,12 @@ cg_status cg_tune_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, const uin
   const uint32_t nc = seg_kib ? ncand : (uint32_t)kNumCandidates;
   if (nc == 0) return set_error(CG_E_ARG, "no candidates");
   if (repeats == 0) repeats = 1;
+  if (c->bb[0].ticket || c->bb[1].ticket)
+    return set_error(CG_E_STATE, "batches still in flight (cg_batch_wait first)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchBufs &K = c->bb[0];
   BatchRun B;
-  CG_TRY(batch_prepare(c, reqs, nreq, st, B));
+  CG_TRY(batch_prepare(c, K, reqs, nreq, st, st, B));
   cudaEvent_t e0, e1;
   CG_CUDA(cudaEventCreate(&e0));
   CG_CUDA(cudaEventCreate(&e1));
@@ -432,11 +514,11 @@ cg_status cg_tune_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, const uin
   uint32_t best = cand[0];
   cg_status status = CG_OK;
   for (uint32_t k = 0; k < nc && status == CG_OK; k++) {
-    status = batch_split(c, B, (uint64_t)cand[k] * 1024, st);
+    status = batch_split(c, K, B, (uint64_t)cand[k] * 1024, st);
     float lo = 0.f;
     for (uint32_t r = 0; r < repeats && status == CG_OK; r++) {
       cudaEventRecord(e0, st);
-      status = batch_levels(c, B, ~kModeCarry, st);  // dry: the shadow is not written
+      status = batch_levels(c, K, B, ~kModeCarry, st);  // dry: the shadow is not written
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) status = set_error(CG_E_CUDA, "tuning run");
       float t = 0.f;

@@ -432,6 +432,63 @@ struct PinBuf {
   }
 };
 
+// Per-batch buffers (device, and pinned host staging), one set per slot.
+struct BatchBufs {
+  DevBuf<cg_copy> b_reqs;
+  DevBuf<uint32_t> b_order;
+  DevBuf<uint64_t> b_segfirst, b_stage;
+  DevBuf<ScanJob> b_jobs;
+  DevBuf<RangeInfo> b_info;
+  DevBuf<Acc> b_acc;
+  DevBuf<cg_report> b_reps;
+  DevBuf<uint32_t> b_counts;
+  DevBuf<uint64_t> b_blocksums;
+  DevBuf<cg_err_record> b_recs;
+  DevBuf<unsigned int> b_err;
+  DevBuf<uint8_t> b_modes;
+  DevBuf<uint8_t> stage;  // overlapping device->device sources
+  PinBuf<uint8_t> h_modes;
+  PinBuf<uint8_t> h_stage_in;  // pinned upload staging
+  PinBuf<cg_report> h_reps;
+  PinBuf<cg_err_record> h_recs;
+  PinBuf<uint64_t> h_total;
+  // a batch in flight in this slot (asynchronous submission)
+  uint64_t ticket = 0;        // 0: free
+  cudaEvent_t done = nullptr;  // recorded after its results' copies
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // around its level kernels
+  uint64_t nreq = 0, nblocks = 0, dev_rec_cap = 0, t_begin = 0;
+  int nlev = 0;
+  int online_slot = -1;
+  uint32_t source = 0, kib = 0;
+  std::vector<float> feat;    // features, kept for an online trial's record
+  void release() {
+    b_reqs.release();
+    b_order.release();
+    b_segfirst.release();
+    b_stage.release();
+    b_jobs.release();
+    b_info.release();
+    b_acc.release();
+    b_reps.release();
+    b_counts.release();
+    b_blocksums.release();
+    b_recs.release();
+    b_err.release();
+    b_modes.release();
+    stage.release();
+    h_modes.release();
+    h_stage_in.release();
+    h_reps.release();
+    h_recs.release();
+    h_total.release();
+    if (done) cudaEventDestroy(done);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    done = t0 = t1 = nullptr;
+    ticket = 0;
+  }
+};
+
 struct ServeEngine;
 
 }  // namespace cgi
@@ -455,24 +512,11 @@ struct cg_ctx {
   cgi::DevBuf<uint64_t> t_base, t_size, t_shadow;
   uint64_t t_version = ~0ull;
   uint64_t t_count = 0;
-  // batch buffers
-  cgi::DevBuf<cg_copy> b_reqs;
-  cgi::DevBuf<uint32_t> b_order;
-  cgi::DevBuf<uint64_t> b_segfirst, b_stage;
-  cgi::DevBuf<cgi::ScanJob> b_jobs;
-  cgi::DevBuf<cgi::RangeInfo> b_info;
-  cgi::DevBuf<cgi::Acc> b_acc;
-  cgi::DevBuf<cg_report> b_reps;
-  cgi::DevBuf<uint32_t> b_counts;
-  cgi::DevBuf<uint64_t> b_blocksums;
-  cgi::DevBuf<cg_err_record> b_recs;
-  cgi::DevBuf<unsigned int> b_err;
-  cgi::DevBuf<uint8_t> b_modes;
-  cgi::PinBuf<uint8_t> h_modes;
-  cgi::PinBuf<uint8_t> h_stage_in;  // pinned upload staging
-  cgi::PinBuf<cg_report> h_reps;
-  cgi::PinBuf<cg_err_record> h_recs;
-  cgi::PinBuf<uint64_t> h_total;
+  // batch buffers: two slots, so that a batch can be planned while the one
+  // before it still runs (slot 0 also serves the synchronous paths)
+  cgi::BatchBufs bb[2];
+  cudaStream_t side = nullptr;  // lookups of batches submitted asynchronously
+  uint64_t next_ticket = 1;
   // batch split choice: tuned entries (features -> segment KiB) and the
   // learned cost model's weights (empty = none)
   std::vector<std::vector<float>> tuned_feat;

@@ -96,26 +96,29 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   }
   if (nargs == 0) return CG_OK;
   if (nargs > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 arguments per call");
+  if (c->bb[0].ticket || c->bb[1].ticket)
+    return set_error(CG_E_STATE, "batches still in flight (cg_batch_wait first)");
+  BatchBufs &K = c->bb[0];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CG_TRY(flush_fills(c, st));
   CG_TRY(ensure_device_table(c, st));
   CG_TRY(c->k_args.ensure(nargs));
   CG_TRY(c->k_fill.ensure(3 * nargs));
-  CG_TRY(c->b_order.ensure(nargs));
-  CG_TRY(c->b_segfirst.ensure(nargs));
-  CG_TRY(c->b_jobs.ensure(nargs));
-  CG_TRY(c->b_info.ensure(nargs));
-  CG_TRY(c->b_acc.ensure(nargs));
-  CG_TRY(c->b_reps.ensure(nargs));
-  CG_TRY(c->b_counts.ensure(nargs));
-  CG_TRY(c->b_err.ensure(1));
+  CG_TRY(K.b_order.ensure(nargs));
+  CG_TRY(K.b_segfirst.ensure(nargs));
+  CG_TRY(K.b_jobs.ensure(nargs));
+  CG_TRY(K.b_info.ensure(nargs));
+  CG_TRY(K.b_acc.ensure(nargs));
+  CG_TRY(K.b_reps.ensure(nargs));
+  CG_TRY(K.b_counts.ensure(nargs));
+  CG_TRY(K.b_err.ensure(1));
   const uint64_t nblocks = (nargs + kFinalizeItems - 1) / kFinalizeItems;
-  CG_TRY(c->b_blocksums.ensure(nblocks + 1));
+  CG_TRY(K.b_blocksums.ensure(nblocks + 1));
   // pinned staging: arguments | order | scan segments | fill groups
   const uint64_t a_bytes = round_up(nargs * sizeof(cg_karg), 16);
   const uint64_t o_bytes = round_up(nargs * 4, 16);
-  CG_TRY(c->h_stage_in.ensure(a_bytes + o_bytes + 16 * nargs + 64));
-  uint8_t *hp = c->h_stage_in.p;
+  CG_TRY(K.h_stage_in.ensure(a_bytes + o_bytes + 16 * nargs + 64));
+  uint8_t *hp = K.h_stage_in.p;
   std::memcpy(hp, args, nargs * sizeof(cg_karg));
   uint32_t *h_order = reinterpret_cast<uint32_t *>(hp + a_bytes);
   uint64_t *h_seg = reinterpret_cast<uint64_t *>(hp + a_bytes + o_bytes);
@@ -135,18 +138,18 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   }
   uint64_t *fill_ptr = c->k_fill.p, *fill_n = c->k_fill.p + nargs, *fill_seg = c->k_fill.p + 2 * nargs;
   CG_CUDA(cudaMemcpyAsync(c->k_args.p, hp, nargs * sizeof(cg_karg), cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_order.p, h_order, nargs * 4, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(c->b_segfirst.p, h_seg, nargs * 8, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_order.p, h_order, nargs * 4, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_segfirst.p, h_seg, nargs * 8, cudaMemcpyHostToDevice, st));
   CG_CUDA(cudaMemcpyAsync(fill_seg, h_fseg, nargs * 8, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemsetAsync(c->b_err.p, 0, sizeof(unsigned int), st));
+  CG_CUDA(cudaMemsetAsync(K.b_err.p, 0, sizeof(unsigned int), st));
   BatchPlan plan{};
   plan.reqs = nullptr;  // only the lookup reads copies; the argument lookup has its own
-  plan.order = c->b_order.p;
-  plan.seg_first = c->b_segfirst.p;
+  plan.order = K.b_order.p;
+  plan.seg_first = K.b_segfirst.p;
   plan.stage = nullptr;
-  plan.jobs = c->b_jobs.p;
-  plan.info = c->b_info.p;
-  plan.acc = c->b_acc.p;
+  plan.jobs = K.b_jobs.p;
+  plan.info = K.b_info.p;
+  plan.acc = K.b_acc.p;
   plan.nreq = nargs;
   plan.seg_chunks = (uint32_t)seg_chunks;
   plan.mode_mask = ~0u;
@@ -155,28 +158,28 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   c->stats.kernels++;
   if (segs) {
     if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, c->b_err.p, st));
+      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, K.b_err.p, st));
     else
       CG_CUDA(launch_scan_level(c->img, plan, 0, nargs, segs, c->sm_count * 8, st));
     c->stats.kernels++;
   }
-  CG_CUDA(launch_finalize(plan, c->b_reps.p, c->b_counts.p, c->b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_finalize(plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
   c->stats.kernels++;
   if (fgroups) {  // after the scans on the same stream: reads see the state before the launch
     CG_CUDA(launch_fill_spans(fill_ptr, fill_n, fill_seg, nargs, fgroups, 0x00, c->sm_count, st));
     c->stats.kernels++;
   }
-  CG_TRY(c->h_total.ensure(2));
-  CG_TRY(c->h_reps.ensure(nargs));
-  CG_CUDA(cudaMemcpyAsync(c->h_total.p + 1, c->b_err.p, sizeof(unsigned int),
+  CG_TRY(K.h_total.ensure(2));
+  CG_TRY(K.h_reps.ensure(nargs));
+  CG_CUDA(cudaMemcpyAsync(K.h_total.p + 1, K.b_err.p, sizeof(unsigned int),
                           cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(c->h_reps.p, c->b_reps.p, nargs * sizeof(cg_report),
+  CG_CUDA(cudaMemcpyAsync(K.h_reps.p, K.b_reps.p, nargs * sizeof(cg_report),
                           cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
-  if (reinterpret_cast<const unsigned int *>(c->h_total.p + 1)[0])
+  if (reinterpret_cast<const unsigned int *>(K.h_total.p + 1)[0])
     return set_error(CG_E_TIMEOUT, "a bounded wait in the scan kernel ran out");
-  if (reps) std::memcpy(reps, c->h_reps.p, nargs * sizeof(cg_report));
-  for (uint64_t i = 0; i < nargs; i++) count_stats(c, c->h_reps.p[i]);
+  if (reps) std::memcpy(reps, K.h_reps.p, nargs * sizeof(cg_report));
+  for (uint64_t i = 0; i < nargs; i++) count_stats(c, K.h_reps.p[i]);
   return CG_OK;
 }
 

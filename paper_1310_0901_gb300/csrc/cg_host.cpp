@@ -274,24 +274,9 @@ cg_status cg_destroy(cg_ctx *c) {
   c->t_base.release();
   c->t_size.release();
   c->t_shadow.release();
-  c->b_reqs.release();
-  c->b_order.release();
-  c->b_segfirst.release();
-  c->b_stage.release();
-  c->b_jobs.release();
-  c->b_info.release();
-  c->b_acc.release();
-  c->b_reps.release();
-  c->b_counts.release();
-  c->b_blocksums.release();
-  c->b_recs.release();
-  c->b_err.release();
-  c->b_modes.release();
-  c->h_modes.release();
-  c->h_stage_in.release();
-  c->h_reps.release();
-  c->h_recs.release();
-  c->h_total.release();
+  c->bb[0].release();
+  c->bb[1].release();
+  if (c->side) cudaStreamDestroy(c->side);
   c->arena.release_all();
   delete c;
   return CG_OK;
