@@ -339,38 +339,55 @@ def run_batched_workload(args, which: str):
     nreq = len(reqs)
     bytes_per_batch = int(reqs["n"].sum())
     stream = torch.cuda.current_stream(dev)
+    reps_out = np.empty(nreq, dtype=cg.REPORT_DTYPE)   # result buffers reused across batches
+    recs_out = np.empty(8 * nreq, dtype=cg.RECORD_DTYPE)
     # the split is autotuned online: the warm-up batches try the candidates
     # (real runs, timed), the timed batches use the fastest
     for _ in range(max(args.warmup, 5 if not args.segment_kib else 0)):
-        stt, reps, recs, total, _ = ctx.check_batch(reqs, rec_cap=8 * nreq)
+        stt, reps, recs, total, _ = ctx.check_batch(reqs, 8 * nreq, None, reps_out, recs_out)
         cg.check(stt, "check_batch")
     s0 = ctx.stats()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        stt, reps, recs, total, _ = ctx.check_batch(reqs, rec_cap=8 * nreq)
+        stt, reps, recs, total, _ = ctx.check_batch(reqs, 8 * nreq, None, reps_out, recs_out)
         cg.check(stt, "check_batch")
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     s1 = ctx.stats()
     # pipelined: two batches in flight, the next one looked up and planned on
     # the host while the one before runs (cg_check_batch_async)
+    reps = reps.copy()  # the last synchronous batch's reports (the roofline reads them)
+    host_s = {"submit": 0.0, "wait": 0.0}
+
     def pipelined(k):
         pend = []
         for _ in range(k):
+            h0 = time.perf_counter()
             stt, t, _ = ctx.check_batch_async(reqs, rec_cap=8 * nreq)
+            host_s["submit"] += time.perf_counter() - h0
             cg.check(stt, "check_batch_async")
             pend.append(t)
             if len(pend) == 2:
-                cg.check(ctx.batch_wait(pend.pop(0), nreq)[0], "batch_wait")
+                h0 = time.perf_counter()
+                cg.check(ctx.batch_wait(pend.pop(0), nreq, 8 * nreq, reps_out, recs_out)[0],
+                         "batch_wait")
+                host_s["wait"] += time.perf_counter() - h0
         for t in pend:
-            cg.check(ctx.batch_wait(t, nreq)[0], "batch_wait")
+            h0 = time.perf_counter()
+            cg.check(ctx.batch_wait(t, nreq, 8 * nreq, reps_out, recs_out)[0], "batch_wait")
+            host_s["wait"] += time.perf_counter() - h0
     pipelined(2)
     torch.cuda.synchronize()
+    host_s["submit"] = host_s["wait"] = 0.0
+    sp0 = ctx.stats()
     tp = time.perf_counter()
     pipelined(args.steps)
     torch.cuda.synchronize()
     dt_pipe = time.perf_counter() - tp
+    sp1 = ctx.stats()
+    host_s["of_which_lookup"] = (sp1["batch_lookup_ns"] - sp0["batch_lookup_ns"]) / 1e9
+    host_s["of_which_plan"] = (sp1["batch_plan_ns"] - sp0["batch_plan_ns"]) / 1e9
     levels = (s1["levels"] - s0["levels"]) / args.steps
     launches = (s1["kernels"] - s0["kernels"]) / args.steps
     per_batch_ms = {k: round((s1[k] - s0[k]) / args.steps / 1e6, 2)
@@ -414,6 +431,7 @@ def run_batched_workload(args, which: str):
         "value": round(batch_cps, 1), "unit": "checks/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(dt_pipe / args.steps * 1e3, 3),
         "mode": "two batches in flight (cg_check_batch_async)",
+        "host_ms_per_batch": {k: round(v / args.steps * 1e3, 2) for k, v in host_s.items()},
         "one_batch_at_a_time": {"checks_per_s": round(sync_cps, 1),
                                 "ms_per_batch": round(dt / args.steps * 1e3, 3)},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",

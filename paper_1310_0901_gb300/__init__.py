@@ -365,29 +365,35 @@ class Context:
                                   ctypes.byref(t), ctypes.byref(bad), _stream_handle(stream))
         return st, int(t.value), int(bad.value)
 
-    def batch_wait(self, ticket: int, nreq: int, rec_cap: int | None = None):
-        """Results of an enqueued batch: (status, reports, records, total)."""
+    def batch_wait(self, ticket: int, nreq: int, rec_cap: int | None = None,
+                   reps_out: np.ndarray | None = None, recs_out: np.ndarray | None = None):
+        """Results of an enqueued batch: (status, reports, records, total).
+        reps_out / recs_out (REPORT_DTYPE / RECORD_DTYPE arrays of at least
+        nreq / rec_cap entries) receive them if given; fresh arrays otherwise."""
         if rec_cap is None:
             rec_cap = 8 * nreq
-        reps = np.zeros(max(1, nreq), dtype=REPORT_DTYPE)
-        recs = np.zeros(max(1, rec_cap), dtype=RECORD_DTYPE)
+        reps = reps_out if reps_out is not None else np.empty(max(1, nreq), dtype=REPORT_DTYPE)
+        recs = recs_out if recs_out is not None else np.empty(max(1, rec_cap), dtype=RECORD_DTYPE)
+        assert len(reps) >= nreq and len(recs) >= min(rec_cap, 1)
         n_rec = u64(0)
         st = cg_batch_wait(self._h, ticket, reps.ctypes.data, recs.ctypes.data, rec_cap,
                            ctypes.byref(n_rec))
         total = int(n_rec.value)
         return st, reps[:nreq], recs[:min(total, rec_cap)], total
 
-    def check_batch(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None):
+    def check_batch(self, reqs: np.ndarray, rec_cap: int | None = None, stream=None,
+                    reps_out: np.ndarray | None = None, recs_out: np.ndarray | None = None):
         """reqs: structured array with the layout of cg_copy (cg_synth.REQ_DTYPE).
         Returns (status, reports as a structured array, records as a
-        structured array, total record count, bad index)."""
+        structured array, total record count, bad index).  reps_out /
+        recs_out, if given, receive the results (no fresh arrays)."""
         reqs = np.ascontiguousarray(reqs)
         assert reqs.dtype.itemsize == 32
         n = len(reqs)
         if rec_cap is None:
             rec_cap = 8 * n
-        reps = np.zeros(n, dtype=REPORT_DTYPE)
-        recs = np.zeros(max(1, rec_cap), dtype=RECORD_DTYPE)
+        reps = reps_out[:n] if reps_out is not None else np.zeros(n, dtype=REPORT_DTYPE)
+        recs = recs_out if recs_out is not None else np.zeros(max(1, rec_cap), dtype=RECORD_DTYPE)
         n_rec = u64(0)
         bad = u64(0)
         st = cg_check_batch(self._h, reqs.ctypes.data if n else None, n,

@@ -157,7 +157,10 @@ cg_status batch_split(cg_ctx *c, BatchBufs &K, BatchRun &B, uint64_t seg_bytes,
       const cg_copy &q = B.reqs[i];
       B.h_segfirst[pos] = acc_segs;
       const bool idle = q.kind == CG_DTOD && !(B.modes[i] & (kModeCarry | kModeReadDev));
-      const uint64_t chunks_ub = (q.n && !idle) ? (q.n + 30) >> 4 : 0;
+      // the TMA engine walks a device->host copy with no valid source in
+      // 128-byte super-chunks (its A bits alone)
+      const bool aonly = B.tma && q.kind == CG_DTOH && !(B.modes[i] & kModeReadDev);
+      const uint64_t chunks_ub = (q.n && !idle) ? (aonly ? (q.n + 254) >> 7 : (q.n + 30) >> 4) : 0;
       acc_segs += (chunks_ub + seg_chunks - 1) / seg_chunks;
     }
     B.lev_segs[l] = acc_segs;

@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
   const Geo g = make_geo(job, img);
-  const int64_t rows = (g.nchunks + 31) >> 5;
+  const bool aonly = a_only<KIND, CARRY>(g);  // super-tiles of A bits alone
+  const int64_t rows = ((aonly ? super_chunks(g) : g.nchunks) + 31) >> 5;
   const int64_t ntiles = (rows + kR - 1) / kR;
   const int64_t gw = (int64_t)blockIdx.x * kTW + wid;
   const int64_t nw = (int64_t)gridDim.x * kTW;
@@ -52,6 +53,9 @@ __global__ void __launch_bounds__(kTW * 32, 1)
       if (t >= ntiles) continue;
       if ((job.mode & kModeStall) && gw == 0 && s == 0)  // injected: expect bytes, copy none
         mbar_arrive_expect_tx(smem_addr(&bars[s]), 16);
+      else if (aonly)
+        issue_tile_a_super(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
+                           smem_addr(&bars[s]));
       else
         issue_tile<KIND>(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
                          smem_addr(&bars[s]));
@@ -66,13 +70,20 @@ __global__ void __launch_bounds__(kTW * 32, 1)
       break;
     }
     parity ^= 1u << s;
-    consume_tile<KIND, CARRY>(g, t * kR * 32, wbase + s * kStage, lane, la);
+    if (aonly)
+      consume_tile_a_super(g, t * kR * 32, wbase + s * kStage, lane, la);
+    else
+      consume_tile<KIND, CARRY>(g, t * kR * 32, wbase + s * kStage, lane, la);
     __syncwarp();
     const int64_t tn = t + (int64_t)kNS * nw;
     if (lane == 0 && tn < ntiles) {
       fence_proxy_async();
-      issue_tile<KIND>(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
-                       smem_addr(&bars[s]));
+      if (aonly)
+        issue_tile_a_super(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
+                           smem_addr(&bars[s]));
+      else
+        issue_tile<KIND>(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
+                         smem_addr(&bars[s]));
     }
     s = s + 1 == kNS ? 0 : s + 1;
   }
@@ -152,7 +163,8 @@ __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, cons
       seg_set_pos(it, p, img, seg_search(p, lo, hi, it.s), pos_end);
     }
     const int64_t k = (int64_t)(it.s - it.first);
-    const int64_t rows = (it.g.nchunks + 31) >> 5;
+    const bool aonly = it.job.kind == CG_DTOH && !(it.job.mode & (kModeCarry | kModeReadDev));
+    const int64_t rows = ((aonly ? super_chunks(it.g) : it.g.nchunks) + 31) >> 5;
     const int64_t r0 = k * seg_rows;
     const int64_t r1 = r0 + seg_rows < rows ? r0 + seg_rows : rows;
     if (r0 < r1) {
@@ -191,7 +203,10 @@ __device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bi
       issue_tile<CG_HTOD>(it.g, a_bits, c0, st, bar);
       break;
     case CG_DTOH:
-      issue_tile<CG_DTOH>(it.g, a_bits, c0, st, bar);
+      if (!(it.job.mode & (kModeCarry | kModeReadDev)))
+        issue_tile_a_super(it.g, a_bits, c0, st, bar);
+      else
+        issue_tile<CG_DTOH>(it.g, a_bits, c0, st, bar);
       break;
     default:
       issue_tile<CG_DTOD>(it.g, a_bits, c0, st, bar);
@@ -213,6 +228,8 @@ __device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp
     case CG_DTOH:
       if (carry)
         consume_tile<CG_DTOH, true>(it.g, c0, sp, lane, la);
+      else if (!(it.job.mode & kModeReadDev))
+        consume_tile_a_super(it.g, c0, sp, lane, la);
       else
         consume_tile<CG_DTOH, false>(it.g, c0, sp, lane, la);
       break;

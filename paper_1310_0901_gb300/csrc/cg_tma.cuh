@@ -129,37 +129,98 @@ __device__ __forceinline__ void issue_tile(const Geo &g, const uint8_t *a_bytes,
   if (abytes) bulk_g2s(st + kVBytes + aoff, a_bytes + asrc, abytes, bar);
 }
 
+// ---------------------------------------------------- A-bits-only tiles
+
 // A device->host copy whose source range is invalid reads no V and carries
-// nothing: its bytes are classified by the destination's A bits alone
-// (unaddressable or good).  Lane L takes 128 copy bytes, i.e. four A words,
-// of the tile instead of walking 16-byte chunks: zeros are counted with
-// popc, the first one found with ffs.
-__device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, const uint8_t *sp,
-                                                    int lane, LaneAcc &la) {
-  const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
-  const int64_t p0 = g.hb0 + 16 * c0;   // host position of the tile's first byte
+// nothing: only its destination's A bits decide (unaddressable or good).
+// The whole-copy kernels give such a copy tiles of kR*32 "super-chunks" of
+// 128 bytes (32 KiB of copy, 4 KiB of A bits per tile) so that each bulk
+// copy is as large as a V tile; the chunk index c of these tiles counts
+// super-chunks on the same anchor grid (copy offset 128*c - ax).
+template <uint32_t KIND, bool CARRY>
+__device__ __forceinline__ bool a_only(const Geo &g) {
+  return KIND == CG_DTOH && !CARRY && !g.has_vin;
+}
+
+__device__ __forceinline__ int64_t super_chunks(const Geo &g) {
+  return (g.ax + (int64_t)g.n + 127) >> 7;
+}
+
+// Lane 0: queue the A bytes of super-tile c0 (host bits [p0, p0 + 32768 +
+// 32), clipped to the copy's) into the stage from its start.
+__device__ __forceinline__ void issue_tile_a_super(const Geo &g, const uint8_t *a_bytes,
+                                                   int64_t c0, uint32_t st, uint32_t bar) {
+  const int64_t p0 = g.hb0 + 128 * c0;
   const int64_t aorig = floor16(p0 >> 3);
-  const int64_t i0 = 16 * c0 - g.ax + 128 * (int64_t)lane;  // copy offset of this lane's bytes
-  const int64_t rel = p0 + 128 * (int64_t)lane - 8 * aorig;  // bit offset in the A window
-  const int64_t w = rel >> 5;
-  const int sh = (int)(rel & 31);
+  const int64_t q0 = p0 > g.hlo ? p0 : g.hlo;
+  const int64_t pe = p0 + 4096 * kR + 32;
+  const int64_t q1 = pe < g.hhi ? pe : g.hhi;
+  uint32_t bytes = 0;
+  int64_t b0 = 0;
+  if (q1 > q0) {
+    b0 = floor16(q0 >> 3);
+    const int64_t b1 = ceil16((q1 + 7) >> 3);
+    bytes = (uint32_t)(b1 - b0);
+  }
+  mbar_arrive_expect_tx(bar, bytes);
+  if (bytes) bulk_g2s(st + (uint32_t)(b0 - aorig), a_bytes + b0, bytes, bar);
+}
+
+// Classify the A words j = L, L + 32, ... (< nwords) of a tile whose first
+// copy byte has offset i0 and whose A window starts bit `rel0` into the
+// stage: word j holds copy bytes [i0 + 32 j, +32).  Lanes read consecutive
+// words (no bank conflicts); each lane's words come in increasing order, so
+// the first zero it finds is its smallest.
+__device__ __forceinline__ void classify_a_words(const Geo &g, const uint32_t *as, int64_t i0,
+                                                 int64_t rel0, int nwords, int lane,
+                                                 LaneAcc &la) {
+  const int64_t w0 = rel0 >> 5;
+  const int sh = (int)(rel0 & 31);
   uint32_t un = 0;
   unsigned long long first = kNone;
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-    const int64_t b0 = i0 + 32 * k;  // copy offset of bit 0 of this word
+  if (i0 >= 0 && i0 + 32 * (int64_t)nwords <= (int64_t)g.n) {  // every bit valid
+    for (int j = lane; j < nwords; j += 32) {
+      const uint32_t zero = ~__funnelshift_r(as[w0 + j], as[w0 + j + 1], sh);
+      un += __popc(zero);
+      if (zero && first == kNone)
+        first = (unsigned long long)(g.obase + i0 + 32 * (int64_t)j + __ffs(zero) - 1);
+    }
+    la.un += un;
+    if (first != kNone && la.fun == kNone) la.fun = first;
+    return;
+  }
+  for (int j = lane; j < nwords; j += 32) {
+    const int64_t b0 = i0 + 32 * (int64_t)j;
     const int64_t lo = b0 < 0 ? -b0 : 0;
     const int64_t rem = (int64_t)g.n - b0;
     const int64_t hi = rem < 32 ? rem : 32;
     if (hi <= lo) continue;
     const uint32_t valid = (hi == 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
-    const uint32_t bits = __funnelshift_r(as[w + k], as[w + k + 1], sh);
-    const uint32_t zero = ~bits & valid;
+    const uint32_t zero = ~__funnelshift_r(as[w0 + j], as[w0 + j + 1], sh) & valid;
     un += __popc(zero);
     if (zero && first == kNone) first = (unsigned long long)(g.obase + b0 + __ffs(zero) - 1);
   }
   la.un += un;
   if (first != kNone && la.fun == kNone) la.fun = first;
+}
+
+// All lanes: classify a super-tile (1024 A words, 32 KiB of copy).
+__device__ __forceinline__ void consume_tile_a_super(const Geo &g, int64_t c0, const uint8_t *sp,
+                                                     int lane, LaneAcc &la) {
+  const int64_t p0 = g.hb0 + 128 * c0;
+  const int64_t aorig = floor16(p0 >> 3);
+  classify_a_words(g, reinterpret_cast<const uint32_t *>(sp), 128 * c0 - g.ax, p0 - 8 * aorig,
+                   32 * 32, lane, la);
+}
+
+// The same for an ordinary 4 KiB tile (128 A words), for the kernels that
+// keep 16-byte chunks (pitched rows).
+__device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, const uint8_t *sp,
+                                                    int lane, LaneAcc &la) {
+  const int64_t p0 = g.hb0 + 16 * c0;  // host position of the tile's first byte
+  const int64_t aorig = floor16(p0 >> 3);
+  classify_a_words(g, reinterpret_cast<const uint32_t *>(sp + kVBytes), 16 * c0 - g.ax,
+                   p0 - 8 * aorig, 16 * kR, lane, la);
 }
 
 // All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
