@@ -86,10 +86,15 @@ REPORT_FIELDS = [f for f, _ in OrReport._fields_]
 RECORD_FIELDS = [f for f, _ in OrRecord._fields_]
 
 
-def build(src: str = SRC, out: str = LIB, werror: bool = True) -> str:
-    """Compile the oracle with plain gcc (no vector intrinsics, portable)."""
+def build(src: str = SRC, out: str = LIB, werror: bool = True, sanitize: bool = False) -> str:
+    """Compile the oracle with plain gcc (no vector intrinsics, portable).
+    sanitize: an AddressSanitizer + UndefinedBehaviorSanitizer build (load
+    it in a process started with the ASan runtime preloaded)."""
     cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-Wextra"]
     cmd += ["-Werror"] if werror else []
+    if sanitize:
+        cmd += ["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                "-fno-sanitize-recover=all"]
     cmd += ["-o", out, src]
     subprocess.run(cmd, check=True)
     return out

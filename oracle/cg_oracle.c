@@ -185,8 +185,10 @@ int or_register_alloc(or_state *s, uint64_t base, uint64_t size) {
   uint64_t lo = lower_bound_freed(s, base);
   uint64_t hi = lo;
   while (hi < s->n_freed && s->freed[hi] - base < size) hi++;
-  memmove(&s->freed[lo], &s->freed[hi], (s->n_freed - hi) * sizeof *s->freed);
-  s->n_freed -= hi - lo;
+  if (hi > lo) {
+    memmove(&s->freed[lo], &s->freed[hi], (s->n_freed - hi) * sizeof *s->freed);
+    s->n_freed -= hi - lo;
+  }
   return OR_OK;
 }
 
@@ -256,7 +258,7 @@ int or_mark(or_state *s, uint64_t dptr, uint64_t n, uint8_t value) {
 
 int or_read_host_v(const or_state *s, uint64_t off, uint64_t n, uint8_t *out) {
   if (off > s->host_n || n > s->host_n - off) return OR_E_HOST_RANGE;
-  memcpy(out, s->host_v + off, n);
+  if (n) memcpy(out, s->host_v + off, n);
   return OR_OK;
 }
 
