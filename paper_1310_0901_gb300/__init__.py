@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libcg.so")
+# CG_LIB_PATH selects another build of the same library (an instrumented one)
+LIB_PATH = os.environ.get("CG_LIB_PATH") or os.path.join(PKG, "libcg.so")
 
 HTOD, DTOH, DTOD = 1, 2, 3
 BYTE_GOOD, BYTE_UNADDR, BYTE_UNDEF = 0, 1, 2

@@ -110,6 +110,7 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   // device source, which the level plan needs
   DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
   const uint64_t t_lookup = now_ns();
+  NvtxRange r_lookup("cg batch: lookup");
   CG_CUDA(launch_lookup(dt, plan, (int)c->cfg.strict_device_undef, (int)c->cfg.carry, look));
   CG_CUDA(launch_job_modes(plan, K.b_modes.p, look));
   c->stats.kernels += 2;
@@ -119,6 +120,7 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   const uint64_t t_plan = now_ns();
   c->stats.batch_lookup_ns += t_plan - t_lookup;
   // dependency levels, exact on validity
+  NvtxRange r_plan("cg batch: plan levels");
   B.lvl = plan_levels(reqs, nreq, c->cfg.carry != 0, B.modes);
   B.nlev = 0;
   for (int l : B.lvl) B.nlev = std::max(B.nlev, l + 1);
@@ -171,6 +173,7 @@ cg_status batch_split(cg_ctx *c, BatchBufs &K, BatchRun &B, uint64_t seg_bytes,
 
 cg_status batch_levels(cg_ctx *c, BatchBufs &K, BatchRun &B, uint32_t mode_mask,
                        cudaStream_t st) {
+  NvtxRange range("cg batch: enqueue level kernels");
   B.plan.mode_mask = mode_mask;
   const bool dry = !(mode_mask & kModeCarry);
   CG_CUDA(cudaMemsetAsync(K.b_err.p, 0, sizeof(unsigned int), st));
@@ -363,6 +366,7 @@ cg_status batch_submit(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t r
     if (!c->bb[k].ticket) slot = k;
   if (slot < 0) return set_error(CG_E_FULL, "two batches in flight: cg_batch_wait first");
   BatchBufs &K = c->bb[slot];
+  NvtxRange range("cg batch: submit");
   K.t_begin = now_ns();
   BatchRun B;
   CG_TRY(batch_prepare(c, K, reqs, nreq, st, look, B));
@@ -411,6 +415,7 @@ cg_status batch_submit(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t r
 cg_status batch_finish(cg_ctx *c, int slot, cg_report *reps, cg_err_record *recs,
                        uint64_t rec_cap, uint64_t *n_rec) {
   BatchBufs &K = c->bb[slot];
+  NvtxRange range("cg batch: wait");
   struct Free {
     BatchBufs &k;
     ~Free() { k.ticket = 0; }

@@ -3,6 +3,7 @@
 // C ABI (cg_host.cpp) and the serving engine (cg_serve.cpp).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -180,6 +181,15 @@ class ShadowArena {
         break;
       }
   }
+};
+
+// A named NVTX range for profilers (ncu --nvtx, nsys) around a host phase;
+// a few instructions when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // ---------------------------------------------------- allocation table

@@ -99,6 +99,7 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   if (c->bb[0].ticket || c->bb[1].ticket)
     return set_error(CG_E_STATE, "batches still in flight (cg_batch_wait first)");
   BatchBufs &K = c->bb[0];
+  NvtxRange range("cg kernel arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CG_TRY(flush_fills(c, st));
   CG_TRY(ensure_device_table(c, st));

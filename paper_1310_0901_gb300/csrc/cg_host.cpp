@@ -499,6 +499,7 @@ static cg_status prepare_single(cg_ctx *c, const cg_copy &q, RangeInfo *ri, Scan
 // the scan; the kernel's last CTA writes the report to `out`.
 static cg_status enqueue_single(cg_ctx *c, const RangeInfo &ri, ScanJob job, bool stage,
                                 uint64_t stage_src, cg_report *out, cudaStream_t st) {
+  NvtxRange range("cg check copy");
   CG_TRY(flush_fills(c, st));
   if (stage) {
     CG_TRY(c->stage.ensure(round_up(job.n, 256)));

@@ -191,6 +191,7 @@ uint64_t row_chunks(const cg_ctx *c, const PitchedJob &j) {
 }
 
 cg_status enqueue3d(cg_ctx *c, Prepared &P, cg_report *out, cudaStream_t st) {
+  NvtxRange range("cg check pitched copy");
   CG_TRY(flush_fills(c, st));
   if (P.trivial) {  // no byte to read: the report alone
     ScanJob none{};

@@ -481,6 +481,7 @@ struct ServeEngine {
                    std::vector<RangeInfo> &infos, std::vector<uint8_t> &modes,
                    std::vector<StageCopy> &stages, std::vector<uint64_t> &stage_ptr,
                    uint64_t stage_bytes, uint64_t bytes) {
+    NvtxRange range("cg serve: launch round");
     const uint64_t n = members.size();
     cudaStream_t s = R.stream;
     // dependency levels inside the round
