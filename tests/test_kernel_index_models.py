@@ -1,0 +1,248 @@
+"""CPU models of the GPU kernels' index arithmetic, run before their first
+GPU launch and kept as tests: for many random geometries, every chunk of
+every row is visited exactly once by the pitched work splits, and every
+bulk copy and shared-memory read of the span and A-bits-only tiles stays
+inside its buffer and window while covering every byte that is classified.
+The models restate the kernels' integer arithmetic (cg_scan_pitched.cu,
+cg_tma.cuh); a change there must be mirrored here.  CPU only."""
+from __future__ import annotations
+
+import random
+
+kR = 8
+kVBytes = 16 * (32 * kR + 1)
+kABytes = 64 * kR + 64
+kStage = ((kVBytes + kABytes) + 127) & ~127
+
+
+def f16(x):
+    return x & ~15
+
+
+def c16(x):
+    return (x + 15) & ~15
+
+
+# ------------------------------------------------ pitched work splits
+
+def _visit_pitched(width, rows, sm, per_sm, uniform, ax0):
+    ax = (lambda r: ax0) if uniform else (lambda r: (r * 7 + 3) % 16)
+    kmax = ((ax0 + width + 15) >> 4) if uniform else (width + 30) >> 4
+    need = {r: (ax(r) + width + 15) >> 4 for r in range(rows)}
+    seen = set()
+    wpc = 8
+    if kmax >= 256:           # scan_pitched_tma_kernel
+        kTW = 16
+        tpr = (kmax + 32 * kR - 1) // (32 * kR)
+        ntiles = rows * tpr
+        grid = min((ntiles + kTW - 1) // kTW, sm * per_sm)
+        nw = grid * kTW
+        for gw in range(nw):
+            for t in range(gw, ntiles, nw):
+                r = t // tpr
+                c0 = (t - r * tpr) * kR * 32
+                for c in range(c0, c0 + kR * 32):
+                    if c < need[r]:
+                        assert (r, c) not in seen
+                        seen.add((r, c))
+    elif kmax > 32:           # scan_pitched_wide_kernel
+        U = 4
+        G = (kmax + 32 * U - 1) // (32 * U)
+        items = rows * G
+        grid = max(1, min((items + wpc - 1) // wpc, sm * per_sm))
+        T = grid * wpc
+        tg, tr = T % G, T // G
+        for warp in range(grid * wpc):
+            grp, r = warp % G, warp // G
+            while r < rows:
+                for k in range(U):
+                    for lane in range(32):
+                        c = grp * 32 * U + 32 * k + lane
+                        if c < need[r]:
+                            assert (r, c) not in seen
+                            seen.add((r, c))
+                grp += tg
+                r += tr
+                if grp >= G:
+                    grp -= G
+                    r += 1
+    else:                     # scan_pitched_narrow_kernel
+        lp = 0
+        while (1 << lp) < kmax:
+            lp += 1
+        P = 1 << lp
+        groups = 32 >> lp
+        U = 1
+        per_step = groups * U
+        grid = max(1, min((rows + per_step * wpc - 1) // (per_step * wpc), sm * per_sm))
+        nwarps = grid * wpc
+        for warp in range(nwarps):
+            for base in range(warp * per_step, rows, nwarps * per_step):
+                for k in range(U):
+                    for lane in range(32):
+                        r = base + k * groups + (lane >> lp)
+                        ls = lane & (P - 1)
+                        if r < rows and ls < need[r]:
+                            assert (r, ls) not in seen
+                            seen.add((r, ls))
+    assert len(seen) == sum(need.values())
+
+
+def test_pitched_work_splits_cover_every_chunk_once():
+    rng = random.Random(2)
+    cases = [(1, 1), (1, 300), (16, 333), (17, 50), (64, 7), (500, 9), (513, 33), (4095, 5),
+             (4096, 5), (4097, 3), (16384, 6)]
+    cases += [(rng.randint(1, 30000), rng.randint(1, 20)) for _ in range(8)]
+    for w, r in cases:
+        for uni in (True, False):
+            for sm, ps in ((152, 3), (1, 1)):
+                _visit_pitched(w, r, sm, ps, uni, ax0=(w * 3) % 16)
+
+
+# ------------------------------------------------ span tiles (short rows)
+
+def make_geo(kind, carry, rdev, n, host_off, dev_src, dev_dst, imgv):
+    host_v = imgv + host_off
+    if kind=='H': anchor = dev_dst if carry else host_v
+    elif kind=='D': anchor = host_v
+    else: anchor = dev_dst if carry else dev_src
+    ax = anchor & 15
+    vin = host_v if kind=='H' else dev_src
+    vw = vin - ax; vr = vw & 15; val = vw - vr
+    g = dict(n=n, ax=ax, vin_al=val, vin_r=vr, vin_lo=vin, vin_hi=vin+n, has_vin=(kind=='H' or rdev),
+             hb0=host_off-ax, hlo=host_off, hhi=host_off+n, nch=(ax+n+15)>>4)
+    return g
+def rows_per_tile(kind, rdev, H, hp, sp, lanes):
+    if H < 2: return 0
+    rt = H
+    if kind=='H' or rdev:
+        pv = hp if kind=='H' else sp
+        room = kVBytes - 62 - 16*lanes
+        if room < 0 or pv == 0: return 0
+        rt = min(rt, room//pv + 1)
+    if kind != 'X':
+        room = (kABytes-32)*8 - 15 - 16*lanes
+        if room < 0 or hp == 0: return 0
+        rt = min(rt, room//hp + 1)
+    return rt if rt >= 2 else 0
+def trial(rng):
+    kind = rng.choice('HDX')  # H htod, D dtoh, X dtod
+    carry = rng.random() < 0.7; rdev = kind != 'H'
+    W = rng.randint(1, 500); H = rng.randint(2, 400); D = rng.choice([1,1,2,3])
+    kmax_bound = (W + 30) >> 4
+    if kmax_bound > 32: return 0
+    hp = W + rng.randint(0, 60); sp = W + rng.randint(0, 60); dp = W + rng.randint(0, 60)
+    if rng.random() < 0.5: dp = (dp + 15)//16*16; sp = (sp+15)//16*16; hp = (hp+15)//16*16
+    hrows = H + rng.randint(0, 3); srows = H + rng.randint(0, 3); drows = H + rng.randint(0, 3)
+    imgv = 0x100000  # 16-aligned base
+    img_n = (D*hrows*hp + 4096 + 127)//128*128
+    host_start = rng.randint(0, 2000) if True else 0
+    if host_start + ((D-1)*hrows + (H-1))*hp + W > img_n: return 0
+    src_buf = 0x4000000 + 256*rng.randint(0, 10)   # allocation shadow (256-aligned)
+    src_size = ((D*srows*sp + 4096)+255)//256*256
+    src_start = src_buf + rng.randint(0, 300)
+    dst_buf = 0x9000000; dst_start = dst_buf + rng.randint(0, 300)
+    # the host's row_chunks: exact when every anchor row has one alignment
+    if kind == 'D' or (kind == 'H' and not carry):
+        a0, pa, ra = imgv + host_start, hp, hrows
+    elif carry:
+        a0, pa, ra = dst_start, dp, drows
+    else:
+        a0, pa, ra = src_start, sp, srows
+    uniform = (H == 1 or pa % 16 == 0) and (D == 1 or (pa*ra) % 16 == 0)
+    kmax = ((a0 & 15) + W + 15) >> 4 if uniform else kmax_bound
+    lp = 0
+    while (1 << lp) < kmax: lp += 1
+    P = 1 << lp
+    rt = rows_per_tile(kind, rdev, H, hp, sp, P)
+    if not rt: return 0
+    tps = (H + rt - 1)//rt; ntiles = tps*D
+    def row(r):
+        z, y = divmod(r, H)
+        return make_geo(kind, carry, rdev, W, host_start + z*hrows*hp + y*hp,
+                        src_start + z*srows*sp + y*sp, dst_start + z*drows*dp + y*dp, imgv)
+    for t in range(ntiles):
+        z = t // tps; y0 = (t - z*tps)*rt; y1 = min(y0 + rt, H)
+        r0, r1 = z*H + y0, z*H + y1
+        g0, g1 = row(r0), row(r1-1)
+        # --- issue
+        vcopy = None; acopy = None
+        if kind == 'H' or g0['has_vin']:
+            vbeg = g0['vin_al']; lo = f16(g0['vin_lo']); hi = min(c16(g1['vin_hi']), vbeg + kVBytes)
+            assert lo >= vbeg
+            if hi > lo:
+                assert (hi - lo) % 16 == 0 and (lo - vbeg) % 16 == 0 and hi - vbeg <= kVBytes
+                vcopy = (lo, hi)
+                # global range inside the input buffer's 16-aligned region
+                if kind == 'H':
+                    assert lo >= imgv and hi <= imgv + img_n
+                else:
+                    assert lo >= src_buf and hi <= src_buf + src_size
+        if kind != 'X':
+            aorig = f16(g0['hb0'] >> 3)
+            q0 = max(g0['hb0'], g0['hlo']); q1 = g1['hhi']
+            if q1 > q0:
+                b0 = f16(q0 >> 3); b1 = min(c16((q1+7) >> 3), aorig + kABytes)
+                assert b0 >= aorig and b0 >= 0 and b1 <= img_n//8 and (b1-b0) % 16 == 0
+                acopy = (b0, b1)
+        # --- consume
+        vbeg = g0['vin_al']; aorig = f16(g0['hb0'] >> 3)
+        for r in range(r0, r1):
+            g = row(r)
+            assert g['nch'] <= P, (g['nch'], P)
+            for c in range(P):
+                if kind == 'H' or g['has_vin']:
+                    k = (g['vin_al'] + 16*c - vbeg) >> 4
+                    assert 0 <= k and (k+2)*16 <= kVBytes, (k, c, P)
+                    # valid bytes of this chunk come from copied bytes
+                    i0 = 16*c - g['ax']
+                    for i in range(max(0, i0), min(W, i0 + 16)):
+                        addr = g['vin_lo'] + i
+                        assert vcopy and vcopy[0] <= addr < vcopy[1], (addr, vcopy)
+                if kind != 'X':
+                    q = g['hb0'] + 16*c
+                    wi = (((q >> 5) << 2) - aorig) >> 2
+                    assert wi >= 0 and (wi+2)*4 <= kABytes, (wi,)
+                    i0 = 16*c - g['ax']
+                    for i in range(max(0, i0), min(W, i0 + 16)):
+                        pos = g['hlo'] + i
+                        assert acopy and acopy[0]*8 <= pos < acopy[1]*8
+    return 1
+
+
+def test_span_tiles_stay_in_bounds_and_cover():
+    rng = random.Random(5)
+    done = sum(trial(rng) for _ in range(600))
+    assert done > 500
+
+
+# ------------------------------------------- A-bits-only super-tiles
+
+def test_a_super_tiles_stay_in_bounds_and_cover():
+    rng = random.Random(3)
+    for _ in range(20000):
+        n = rng.randint(1, 1 << 22)
+        img_n = ((rng.randint(n, n + 10000) + 127) // 128) * 128
+        hlo = rng.randint(0, img_n - n)
+        hhi = hlo + n
+        ax = rng.randint(0, 15)
+        hb0 = hlo - ax
+        nsc = (ax + n + 127) >> 7
+        ntiles = ((nsc + 31) // 32 + kR - 1) // kR
+        t = rng.randint(0, ntiles - 1)
+        c0 = t * kR * 32
+        p0 = hb0 + 128 * c0
+        aorig = f16(p0 >> 3)
+        q0 = max(p0, hlo)
+        q1 = min(p0 + 4096 * kR + 32, hhi)
+        if q1 > q0:
+            b0 = f16(q0 >> 3)
+            b1 = c16((q1 + 7) >> 3)
+            assert b0 >= aorig and b1 - aorig <= kStage and b1 <= img_n // 8 and b0 >= 0
+            for lane in (0, 31):
+                i0 = 128 * c0 - ax + 1024 * lane
+                lo_i, hi_i = max(0, i0), min(n, i0 + 1024)
+                if hi_i > lo_i:
+                    assert b0 * 8 <= hlo + lo_i and hlo + hi_i <= b1 * 8
+        w0 = (p0 - 8 * aorig) >> 5
+        assert (w0 + 1024 + 1) * 4 <= 4112   # the last word read, lane 31's (j = 1023) + 1
