@@ -168,7 +168,11 @@ typedef struct cg_config {
                                    new shape first try the split candidates
                                    16..256 KiB in turn (real runs, timed), then
                                    keep the fastest (see cg_choose_segment) */
-  uint32_t reserved[7];
+  uint32_t batch_direct_launch; /* 1: issue a batch's kernels one by one;
+                                   0 (default): capture them into a CUDA graph
+                                   (updated in place when the next batch has
+                                   the same shape) and launch that */
+  uint32_t reserved[6];
 } cg_config;
 
 typedef struct cg_ctx cg_ctx;

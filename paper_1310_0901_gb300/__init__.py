@@ -88,7 +88,8 @@ class cg_config(ctypes.Structure):
     _fields_ = [("carry", u32), ("strict_device_undef", u32), ("shadow_slab_bytes", u64),
                 ("shadow_budget_bytes", u64), ("scan_ctas_per_sm", u32),
                 ("batch_segment_kib", u32), ("batch_ctas_per_sm", u32),
-                ("scan_engine", u32), ("batch_autotune", u32), ("reserved", u32 * 7)]
+                ("scan_engine", u32), ("batch_autotune", u32), ("batch_direct_launch", u32),
+                ("reserved", u32 * 6)]
 
 
 class cg_stats(ctypes.Structure):

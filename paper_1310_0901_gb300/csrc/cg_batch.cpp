@@ -382,29 +382,70 @@ cg_status batch_submit(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t r
   if (!K.done) CG_CUDA(cudaEventCreateWithFlags(&K.done, cudaEventDisableTiming));
   if (!K.t0) CG_CUDA(cudaEventCreate(&K.t0));
   if (!K.t1) CG_CUDA(cudaEventCreate(&K.t1));
-  CG_CUDA(cudaEventRecord(K.t0, st));
-  CG_TRY(batch_levels(c, K, B, ~0u, st));
-  CG_CUDA(cudaEventRecord(K.t1, st));
   K.nreq = nreq;
   K.nlev = B.nlev;
   K.nblocks = (nreq + kFinalizeItems - 1) / kFinalizeItems;
   CG_TRY(K.b_blocksums.ensure(K.nblocks + 1));
   K.dev_rec_cap = std::min<uint64_t>(rec_cap, nreq * CG_NFLAGS);
   CG_TRY(K.b_recs.ensure(std::max<uint64_t>(K.dev_rec_cap, 1)));
-  const int strict = (int)c->cfg.strict_device_undef;
-  CG_CUDA(launch_finalize(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
-  CG_CUDA(launch_scan_block_sums(K.b_blocksums.p, K.nblocks, nullptr, st));
-  CG_CUDA(launch_emit_records(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems,
-                              strict, K.b_recs.p, K.dev_rec_cap, st));
-  c->stats.kernels += K.dev_rec_cap ? 3 : 2;
   CG_TRY(K.h_total.ensure(2));
   CG_TRY(K.h_reps.ensure(nreq));
+  // the batch's device work: on `st` directly, or captured on the context's
+  // capture stream into a CUDA graph that is then launched on `st`
+  const bool graph = !c->cfg.batch_direct_launch;
+  if (graph && !c->cap) CG_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  cudaStream_t es = graph ? c->cap : st;
+  struct Capture {  // ends a capture left open by an error
+    cudaStream_t s = nullptr;
+    ~Capture() {
+      if (!s) return;
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  } open_capture;
+  if (graph) {
+    CG_CUDA(cudaStreamBeginCapture(es, cudaStreamCaptureModeRelaxed));
+    open_capture.s = es;
+  } else {
+    CG_CUDA(cudaEventRecord(K.t0, st));
+  }
+  CG_TRY(batch_levels(c, K, B, ~0u, es));
+  if (!graph) CG_CUDA(cudaEventRecord(K.t1, st));
+  const int strict = (int)c->cfg.strict_device_undef;
+  CG_CUDA(launch_finalize(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, es));
+  CG_CUDA(launch_scan_block_sums(K.b_blocksums.p, K.nblocks, nullptr, es));
+  CG_CUDA(launch_emit_records(B.plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems,
+                              strict, K.b_recs.p, K.dev_rec_cap, es));
+  c->stats.kernels += K.dev_rec_cap ? 3 : 2;
   CG_CUDA(cudaMemcpyAsync(K.h_total.p, K.b_blocksums.p + K.nblocks, 8, cudaMemcpyDeviceToHost,
-                          st));
+                          es));
   CG_CUDA(cudaMemcpyAsync(K.h_total.p + 1, K.b_err.p, sizeof(unsigned int),
-                          cudaMemcpyDeviceToHost, st));
+                          cudaMemcpyDeviceToHost, es));
   CG_CUDA(cudaMemcpyAsync(K.h_reps.p, K.b_reps.p, nreq * sizeof(cg_report),
-                          cudaMemcpyDeviceToHost, st));
+                          cudaMemcpyDeviceToHost, es));
+  if (graph) {
+    cudaGraph_t g = nullptr;
+    open_capture.s = nullptr;
+    CG_CUDA(cudaStreamEndCapture(es, &g));
+    cudaError_t e = cudaErrorUnknown;
+    if (K.exec) {  // same shape as this slot's last batch: update in place
+      cudaGraphExecUpdateResultInfo info{};
+      e = cudaGraphExecUpdate(K.exec, g, &info);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(K.exec);
+        K.exec = nullptr;
+      }
+    }
+    if (!K.exec) e = cudaGraphInstantiate(&K.exec, g, 0);
+    cudaGraphDestroy(g);
+    CG_CUDA(e);
+    CG_CUDA(cudaEventRecord(K.t0, st));
+    CG_CUDA(cudaGraphLaunch(K.exec, st));
+    CG_CUDA(cudaEventRecord(K.t1, st));
+  }
   CG_CUDA(cudaEventRecord(K.done, st));
   K.ticket = c->next_ticket++;
   *slot_out = slot;

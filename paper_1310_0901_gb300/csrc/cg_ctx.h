@@ -466,6 +466,7 @@ struct BatchBufs {
   uint64_t ticket = 0;        // 0: free
   cudaEvent_t done = nullptr;  // recorded after its results' copies
   cudaEvent_t t0 = nullptr, t1 = nullptr;  // around its level kernels
+  cudaGraphExec_t exec = nullptr;           // the batch's kernels as a CUDA graph
   uint64_t nreq = 0, nblocks = 0, dev_rec_cap = 0, t_begin = 0;
   int nlev = 0;
   int online_slot = -1;
@@ -491,6 +492,8 @@ struct BatchBufs {
     h_reps.release();
     h_recs.release();
     h_total.release();
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
     if (done) cudaEventDestroy(done);
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
@@ -526,6 +529,7 @@ struct cg_ctx {
   // before it still runs (slot 0 also serves the synchronous paths)
   cgi::BatchBufs bb[2];
   cudaStream_t side = nullptr;  // lookups of batches submitted asynchronously
+  cudaStream_t cap = nullptr;   // where a batch's kernels are captured into a graph
   uint64_t next_ticket = 1;
   // batch split choice: tuned entries (features -> segment KiB) and the
   // learned cost model's weights (empty = none)

@@ -277,6 +277,7 @@ cg_status cg_destroy(cg_ctx *c) {
   c->bb[0].release();
   c->bb[1].release();
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->cap) cudaStreamDestroy(c->cap);
   c->arena.release_all();
   delete c;
   return CG_OK;

@@ -22,12 +22,16 @@ def cg():
     return m
 
 
-@pytest.mark.parametrize("seed,engine", [(0, 0), (1, 1)])
-def test_pipelined_batches_equal_sequential(cg, seed, engine):
+@pytest.mark.parametrize("seed,engine,direct", [(0, 0, 0), (1, 1, 0), (2, 0, 1)])
+def test_pipelined_batches_equal_sequential(cg, seed, engine, direct):
+    """direct = 0: every batch's kernels run as a CUDA graph (updated in place
+    for batches of the same shape); 1: launched one by one."""
     w = S.small(seed)
     parts = np.array_split(w.reqs, 6)
-    ctx_a, orc, (a_a, v_a) = U.make_pair(w.image, w.table, scan_engine=engine)
-    ctx_b, _, (a_b, v_b) = U.make_pair(w.image, w.table, scan_engine=engine)
+    ctx_a, orc, (a_a, v_a) = U.make_pair(w.image, w.table, scan_engine=engine,
+                                         batch_direct_launch=direct)
+    ctx_b, _, (a_b, v_b) = U.make_pair(w.image, w.table, scan_engine=engine,
+                                       batch_direct_launch=1 - direct)
     pending = []
     got = []
     for p in parts:
