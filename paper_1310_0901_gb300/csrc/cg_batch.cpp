@@ -259,13 +259,12 @@ constexpr float kClose = 0.5f;
 
 // Segment size for a batch when the configuration leaves it open: a tuned
 // entry close to this batch's features; else, with online tuning on, the
-// next trial for this shape (*online_slot set); else the learned model's
-// argmin over the candidates; else 64 KiB.
-uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_t *source,
-                    int *online_slot) {
+// next untried candidate for this shape (*source = 4: a trial, recorded when
+// the batch finishes); else the learned model's argmin over the candidates;
+// else 64 KiB.
+uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_t *source) {
   float f[CG_NFEAT];
   features(reqs, nreq, f);
-  if (online_slot) *online_slot = -1;
   float best_d = kClose;
   int best = -1;
   for (size_t e = 0; e < c->tuned_feat.size(); e++) {
@@ -289,8 +288,7 @@ uint32_t choose_kib(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint32_
         slot = (int)e;
       }
     }
-    const uint32_t next = slot >= 0 ? c->online[slot].next : 0;
-    if (online_slot) *online_slot = slot;  // -1: a new shape (an entry is made on use)
+    const uint32_t next = slot >= 0 ? c->online[slot].next : 0;  // a new shape: the first
     if (source) *source = 4;
     return kOnlineKib[next < kNumOnline ? next : 0];
   }
@@ -371,9 +369,8 @@ cg_status batch_submit(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, uint64_t r
   BatchRun B;
   CG_TRY(batch_prepare(c, K, reqs, nreq, st, look, B));
   K.source = 3;
-  K.online_slot = -1;
   K.kib = c->cfg.batch_segment_kib ? c->cfg.batch_segment_kib
-                                   : choose_kib(c, reqs, nreq, &K.source, &K.online_slot);
+                                   : choose_kib(c, reqs, nreq, &K.source);
   if (K.source == 4) {
     K.feat.resize(CG_NFEAT);
     features(reqs, nreq, K.feat.data());
@@ -504,7 +501,6 @@ cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_repor
   if (!c || (nreq && !reqs) || !n_rec || (rec_cap && !recs))
     return set_error(CG_E_ARG, "NULL argument");
   if (nreq == 0) {
-    for (uint64_t i = 0; i < nreq; i++) CG_TRY(validate(c, reqs[i]));
     *n_rec = 0;
     return CG_OK;
   }
@@ -618,7 +614,7 @@ cg_status cg_choose_segment(const cg_ctx *c, const cg_copy *reqs, uint64_t nreq,
     if (source) *source = 3;
     return CG_OK;
   }
-  *seg_kib = choose_kib(c, reqs, nreq, source, nullptr);
+  *seg_kib = choose_kib(c, reqs, nreq, source);
   return CG_OK;
 }
 

@@ -469,7 +469,6 @@ struct BatchBufs {
   cudaGraphExec_t exec = nullptr;           // the batch's kernels as a CUDA graph
   uint64_t nreq = 0, nblocks = 0, dev_rec_cap = 0, t_begin = 0;
   int nlev = 0;
-  int online_slot = -1;
   uint32_t source = 0, kib = 0;
   std::vector<float> feat;    // features, kept for an online trial's record
   void release() {
