@@ -543,9 +543,12 @@ struct cg_ctx {
     float best_ms = 0.f;
   };
   std::vector<OnlineTune> online;
-  // kernel-argument checks: the arguments, fill spans and their groups
-  cgi::DevBuf<cg_karg> k_args;
-  cgi::DevBuf<uint64_t> k_fill;  // ptr[n], bytes[n], first group[n]
+  // kernel-argument checks: one upload (arguments | order | scan segments |
+  // fill groups) then the fill spans the lookup writes; one read-back
+  // (reports | error flag)
+  cgi::DevBuf<uint8_t> k_in;
+  cgi::DevBuf<uint8_t> k_out;
+  cgi::PinBuf<uint8_t> h_kin, h_kout;
   // device arrays (Fig. 2's second list): handle -> dimensions and shadow
   struct ArrayInfo {
     uint64_t w, h, d;

@@ -103,23 +103,24 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CG_TRY(flush_fills(c, st));
   CG_TRY(ensure_device_table(c, st));
-  CG_TRY(c->k_args.ensure(nargs));
-  CG_TRY(c->k_fill.ensure(3 * nargs));
-  CG_TRY(K.b_order.ensure(nargs));
-  CG_TRY(K.b_segfirst.ensure(nargs));
   CG_TRY(K.b_jobs.ensure(nargs));
   CG_TRY(K.b_info.ensure(nargs));
   CG_TRY(K.b_acc.ensure(nargs));
-  CG_TRY(K.b_reps.ensure(nargs));
   CG_TRY(K.b_counts.ensure(nargs));
-  CG_TRY(K.b_err.ensure(1));
   const uint64_t nblocks = (nargs + kFinalizeItems - 1) / kFinalizeItems;
   CG_TRY(K.b_blocksums.ensure(nblocks + 1));
-  // pinned staging: arguments | order | scan segments | fill groups
+  // upload layout: arguments | order | scan segments | fill groups, then the
+  // fill spans (pointer, bytes) the lookup writes on the device
   const uint64_t a_bytes = round_up(nargs * sizeof(cg_karg), 16);
   const uint64_t o_bytes = round_up(nargs * 4, 16);
-  CG_TRY(K.h_stage_in.ensure(a_bytes + o_bytes + 16 * nargs + 64));
-  uint8_t *hp = K.h_stage_in.p;
+  const uint64_t up = a_bytes + o_bytes + 16 * nargs;
+  CG_TRY(c->k_in.ensure(up + 16 * nargs));
+  CG_TRY(c->h_kin.ensure(up));
+  // read-back layout: reports | error flag
+  const uint64_t r_bytes = round_up(nargs * sizeof(cg_report), 16);
+  CG_TRY(c->k_out.ensure(r_bytes + 16));
+  CG_TRY(c->h_kout.ensure(r_bytes + 16));
+  uint8_t *hp = c->h_kin.p;
   std::memcpy(hp, args, nargs * sizeof(cg_karg));
   uint32_t *h_order = reinterpret_cast<uint32_t *>(hp + a_bytes);
   uint64_t *h_seg = reinterpret_cast<uint64_t *>(hp + a_bytes + o_bytes);
@@ -137,16 +138,19 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
     if ((args[i].access & CG_ARG_READ) && n) segs += (((n + 30) >> 4) + seg_chunks - 1) / seg_chunks;
     if (args[i].access & CG_ARG_WRITE) fgroups += fill_span_groups(n);
   }
-  uint64_t *fill_ptr = c->k_fill.p, *fill_n = c->k_fill.p + nargs, *fill_seg = c->k_fill.p + 2 * nargs;
-  CG_CUDA(cudaMemcpyAsync(c->k_args.p, hp, nargs * sizeof(cg_karg), cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(K.b_order.p, h_order, nargs * 4, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(K.b_segfirst.p, h_seg, nargs * 8, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemcpyAsync(fill_seg, h_fseg, nargs * 8, cudaMemcpyHostToDevice, st));
-  CG_CUDA(cudaMemsetAsync(K.b_err.p, 0, sizeof(unsigned int), st));
+  uint8_t *dp = c->k_in.p;
+  const cg_karg *d_args = reinterpret_cast<const cg_karg *>(dp);
+  uint32_t *d_order = reinterpret_cast<uint32_t *>(dp + a_bytes);
+  uint64_t *d_seg = reinterpret_cast<uint64_t *>(dp + a_bytes + o_bytes);
+  uint64_t *fill_seg = d_seg + nargs;
+  uint64_t *fill_ptr = fill_seg + nargs, *fill_n = fill_ptr + nargs;
+  cg_report *d_reps = reinterpret_cast<cg_report *>(c->k_out.p);
+  unsigned int *d_err = reinterpret_cast<unsigned int *>(c->k_out.p + r_bytes);
+  CG_CUDA(cudaMemcpyAsync(dp, hp, up, cudaMemcpyHostToDevice, st));
   BatchPlan plan{};
   plan.reqs = nullptr;  // only the lookup reads copies; the argument lookup has its own
-  plan.order = K.b_order.p;
-  plan.seg_first = K.b_segfirst.p;
+  plan.order = d_order;
+  plan.seg_first = d_seg;
   plan.stage = nullptr;
   plan.jobs = K.b_jobs.p;
   plan.info = K.b_info.p;
@@ -155,32 +159,28 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   plan.seg_chunks = (uint32_t)seg_chunks;
   plan.mode_mask = ~0u;
   DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
-  CG_CUDA(launch_karg_lookup(dt, plan, c->k_args.p, fill_ptr, fill_n, (int)c->cfg.carry, st));
+  CG_CUDA(launch_karg_lookup(dt, plan, d_args, fill_ptr, fill_n, (int)c->cfg.carry, d_err, st));
   c->stats.kernels++;
   if (segs) {
     if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, K.b_err.p, st));
+      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, d_err, st));
     else
       CG_CUDA(launch_scan_level(c->img, plan, 0, nargs, segs, c->sm_count * 8, st));
     c->stats.kernels++;
   }
-  CG_CUDA(launch_finalize(plan, K.b_reps.p, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_finalize(plan, d_reps, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
   c->stats.kernels++;
   if (fgroups) {  // after the scans on the same stream: reads see the state before the launch
     CG_CUDA(launch_fill_spans(fill_ptr, fill_n, fill_seg, nargs, fgroups, 0x00, c->sm_count, st));
     c->stats.kernels++;
   }
-  CG_TRY(K.h_total.ensure(2));
-  CG_TRY(K.h_reps.ensure(nargs));
-  CG_CUDA(cudaMemcpyAsync(K.h_total.p + 1, K.b_err.p, sizeof(unsigned int),
-                          cudaMemcpyDeviceToHost, st));
-  CG_CUDA(cudaMemcpyAsync(K.h_reps.p, K.b_reps.p, nargs * sizeof(cg_report),
-                          cudaMemcpyDeviceToHost, st));
+  CG_CUDA(cudaMemcpyAsync(c->h_kout.p, c->k_out.p, r_bytes + 16, cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
-  if (reinterpret_cast<const unsigned int *>(K.h_total.p + 1)[0])
+  if (reinterpret_cast<const unsigned int *>(c->h_kout.p + r_bytes)[0])
     return set_error(CG_E_TIMEOUT, "a bounded wait in the scan kernel ran out");
-  if (reps) std::memcpy(reps, K.h_reps.p, nargs * sizeof(cg_report));
-  for (uint64_t i = 0; i < nargs; i++) count_stats(c, K.h_reps.p[i]);
+  const cg_report *h_reps = reinterpret_cast<const cg_report *>(c->h_kout.p);
+  if (reps) std::memcpy(reps, h_reps, nargs * sizeof(cg_report));
+  for (uint64_t i = 0; i < nargs; i++) count_stats(c, h_reps[i]);
   return CG_OK;
 }
 

@@ -136,8 +136,9 @@ cudaError_t launch_fill_spans(const uint64_t *ptr, const uint64_t *n, const uint
 __global__ void __launch_bounds__(256) karg_lookup_kernel(DevTable t, BatchPlan p,
                                                           const cg_karg *args, uint64_t *fill_ptr,
                                                           uint64_t *fill_n, uint32_t stride,
-                                                          int carry_on) {
+                                                          int carry_on, unsigned int *err) {
   extern __shared__ uint64_t spl[];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;  // the scan after this may set it
   const uint64_t nspl = (t.count + stride - 1) / stride;
   for (uint64_t k = threadIdx.x; k < nspl; k += blockDim.x) spl[k] = __ldg(t.base + k * stride);
   __syncthreads();
@@ -181,7 +182,8 @@ __global__ void __launch_bounds__(256) karg_lookup_kernel(DevTable t, BatchPlan 
 }
 
 cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_karg *args,
-                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, cudaStream_t st) {
+                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, unsigned int *err,
+                               cudaStream_t st) {
   if (p.nreq == 0) return cudaSuccess;
   uint32_t stride = 256;
   while ((t.count + stride - 1) / stride > 6144) stride <<= 1;
@@ -190,7 +192,7 @@ cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_k
   uint64_t blocks = (p.nreq + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   karg_lookup_kernel<<<(unsigned)blocks, 256, smem, st>>>(t, p, args, fill_ptr, fill_n, stride,
-                                                          carry);
+                                                          carry, err);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,8 @@ cudaError_t launch_fill_spans(const uint64_t *ptr, const uint64_t *n, const uint
                               uint64_t count, uint64_t nsegs, uint8_t value, int sm_count,
                               cudaStream_t st);
 cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_karg *args,
-                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, cudaStream_t st);
+                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, unsigned int *err,
+                               cudaStream_t st);
 
 
 }  // namespace cgi
