@@ -496,6 +496,17 @@ cg_status cg_mlp_grad(const float *x, const float *t, uint32_t n, uint32_t hidde
 cg_status cg_choose_segment(const cg_ctx *ctx, const cg_copy *reqs, uint64_t nreq,
                             uint32_t *seg_kib, uint32_t *source);
 
+/* The tuned split entries the context holds (batch features -> segment
+ * KiB, from cg_tune_batch with CG_TUNE_REMEMBER or finished online trials),
+ * for saving: up to cap entries into feat (cap * CG_NFEAT floats) and kib
+ * (host); *count gets how many there are. */
+cg_status cg_get_tuned(const cg_ctx *ctx, float *feat, uint32_t *kib, uint32_t cap,
+                       uint32_t *count);
+
+/* Add tuned entries (e.g. saved from an earlier run): count entries of
+ * CG_NFEAT features and a segment size in KiB (> 0) each. */
+cg_status cg_add_tuned(cg_ctx *ctx, const float *feat, const uint32_t *kib, uint32_t count);
+
 /* --------------------------------------------------------------- serving */
 
 /* A serving loop in the context: client threads submit requests into

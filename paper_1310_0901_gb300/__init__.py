@@ -164,6 +164,8 @@ SIGNATURES = [
     ("cg_check_batch_async", i32, [vp, vp, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                    vp]),
     ("cg_batch_wait", i32, [vp, u64, vp, vp, u64, ctypes.POINTER(u64)]),
+    ("cg_get_tuned", i32, [vp, vp, vp, u32, ctypes.POINTER(u32)]),
+    ("cg_add_tuned", i32, [vp, vp, vp, u32]),
     ("cg_inject_fault", i32, [vp, u32]),
     ("cg_snapshot", i32, [vp, ctypes.c_char_p]),
     ("cg_restore", i32, [vp, ctypes.c_char_p]),
@@ -426,6 +428,32 @@ class Context:
             return
         w = np.ascontiguousarray(weights, dtype=np.float32)
         check(cg_set_cost_model(self._h, w.ctypes.data, hidden), "cg_set_cost_model")
+
+    def save_tuning(self, path: str) -> int:
+        """Write the tuned split entries to a JSON file; returns how many."""
+        import json
+        n = u32(0)
+        check(cg_get_tuned(self._h, None, None, 0, ctypes.byref(n)), "cg_get_tuned")
+        k = n.value
+        feat = np.zeros((max(1, k), NFEAT), dtype=np.float32)
+        kib = np.zeros(max(1, k), dtype=np.uint32)
+        check(cg_get_tuned(self._h, feat.ctypes.data, kib.ctypes.data, k, ctypes.byref(n)),
+              "cg_get_tuned")
+        with open(path, "w") as f:
+            json.dump({"nfeat": NFEAT, "features": feat[:k].tolist(),
+                       "segment_kib": kib[:k].tolist()}, f)
+        return k
+
+    def load_tuning(self, path: str) -> int:
+        """Add the tuned split entries of a JSON file written by save_tuning."""
+        import json
+        d = json.load(open(path))
+        if d["nfeat"] != NFEAT:
+            raise ValueError(f"tuning file has {d['nfeat']} features, libcg uses {NFEAT}")
+        feat = np.ascontiguousarray(d["features"], dtype=np.float32).reshape(-1, NFEAT)
+        kib = np.ascontiguousarray(d["segment_kib"], dtype=np.uint32)
+        check(cg_add_tuned(self._h, feat.ctypes.data, kib.ctypes.data, len(kib)), "cg_add_tuned")
+        return len(kib)
 
     def choose_segment(self, reqs: np.ndarray) -> tuple[int, int]:
         reqs = np.ascontiguousarray(reqs)

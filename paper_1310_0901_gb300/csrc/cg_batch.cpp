@@ -494,6 +494,29 @@ cg_status batch_finish(cg_ctx *c, int slot, cg_report *reps, cg_err_record *recs
 
 extern "C" {
 
+cg_status cg_get_tuned(const cg_ctx *c, float *feat, uint32_t *kib, uint32_t cap,
+                       uint32_t *count) {
+  if (!c || !count || (cap && (!feat || !kib))) return set_error(CG_E_ARG, "NULL argument");
+  const uint32_t n = (uint32_t)c->tuned_kib.size();
+  for (uint32_t e = 0; e < n && e < cap; e++) {
+    std::memcpy(feat + (size_t)e * CG_NFEAT, c->tuned_feat[e].data(), CG_NFEAT * sizeof(float));
+    kib[e] = c->tuned_kib[e];
+  }
+  *count = n;
+  return CG_OK;
+}
+
+cg_status cg_add_tuned(cg_ctx *c, const float *feat, const uint32_t *kib, uint32_t count) {
+  if (!c || (count && (!feat || !kib))) return set_error(CG_E_ARG, "NULL argument");
+  for (uint32_t e = 0; e < count; e++)
+    if (kib[e] == 0) return set_error(CG_E_ARG, "segment size 0");
+  for (uint32_t e = 0; e < count; e++) {
+    c->tuned_feat.emplace_back(feat + (size_t)e * CG_NFEAT, feat + (size_t)(e + 1) * CG_NFEAT);
+    c->tuned_kib.push_back(kib[e]);
+  }
+  return CG_OK;
+}
+
 cg_status cg_check_batch(cg_ctx *c, const cg_copy *reqs, uint64_t nreq, cg_report *reps,
                          cg_err_record *recs, uint64_t rec_cap, uint64_t *n_rec,
                          uint64_t *bad_index, void *stream) {

@@ -98,3 +98,25 @@ def test_online_autotune_tries_then_keeps_fastest(cg):
     assert trials == [16, 32, 64, 128, 256]
     assert seen[5][1] == 1 and seen[6] == seen[5] and seen[5][0] in trials
     U.assert_same_state(ctx, orc, v, w.table)
+
+
+def test_tuned_entries_survive_save_and_load(cg, tmp_path):
+    """Tuned split entries written to JSON and loaded into a fresh context
+    choose the same segment size (source 1) for the same batch."""
+    import json
+    w = S.small(7)
+    ctx, _, _ = U.make_pair(w.image, w.table)
+    best, _ = ctx.tune_batch(w.reqs, repeats=1)
+    assert ctx.choose_segment(w.reqs) == (best, 1)
+    path = str(tmp_path / "tuned.json")
+    assert ctx.save_tuning(path) == 1
+    d = json.load(open(path))
+    assert d["nfeat"] == cg.NFEAT and d["segment_kib"] == [best]
+    ctx2, _, _ = U.make_pair(w.image, w.table)
+    assert ctx2.choose_segment(w.reqs)[1] != 1
+    assert ctx2.load_tuning(path) == 1
+    assert ctx2.choose_segment(w.reqs) == (best, 1)
+    d["segment_kib"] = [0]
+    json.dump(d, open(path, "w"))
+    with pytest.raises(cg.CgError):
+        cg.Context().load_tuning(path)
