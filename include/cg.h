@@ -189,6 +189,8 @@ typedef struct cg_stats {
   uint64_t batch_ns;      /* wall time inside cg_check_batch */
   uint64_t batch_plan_ns; /* of which: host dependency planning */
   uint64_t batch_lookup_ns; /* of which: device lookup incl. its read-back */
+  uint64_t table_uploads;   /* whole-table uploads of the device copy */
+  uint64_t table_merges;    /* incremental device updates (merge kernel) */
 } cg_stats;
 
 /* ------------------------------------------------------------- lifetime */
@@ -704,6 +706,14 @@ cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry,
                          const uint8_t *modes, int32_t *level, uint32_t *n_levels);
 
 cg_status cg_get_stats(const cg_ctx *ctx, cg_stats *out);
+
+/* The allocation table as the device copy holds it, brought up to date
+ * first (an incremental merge on the device, or a whole upload): up to cap
+ * entries into base, size and shadow (host arrays, shadow may be NULL) in
+ * base order; *count gets the number of live entries.  Synchronises
+ * `stream`.  Not allowed while serving or with batches in flight. */
+cg_status cg_device_table(cg_ctx *ctx, uint64_t *base, uint64_t *size, uint64_t *shadow,
+                          uint64_t cap, uint64_t *count, void *stream);
 
 /* Text for a report, e.g. for a device->host overrun:
  *   "device->host copy of 8000000 bytes overruns its source allocation:

@@ -96,7 +96,7 @@ class cg_stats(ctypes.Structure):
     _fields_ = [("checks", u64), ("bytes_checked", u64), ("batches", u64), ("levels", u64),
                 ("kernels", u64), ("errors", u64 * 9), ("live_allocs", u64),
                 ("shadow_bytes", u64), ("batch_ns", u64), ("batch_plan_ns", u64),
-                ("batch_lookup_ns", u64)]
+                ("batch_lookup_ns", u64), ("table_uploads", u64), ("table_merges", u64)]
 
 
 class cg_request(ctypes.Structure):
@@ -185,6 +185,7 @@ SIGNATURES = [
     ("cg_choose_segment", i32, [vp, vp, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]),
     ("cg_plan_levels", i32, [vp, u64, u32, vp, vp, ctypes.POINTER(u32)]),
     ("cg_get_stats", i32, [vp, ctypes.POINTER(cg_stats)]),
+    ("cg_device_table", i32, [vp, vp, vp, vp, u64, ctypes.POINTER(u64), vp]),
     ("cg_format_report", i32, [ctypes.POINTER(cg_report), u32, ctypes.c_char_p, ctypes.c_size_t]),
     ("cg_last_error", ctypes.c_char_p, []),
     ("cg_version", ctypes.c_char_p, []),
@@ -497,6 +498,17 @@ class Context:
         s = cg_serve_stats()
         check(cg_serve_stop(self._h, ctypes.byref(s)), "cg_serve_stop")
         return {f: getattr(s, f) for f, _ in cg_serve_stats._fields_}
+
+    def device_table(self, stream=None) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(base, size, shadow) of the device copy of the allocation table."""
+        n = u64(0)
+        check(cg_device_table(self._h, None, None, None, 0, ctypes.byref(n),
+                              _stream_handle(stream)), "cg_device_table")
+        k = n.value
+        out = [np.zeros(max(1, k), dtype=np.uint64) for _ in range(3)]
+        check(cg_device_table(self._h, out[0].ctypes.data, out[1].ctypes.data, out[2].ctypes.data,
+                              k, ctypes.byref(n), _stream_handle(stream)), "cg_device_table")
+        return tuple(a[:k] for a in out)
 
     def stats(self) -> dict:
         s = cg_stats()

@@ -204,7 +204,9 @@ class AllocTable {
   std::set<uint64_t> freed;
   uint64_t dead = 0;
   uint64_t live = 0;
-  uint64_t version = 0;
+  uint64_t version = 0;       // any change
+  uint64_t main_version = 0;  // changes of the main array's order (merges)
+  std::vector<uint64_t> dead_idx;  // main indices tombstoned since the last merge
 
   struct Hit {
     bool ok;
@@ -261,6 +263,7 @@ class AllocTable {
         *sh = shadow[j];
         size[j] = 0;
         dead++;
+        dead_idx.push_back(j);
         goto removed;
       }
     }
@@ -305,6 +308,8 @@ class AllocTable {
     shadow.swap(nh);
     delta.clear();
     dead = 0;
+    dead_idx.clear();
+    main_version++;
   }
 };
 
@@ -523,7 +528,13 @@ struct cg_ctx {
   cgi::PinBuf<uint64_t> h_fill;
   cgi::DevBuf<uint64_t> t_base, t_size, t_shadow;
   uint64_t t_version = ~0ull;
+  uint64_t t_main = ~0ull;  // table.main_version the device copy equals
   uint64_t t_count = 0;
+  // incremental updates: the merge kernel writes the other buffer set from
+  // the uploaded registrations and dead indices (t_delta, staged in h_tdelta)
+  cgi::DevBuf<uint64_t> t_base2, t_size2, t_shadow2, t_delta;
+  cgi::PinBuf<uint64_t> h_tdelta;
+  cudaEvent_t t_ev = nullptr;  // the last table update's copies and merge
   // batch buffers: two slots, so that a batch can be planned while the one
   // before it still runs (slot 0 also serves the synchronous paths)
   cgi::BatchBufs bb[2];

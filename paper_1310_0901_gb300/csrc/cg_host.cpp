@@ -158,10 +158,59 @@ cg_status cgi::flush_fills(cg_ctx *c, cudaStream_t st) {
   return CG_OK;
 }
 
+// Bring the device copy of the table up to date.  When the device holds
+// the host's main array as of its last merge, only the registrations and
+// the dead indices since then are uploaded, and the merge kernel builds the
+// new table on the device, in the order the host merge gives; otherwise
+// the whole table is uploaded.
 cg_status cgi::ensure_device_table(cg_ctx *c, cudaStream_t st) {
   AllocTable &t = c->table;
-  if (!t.delta.empty() || t.dead) t.merge();
-  if (c->t_version == t.version && c->t_count == t.base.size()) return CG_OK;
+  const bool pending = !t.delta.empty() || t.dead;
+  if (pending && c->t_main == t.main_version && c->t_count == t.base.size() && c->t_count) {
+    const uint64_t m = t.delta.size(), d = t.dead_idx.size();
+    const uint64_t n_new = c->t_count - d + m;
+    CG_TRY(c->t_base2.ensure(n_new));
+    CG_TRY(c->t_size2.ensure(n_new));
+    CG_TRY(c->t_shadow2.ensure(n_new));
+    CG_TRY(c->t_delta.ensure(3 * m + d));
+    if (!c->t_ev) CG_CUDA(cudaEventCreateWithFlags(&c->t_ev, cudaEventDisableTiming));
+    CG_CUDA(cudaEventSynchronize(c->t_ev));  // the staging buffer's last copy is done
+    CG_TRY(c->h_tdelta.ensure(3 * m + d));
+    uint64_t *h = c->h_tdelta.p;
+    uint64_t k = 0;
+    for (const auto &e : t.delta) {
+      h[k] = e.first;
+      h[m + k] = e.second.first;
+      h[2 * m + k] = e.second.second;
+      k++;
+    }
+    std::copy(t.dead_idx.begin(), t.dead_idx.end(), h + 3 * m);
+    std::sort(h + 3 * m, h + 3 * m + d);
+    if (3 * m + d)
+      CG_CUDA(cudaMemcpyAsync(c->t_delta.p, h, (3 * m + d) * 8, cudaMemcpyHostToDevice, st));
+    const uint64_t *dd = c->t_delta.p;
+    DevTable old{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
+    CG_CUDA(launch_table_merge(old, dd, dd + m, dd + 2 * m, m, dd + 3 * m, d, c->t_base2.p,
+                               c->t_size2.p, c->t_shadow2.p, c->sm_count, st));
+    CG_CUDA(cudaEventRecord(c->t_ev, st));
+    c->stats.kernels++;
+    c->stats.table_merges++;
+    std::swap(c->t_base.p, c->t_base2.p);
+    std::swap(c->t_base.cap, c->t_base2.cap);
+    std::swap(c->t_size.p, c->t_size2.p);
+    std::swap(c->t_size.cap, c->t_size2.cap);
+    std::swap(c->t_shadow.p, c->t_shadow2.p);
+    std::swap(c->t_shadow.cap, c->t_shadow2.cap);
+    t.merge();
+    c->t_main = t.main_version;
+    c->t_version = t.version;
+    c->t_count = n_new;
+    return CG_OK;
+  }
+  if (pending) t.merge();
+  if (c->t_version == t.version && c->t_main == t.main_version && c->t_count == t.base.size())
+    return CG_OK;
+  if (c->t_ev) CG_CUDA(cudaEventSynchronize(c->t_ev));  // a merge may still write t_base
   const uint64_t n = t.base.size();
   CG_TRY(c->t_base.ensure(n));
   CG_TRY(c->t_size.ensure(n));
@@ -173,7 +222,9 @@ cg_status cgi::ensure_device_table(cg_ctx *c, cudaStream_t st) {
     CG_CUDA(cudaStreamSynchronize(st));  // host vectors may change after return
   }
   c->t_version = t.version;
+  c->t_main = t.main_version;
   c->t_count = n;
+  c->stats.table_uploads++;
   return CG_OK;
 }
 
@@ -274,6 +325,12 @@ cg_status cg_destroy(cg_ctx *c) {
   c->t_base.release();
   c->t_size.release();
   c->t_shadow.release();
+  c->t_base2.release();
+  c->t_size2.release();
+  c->t_shadow2.release();
+  c->t_delta.release();
+  c->h_tdelta.release();
+  if (c->t_ev) cudaEventDestroy(c->t_ev);
   c->bb[0].release();
   c->bb[1].release();
   c->k_in.release();
@@ -588,6 +645,25 @@ cg_status cg_get_stats(const cg_ctx *c, cg_stats *out) {
   *out = c->stats;
   out->live_allocs = c->table.live;
   out->shadow_bytes = c->arena.held;
+  return CG_OK;
+}
+
+cg_status cg_device_table(cg_ctx *c, uint64_t *base, uint64_t *size, uint64_t *shadow,
+                          uint64_t cap, uint64_t *count, void *stream) {
+  if (c && c->serve) return set_error(CG_E_STATE, "not allowed while serving");
+  if (!c || !count || (cap && (!base || !size))) return set_error(CG_E_ARG, "NULL argument");
+  if (c->bb[0].ticket || c->bb[1].ticket)
+    return set_error(CG_E_STATE, "batches still in flight (cg_batch_wait first)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CG_TRY(ensure_device_table(c, st));
+  const uint64_t k = std::min<uint64_t>(cap, c->t_count);
+  if (k) {
+    CG_CUDA(cudaMemcpyAsync(base, c->t_base.p, k * 8, cudaMemcpyDeviceToHost, st));
+    CG_CUDA(cudaMemcpyAsync(size, c->t_size.p, k * 8, cudaMemcpyDeviceToHost, st));
+    if (shadow) CG_CUDA(cudaMemcpyAsync(shadow, c->t_shadow.p, k * 8, cudaMemcpyDeviceToHost, st));
+  }
+  CG_CUDA(cudaStreamSynchronize(st));
+  *count = c->t_count;
   return CG_OK;
 }
 

@@ -221,6 +221,75 @@ cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int
   return cudaGetLastError();
 }
 
+// -------------------------------------------------- table merge (update)
+
+// Number of entries of the sorted array a[0..n) below x.
+__device__ __forceinline__ uint64_t count_below(const uint64_t *a, uint64_t n, uint64_t x) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// The device table brought up to date in one pass (Sec. 2: the list of
+// allocations changes with every cudaMalloc / cudaFree wrapper): the old
+// sorted table minus the entries at the (sorted) indices `dead`, plus the
+// (sorted) registrations ins_*, written in base order into the other
+// buffer.  Each entry computes its place directly: an old entry i goes to
+// i - (dead indices below i) + (registrations below its base); a
+// registration k goes to k + (old entries below its base, not dead).  A
+// registration may reuse the base of a dead entry; it never meets a live
+// one (registrations do not overlap live allocations).
+__global__ void __launch_bounds__(256) table_merge_kernel(DevTable t, const uint64_t *ins_base,
+                                                          const uint64_t *ins_size,
+                                                          const uint64_t *ins_shadow, uint64_t m,
+                                                          const uint64_t *dead, uint64_t d,
+                                                          uint64_t *nb, uint64_t *ns,
+                                                          uint64_t *nh) {
+  const uint64_t total = t.count + m;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t o, b, sz, sh;
+    if (i < t.count) {
+      const uint64_t r = count_below(dead, d, i);
+      if (r < d && __ldg(dead + r) == i) continue;
+      b = __ldg(t.base + i);
+      sz = __ldg(t.size + i);
+      sh = __ldg(t.shadow + i);
+      o = i - r + count_below(ins_base, m, b);
+    } else {
+      const uint64_t k = i - t.count;
+      b = __ldg(ins_base + k);
+      sz = __ldg(ins_size + k);
+      sh = __ldg(ins_shadow + k);
+      const uint64_t j = count_below(t.base, t.count, b);
+      o = k + j - count_below(dead, d, j);
+    }
+    nb[o] = b;
+    ns[o] = sz;
+    nh[o] = sh;
+  }
+}
+
+cudaError_t launch_table_merge(const DevTable &t, const uint64_t *ins_base,
+                               const uint64_t *ins_size, const uint64_t *ins_shadow, uint64_t m,
+                               const uint64_t *dead, uint64_t d, uint64_t *nb, uint64_t *ns,
+                               uint64_t *nh, int sm_count, cudaStream_t st) {
+  const uint64_t total = t.count + m;
+  if (total == 0) return cudaSuccess;
+  uint64_t blocks = (total + 255) / 256;
+  const uint64_t cap = (uint64_t)(sm_count > 0 ? sm_count : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  table_merge_kernel<<<(unsigned)blocks, 256, 0, st>>>(t, ins_base, ins_size, ins_shadow, m, dead,
+                                                       d, nb, ns, nh);
+  return cudaGetLastError();
+}
+
 // The job mode bits of every request, packed one byte each for the host's
 // level planner.
 __global__ void job_modes_kernel(const ScanJob *jobs, uint64_t nreq, uint8_t *modes) {

@@ -132,3 +132,29 @@ def test_planner_on_small_workload_is_exact():
     w = S.small(0)
     lv, nl = cg.plan_levels(w.reqs, carry=True)
     assert lv.tolist() == _brute_levels(w.reqs)
+
+
+def test_binding_structs_match_the_compiled_header(tmp_path):
+    """Every ctypes mirror of a header struct has the size and field offsets a
+    C compiler gives the header's declaration."""
+    mirrors = {n: getattr(cg, n) for n in ("cg_copy", "cg_report", "cg_err_record", "cg_config",
+                                           "cg_stats", "cg_side3d", "cg_copy3d", "cg_karg",
+                                           "cg_request", "cg_result", "cg_serve_config",
+                                           "cg_serve_stats")}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cg.h"', "int main(void) {"]
+    for n, t in mirrors.items():
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in t._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = dict(ln.split() for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for n, t in mirrors.items():
+        assert int(got[n]) == ctypes.sizeof(t), n
+        for f, _ in t._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(t, f).offset, f"{n}.{f}"

@@ -1,10 +1,12 @@
 """CPU models of the GPU kernels' index arithmetic, run before their first
 GPU launch and kept as tests: for many random geometries, every chunk of
-every row is visited exactly once by the pitched work splits, and every
+every row is visited exactly once by the pitched work splits, every
 bulk copy and shared-memory read of the span and A-bits-only tiles stays
-inside its buffer and window while covering every byte that is classified.
-The models restate the kernels' integer arithmetic (cg_scan_pitched.cu,
-cg_tma.cuh); a change there must be mirrored here.  CPU only."""
+inside its buffer and window while covering every byte that is classified,
+and the table merge writes every entry of the new table exactly once, in
+the host merge's order.  The models restate the kernels' integer
+arithmetic (cg_scan_pitched.cu, cg_tma.cuh, cg_kernels.cu); a change there
+must be mirrored here.  CPU only."""
 from __future__ import annotations
 
 import random
@@ -246,3 +248,55 @@ def test_a_super_tiles_stay_in_bounds_and_cover():
                     assert b0 * 8 <= hlo + lo_i and hlo + hi_i <= b1 * 8
         w0 = (p0 - 8 * aorig) >> 5
         assert (w0 + 1024 + 1) * 4 <= 4112   # the last word read, lane 31's (j = 1023) + 1
+
+
+# ------------------------------------------------ table merge
+
+def _count_below(a, x):
+    lo, hi = 0, len(a)
+    while lo < hi:
+        mid = (lo + hi) >> 1
+        if a[mid] < x:
+            lo = mid + 1
+        else:
+            hi = mid
+    return lo
+
+
+def _merge_model(base, dead, ins):
+    """Places as table_merge_kernel computes them; None where it skips."""
+    n, m = len(base), len(ins)
+    out = [None] * (n - len(dead) + m)
+    for i in range(n + m):
+        if i < n:
+            r = _count_below(dead, i)
+            if r < len(dead) and dead[r] == i:
+                continue
+            o = i - r + _count_below(ins, base[i])
+            b = base[i]
+        else:
+            k = i - n
+            j = _count_below(base, ins[k])
+            o = k + j - _count_below(dead, j)
+            b = ins[k]
+        assert 0 <= o < len(out) and out[o] is None
+        out[o] = b
+    return out
+
+
+def test_table_merge_places_every_entry_once_in_base_order():
+    rng = random.Random(11)
+    for _ in range(3000):
+        n = rng.randrange(0, 40)
+        base = sorted(rng.sample(range(0, 4000, 4), n))
+        dead = sorted(rng.sample(range(n), rng.randrange(0, n + 1)))
+        live = [base[i] for i in range(n) if i not in set(dead)]
+        # registrations: fresh bases, and some at the base of a dead entry
+        pool = [b for b in range(2, 4000, 4)] + [base[i] for i in dead]
+        ins = sorted(set(rng.sample(pool, rng.randrange(0, 12))))
+        if n == 0 and not ins:
+            continue
+        # the host merge: registrations below each main entry first, then
+        # the entry itself if live
+        want = sorted(live + ins)
+        assert _merge_model(base, dead, ins) == want
