@@ -204,9 +204,25 @@ class AllocTable {
   std::set<uint64_t> freed;
   uint64_t dead = 0;
   uint64_t live = 0;
-  uint64_t version = 0;       // any change
-  uint64_t main_version = 0;  // changes of the main array's order (merges)
-  std::vector<uint64_t> dead_idx;  // main indices tombstoned since the last merge
+  uint64_t version = 0;
+  // Changes since the device copy was last brought up to date, while it is
+  // tracked (dev_track): registrations it lacks, and bases it still holds
+  // that were freed.  Kept by base, so the host's own merges do not matter.
+  bool dev_track = false;
+  std::map<uint64_t, std::pair<uint64_t, uint64_t>> dev_added;
+  std::vector<uint64_t> dev_removed;
+
+  void dev_synced() {
+    dev_track = true;
+    dev_added.clear();
+    dev_removed.clear();
+  }
+  void dev_stale() {
+    dev_track = false;
+    dev_added.clear();
+    dev_removed.clear();
+  }
+  uint64_t dev_limit() const { return std::max<uint64_t>(65536, live / 4); }
 
   struct Hit {
     bool ok;
@@ -249,6 +265,10 @@ class AllocTable {
     delta[b] = {s, sh};
     live++;
     version++;
+    if (dev_track) {
+      dev_added[b] = {s, sh};
+      if (dev_added.size() > dev_limit()) dev_stale();
+    }
     freed.erase(freed.lower_bound(b), freed.lower_bound(b + s));  // R13
     if (delta.size() > std::max<uint64_t>(4096, base.size() / 8)) merge();
   }
@@ -263,7 +283,6 @@ class AllocTable {
         *sh = shadow[j];
         size[j] = 0;
         dead++;
-        dead_idx.push_back(j);
         goto removed;
       }
     }
@@ -277,6 +296,10 @@ class AllocTable {
   removed:
     live--;
     version++;
+    if (dev_track && dev_added.erase(b) == 0) {
+      dev_removed.push_back(b);
+      if (dev_removed.size() > dev_limit()) dev_stale();
+    }
     freed.insert(b);
     if (dead > 1024 && dead > base.size() / 4) merge();
     return true;
@@ -308,8 +331,6 @@ class AllocTable {
     shadow.swap(nh);
     delta.clear();
     dead = 0;
-    dead_idx.clear();
-    main_version++;
   }
 };
 
@@ -527,11 +548,9 @@ struct cg_ctx {
   cgi::DevBuf<uint64_t> d_fill;
   cgi::PinBuf<uint64_t> h_fill;
   cgi::DevBuf<uint64_t> t_base, t_size, t_shadow;
-  uint64_t t_version = ~0ull;
-  uint64_t t_main = ~0ull;  // table.main_version the device copy equals
   uint64_t t_count = 0;
   // incremental updates: the merge kernel writes the other buffer set from
-  // the uploaded registrations and dead indices (t_delta, staged in h_tdelta)
+  // the uploaded registrations and freed bases (t_delta, staged in h_tdelta)
   cgi::DevBuf<uint64_t> t_base2, t_size2, t_shadow2, t_delta;
   cgi::PinBuf<uint64_t> h_tdelta;
   cudaEvent_t t_ev = nullptr;  // the last table update's copies and merge

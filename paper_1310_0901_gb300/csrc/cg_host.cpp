@@ -100,7 +100,12 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
     }
   };
   auto compress = [&](std::vector<Ep> &e) -> int {
-    radix_sort(e);
+    // the radix passes cost ~2048-entry scans each: small sets sort directly
+    // (only the ranks of values matter, so the order of ties is free)
+    if (e.size() < 1024)
+      std::sort(e.begin(), e.end(), [](const Ep &a, const Ep &b) { return a.v < b.v; });
+    else
+      radix_sort(e);
     int rank = -1;
     uint64_t prev = 0;
     for (size_t k = 0; k < e.size(); k++) {
@@ -158,58 +163,56 @@ cg_status cgi::flush_fills(cg_ctx *c, cudaStream_t st) {
   return CG_OK;
 }
 
-// Bring the device copy of the table up to date.  When the device holds
-// the host's main array as of its last merge, only the registrations and
-// the dead indices since then are uploaded, and the merge kernel builds the
-// new table on the device, in the order the host merge gives; otherwise
+// Bring the device copy of the table up to date.  While the device copy
+// is tracked, only the registrations and the freed bases since its last
+// update are uploaded, and the merge kernel builds the new table on the
+// device; otherwise (first use, or too many changes) the host merges and
 // the whole table is uploaded.
 cg_status cgi::ensure_device_table(cg_ctx *c, cudaStream_t st) {
   AllocTable &t = c->table;
-  const bool pending = !t.delta.empty() || t.dead;
-  if (pending && c->t_main == t.main_version && c->t_count == t.base.size() && c->t_count) {
-    const uint64_t m = t.delta.size(), d = t.dead_idx.size();
-    const uint64_t n_new = c->t_count - d + m;
-    CG_TRY(c->t_base2.ensure(n_new));
-    CG_TRY(c->t_size2.ensure(n_new));
-    CG_TRY(c->t_shadow2.ensure(n_new));
-    CG_TRY(c->t_delta.ensure(3 * m + d));
-    if (!c->t_ev) CG_CUDA(cudaEventCreateWithFlags(&c->t_ev, cudaEventDisableTiming));
-    CG_CUDA(cudaEventSynchronize(c->t_ev));  // the staging buffer's last copy is done
-    CG_TRY(c->h_tdelta.ensure(3 * m + d));
-    uint64_t *h = c->h_tdelta.p;
-    uint64_t k = 0;
-    for (const auto &e : t.delta) {
-      h[k] = e.first;
-      h[m + k] = e.second.first;
-      h[2 * m + k] = e.second.second;
-      k++;
+  if (t.dev_track) {
+    const uint64_t m = t.dev_added.size(), d = t.dev_removed.size();
+    if (m == 0 && d == 0) return CG_OK;
+    if (d <= c->t_count && c->t_count - d + m == t.live) {
+      const uint64_t n_new = t.live;
+      CG_TRY(c->t_base2.ensure(n_new));
+      CG_TRY(c->t_size2.ensure(n_new));
+      CG_TRY(c->t_shadow2.ensure(n_new));
+      CG_TRY(c->t_delta.ensure(3 * m + d));
+      if (!c->t_ev) CG_CUDA(cudaEventCreateWithFlags(&c->t_ev, cudaEventDisableTiming));
+      CG_CUDA(cudaEventSynchronize(c->t_ev));  // the staging buffer's last copy is done
+      CG_TRY(c->h_tdelta.ensure(3 * m + d));
+      uint64_t *h = c->h_tdelta.p;
+      uint64_t k = 0;
+      for (const auto &e : t.dev_added) {
+        h[k] = e.first;
+        h[m + k] = e.second.first;
+        h[2 * m + k] = e.second.second;
+        k++;
+      }
+      std::copy(t.dev_removed.begin(), t.dev_removed.end(), h + 3 * m);
+      std::sort(h + 3 * m, h + 3 * m + d);
+      if (3 * m + d)
+        CG_CUDA(cudaMemcpyAsync(c->t_delta.p, h, (3 * m + d) * 8, cudaMemcpyHostToDevice, st));
+      const uint64_t *dd = c->t_delta.p;
+      DevTable old{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
+      CG_CUDA(launch_table_merge(old, dd, dd + m, dd + 2 * m, m, dd + 3 * m, d, c->t_base2.p,
+                                 c->t_size2.p, c->t_shadow2.p, c->sm_count, st));
+      CG_CUDA(cudaEventRecord(c->t_ev, st));
+      c->stats.kernels++;
+      c->stats.table_merges++;
+      std::swap(c->t_base.p, c->t_base2.p);
+      std::swap(c->t_base.cap, c->t_base2.cap);
+      std::swap(c->t_size.p, c->t_size2.p);
+      std::swap(c->t_size.cap, c->t_size2.cap);
+      std::swap(c->t_shadow.p, c->t_shadow2.p);
+      std::swap(c->t_shadow.cap, c->t_shadow2.cap);
+      c->t_count = n_new;
+      t.dev_synced();
+      return CG_OK;
     }
-    std::copy(t.dead_idx.begin(), t.dead_idx.end(), h + 3 * m);
-    std::sort(h + 3 * m, h + 3 * m + d);
-    if (3 * m + d)
-      CG_CUDA(cudaMemcpyAsync(c->t_delta.p, h, (3 * m + d) * 8, cudaMemcpyHostToDevice, st));
-    const uint64_t *dd = c->t_delta.p;
-    DevTable old{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
-    CG_CUDA(launch_table_merge(old, dd, dd + m, dd + 2 * m, m, dd + 3 * m, d, c->t_base2.p,
-                               c->t_size2.p, c->t_shadow2.p, c->sm_count, st));
-    CG_CUDA(cudaEventRecord(c->t_ev, st));
-    c->stats.kernels++;
-    c->stats.table_merges++;
-    std::swap(c->t_base.p, c->t_base2.p);
-    std::swap(c->t_base.cap, c->t_base2.cap);
-    std::swap(c->t_size.p, c->t_size2.p);
-    std::swap(c->t_size.cap, c->t_size2.cap);
-    std::swap(c->t_shadow.p, c->t_shadow2.p);
-    std::swap(c->t_shadow.cap, c->t_shadow2.cap);
-    t.merge();
-    c->t_main = t.main_version;
-    c->t_version = t.version;
-    c->t_count = n_new;
-    return CG_OK;
   }
-  if (pending) t.merge();
-  if (c->t_version == t.version && c->t_main == t.main_version && c->t_count == t.base.size())
-    return CG_OK;
+  if (!t.delta.empty() || t.dead) t.merge();
   if (c->t_ev) CG_CUDA(cudaEventSynchronize(c->t_ev));  // a merge may still write t_base
   const uint64_t n = t.base.size();
   CG_TRY(c->t_base.ensure(n));
@@ -221,10 +224,9 @@ cg_status cgi::ensure_device_table(cg_ctx *c, cudaStream_t st) {
     CG_CUDA(cudaMemcpyAsync(c->t_shadow.p, t.shadow.data(), n * 8, cudaMemcpyHostToDevice, st));
     CG_CUDA(cudaStreamSynchronize(st));  // host vectors may change after return
   }
-  c->t_version = t.version;
-  c->t_main = t.main_version;
   c->t_count = n;
   c->stats.table_uploads++;
+  t.dev_synced();
   return CG_OK;
 }
 

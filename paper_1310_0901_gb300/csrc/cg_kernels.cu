@@ -238,13 +238,14 @@ __device__ __forceinline__ uint64_t count_below(const uint64_t *a, uint64_t n, u
 
 // The device table brought up to date in one pass (Sec. 2: the list of
 // allocations changes with every cudaMalloc / cudaFree wrapper): the old
-// sorted table minus the entries at the (sorted) indices `dead`, plus the
-// (sorted) registrations ins_*, written in base order into the other
-// buffer.  Each entry computes its place directly: an old entry i goes to
-// i - (dead indices below i) + (registrations below its base); a
-// registration k goes to k + (old entries below its base, not dead).  A
-// registration may reuse the base of a dead entry; it never meets a live
-// one (registrations do not overlap live allocations).
+// sorted table minus the entries whose bases are in the sorted list
+// `dead`, plus the (sorted) registrations ins_*, written in base order into
+// the other buffer.  Each entry computes its place directly: an old entry
+// goes to its index - (dead bases below its base) + (registrations below
+// its base); a registration k goes to k + (old bases below its base) -
+// (dead bases below it).  A registration may reuse the base of a dead
+// entry; it never meets a live one (registrations do not overlap live
+// allocations).
 __global__ void __launch_bounds__(256) table_merge_kernel(DevTable t, const uint64_t *ins_base,
                                                           const uint64_t *ins_size,
                                                           const uint64_t *ins_shadow, uint64_t m,
@@ -256,9 +257,9 @@ __global__ void __launch_bounds__(256) table_merge_kernel(DevTable t, const uint
        i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t o, b, sz, sh;
     if (i < t.count) {
-      const uint64_t r = count_below(dead, d, i);
-      if (r < d && __ldg(dead + r) == i) continue;
       b = __ldg(t.base + i);
+      const uint64_t r = count_below(dead, d, b);
+      if (r < d && __ldg(dead + r) == b) continue;
       sz = __ldg(t.size + i);
       sh = __ldg(t.shadow + i);
       o = i - r + count_below(ins_base, m, b);
@@ -267,8 +268,7 @@ __global__ void __launch_bounds__(256) table_merge_kernel(DevTable t, const uint
       b = __ldg(ins_base + k);
       sz = __ldg(ins_size + k);
       sh = __ldg(ins_shadow + k);
-      const uint64_t j = count_below(t.base, t.count, b);
-      o = k + j - count_below(dead, d, j);
+      o = k + count_below(t.base, t.count, b) - count_below(dead, d, b);
     }
     nb[o] = b;
     ns[o] = sz;

@@ -19,8 +19,9 @@ uint32_t scan_tma_tile_bytes();  // a batched segment is a whole number of these
 cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
                                   unsigned int *err_flag, cudaStream_t st);
-// New device table = old minus the sorted indices `dead` plus the sorted
-// registrations, into nb/ns/nh (count - d + m entries).
+// New device table = old minus the entries whose bases are in the sorted
+// list `dead`, plus the sorted registrations, into nb/ns/nh (count - d + m
+// entries).
 cudaError_t launch_table_merge(const DevTable &t, const uint64_t *ins_base,
                                const uint64_t *ins_size, const uint64_t *ins_shadow, uint64_t m,
                                const uint64_t *dead, uint64_t d, uint64_t *nb, uint64_t *ns,

@@ -124,15 +124,15 @@ struct StageCopy {
 struct RoundSlot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  DevBuf<uint8_t> d_up;  // packed jobs | info | acc | order | seg_first | stage ptrs
-  DevBuf<cg_report> reps;
+  // packed jobs | info | acc | order | seg_first | stage ptrs | error flag |
+  // reports: one upload of everything up to the (zeroed) error flag, one
+  // read-back of the flag and the reports
+  DevBuf<uint8_t> d_up;
   DevBuf<uint32_t> counts;
   DevBuf<uint64_t> blocksums;
-  DevBuf<unsigned int> err;
   DevBuf<uint8_t> stage;
   PinBuf<uint8_t> h_up;
-  PinBuf<cg_report> h_reps;
-  PinBuf<unsigned int> h_err;
+  PinBuf<uint8_t> h_down;  // error flag (16 bytes) | reports
   bool busy = false;
   uint64_t id = 0;
   uint64_t bytes = 0;
@@ -183,14 +183,15 @@ struct ServeEngine {
       if (!r.busy) continue;
       const cudaError_t e = cudaEventQuery(r.done);
       if (e == cudaErrorNotReady) continue;
-      const bool ok = e == cudaSuccess && r.h_err.p[0] == 0;
+      const bool ok = e == cudaSuccess && *reinterpret_cast<const unsigned int *>(r.h_down.p) == 0;
+      const cg_report *h_reps = reinterpret_cast<const cg_report *>(r.h_down.p + 16);
       if (e != cudaSuccess) cudaGetLastError();
       {
         std::lock_guard<std::mutex> g(stats_mu);
         for (size_t i = 0; i < r.members.size(); i++) {
           RingSlot *sl = r.members[i];
           const int64_t race = sl->res.report.race_seq;  // set at admission
-          sl->res.report = r.h_reps.p[i];
+          sl->res.report = h_reps[i];
           if (race >= 0) {
             sl->res.report.flags |= CG_F_CONCURRENT;
             sl->res.report.race_seq = race;
@@ -498,9 +499,12 @@ struct ServeEngine {
     const uint64_t o_order = round_up(o_acc + n * sizeof(Acc), 16);
     const uint64_t o_seg = round_up(o_order + n * 4, 16);
     const uint64_t o_stage = round_up(o_seg + n * 8, 16);
-    const uint64_t total = round_up(o_stage + n * 8, 16);
+    const uint64_t o_err = round_up(o_stage + n * 8, 16);
+    const uint64_t total = o_err + 16;  // uploaded
+    const uint64_t down = 16 + n * sizeof(cg_report);
     CG_TRY(R.h_up.ensure(total));
-    CG_TRY(R.d_up.ensure(total));
+    CG_TRY(R.d_up.ensure(total + n * sizeof(cg_report)));
+    CG_TRY(R.h_down.ensure(down));
     if (stage_bytes) {
       CG_TRY(R.stage.ensure(stage_bytes));
       const uint64_t base = reinterpret_cast<uint64_t>(R.stage.p);
@@ -523,6 +527,7 @@ struct ServeEngine {
     uint32_t *ho = reinterpret_cast<uint32_t *>(h + o_order);
     uint64_t *hs = reinterpret_cast<uint64_t *>(h + o_seg);
     std::memcpy(h + o_stage, stage_ptr.data(), n * 8);
+    std::memset(h + o_err, 0, 16);
     {
       std::vector<uint64_t> fill(lev_start.begin(), lev_start.end() - 1);
       for (uint64_t i = 0; i < n; i++) ho[fill[lvl[i]]++] = (uint32_t)i;
@@ -570,13 +575,10 @@ struct ServeEngine {
     CG_TRY(flush_fills(c, s));
     CG_CUDA(cudaMemcpyAsync(R.d_up.p, h, total, cudaMemcpyHostToDevice, s));
     const uint64_t nblocks = (n + kFinalizeItems - 1) / kFinalizeItems;
-    CG_TRY(R.reps.ensure(n));
     CG_TRY(R.counts.ensure(n));
     CG_TRY(R.blocksums.ensure(nblocks + 1));
-    CG_TRY(R.err.ensure(1));
-    CG_TRY(R.h_reps.ensure(n));
-    CG_TRY(R.h_err.ensure(1));
-    CG_CUDA(cudaMemsetAsync(R.err.p, 0, sizeof(unsigned int), s));
+    unsigned int *d_err = reinterpret_cast<unsigned int *>(R.d_up.p + o_err);
+    cg_report *d_reps = reinterpret_cast<cg_report *>(R.d_up.p + o_err + 16);
     BatchPlan plan{};
     plan.reqs = nullptr;
     plan.jobs = reinterpret_cast<ScanJob *>(R.d_up.p + o_jobs);
@@ -602,13 +604,12 @@ struct ServeEngine {
                                   c->sm_count * 8, s));
       else
         CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
-                                      c->sm_count, R.err.p, s));
+                                      c->sm_count, d_err, s));
       kernels++;
     }
-    CG_CUDA(launch_finalize(plan, R.reps.p, R.counts.p, R.blocksums.p, kFinalizeItems, s));
+    CG_CUDA(launch_finalize(plan, d_reps, R.counts.p, R.blocksums.p, kFinalizeItems, s));
     kernels++;
-    CG_CUDA(cudaMemcpyAsync(R.h_reps.p, R.reps.p, n * sizeof(cg_report), cudaMemcpyDeviceToHost, s));
-    CG_CUDA(cudaMemcpyAsync(R.h_err.p, R.err.p, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    CG_CUDA(cudaMemcpyAsync(R.h_down.p, R.d_up.p + o_err, down, cudaMemcpyDeviceToHost, s));
     CG_CUDA(cudaEventRecord(R.done, s));
     R.busy = true;
     R.id = round_id;
@@ -820,14 +821,11 @@ cg_status cg_serve_stop(cg_ctx *c, cg_serve_stats *out) {
     cudaStreamDestroy(r.stream);
     cudaEventDestroy(r.done);
     r.d_up.release();
-    r.reps.release();
     r.counts.release();
     r.blocksums.release();
-    r.err.release();
     r.stage.release();
     r.h_up.release();
-    r.h_reps.release();
-    r.h_err.release();
+    r.h_down.release();
   }
   if (out) {
     std::lock_guard<std::mutex> g(e->stats_mu);

@@ -156,7 +156,7 @@ cg_status cg_restore(cg_ctx *c, const char *path) {
     CG_TRY(get(F.f, &h));
     c->freed_arrays.insert(h);
   }
-  c->table.version++;  // the device copy of the table is rebuilt on next use
+  c->table.dev_stale();  // the device copy of the table is rebuilt on next use
   return CG_OK;
 }
 

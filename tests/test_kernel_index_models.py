@@ -264,21 +264,21 @@ def _count_below(a, x):
 
 
 def _merge_model(base, dead, ins):
-    """Places as table_merge_kernel computes them; None where it skips."""
+    """Places as table_merge_kernel computes them (dead: sorted bases of
+    freed entries); None where it skips."""
     n, m = len(base), len(ins)
     out = [None] * (n - len(dead) + m)
     for i in range(n + m):
         if i < n:
-            r = _count_below(dead, i)
-            if r < len(dead) and dead[r] == i:
-                continue
-            o = i - r + _count_below(ins, base[i])
             b = base[i]
+            r = _count_below(dead, b)
+            if r < len(dead) and dead[r] == b:
+                continue
+            o = i - r + _count_below(ins, b)
         else:
             k = i - n
-            j = _count_below(base, ins[k])
-            o = k + j - _count_below(dead, j)
             b = ins[k]
+            o = k + _count_below(base, b) - _count_below(dead, b)
         assert 0 <= o < len(out) and out[o] is None
         out[o] = b
     return out
@@ -289,14 +289,13 @@ def test_table_merge_places_every_entry_once_in_base_order():
     for _ in range(3000):
         n = rng.randrange(0, 40)
         base = sorted(rng.sample(range(0, 4000, 4), n))
-        dead = sorted(rng.sample(range(n), rng.randrange(0, n + 1)))
-        live = [base[i] for i in range(n) if i not in set(dead)]
+        dead_i = set(rng.sample(range(n), rng.randrange(0, n + 1)))
+        dead = sorted(base[i] for i in dead_i)
+        live = [base[i] for i in range(n) if i not in dead_i]
         # registrations: fresh bases, and some at the base of a dead entry
-        pool = [b for b in range(2, 4000, 4)] + [base[i] for i in dead]
+        pool = [b for b in range(2, 4000, 4)] + dead
         ins = sorted(set(rng.sample(pool, rng.randrange(0, 12))))
         if n == 0 and not ins:
             continue
-        # the host merge: registrations below each main entry first, then
-        # the entry itself if live
         want = sorted(live + ins)
         assert _merge_model(base, dead, ins) == want
