@@ -878,7 +878,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=S.SERVE_RATE)
     ap.add_argument("--serve-image-gib", type=int, default=32)
-    ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--extras", type=int, default=1,
                     help="1: add the batched and serving figures to the default line")
     ap.add_argument("--segment-kib", type=int, default=0)

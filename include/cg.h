@@ -562,7 +562,7 @@ typedef struct cg_serve_config {
   uint32_t clients;       /* client rings, 1..64 (0 = 8) */
   uint32_t ring_capacity; /* requests per client, a power of two (0 = 4096) */
   uint32_t max_round;     /* checks per round at most (0 = 8192) */
-  uint32_t streams;       /* rounds on the GPU at once, 1..8 (0 = 2) */
+  uint32_t streams;       /* rounds on the GPU at once, 1..8 (0 = 4) */
   uint64_t budget_bytes;  /* bytes of admitted, unfinished checks (0 = 8 GiB);
                              a single larger check is still admitted alone */
   uint32_t reserved[10];

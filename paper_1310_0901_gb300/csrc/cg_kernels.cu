@@ -421,6 +421,28 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(BatchPlan p, cg_repo
   if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
+// Reports of a serving round written straight into pinned host memory (no
+// read-back copy): out = error flag (16 bytes) | reports.  Runs after the
+// round's level kernels on the same stream, so the flag is final.
+__global__ void __launch_bounds__(kThreads) serve_finalize_kernel(BatchPlan p,
+                                                                  const unsigned int *err,
+                                                                  uint8_t *out) {
+  const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (i == 0) *reinterpret_cast<unsigned int *>(out) = *err;
+  if (i < p.nreq) {
+    cg_report r;
+    assemble_report(&r, p.info[i], p.acc[i]);
+    reinterpret_cast<cg_report *>(out + 16)[i] = r;
+  }
+}
+
+cudaError_t launch_serve_finalize(const BatchPlan &p, const unsigned int *err, uint8_t *out,
+                                  cudaStream_t st) {
+  const uint64_t nb = (p.nreq + kThreads - 1) / kThreads;
+  serve_finalize_kernel<<<(unsigned)(nb ? nb : 1), kThreads, 0, st>>>(p, err, out);
+  return cudaGetLastError();
+}
+
 // Exclusive scan of the block sums in one CTA; total count at block_sums[nblocks].
 __global__ void __launch_bounds__(kThreads) scan_block_sums_kernel(uint64_t *sums,
                                                                    uint64_t nblocks) {

@@ -31,6 +31,10 @@ cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int
 cudaError_t launch_job_modes(const BatchPlan &p, uint8_t *modes, cudaStream_t st);
 cudaError_t launch_scan_level(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                               uint64_t pos_end, uint64_t n_segs, int grid, cudaStream_t st);
+// Serving: the error flag and the reports into `out` (pinned host memory
+// the kernel writes directly): flag (16 bytes) | nreq reports.
+cudaError_t launch_serve_finalize(const BatchPlan &p, const unsigned int *err, uint8_t *out,
+                                  cudaStream_t st);
 cudaError_t launch_finalize(const BatchPlan &p, cg_report *reps, uint32_t *counts,
                             uint64_t *block_sums, int items_per_block, cudaStream_t st);
 cudaError_t launch_scan_block_sums(uint64_t *block_sums, uint64_t nblocks, uint64_t *total,

@@ -124,15 +124,12 @@ struct StageCopy {
 struct RoundSlot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  // packed jobs | info | acc | order | seg_first | stage ptrs | error flag |
-  // reports: one upload of everything up to the (zeroed) error flag, one
-  // read-back of the flag and the reports
+  // packed jobs | info | acc | order | seg_first | stage ptrs | error flag:
+  // one upload per round (the flag zeroed)
   DevBuf<uint8_t> d_up;
-  DevBuf<uint32_t> counts;
-  DevBuf<uint64_t> blocksums;
   DevBuf<uint8_t> stage;
   PinBuf<uint8_t> h_up;
-  PinBuf<uint8_t> h_down;  // error flag (16 bytes) | reports
+  PinBuf<uint8_t> h_down;  // error flag (16 bytes) | reports, written by the GPU
   bool busy = false;
   uint64_t id = 0;
   uint64_t bytes = 0;
@@ -503,7 +500,7 @@ struct ServeEngine {
     const uint64_t total = o_err + 16;  // uploaded
     const uint64_t down = 16 + n * sizeof(cg_report);
     CG_TRY(R.h_up.ensure(total));
-    CG_TRY(R.d_up.ensure(total + n * sizeof(cg_report)));
+    CG_TRY(R.d_up.ensure(total));
     CG_TRY(R.h_down.ensure(down));
     if (stage_bytes) {
       CG_TRY(R.stage.ensure(stage_bytes));
@@ -574,11 +571,7 @@ struct ServeEngine {
     }
     CG_TRY(flush_fills(c, s));
     CG_CUDA(cudaMemcpyAsync(R.d_up.p, h, total, cudaMemcpyHostToDevice, s));
-    const uint64_t nblocks = (n + kFinalizeItems - 1) / kFinalizeItems;
-    CG_TRY(R.counts.ensure(n));
-    CG_TRY(R.blocksums.ensure(nblocks + 1));
     unsigned int *d_err = reinterpret_cast<unsigned int *>(R.d_up.p + o_err);
-    cg_report *d_reps = reinterpret_cast<cg_report *>(R.d_up.p + o_err + 16);
     BatchPlan plan{};
     plan.reqs = nullptr;
     plan.jobs = reinterpret_cast<ScanJob *>(R.d_up.p + o_jobs);
@@ -607,9 +600,8 @@ struct ServeEngine {
                                       c->sm_count, d_err, s));
       kernels++;
     }
-    CG_CUDA(launch_finalize(plan, d_reps, R.counts.p, R.blocksums.p, kFinalizeItems, s));
+    CG_CUDA(launch_serve_finalize(plan, d_err, R.h_down.p, s));
     kernels++;
-    CG_CUDA(cudaMemcpyAsync(R.h_down.p, R.d_up.p + o_err, down, cudaMemcpyDeviceToHost, s));
     CG_CUDA(cudaEventRecord(R.done, s));
     R.busy = true;
     R.id = round_id;
@@ -663,7 +655,7 @@ cg_status cg_serve_start(cg_ctx *c, const cg_serve_config *cfg_in) {
   if (!cfg.clients) cfg.clients = 8;
   if (!cfg.ring_capacity) cfg.ring_capacity = 4096;
   if (!cfg.max_round) cfg.max_round = 8192;
-  if (!cfg.streams) cfg.streams = 2;
+  if (!cfg.streams) cfg.streams = 4;
   if (!cfg.budget_bytes) cfg.budget_bytes = 8ull << 30;
   if (cfg.clients > 64 || cfg.streams > 8 || (cfg.ring_capacity & (cfg.ring_capacity - 1)) ||
       cfg.ring_capacity < 2)
@@ -821,8 +813,6 @@ cg_status cg_serve_stop(cg_ctx *c, cg_serve_stats *out) {
     cudaStreamDestroy(r.stream);
     cudaEventDestroy(r.done);
     r.d_up.release();
-    r.counts.release();
-    r.blocksums.release();
     r.stage.release();
     r.h_up.release();
     r.h_down.release();
