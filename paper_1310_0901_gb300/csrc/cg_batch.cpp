@@ -128,8 +128,27 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   for (int l : B.lvl) B.lev_start[l + 1]++;
   for (int l = 0; l < B.nlev; l++) B.lev_start[l + 1] += B.lev_start[l];
   {
+    // within a level, copies in decreasing order of work (power-of-two
+    // classes, stable): a level's segments are dealt to the warps in
+    // turn, so the last turns hold the short segments of small copies
+    // and the level's tail is short (copies of one level touch disjoint
+    // shadow, so their order is free)
+    const bool tma = c->cfg.scan_engine != 1 && !c->img_on_host;
+    std::vector<uint8_t> cls(nreq);
+    uint64_t cnt[66] = {0};
+    for (uint64_t i = 0; i < nreq; i++) {
+      const cg_copy &q = reqs[i];
+      uint64_t work = q.n;
+      if (q.kind == CG_DTOD && !(B.modes[i] & (kModeCarry | kModeReadDev))) work = 0;
+      if (tma && q.kind == CG_DTOH && !(B.modes[i] & kModeReadDev)) work = q.n >> 3;
+      cls[i] = (uint8_t)(work ? 64 - __builtin_clzll(work) : 0);
+      cnt[65 - cls[i]]++;
+    }
+    for (int k = 1; k < 66; k++) cnt[k] += cnt[k - 1];
+    std::vector<uint32_t> by_work(nreq);
+    for (uint64_t i = 0; i < nreq; i++) by_work[cnt[64 - cls[i]]++] = (uint32_t)i;
     std::vector<uint64_t> fill(B.lev_start.begin(), B.lev_start.end() - 1);
-    for (uint64_t i = 0; i < nreq; i++) B.h_order[fill[B.lvl[i]]++] = (uint32_t)i;
+    for (uint32_t i : by_work) B.h_order[fill[B.lvl[i]]++] = i;
   }
   for (auto &sc : B.stages) sc.level = B.lvl[sc.req];
   std::sort(B.stages.begin(), B.stages.end(),
@@ -137,6 +156,7 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   c->stats.batch_plan_ns += now_ns() - t_plan;
   CG_CUDA(cudaMemcpyAsync(K.b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
   B.tma = c->cfg.scan_engine != 1 && !c->img_on_host;
+  CG_TRY(K.b_claim.ensure((uint64_t)B.nlev));
   int per_sm = (int)c->cfg.batch_ctas_per_sm;
   if (per_sm <= 0) per_sm = B.tma ? 1 : 8;
   B.grid = c->sm_count * per_sm;
@@ -177,6 +197,8 @@ cg_status batch_levels(cg_ctx *c, BatchBufs &K, BatchRun &B, uint32_t mode_mask,
   B.plan.mode_mask = mode_mask;
   const bool dry = !(mode_mask & kModeCarry);
   CG_CUDA(cudaMemsetAsync(K.b_err.p, 0, sizeof(unsigned int), st));
+  if (B.tma)  // one segment-claim counter per level
+    CG_CUDA(cudaMemsetAsync(K.b_claim.p, 0, (size_t)B.nlev * sizeof(unsigned long long), st));
   size_t sci = 0;
   for (int l = 0; l < B.nlev; l++) {
     for (; !dry && sci < B.stages.size() && B.stages[sci].level == l; sci++)
@@ -185,7 +207,7 @@ cg_status batch_levels(cg_ctx *c, BatchBufs &K, BatchRun &B, uint32_t mode_mask,
                               cudaMemcpyDeviceToDevice, st));
     if (B.tma)
       CG_CUDA(launch_scan_level_tma(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1],
-                                    B.lev_segs[l], B.grid, K.b_err.p, st));
+                                    B.lev_segs[l], B.grid, K.b_claim.p + l, K.b_err.p, st));
     else
       CG_CUDA(launch_scan_level(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1], B.lev_segs[l],
                                 B.grid, st));

@@ -481,6 +481,7 @@ struct BatchBufs {
   DevBuf<uint64_t> b_blocksums;
   DevBuf<cg_err_record> b_recs;
   DevBuf<unsigned int> b_err;
+  DevBuf<unsigned long long> b_claim;  // per-level segment-claim counters
   DevBuf<uint8_t> b_modes;
   DevBuf<uint8_t> stage;  // overlapping device->device sources
   PinBuf<uint8_t> h_modes;
@@ -510,6 +511,7 @@ struct BatchBufs {
     b_blocksums.release();
     b_recs.release();
     b_err.release();
+    b_claim.release();
     b_modes.release();
     stage.release();
     h_modes.release();

@@ -102,14 +102,44 @@ __global__ void __launch_bounds__(kTW * 32, 1)
 
 // ------------------------------------------------ batched: one level
 
-// The tiles a warp processes in one level, in order: segments w, w + W,
-// w + 2W, ... of the level's segment list (warps interleave, so the bytes
-// streamed at any moment are close together), each segment's tiles in
-// turn.  The copy owning a segment is found by one binary search per warp,
-// then by galloping forward from the previous copy (segments of a copy are
-// consecutive, so a step of W segments usually stays in the same copy).
-// Producer and consumer walk identical iterators, the producer kNS tiles
-// ahead.
+// The tiles a warp processes in one level, in order: segment w first,
+// then either segments w + W, w + 2W, ... (static) or, with a claim
+// counter, the next unclaimed segment each time (dynamic: a warp that drew
+// cheap segments takes more, so the level ends with every warp busy to its
+// last segment).  Either way a warp's segments increase, and each
+// segment's tiles are taken in turn.  The copy owning a segment is found by
+// one binary search per warp, then by galloping forward from the previous
+// copy.  Producer and consumer walk the same segment sequence, the producer
+// kNS tiles ahead: the producer claims and hands each claim to the
+// consumer through a small per-warp ring in shared memory.  (Claiming one
+// segment ahead, to hide the atomic's latency, lengthened each level's
+// tail: slower on error-dense batches.)
+constexpr int kSegQ = 8;  // ring entries: at most 2 * kNS + 3 claims outstanding
+
+struct SegSrc {
+  unsigned long long *ctr;  // null: static striding
+  uint64_t *q;              // this warp's ring (dynamic only)
+  uint64_t step;            // W
+  uint32_t n;               // claims pushed (producer) or popped (consumer)
+  bool prod;
+  __device__ __forceinline__ uint64_t next(uint64_t cur, int lane) {
+    if (!ctr) return cur + step;
+    uint64_t v = 0;
+    if (prod) {
+      if (lane == 0) {
+        v = step + atomicAdd(ctr, 1ull);
+        q[n & (kSegQ - 1)] = v;
+      }
+      v = __shfl_sync(CG_FULL, v, 0);
+    } else {
+      __syncwarp();
+      v = q[n & (kSegQ - 1)];
+    }
+    n++;
+    return v;
+  }
+};
+
 struct SegIter {
   uint64_t s;      // current segment id
   uint64_t pos;    // order position of the current copy
@@ -147,9 +177,10 @@ __device__ __forceinline__ uint64_t seg_search(const BatchPlan &p, uint64_t lo, 
   return lo;
 }
 
-// Settle on segment it.s (or the first non-empty one among s, s+W, ...).
+// Settle on segment it.s (or the first non-empty one after it).
 __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, const Image &img,
-                                           uint64_t pos_end, uint64_t n_segs, uint64_t step) {
+                                           uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                           int lane) {
   const int64_t seg_rows = p.seg_chunks >> 5;
   while (it.s < n_segs) {
     if (it.s >= it.next) {  // gallop forward from the next position
@@ -173,26 +204,27 @@ __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, cons
       it.valid = true;
       return;
     }
-    it.s += step;  // an empty trailing segment (the count was an upper bound)
+    it.s = src.next(it.s, lane);  // an empty trailing segment (the count was an upper bound)
   }
   it.valid = false;
 }
 
 __device__ __forceinline__ void seg_begin(SegIter &it, const BatchPlan &p, const Image &img,
                                           uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
-                                          uint64_t s, uint64_t step) {
+                                          uint64_t s, SegSrc &src, int lane) {
   it.s = s;
   it.valid = false;
   if (s >= n_segs) return;
   seg_set_pos(it, p, img, seg_search(p, pos_begin, pos_end, s), pos_end);
-  seg_settle(it, p, img, pos_end, n_segs, step);
+  seg_settle(it, p, img, pos_end, n_segs, src, lane);
 }
 
 __device__ __forceinline__ void seg_advance(SegIter &it, const BatchPlan &p, const Image &img,
-                                            uint64_t pos_end, uint64_t n_segs, uint64_t step) {
+                                            uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                            int lane) {
   if (++it.t < it.t_end) return;
-  it.s += step;
-  seg_settle(it, p, img, pos_end, n_segs, step);
+  it.s = src.next(it.s, lane);
+  seg_settle(it, p, img, pos_end, n_segs, src, lane);
 }
 
 __device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bits, uint32_t st,
@@ -244,7 +276,7 @@ __device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp
 
 __global__ void __launch_bounds__(kTW * 32, 1)
     scan_level_tma_kernel(Image img, BatchPlan p, uint64_t pos_begin, uint64_t pos_end,
-                          uint64_t n_segs, unsigned int *err_flag) {
+                          uint64_t n_segs, unsigned long long *claim, unsigned int *err_flag) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
@@ -252,6 +284,8 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   const int wid = threadIdx.x >> 5;
   uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  uint64_t *segq = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem +
+                                                 (size_t)kTW * kNS * 8) + wid * kSegQ;
   const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
   const uint64_t nw = (uint64_t)gridDim.x * kTW;
   if (lane == 0) {
@@ -259,14 +293,17 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     fence_mbar_init();
   }
   __syncwarp();
+  SegSrc psrc{claim, segq, nw, 0, true};
+  SegSrc csrc{claim, segq, nw, 0, false};
   SegIter prod, cons;
-  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, nw);
-  cons = prod;
+  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, psrc, lane);
+  cons = prod;  // the first segment is the warp's own (w), settled identically
+  csrc.n = psrc.n;
   int issued = 0;
   for (int s = 0; s < kNS && prod.valid; s++) {
     if (lane == 0) seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
     issued++;
-    seg_advance(prod, p, img, pos_end, n_segs, nw);
+    seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
   }
   LaneAcc la;
   lane_acc_reset(la);
@@ -289,12 +326,15 @@ __global__ void __launch_bounds__(kTW * 32, 1)
         seg_issue(prod, img.a_bits, smem_addr(wbase + stage * kStage), smem_addr(&bars[stage]));
       }
       issued++;
-      seg_advance(prod, p, img, pos_end, n_segs, nw);
+      seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
     }
     const uint32_t req = cons.req;
     const uint64_t seg = cons.s;
-    seg_advance(cons, p, img, pos_end, n_segs, nw);
-    if (!cons.valid || cons.s != seg) warp_flush(la, &p.acc[req], lane);  // segment done
+    seg_advance(cons, p, img, pos_end, n_segs, csrc, lane);
+    (void)seg;
+    // a warp's segments increase, so it never comes back to a copy it left:
+    // its counts for that copy are flushed when the copy changes
+    if (!cons.valid || cons.req != req) warp_flush(la, &p.acc[req], lane);
     stage = stage + 1 == kNS ? 0 : stage + 1;
   }
   if (failed) {  // drain the copies still in flight, bounded
@@ -309,21 +349,27 @@ __global__ void __launch_bounds__(kTW * 32, 1)
 
 cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
-                                  unsigned int *err_flag, cudaStream_t st) {
+                                  unsigned long long *claim, unsigned int *err_flag,
+                                  cudaStream_t st) {
   if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
+  constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
   static int per_sm = 0;
   if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(scan_level_tma_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    per_sm = tma_ctas_per_sm(scan_level_tma_kernel);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_level_tma_kernel, kTW * 32, smem) !=
+            cudaSuccess ||
+        n < 1)
+      n = 1;
+    per_sm = n;
   }
   const uint64_t cap = (uint64_t)max_ctas * (uint64_t)per_sm;  // max_ctas counts SMs
   const uint64_t ctas = (n_segs + kTW - 1) / kTW;
   const unsigned g = (unsigned)(ctas < cap ? ctas : cap);
-  scan_level_tma_kernel<<<g, kTW * 32, kSmemBytes, st>>>(img, p, pos_begin, pos_end, n_segs,
-                                                         err_flag);
+  scan_level_tma_kernel<<<g, kTW * 32, smem, st>>>(img, p, pos_begin, pos_end, n_segs, claim,
+                                                   err_flag);
   return cudaGetLastError();
 }
 

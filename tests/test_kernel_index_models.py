@@ -299,3 +299,118 @@ def test_table_merge_places_every_entry_once_in_base_order():
             continue
         want = sorted(live + ins)
         assert _merge_model(base, dead, ins) == want
+
+
+# ------------------------------------------------ dynamic segment claims
+
+kSegQ = 8
+
+
+class _Src:
+    """SegSrc: static striding, or claims taken by the producer and handed
+    to the consumer through the warp's ring."""
+
+    def __init__(self, shared, ring, step, prod):
+        self.shared, self.ring, self.step, self.prod, self.n = shared, ring, step, prod, 0
+
+    def claim(self):
+        v = self.step + self.shared["ctr"]
+        self.shared["ctr"] += 1
+        return v
+
+    def next(self, cur):
+        if self.shared is None:
+            return cur + self.step
+        if self.prod:
+            v = self.claim()
+            self.ring["q"][self.n & (kSegQ - 1)] = v
+            self.ring["pushed"] += 1
+            assert self.ring["pushed"] - self.ring["popped"] <= kSegQ, "ring overflow"
+        else:
+            v = self.ring["q"][self.n & (kSegQ - 1)]
+            self.ring["popped"] += 1
+            assert self.ring["popped"] <= self.ring["pushed"], "pop before push"
+        self.n += 1
+        return v
+
+
+class _It:
+    def __init__(self):
+        self.s = self.t = self.t_end = 0
+        self.valid = False
+
+    def copy(self):
+        o = _It()
+        o.__dict__.update(self.__dict__)
+        return o
+
+
+def _settle(it, tiles, src):
+    while it.s < len(tiles):
+        if tiles[it.s]:
+            it.t, it.t_end, it.valid = 0, tiles[it.s], True
+            return
+        it.s = src.next(it.s)
+    it.valid = False
+
+
+def _advance(it, tiles, src):
+    it.t += 1
+    if it.t < it.t_end:
+        return
+    it.s = src.next(it.s)
+    _settle(it, tiles, src)
+
+
+def _warp(gw, nw, tiles, shared, kNS, consumed):
+    """One warp of scan_level_tma_kernel, a generator yielding after every
+    consumed tile (so warps interleave their claims)."""
+    ring = {"q": [None] * kSegQ, "pushed": 0, "popped": 0}
+    psrc = _Src(shared, ring, nw, True)
+    csrc = _Src(shared, ring, nw, False)
+    prod = _It()
+    prod.s = gw
+    if gw < len(tiles):
+        _settle(prod, tiles, psrc)
+    cons = prod.copy()
+    csrc.n = psrc.n
+    ring["popped"] = ring["pushed"]
+    issued = []
+    for _ in range(kNS):
+        if not prod.valid:
+            break
+        issued.append((prod.s, prod.t))
+        _advance(prod, tiles, psrc)
+    while cons.valid:
+        assert issued and issued.pop(0) == (cons.s, cons.t)
+        consumed.append((cons.s, cons.t))
+        if prod.valid:
+            issued.append((prod.s, prod.t))
+            _advance(prod, tiles, psrc)
+        _advance(cons, tiles, csrc)
+        yield
+
+
+def test_dynamic_segment_claims_cover_every_tile_once():
+    rng = random.Random(21)
+    for trial in range(400):
+        n_segs = rng.randrange(1, 120)
+        # tiles per segment; 0 = an empty trailing segment (after a copy)
+        tiles = [rng.choice([1, 1, 2, 3, 16]) for _ in range(n_segs)]
+        for k in range(1, n_segs):
+            if rng.random() < 0.2 and tiles[k - 1]:
+                tiles[k] = 0
+        nw = rng.choice([1, 2, 5, 16, 64])
+        for dynamic in (False, True):
+            shared = {"ctr": 0} if dynamic else None
+            consumed = []
+            warps = [_warp(w, nw, tiles, shared, 2, consumed) for w in range(nw)]
+            live = list(warps)
+            while live:
+                g = rng.choice(live)
+                try:
+                    next(g)
+                except StopIteration:
+                    live.remove(g)
+            want = sorted((s, t) for s in range(n_segs) for t in range(tiles[s]))
+            assert sorted(consumed) == want, (trial, dynamic)
