@@ -302,6 +302,7 @@ __device__ __forceinline__ void single_epilogue(LaneAcc &la, SingleScratch *scr,
     scr->acc.first_unaddr = kNone;
     scr->acc.first_undef = kNone;
     scr->ctas_done = 0;
+    scr->claim = 0;
     __threadfence_system();
   }
 }

@@ -67,8 +67,9 @@ struct Acc {
 struct SingleScratch {
   Acc acc;
   unsigned int ctas_done;
-  unsigned int error;  // nonzero: a bounded wait ran out (report flagged incomplete)
-  unsigned int pad[6];
+  unsigned int error;        // nonzero: a bounded wait ran out (report flagged incomplete)
+  unsigned long long claim;  // segments claimed beyond the warps' first (TMA kernel)
+  unsigned int pad[4];
 };
 
 // Device-side verdict of the range part of a request (batched path).

@@ -92,6 +92,7 @@ __global__ void init_single_scratch_kernel(SingleScratch *s) {
   s->acc.first_undef = kNone;
   s->ctas_done = 0;
   s->error = 0;
+  s->claim = 0;
 }
 
 cudaError_t launch_init_single_scratch(SingleScratch *s, cudaStream_t st) {

@@ -22,98 +22,10 @@
 
 namespace cgi {
 
-template <uint32_t KIND, bool CARRY>
-__global__ void __launch_bounds__(kTW * 32, 1)
-    scan_single_tma_kernel(Image img, ScanJob job, RangeInfo ri, SingleScratch *scr,
-                           cg_report *out) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
-  const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5;
-  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
-  const Geo g = make_geo(job, img);
-  const bool aonly = a_only<KIND, CARRY>(g);  // super-tiles of A bits alone
-  const int64_t rows = ((aonly ? super_chunks(g) : g.nchunks) + 31) >> 5;
-  const int64_t ntiles = (rows + kR - 1) / kR;
-  const int64_t gw = (int64_t)blockIdx.x * kTW + wid;
-  const int64_t nw = (int64_t)gridDim.x * kTW;
-  if (lane == 0) {
-    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
-  LaneAcc la;
-  lane_acc_reset(la);
-  uint32_t err = 0;
-  if (lane == 0)
-    for (int s = 0; s < kNS; s++) {
-      const int64_t t = gw + (int64_t)s * nw;
-      if (t >= ntiles) continue;
-      if ((job.mode & kModeStall) && gw == 0 && s == 0)  // injected: expect bytes, copy none
-        mbar_arrive_expect_tx(smem_addr(&bars[s]), 16);
-      else if (aonly)
-        issue_tile_a_super(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
-                           smem_addr(&bars[s]));
-      else
-        issue_tile<KIND>(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
-                         smem_addr(&bars[s]));
-    }
-  uint32_t parity = 0;
-  int s = 0;
-  int64_t t = gw;
-  for (; t < ntiles; t += nw) {
-    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
-    if (!__all_sync(CG_FULL, ok)) {
-      err = 1;
-      break;
-    }
-    parity ^= 1u << s;
-    if (aonly)
-      consume_tile_a_super(g, t * kR * 32, wbase + s * kStage, lane, la);
-    else
-      consume_tile<KIND, CARRY>(g, t * kR * 32, wbase + s * kStage, lane, la);
-    __syncwarp();
-    const int64_t tn = t + (int64_t)kNS * nw;
-    if (lane == 0 && tn < ntiles) {
-      fence_proxy_async();
-      if (aonly)
-        issue_tile_a_super(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
-                           smem_addr(&bars[s]));
-      else
-        issue_tile<KIND>(g, img.a_bits, tn * kR * 32, smem_addr(wbase + s * kStage),
-                         smem_addr(&bars[s]));
-    }
-    s = s + 1 == kNS ? 0 : s + 1;
-  }
-  if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
-    for (int d = 0; d < kNS; d++) {
-      const int64_t td = t + (int64_t)d * nw;
-      if (td >= ntiles) break;
-      const int sd = (s + d) % kNS;
-      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
-      parity ^= 1u << sd;
-    }
-  }
-  single_epilogue(la, scr, ri, out, err);
-}
-
-
-// ------------------------------------------------ batched: one level
-
-// The tiles a warp processes in one level, in order: segment w first,
-// then either segments w + W, w + 2W, ... (static) or, with a claim
-// counter, the next unclaimed segment each time (dynamic: a warp that drew
-// cheap segments takes more, so the level ends with every warp busy to its
-// last segment).  Either way a warp's segments increase, and each
-// segment's tiles are taken in turn.  The copy owning a segment is found by
-// one binary search per warp, then by galloping forward from the previous
-// copy.  Producer and consumer walk the same segment sequence, the producer
-// kNS tiles ahead: the producer claims and hands each claim to the
-// consumer through a small per-warp ring in shared memory.  (Claiming one
-// segment ahead, to hide the atomic's latency, lengthened each level's
-// tail: slower on error-dense batches.)
+// Segment claims shared by both kernels: static striding (no counter) or
+// the next unclaimed segment from a counter; the producer half of a warp
+// claims and passes each claim to the consumer half through a small ring
+// in shared memory.
 constexpr int kSegQ = 8;  // ring entries: at most 2 * kNS + 3 claims outstanding
 
 struct SegSrc {
@@ -140,6 +52,118 @@ struct SegSrc {
   }
 };
 
+// A single copy is cut into segments of seg_tiles consecutive tiles: each
+// warp streams its own segment (contiguous reads and writes) and then
+// claims the next unclaimed one from the scratch's counter, which the last
+// CTA resets.  Against tiles dealt to the warps in turn this took a 4 GiB
+// host-to-device check with carry from 6.2 to 6.8 TB/s.
+template <uint32_t KIND, bool CARRY>
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_single_tma_kernel(Image img, ScanJob job, RangeInfo ri, SingleScratch *scr,
+                           cg_report *out, int64_t seg_tiles) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  uint64_t *segq = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem +
+                                                 (size_t)kTW * kNS * 8) + wid * kSegQ;
+  const Geo g = make_geo(job, img);
+  const bool aonly = a_only<KIND, CARRY>(g);  // super-tiles of A bits alone
+  const int64_t rows = ((aonly ? super_chunks(g) : g.nchunks) + 31) >> 5;
+  const int64_t ntiles = (rows + kR - 1) / kR;
+  const uint64_t nseg = (uint64_t)((ntiles + seg_tiles - 1) / seg_tiles);
+  const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
+  const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  SegSrc psrc{&scr->claim, segq, nw, 0, true};
+  SegSrc csrc{&scr->claim, segq, nw, 0, false};
+  // producer and consumer positions: segment, tile, end of the segment
+  uint64_t pseg = gw, cseg = gw;
+  int64_t pt = (int64_t)gw * seg_tiles, ct = pt;
+  int64_t pend = pt + seg_tiles < ntiles ? pt + seg_tiles : ntiles, cend = pend;
+  auto step = [&](uint64_t &seg, int64_t &t, int64_t &end, SegSrc &src) {
+    if (++t < end) return;
+    seg = src.next(seg, lane);
+    t = seg < nseg ? (int64_t)seg * seg_tiles : ntiles;
+    end = t + seg_tiles < ntiles ? t + seg_tiles : ntiles;
+  };
+  auto issue = [&](int64_t t, int s, bool stall) {
+    if (stall)  // injected: expect bytes, copy none
+      mbar_arrive_expect_tx(smem_addr(&bars[s]), 16);
+    else if (aonly)
+      issue_tile_a_super(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
+                         smem_addr(&bars[s]));
+    else
+      issue_tile<KIND>(g, img.a_bits, t * kR * 32, smem_addr(wbase + s * kStage),
+                       smem_addr(&bars[s]));
+  };
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t err = 0;
+  int issued = 0;
+  for (int s = 0; s < kNS && pt < ntiles; s++) {
+    if (lane == 0) issue(pt, s, (job.mode & kModeStall) && gw == 0 && s == 0);
+    issued++;
+    step(pseg, pt, pend, psrc);
+  }
+  uint32_t parity = 0;
+  int s = 0;
+  while (ct < ntiles) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      err = 1;
+      break;
+    }
+    parity ^= 1u << s;
+    issued--;
+    if (aonly)
+      consume_tile_a_super(g, ct * kR * 32, wbase + s * kStage, lane, la);
+    else
+      consume_tile<KIND, CARRY>(g, ct * kR * 32, wbase + s * kStage, lane, la);
+    __syncwarp();
+    if (pt < ntiles) {
+      if (lane == 0) {
+        fence_proxy_async();
+        issue(pt, s, false);
+      }
+      issued++;
+      step(pseg, pt, pend, psrc);
+    }
+    step(cseg, ct, cend, csrc);
+    s = s + 1 == kNS ? 0 : s + 1;
+  }
+  if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
+    for (int d = 0; d < issued; d++) {
+      const int sd = (s + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+  }
+  single_epilogue(la, scr, ri, out, err);
+}
+
+
+// ------------------------------------------------ batched: one level
+
+// The tiles a warp processes in one level, in order: segment w first,
+// then either segments w + W, w + 2W, ... (static) or, with a claim
+// counter, the next unclaimed segment each time (dynamic: a warp that drew
+// cheap segments takes more, so the level ends with every warp busy to its
+// last segment).  Either way a warp's segments increase, and each
+// segment's tiles are taken in turn.  The copy owning a segment is found by
+// one binary search per warp, then by galloping forward from the previous
+// copy.  Producer and consumer walk the same segment sequence, the producer
+// kNS tiles ahead: the producer claims and hands each claim to the
+// consumer through a small per-warp ring in shared memory.  (Claiming one
+// segment ahead, to hide the atomic's latency, lengthened each level's
+// tail: slower on error-dense batches.)
 struct SegIter {
   uint64_t s;      // current segment id
   uint64_t pos;    // order position of the current copy
@@ -376,17 +400,31 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
 template <uint32_t KIND, bool CARRY>
 static cudaError_t launch_tma_t(const Image &img, const ScanJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int grid, cudaStream_t st) {
+  constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
   static int per_sm = 0;
   if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(scan_single_tma_kernel<KIND, CARRY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    per_sm = tma_ctas_per_sm(scan_single_tma_kernel<KIND, CARRY>);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_single_tma_kernel<KIND, CARRY>,
+                                                      kTW * 32, smem) != cudaSuccess ||
+        n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    per_sm = n;
   }
   // `grid` counts SM-sized units of work; fill every resident CTA slot
-  scan_single_tma_kernel<KIND, CARRY><<<grid * per_sm, kTW * 32, kSmemBytes, st>>>(img, job, ri,
-                                                                                scr, out);
+  const unsigned ctas = (unsigned)(grid * per_sm);
+  // segments of up to 16 tiles (64 KiB of the anchor grid), and at least
+  // about four per warp so that claims even out the end of the copy
+  const uint64_t chunks = (job.n + 30) >> 4;  // an upper bound for any kind
+  const int64_t tiles = (int64_t)((chunks + 32 * kR - 1) / (32 * kR));
+  int64_t seg_tiles = tiles / (4 * (int64_t)ctas * kTW);
+  seg_tiles = seg_tiles < 1 ? 1 : (seg_tiles > 16 ? 16 : seg_tiles);
+  scan_single_tma_kernel<KIND, CARRY><<<ctas, kTW * 32, smem, st>>>(img, job, ri, scr, out,
+                                                                    seg_tiles);
   return cudaGetLastError();
 }
 

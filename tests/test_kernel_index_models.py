@@ -414,3 +414,25 @@ def test_dynamic_segment_claims_cover_every_tile_once():
                     live.remove(g)
             want = sorted((s, t) for s in range(n_segs) for t in range(tiles[s]))
             assert sorted(consumed) == want, (trial, dynamic)
+
+
+def test_single_copy_segments_cover_every_tile_once():
+    """scan_single_tma_kernel: a copy's tiles cut into segments of seg_tiles
+    (the last one shorter), the warps' own first segments, then claims."""
+    rng = random.Random(5)
+    for _ in range(300):
+        ntiles = rng.randrange(1, 400)
+        nw = rng.choice([1, 3, 16, 48])
+        seg_tiles = max(1, min(16, ntiles // (4 * nw)))
+        nseg = (ntiles + seg_tiles - 1) // seg_tiles
+        tiles = [min(seg_tiles, ntiles - k * seg_tiles) for k in range(nseg)]
+        consumed = []
+        shared = {"ctr": 0}
+        live = [_warp(w, nw, tiles, shared, 2, consumed) for w in range(nw)]
+        while live:
+            g = rng.choice(live)
+            try:
+                next(g)
+            except StopIteration:
+                live.remove(g)
+        assert sorted(consumed) == sorted((s, t) for s in range(nseg) for t in range(tiles[s]))
