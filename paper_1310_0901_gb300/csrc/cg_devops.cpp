@@ -109,11 +109,12 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   CG_TRY(K.b_counts.ensure(nargs));
   const uint64_t nblocks = (nargs + kFinalizeItems - 1) / kFinalizeItems;
   CG_TRY(K.b_blocksums.ensure(nblocks + 1));
-  // upload layout: arguments | order | scan segments | fill groups, then the
-  // fill spans (pointer, bytes) the lookup writes on the device
+  // upload layout: arguments | order | scan segments | fill groups | the
+  // scan's segment-claim counter (zero), then the fill spans (pointer,
+  // bytes) the lookup writes on the device
   const uint64_t a_bytes = round_up(nargs * sizeof(cg_karg), 16);
   const uint64_t o_bytes = round_up(nargs * 4, 16);
-  const uint64_t up = a_bytes + o_bytes + 16 * nargs;
+  const uint64_t up = a_bytes + o_bytes + 16 * nargs + 16;
   CG_TRY(c->k_in.ensure(up + 16 * nargs));
   CG_TRY(c->h_kin.ensure(up));
   // read-back layout: reports | error flag
@@ -125,6 +126,7 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   uint32_t *h_order = reinterpret_cast<uint32_t *>(hp + a_bytes);
   uint64_t *h_seg = reinterpret_cast<uint64_t *>(hp + a_bytes + o_bytes);
   uint64_t *h_fseg = h_seg + nargs;
+  std::memset(hp + up - 16, 0, 16);
   const bool tma = c->cfg.scan_engine != 1;  // the scans read device memory only
   const uint64_t quantum = tma ? scan_tma_tile_bytes() : 2048;
   const uint64_t seg_bytes = std::max<uint64_t>(quantum, (65536 + quantum - 1) / quantum * quantum);
@@ -143,7 +145,8 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   uint32_t *d_order = reinterpret_cast<uint32_t *>(dp + a_bytes);
   uint64_t *d_seg = reinterpret_cast<uint64_t *>(dp + a_bytes + o_bytes);
   uint64_t *fill_seg = d_seg + nargs;
-  uint64_t *fill_ptr = fill_seg + nargs, *fill_n = fill_ptr + nargs;
+  unsigned long long *claim = reinterpret_cast<unsigned long long *>(dp + up - 16);
+  uint64_t *fill_ptr = reinterpret_cast<uint64_t *>(dp + up), *fill_n = fill_ptr + nargs;
   cg_report *d_reps = reinterpret_cast<cg_report *>(c->k_out.p);
   unsigned int *d_err = reinterpret_cast<unsigned int *>(c->k_out.p + r_bytes);
   CG_CUDA(cudaMemcpyAsync(dp, hp, up, cudaMemcpyHostToDevice, st));
@@ -163,7 +166,7 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   c->stats.kernels++;
   if (segs) {
     if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, nullptr, d_err, st));
+      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, claim, d_err, st));
     else
       CG_CUDA(launch_scan_level(c->img, plan, 0, nargs, segs, c->sm_count * 8, st));
     c->stats.kernels++;

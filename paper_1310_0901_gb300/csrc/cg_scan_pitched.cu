@@ -179,12 +179,15 @@ __global__ void __launch_bounds__(kPThreads) scan_pitched_wide_kernel(Image img,
 
 // ------------------------------------------------------------- long rows
 
-// The plain copy's TMA pipeline over tiles t = (row, tile in row), tiles in
-// grid-stride order per warp; lane 0 keeps kNS tiles in flight.
+// The plain copy's TMA pipeline over tiles t = (row, tile in row): each
+// warp streams segments of seg_tiles consecutive tiles (its own first, then
+// the next unclaimed one from the scratch's counter); lane 0 keeps kNS
+// tiles in flight.
 template <uint32_t KIND, bool CARRY>
 __global__ void __launch_bounds__(kTW * 32, 1)
     scan_pitched_tma_kernel(Image img, PitchedJob pj, RangeInfo ri, SingleScratch *scr,
-                            cg_report *out, uint64_t tiles_per_row, uint64_t ntiles) {
+                            cg_report *out, uint64_t tiles_per_row, uint64_t ntiles,
+                            uint64_t seg_tiles) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
@@ -192,57 +195,72 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   const int wid = threadIdx.x >> 5;
   uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  uint64_t *segq = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem +
+                                                 (size_t)kTW * kNS * 8) + wid * kSegQ;
   const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
   const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  const uint64_t nseg = (ntiles + seg_tiles - 1) / seg_tiles;
   if (lane == 0) {
     for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
     fence_mbar_init();
   }
   __syncwarp();
+  SegSrc psrc{&scr->claim, segq, nw, 0, true};
+  SegSrc csrc{&scr->claim, segq, nw, 0, false};
+  uint64_t pseg = gw, cseg = gw;
+  uint64_t pt = gw < nseg ? gw * seg_tiles : ntiles, ct = pt;
+  uint64_t pend = pt + seg_tiles < ntiles ? pt + seg_tiles : ntiles, cend = pend;
+  auto step = [&](uint64_t &seg, uint64_t &t, uint64_t &end, SegSrc &src) {
+    if (++t < end) return;
+    seg = src.next(seg, lane);
+    t = seg < nseg ? seg * seg_tiles : ntiles;
+    end = t + seg_tiles < ntiles ? t + seg_tiles : ntiles;
+  };
+  auto issue = [&](uint64_t t, int s) {
+    const uint64_t r = t / tiles_per_row;
+    const Geo g = row_geo(pj, img, KIND, r);
+    issue_tile<KIND>(g, img.a_bits, (int64_t)(t - r * tiles_per_row) * kR * 32,
+                     smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+  };
   LaneAcc la;
   lane_acc_reset(la);
   uint32_t err = 0;
-  if (lane == 0)
-    for (int s = 0; s < kNS; s++) {
-      const uint64_t t = gw + (uint64_t)s * nw;
-      if (t < ntiles) {
-        const uint64_t r = t / tiles_per_row;
-        const Geo g = row_geo(pj, img, KIND, r);
-        issue_tile<KIND>(g, img.a_bits, (int64_t)(t - r * tiles_per_row) * kR * 32,
-                         smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
-      }
-    }
+  int issued = 0;
+  for (int s = 0; s < kNS && pt < ntiles; s++) {
+    if (lane == 0) issue(pt, s);
+    issued++;
+    step(pseg, pt, pend, psrc);
+  }
   uint32_t parity = 0;
   int s = 0;
-  uint64_t t = gw;
-  for (; t < ntiles; t += nw) {
+  while (ct < ntiles) {
     const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (parity >> s) & 1u);
     if (!__all_sync(CG_FULL, ok)) {
       err = 1;
       break;
     }
     parity ^= 1u << s;
+    issued--;
     {
-      const uint64_t r = t / tiles_per_row;
+      const uint64_t r = ct / tiles_per_row;
       const Geo g = row_geo(pj, img, KIND, r);
-      consume_tile<KIND, CARRY>(g, (int64_t)(t - r * tiles_per_row) * kR * 32, wbase + s * kStage,
-                                lane, la);
+      consume_tile<KIND, CARRY>(g, (int64_t)(ct - r * tiles_per_row) * kR * 32,
+                                wbase + s * kStage, lane, la);
     }
     __syncwarp();
-    const uint64_t tn = t + (uint64_t)kNS * nw;
-    if (lane == 0 && tn < ntiles) {
-      fence_proxy_async();
-      const uint64_t r = tn / tiles_per_row;
-      const Geo g = row_geo(pj, img, KIND, r);
-      issue_tile<KIND>(g, img.a_bits, (int64_t)(tn - r * tiles_per_row) * kR * 32,
-                       smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    if (pt < ntiles) {
+      if (lane == 0) {
+        fence_proxy_async();
+        issue(pt, s);
+      }
+      issued++;
+      step(pseg, pt, pend, psrc);
     }
+    step(cseg, ct, cend, csrc);
     s = s + 1 == kNS ? 0 : s + 1;
   }
   if (err) {  // drain: wait (bounded) for the copies this warp still has in flight
-    for (int d = 0; d < kNS; d++) {
-      const uint64_t td = t + (uint64_t)d * nw;
-      if (td >= ntiles) break;
+    for (int d = 0; d < issued; d++) {
       const int sd = (s + d) % kNS;
       mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
       parity ^= 1u << sd;
@@ -529,21 +547,31 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
   const uint64_t rows = job.height * job.depth;
   const uint64_t wpc = kPThreads / 32;
   if (kmax >= kTmaRowChunks && tma_ok) {
+    constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
     static int per_sm = 0;
     if (!per_sm) {
       cudaError_t e = cudaFuncSetAttribute(scan_pitched_tma_kernel<KIND, CARRY>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kSmemBytes);
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      per_sm = tma_ctas_per_sm(scan_pitched_tma_kernel<KIND, CARRY>);
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_pitched_tma_kernel<KIND, CARRY>,
+                                                        kTW * 32, smem) != cudaSuccess ||
+          n < 1) {
+        cudaGetLastError();
+        n = 1;
+      }
+      per_sm = n;
     }
     const uint64_t tpr = (kmax + 32 * kR - 1) / (32 * kR);
     const uint64_t ntiles = rows * tpr;
     const uint64_t need = (ntiles + kTW - 1) / kTW;
     const uint64_t cap = (uint64_t)sm_count * per_sm;
     const unsigned grid = (unsigned)(need < cap ? need : cap);
-    scan_pitched_tma_kernel<KIND, CARRY><<<grid, kTW * 32, kSmemBytes, st>>>(img, job, ri, scr, out,
-                                                                             tpr, ntiles);
+    // segments of up to 16 tiles, at least about four per warp
+    uint64_t seg_tiles = ntiles / (4 * (uint64_t)grid * kTW);
+    seg_tiles = seg_tiles < 1 ? 1 : (seg_tiles > 16 ? 16 : seg_tiles);
+    scan_pitched_tma_kernel<KIND, CARRY><<<grid, kTW * 32, smem, st>>>(img, job, ri, scr, out, tpr,
+                                                                       ntiles, seg_tiles);
     return cudaGetLastError();
   }
   if (kmax > 32) {

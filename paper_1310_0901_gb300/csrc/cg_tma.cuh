@@ -260,6 +260,36 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
 }
 
 
+// Segment claims of the TMA kernels: static striding (no counter) or
+// the next unclaimed segment from a counter; the producer half of a warp
+// claims and passes each claim to the consumer half through a small ring
+// in shared memory.
+constexpr int kSegQ = 8;  // ring entries: at most 2 * kNS + 3 claims outstanding
+
+struct SegSrc {
+  unsigned long long *ctr;  // null: static striding
+  uint64_t *q;              // this warp's ring (dynamic only)
+  uint64_t step;            // W
+  uint32_t n;               // claims pushed (producer) or popped (consumer)
+  bool prod;
+  __device__ __forceinline__ uint64_t next(uint64_t cur, int lane) {
+    if (!ctr) return cur + step;
+    uint64_t v = 0;
+    if (prod) {
+      if (lane == 0) {
+        v = step + atomicAdd(ctr, 1ull);
+        q[n & (kSegQ - 1)] = v;
+      }
+      v = __shfl_sync(CG_FULL, v, 0);
+    } else {
+      __syncwarp();
+      v = q[n & (kSegQ - 1)];
+    }
+    n++;
+    return v;
+  }
+};
+
 // CTAs of a TMA kernel that fit on one SM (shared memory bound).
 template <typename K>
 static int tma_ctas_per_sm(K kernel) {
