@@ -48,9 +48,13 @@ def _dist():
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons while running.
+    start() returns once the sampler has written its first sample, so the
+    region that follows is covered; stop() keeps the samples taken between
+    start() and stop() (by their timestamps), or the first one after start()
+    when the region was shorter than one sampling interval."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -65,14 +69,34 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t_end = time.time() + 5.0
+        while time.time() < t_end and self.proc.poll() is None:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.005)
+        self.t0 = time.time()
+
+    @staticmethod
+    def _stamp(text: str) -> float | None:
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text, fmt).timestamp()
+            except ValueError:
+                continue
+        return None
 
     def stop(self) -> dict | None:
         if self.proc is None:
             return None
+        t1 = time.time()
+        time.sleep(0.05)  # one more sample past the region's end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -82,18 +106,24 @@ class Clocks:
         rows = []
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                rows.append((self._stamp(parts[0]), float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
         if not rows:
             return None
+        inside = [r for r in rows if r[0] is not None and self.t0 <= r[0] <= t1]
+        if not inside:
+            after = [r for r in rows if r[0] is not None and r[0] >= self.t0]
+            inside = after[:1] or rows[-1:]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, x in enumerate(r) if x == "Active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
-                "reasons": reasons, "samples": len(rows)}
+        reasons = sorted({names[i] for _, _, _, r in inside for i, x in enumerate(r)
+                          if x == "Active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": inside[0][2],
+                "reasons": reasons, "samples": len(inside),
+                "region_s": round(t1 - self.t0, 3)}
 
 
 def reduce_max(value: float, device=None) -> float:
@@ -738,7 +768,7 @@ def _profiled_traffic():
     """DRAM bytes per 4 GiB launch from the committed ncu summary, or None
     when the kernel sources changed since that capture."""
     import re
-    p = os.path.join(ROOT, "profiles", "scan_single_tma_htod_256MiB.md")
+    p = os.path.join(ROOT, "profiles", "scan_single_tma_htod_1GiB_4GiB.md")
     if not os.path.exists(p):
         return None
     m = re.search(r"traffic_per_launch_bytes=(\d+); kernel_hash=(\w+)", open(p).read())
