@@ -13,7 +13,7 @@ LIB = os.path.join(PKG, "libcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
-SOURCES = ["cg_kernels.cu", "cg_scan_tma.cu", "cg_noalloc.cu", "cg_mlp.cu", "cg_scan_pitched.cu",
+SOURCES = ["cg_kernels.cu", "cg_scan_tma.cu", "cg_scan_level.cu", "cg_noalloc.cu", "cg_mlp.cu", "cg_scan_pitched.cu",
            "cg_devops_kernels.cu", "cg_host.cpp", "cg_batch.cpp", "cg_serve.cpp", "cg_pitched.cpp",
            "cg_devops.cpp", "cg_snapshot.cpp"]
 

@@ -207,7 +207,7 @@ cg_status batch_levels(cg_ctx *c, BatchBufs &K, BatchRun &B, uint32_t mode_mask,
                               cudaMemcpyDeviceToDevice, st));
     if (B.tma)
       CG_CUDA(launch_scan_level_tma(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1],
-                                    B.lev_segs[l], B.grid, K.b_claim.p + l, K.b_err.p, st));
+                                    B.lev_segs[l], B.grid, K.b_claim.p + l, K.b_err.p, l > 0, st));
     else
       CG_CUDA(launch_scan_level(c->img, B.plan, B.lev_start[l], B.lev_start[l + 1], B.lev_segs[l],
                                 B.grid, st));

@@ -166,7 +166,7 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   c->stats.kernels++;
   if (segs) {
     if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, claim, d_err, st));
+      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, claim, d_err, false, st));
     else
       CG_CUDA(launch_scan_level(c->img, plan, 0, nargs, segs, c->sm_count * 8, st));
     c->stats.kernels++;

@@ -17,10 +17,12 @@ cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const R
 int scan_single_tma_grid(int sm_count, uint64_t n);
 uint32_t scan_tma_tile_bytes();  // a batched segment is a whole number of these
 // claim: per-level counter, zero before the launch (dynamic segment
-// claiming), or null (static striding).
+// claiming), or null (static striding).  overlap: launched as a
+// programmatic dependent of the kernel before it on `st` (its prologue
+// overlaps that kernel's tail; it waits for it before reading shadow).
 cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
-                                  unsigned long long *claim, unsigned int *err_flag,
+                                  unsigned long long *claim, unsigned int *err_flag, bool overlap,
                                   cudaStream_t st);
 // New device table = old minus the entries whose bases are in the sorted
 // list `dead`, plus the sorted registrations, into nb/ns/nh (count - d + m

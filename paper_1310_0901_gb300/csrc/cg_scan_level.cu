@@ -1,0 +1,283 @@
+// cg_scan_level.cu -- one dependency level of a batch on the TMA engine.
+//
+// The level's copies are cut into segments; each warp runs its own
+// pipeline of kNS shared-memory stages (as the single-copy kernel) over the
+// segments it takes, classifies and carries each tile out of shared memory
+// and adds its counts to the copy's accumulator.  Every wait is bounded;
+// on expiry the warp drains its copies in flight and raises the batch's
+// error flag.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cg_tma.cuh"
+#include "cg_launch.h"
+
+namespace cgi {
+
+// ------------------------------------------------ batched: one level
+
+// The tiles a warp processes in one level, in order: segment w first,
+// then either segments w + W, w + 2W, ... (static) or, with a claim
+// counter, the next unclaimed segment each time (dynamic: a warp that drew
+// cheap segments takes more, so the level ends with every warp busy to its
+// last segment).  Either way a warp's segments increase, and each
+// segment's tiles are taken in turn.  The copy owning a segment is found by
+// one binary search per warp, then by galloping forward from the previous
+// copy.  Producer and consumer walk the same segment sequence, the producer
+// kNS tiles ahead: the producer claims and hands each claim to the
+// consumer through a small per-warp ring in shared memory.  (Claiming one
+// segment ahead, to hide the atomic's latency, lengthened each level's
+// tail: slower on error-dense batches.)
+struct SegIter {
+  uint64_t s;      // current segment id
+  uint64_t pos;    // order position of the current copy
+  uint64_t first;  // its first segment id
+  uint64_t next;   // first segment id of the next position (or ~0)
+  uint32_t req;    // its request
+  ScanJob job;
+  Geo g;
+  int64_t t, t_end;  // tile range of the segment
+  bool valid;
+};
+
+__device__ __forceinline__ void seg_set_pos(SegIter &it, const BatchPlan &p, const Image &img,
+                                            uint64_t pos, uint64_t pos_end) {
+  it.pos = pos;
+  it.first = __ldg(p.seg_first + pos);
+  it.next = pos + 1 < pos_end ? __ldg(p.seg_first + pos + 1) : ~0ull;
+  it.req = __ldg(p.order + pos);
+  it.job = p.jobs[it.req];
+  it.job.mode &= p.mode_mask;
+  it.g = make_geo(it.job, img);
+}
+
+// last position in [lo, hi) whose first segment is <= s, given that
+// position lo qualifies
+__device__ __forceinline__ uint64_t seg_search(const BatchPlan &p, uint64_t lo, uint64_t hi,
+                                               uint64_t s) {
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (__ldg(p.seg_first + mid) <= s)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Settle on segment it.s (or the first non-empty one after it).
+__device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, const Image &img,
+                                           uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                           int lane) {
+  const int64_t seg_rows = p.seg_chunks >> 5;
+  while (it.s < n_segs) {
+    if (it.s >= it.next) {  // gallop forward from the next position
+      uint64_t lo = it.pos + 1, span = 1, hi = lo + 1;
+      while (hi < pos_end && __ldg(p.seg_first + hi) <= it.s) {
+        lo = hi;
+        span <<= 1;
+        hi = lo + span;
+      }
+      if (hi > pos_end) hi = pos_end;
+      seg_set_pos(it, p, img, seg_search(p, lo, hi, it.s), pos_end);
+    }
+    const int64_t k = (int64_t)(it.s - it.first);
+    const bool aonly = it.job.kind == CG_DTOH && !(it.job.mode & (kModeCarry | kModeReadDev));
+    const int64_t rows = ((aonly ? super_chunks(it.g) : it.g.nchunks) + 31) >> 5;
+    const int64_t r0 = k * seg_rows;
+    const int64_t r1 = r0 + seg_rows < rows ? r0 + seg_rows : rows;
+    if (r0 < r1) {
+      it.t = r0 / kR;
+      it.t_end = (r1 + kR - 1) / kR;
+      it.valid = true;
+      return;
+    }
+    it.s = src.next(it.s, lane);  // an empty trailing segment (the count was an upper bound)
+  }
+  it.valid = false;
+}
+
+__device__ __forceinline__ void seg_begin(SegIter &it, const BatchPlan &p, const Image &img,
+                                          uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
+                                          uint64_t s, SegSrc &src, int lane) {
+  it.s = s;
+  it.valid = false;
+  if (s >= n_segs) return;
+  seg_set_pos(it, p, img, seg_search(p, pos_begin, pos_end, s), pos_end);
+  seg_settle(it, p, img, pos_end, n_segs, src, lane);
+}
+
+__device__ __forceinline__ void seg_advance(SegIter &it, const BatchPlan &p, const Image &img,
+                                            uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                            int lane) {
+  if (++it.t < it.t_end) return;
+  it.s = src.next(it.s, lane);
+  seg_settle(it, p, img, pos_end, n_segs, src, lane);
+}
+
+__device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bits, uint32_t st,
+                                          uint32_t bar) {
+  const int64_t c0 = it.t * kR * 32;
+  switch (it.job.kind) {
+    case CG_HTOD:
+      issue_tile<CG_HTOD>(it.g, a_bits, c0, st, bar);
+      break;
+    case CG_DTOH:
+      if (!(it.job.mode & (kModeCarry | kModeReadDev)))
+        issue_tile_a_super(it.g, a_bits, c0, st, bar);
+      else
+        issue_tile<CG_DTOH>(it.g, a_bits, c0, st, bar);
+      break;
+    default:
+      issue_tile<CG_DTOD>(it.g, a_bits, c0, st, bar);
+      break;
+  }
+}
+
+__device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp, int lane,
+                                            LaneAcc &la) {
+  const int64_t c0 = it.t * kR * 32;
+  const bool carry = it.job.mode & kModeCarry;
+  switch (it.job.kind) {
+    case CG_HTOD:
+      if (carry)
+        consume_tile<CG_HTOD, true>(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_HTOD, false>(it.g, c0, sp, lane, la);
+      break;
+    case CG_DTOH:
+      if (carry)
+        consume_tile<CG_DTOH, true>(it.g, c0, sp, lane, la);
+      else if (!(it.job.mode & kModeReadDev))
+        consume_tile_a_super(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_DTOH, false>(it.g, c0, sp, lane, la);
+      break;
+    default:
+      if (carry)
+        consume_tile<CG_DTOD, true>(it.g, c0, sp, lane, la);
+      else
+        consume_tile<CG_DTOD, false>(it.g, c0, sp, lane, la);
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(kTW * 32, 1)
+    scan_level_tma_kernel(Image img, BatchPlan p, uint64_t pos_begin, uint64_t pos_end,
+                          uint64_t n_segs, unsigned long long *claim, unsigned int *err_flag) {
+  // levels launched back to back may overlap: the next level's grid is
+  // scheduled as this one's CTAs leave, runs its prologue (which reads only
+  // the batch's plan), and waits for this grid before touching any shadow
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
+  uint64_t *segq = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem +
+                                                 (size_t)kTW * kNS * 8) + wid * kSegQ;
+  const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
+  const uint64_t nw = (uint64_t)gridDim.x * kTW;
+  if (lane == 0) {
+    for (int s = 0; s < kNS; s++) mbar_init(smem_addr(&bars[s]), 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  SegSrc psrc{claim, segq, nw, 0, true};
+  SegSrc csrc{claim, segq, nw, 0, false};
+  SegIter prod, cons;
+  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, psrc, lane);
+  cons = prod;  // the first segment is the warp's own (w), settled identically
+  csrc.n = psrc.n;
+  asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous level is complete
+  int issued = 0;
+  for (int s = 0; s < kNS && prod.valid; s++) {
+    if (lane == 0) seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    issued++;
+    seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
+  }
+  LaneAcc la;
+  lane_acc_reset(la);
+  uint32_t parity = 0;
+  int stage = 0;
+  bool failed = false;
+  while (cons.valid) {
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), (parity >> stage) & 1u);
+    if (!__all_sync(CG_FULL, ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u << stage;
+    issued--;
+    seg_consume(cons, wbase + stage * kStage, lane, la);
+    __syncwarp();
+    if (prod.valid) {
+      if (lane == 0) {
+        fence_proxy_async();
+        seg_issue(prod, img.a_bits, smem_addr(wbase + stage * kStage), smem_addr(&bars[stage]));
+      }
+      issued++;
+      seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
+    }
+    const uint32_t req = cons.req;
+    const uint64_t seg = cons.s;
+    seg_advance(cons, p, img, pos_end, n_segs, csrc, lane);
+    (void)seg;
+    // a warp's segments increase, so it never comes back to a copy it left:
+    // its counts for that copy are flushed when the copy changes
+    if (!cons.valid || cons.req != req) warp_flush(la, &p.acc[req], lane);
+    stage = stage + 1 == kNS ? 0 : stage + 1;
+  }
+  if (failed) {  // drain the copies still in flight, bounded
+    for (int d = 0; d < issued; d++) {
+      const int sd = (stage + d) % kNS;
+      mbar_wait_bounded(smem_addr(&bars[sd]), (parity >> sd) & 1u);
+      parity ^= 1u << sd;
+    }
+    if (lane == 0) atomicOr(err_flag, 1u);
+  }
+}
+
+cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
+                                  uint64_t pos_end, uint64_t n_segs, int max_ctas,
+                                  unsigned long long *claim, unsigned int *err_flag, bool overlap,
+                                  cudaStream_t st) {
+  if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
+  constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(scan_level_tma_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_level_tma_kernel, kTW * 32, smem) !=
+            cudaSuccess ||
+        n < 1)
+      n = 1;
+    per_sm = n;
+  }
+  const uint64_t cap = (uint64_t)max_ctas * (uint64_t)per_sm;  // max_ctas counts SMs
+  const uint64_t ctas = (n_segs + kTW - 1) / kTW;
+  const unsigned g = (unsigned)(ctas < cap ? ctas : cap);
+  if (overlap) {  // programmatic dependent launch after the previous level
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g);
+    cfg.blockDim = dim3(kTW * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, scan_level_tma_kernel, img, p, pos_begin, pos_end, n_segs,
+                              claim, err_flag);
+  }
+  scan_level_tma_kernel<<<g, kTW * 32, smem, st>>>(img, p, pos_begin, pos_end, n_segs, claim,
+                                                   err_flag);
+  return cudaGetLastError();
+}
+
+}  // namespace cgi

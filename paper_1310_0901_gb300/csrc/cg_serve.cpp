@@ -597,7 +597,7 @@ struct ServeEngine {
                                   c->sm_count * 8, s));
       else
         CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
-                                      c->sm_count, nullptr, d_err, s));
+                                      c->sm_count, nullptr, d_err, false, s));
       kernels++;
     }
     CG_CUDA(launch_serve_finalize(plan, d_err, R.h_down.p, s));
