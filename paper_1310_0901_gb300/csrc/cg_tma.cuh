@@ -233,7 +233,11 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   }
   const uint4 *vs = reinterpret_cast<const uint4 *>(sp);
   const uint32_t *as = reinterpret_cast<const uint32_t *>(sp + kVBytes);
-  const int64_t aorig = floor16((g.hb0 + 16 * c0) >> 3);
+  // bit offset of the tile's first chunk in the tile's A window (which
+  // starts at the 16-byte-aligned A byte holding it): in [0, 136), so the
+  // per-chunk A addressing below stays in 32-bit arithmetic
+  const int64_t p0 = g.hb0 + 16 * c0;
+  const int32_t qbase = (int32_t)(p0 - 8 * floor16(p0 >> 3));
   const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
   const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
 #pragma unroll 4
@@ -247,9 +251,9 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
     }
     uint32_t a16 = 0xFFFFu;
     if (KIND != CG_DTOD) {
-      const int64_t q = g.hb0 + 16 * c;
-      const int sh = (int)(q & 31);
-      const int64_t wi = (((q >> 5) << 2) - aorig) >> 2;
+      const int32_t qb = qbase + 16 * k;
+      const int sh = qb & 31;
+      const int wi = qb >> 5;
       const uint32_t w0 = as[wi];
       const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
       a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;

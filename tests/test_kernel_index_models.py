@@ -436,3 +436,23 @@ def test_single_copy_segments_cover_every_tile_once():
             except StopIteration:
                 live.remove(g)
         assert sorted(consumed) == sorted((s, t) for s in range(nseg) for t in range(tiles[s]))
+
+
+def test_tile_a_addressing_32bit_equals_64bit():
+    """consume_tile's A word index and shift, computed in 32 bits from the
+    tile's base, equal the 64-bit form and stay inside the A window."""
+    rng = random.Random(9)
+    abytes = 64 * kR + 64
+    for _ in range(20000):
+        hb0 = rng.randrange(-15, 1 << 40)
+        c0 = rng.randrange(0, 1 << 28) * kR * 32
+        p0 = hb0 + 16 * c0
+        aorig = (p0 >> 3) & ~15
+        qbase = p0 - 8 * aorig
+        assert 0 <= qbase < 136
+        for k in (0, 1, 31, 32, 33, rng.randrange(kR * 32), kR * 32 - 1):
+            q = hb0 + 16 * (c0 + k)
+            wi64 = (((q >> 5) << 2) - aorig) >> 2
+            qb = qbase + 16 * k
+            assert (qb >> 5, qb & 31) == (wi64, q & 31)
+            assert 4 * (qb >> 5) + 8 <= abytes
