@@ -28,6 +28,11 @@ namespace cgi {
 // consumer through a small per-warp ring in shared memory.  (Claiming one
 // segment ahead, to hide the atomic's latency, lengthened each level's
 // tail: slower on error-dense batches.)
+#ifndef CG_LEVEL_UNROLL
+#define CG_LEVEL_UNROLL 2
+#endif
+constexpr int kLevelUnroll = CG_LEVEL_UNROLL;  // rows unrolled per consumed tile
+
 struct SegIter {
   uint64_t s;      // current segment id
   uint64_t pos;    // order position of the current copy
@@ -141,23 +146,23 @@ __device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp
   switch (it.job.kind) {
     case CG_HTOD:
       if (carry)
-        consume_tile<CG_HTOD, true>(it.g, c0, sp, lane, la);
+        consume_tile<CG_HTOD, true, kLevelUnroll>(it.g, c0, sp, lane, la);
       else
-        consume_tile<CG_HTOD, false>(it.g, c0, sp, lane, la);
+        consume_tile<CG_HTOD, false, kLevelUnroll>(it.g, c0, sp, lane, la);
       break;
     case CG_DTOH:
       if (carry)
-        consume_tile<CG_DTOH, true>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOH, true, kLevelUnroll>(it.g, c0, sp, lane, la);
       else if (!(it.job.mode & kModeReadDev))
         consume_tile_a_super(it.g, c0, sp, lane, la);
       else
-        consume_tile<CG_DTOH, false>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOH, false, kLevelUnroll>(it.g, c0, sp, lane, la);
       break;
     default:
       if (carry)
-        consume_tile<CG_DTOD, true>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOD, true, kLevelUnroll>(it.g, c0, sp, lane, la);
       else
-        consume_tile<CG_DTOD, false>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOD, false, kLevelUnroll>(it.g, c0, sp, lane, la);
       break;
   }
 }

@@ -224,7 +224,9 @@ __device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, co
 }
 
 // All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
-template <uint32_t KIND, bool CARRY>
+// U: rows unrolled (the level kernel, which inlines every kind, takes fewer
+// to keep its code small).
+template <uint32_t KIND, bool CARRY, int U = 4>
 __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uint8_t *sp,
                                              int lane, LaneAcc &la) {
   if (KIND == CG_DTOH && !CARRY && !g.has_vin) {  // nothing but the destination's A bits
@@ -240,7 +242,7 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   const int32_t qbase = (int32_t)(p0 - 8 * floor16(p0 >> 3));
   const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
   const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
-#pragma unroll 4
+#pragma unroll U
   for (int u = 0; u < kR; u++) {
     const int k = 32 * u + lane;
     const int64_t c = c0 + k;
