@@ -575,11 +575,11 @@ struct cg_ctx {
     float best_ms = 0.f;
   };
   std::vector<OnlineTune> online;
-  // kernel-argument checks: one upload (arguments | order | scan segments |
-  // fill groups) then the fill spans the lookup writes; one read-back
-  // (reports | error flag)
+  // kernel-argument checks: one upload (jobs | range verdicts |
+  // accumulators | order | scan segments | fill spans | claim counter |
+  // error flag) and the pinned buffer the finalize kernel writes (error
+  // flag | reports)
   cgi::DevBuf<uint8_t> k_in;
-  cgi::DevBuf<uint8_t> k_out;
   cgi::PinBuf<uint8_t> h_kin, h_kout;
   // device arrays (Fig. 2's second list): handle -> dimensions and shadow
   struct ArrayInfo {

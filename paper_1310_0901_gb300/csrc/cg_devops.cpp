@@ -2,12 +2,12 @@
 //
 // A memset is one range check on the host mirror plus a fill of the written
 // bytes' V shadow with zeros (one launch).  The arguments of a kernel launch
-// are checked together on the GPU: a lookup kernel over the device table
-// gives every argument its verdicts, the batched scan kernels count the
-// undefined bytes of in-range read arguments (one level: nothing is
-// carried, every read sees the state before the launch), the finalize
-// kernel builds the reports, and a fill kernel then defines the in-range
-// write arguments.
+// are checked together: their ranges on the host mirror (as single checks),
+// then on the GPU the batched scan kernel counts the undefined bytes of
+// in-range read arguments (one level: nothing is carried, every read sees
+// the state before the launch), a finalize kernel writes the reports into
+// pinned host memory, and a fill kernel defines the in-range write
+// arguments.  One upload, three launches, one synchronisation.
 #include <cuda_runtime.h>
 
 #include "cg_ctx.h"
@@ -98,90 +98,109 @@ cg_status cg_check_kernel_args(cg_ctx *c, const cg_karg *args, uint64_t nargs, c
   if (nargs > 0xFFFFFFFFull) return set_error(CG_E_TOO_BIG, "at most 2^32-1 arguments per call");
   if (c->bb[0].ticket || c->bb[1].ticket)
     return set_error(CG_E_STATE, "batches still in flight (cg_batch_wait first)");
-  BatchBufs &K = c->bb[0];
   NvtxRange range("cg kernel arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CG_TRY(flush_fills(c, st));
-  CG_TRY(ensure_device_table(c, st));
-  CG_TRY(K.b_jobs.ensure(nargs));
-  CG_TRY(K.b_info.ensure(nargs));
-  CG_TRY(K.b_acc.ensure(nargs));
-  CG_TRY(K.b_counts.ensure(nargs));
-  const uint64_t nblocks = (nargs + kFinalizeItems - 1) / kFinalizeItems;
-  CG_TRY(K.b_blocksums.ensure(nblocks + 1));
-  // upload layout: arguments | order | scan segments | fill groups | the
-  // scan's segment-claim counter (zero), then the fill spans (pointer,
-  // bytes) the lookup writes on the device
-  const uint64_t a_bytes = round_up(nargs * sizeof(cg_karg), 16);
-  const uint64_t o_bytes = round_up(nargs * 4, 16);
-  const uint64_t up = a_bytes + o_bytes + 16 * nargs + 16;
-  CG_TRY(c->k_in.ensure(up + 16 * nargs));
+  // upload layout (16-byte aligned parts): jobs | range verdicts |
+  // accumulators | order | scan segments | fill spans (pointer, bytes,
+  // first group) | segment-claim counter | error flag; the last two zero
+  const uint64_t o_info = round_up(nargs * sizeof(ScanJob), 16);
+  const uint64_t o_acc = o_info + round_up(nargs * sizeof(RangeInfo), 16);
+  const uint64_t o_order = o_acc + round_up(nargs * sizeof(Acc), 16);
+  const uint64_t o_seg = o_order + round_up(nargs * 4, 16);
+  const uint64_t o_fill = o_seg + round_up(nargs * 8, 16);
+  const uint64_t o_claim = o_fill + round_up(3 * nargs * 8, 16);
+  const uint64_t up = o_claim + 32;
+  CG_TRY(c->k_in.ensure(up));
   CG_TRY(c->h_kin.ensure(up));
-  // read-back layout: reports | error flag
-  const uint64_t r_bytes = round_up(nargs * sizeof(cg_report), 16);
-  CG_TRY(c->k_out.ensure(r_bytes + 16));
-  CG_TRY(c->h_kout.ensure(r_bytes + 16));
+  // read-back (written by the finalize kernel into pinned memory): error
+  // flag (16 bytes) | reports
+  CG_TRY(c->h_kout.ensure(16 + nargs * sizeof(cg_report)));
   uint8_t *hp = c->h_kin.p;
-  std::memcpy(hp, args, nargs * sizeof(cg_karg));
-  uint32_t *h_order = reinterpret_cast<uint32_t *>(hp + a_bytes);
-  uint64_t *h_seg = reinterpret_cast<uint64_t *>(hp + a_bytes + o_bytes);
-  uint64_t *h_fseg = h_seg + nargs;
-  std::memset(hp + up - 16, 0, 16);
-  const bool tma = c->cfg.scan_engine != 1;  // the scans read device memory only
+  ScanJob *h_jobs = reinterpret_cast<ScanJob *>(hp);
+  RangeInfo *h_info = reinterpret_cast<RangeInfo *>(hp + o_info);
+  Acc *h_acc = reinterpret_cast<Acc *>(hp + o_acc);
+  uint32_t *h_order = reinterpret_cast<uint32_t *>(hp + o_order);
+  uint64_t *h_seg = reinterpret_cast<uint64_t *>(hp + o_seg);
+  uint64_t *h_fptr = reinterpret_cast<uint64_t *>(hp + o_fill);
+  uint64_t *h_fn = h_fptr + nargs, *h_fseg = h_fn + nargs;
+  std::memset(hp + o_claim, 0, 32);
+  const bool tma = c->cfg.scan_engine != 1 && !c->img_on_host;  // the scans read device memory only
   const uint64_t quantum = tma ? scan_tma_tile_bytes() : 2048;
   const uint64_t seg_bytes = std::max<uint64_t>(quantum, (65536 + quantum - 1) / quantum * quantum);
   const uint64_t seg_chunks = seg_bytes / 16;
   uint64_t segs = 0, fgroups = 0;
+  // the range part of every argument on the host mirror (as single
+  // checks): its read side as a copy source, its write side as a
+  // destination (R23)
   for (uint64_t i = 0; i < nargs; i++) {
+    const cg_karg &q = args[i];
+    RangeInfo ri{};
+    ri.kind = CG_DTOD;  // undefined bytes of a device source: the warning class
+    ri.n = q.bytes;
+    ScanJob j{};
+    j.kind = CG_DTOD;
+    j.n = q.bytes;
+    uint64_t sh = 0, dsh = 0, fn = 0;
+    if (q.access & CG_ARG_READ) {
+      const bool ok = host_side(c, q.ptr, q.bytes, &ri.found_src, &ri.base_src, &ri.size_src, &sh,
+                                &ri.flags, CG_F_UNALLOC_SRC, CG_F_OVERRUN_SRC);
+      if (ok && q.bytes) {
+        j.mode = kModeReadDev;
+        j.dev_src = sh;
+      }
+    }
+    if (q.access & CG_ARG_WRITE) {
+      const bool ok = host_side(c, q.ptr, q.bytes, &ri.found_dst, &ri.base_dst, &ri.size_dst, &dsh,
+                                &ri.flags, CG_F_UNALLOC_DST, CG_F_OVERRUN_DST);
+      if (ok && c->cfg.carry) fn = q.bytes;
+    }
+    h_jobs[i] = j;
+    h_info[i] = ri;
+    h_acc[i] = Acc{0, 0, kNone, kNone};
     h_order[i] = (uint32_t)i;
     h_seg[i] = segs;
+    if (j.mode & kModeReadDev) segs += (((q.bytes + 30) >> 4) + seg_chunks - 1) / seg_chunks;
+    h_fptr[i] = dsh;
+    h_fn[i] = fn;
     h_fseg[i] = fgroups;
-    const uint64_t n = args[i].bytes;
-    if ((args[i].access & CG_ARG_READ) && n) segs += (((n + 30) >> 4) + seg_chunks - 1) / seg_chunks;
-    if (args[i].access & CG_ARG_WRITE) fgroups += fill_span_groups(n);
+    fgroups += fill_span_groups(fn);
   }
   uint8_t *dp = c->k_in.p;
-  const cg_karg *d_args = reinterpret_cast<const cg_karg *>(dp);
-  uint32_t *d_order = reinterpret_cast<uint32_t *>(dp + a_bytes);
-  uint64_t *d_seg = reinterpret_cast<uint64_t *>(dp + a_bytes + o_bytes);
-  uint64_t *fill_seg = d_seg + nargs;
-  unsigned long long *claim = reinterpret_cast<unsigned long long *>(dp + up - 16);
-  uint64_t *fill_ptr = reinterpret_cast<uint64_t *>(dp + up), *fill_n = fill_ptr + nargs;
-  cg_report *d_reps = reinterpret_cast<cg_report *>(c->k_out.p);
-  unsigned int *d_err = reinterpret_cast<unsigned int *>(c->k_out.p + r_bytes);
   CG_CUDA(cudaMemcpyAsync(dp, hp, up, cudaMemcpyHostToDevice, st));
   BatchPlan plan{};
-  plan.reqs = nullptr;  // only the lookup reads copies; the argument lookup has its own
-  plan.order = d_order;
-  plan.seg_first = d_seg;
+  plan.reqs = nullptr;
+  plan.jobs = reinterpret_cast<ScanJob *>(dp);
+  plan.info = reinterpret_cast<RangeInfo *>(dp + o_info);
+  plan.acc = reinterpret_cast<Acc *>(dp + o_acc);
+  plan.order = reinterpret_cast<const uint32_t *>(dp + o_order);
+  plan.seg_first = reinterpret_cast<const uint64_t *>(dp + o_seg);
   plan.stage = nullptr;
-  plan.jobs = K.b_jobs.p;
-  plan.info = K.b_info.p;
-  plan.acc = K.b_acc.p;
   plan.nreq = nargs;
   plan.seg_chunks = (uint32_t)seg_chunks;
   plan.mode_mask = ~0u;
-  DevTable dt{c->t_base.p, c->t_size.p, c->t_shadow.p, c->t_count};
-  CG_CUDA(launch_karg_lookup(dt, plan, d_args, fill_ptr, fill_n, (int)c->cfg.carry, d_err, st));
-  c->stats.kernels++;
-  if (segs) {
+  const uint64_t *d_fill = reinterpret_cast<const uint64_t *>(dp + o_fill);
+  unsigned long long *claim = reinterpret_cast<unsigned long long *>(dp + o_claim);
+  unsigned int *d_err = reinterpret_cast<unsigned int *>(dp + o_claim + 16);
+  if (segs) {  // one level: nothing is carried, every read sees the state before the launch
     if (tma)
-      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, claim, d_err, false, st));
+      CG_CUDA(launch_scan_level_tma(c->img, plan, 0, nargs, segs, c->sm_count, claim, d_err, false,
+                                    st));
     else
       CG_CUDA(launch_scan_level(c->img, plan, 0, nargs, segs, c->sm_count * 8, st));
     c->stats.kernels++;
   }
-  CG_CUDA(launch_finalize(plan, d_reps, K.b_counts.p, K.b_blocksums.p, kFinalizeItems, st));
+  CG_CUDA(launch_finalize_host(plan, d_err, c->h_kout.p, st));
   c->stats.kernels++;
-  if (fgroups) {  // after the scans on the same stream: reads see the state before the launch
-    CG_CUDA(launch_fill_spans(fill_ptr, fill_n, fill_seg, nargs, fgroups, 0x00, c->sm_count, st));
+  if (fgroups) {  // after the scan on the same stream
+    CG_CUDA(launch_fill_spans(d_fill, d_fill + nargs, d_fill + 2 * nargs, nargs, fgroups, 0x00,
+                              c->sm_count, st));
     c->stats.kernels++;
   }
-  CG_CUDA(cudaMemcpyAsync(c->h_kout.p, c->k_out.p, r_bytes + 16, cudaMemcpyDeviceToHost, st));
   CG_CUDA(cudaStreamSynchronize(st));
-  if (reinterpret_cast<const unsigned int *>(c->h_kout.p + r_bytes)[0])
+  if (reinterpret_cast<const unsigned int *>(c->h_kout.p)[0])
     return set_error(CG_E_TIMEOUT, "a bounded wait in the scan kernel ran out");
-  const cg_report *h_reps = reinterpret_cast<const cg_report *>(c->h_kout.p);
+  const cg_report *h_reps = reinterpret_cast<const cg_report *>(c->h_kout.p + 16);
   if (reps) std::memcpy(reps, h_reps, nargs * sizeof(cg_report));
   for (uint64_t i = 0; i < nargs; i++) count_stats(c, h_reps[i]);
   return CG_OK;

@@ -3,15 +3,13 @@
 // A memset or a kernel's write argument makes its device bytes defined:
 // their V shadow is filled with zeros (1 byte written per byte, HBM-bound).
 // Fills are laid out on the 16-byte grid of the span they cover: whole
-// aligned vectors inside, byte stores at a ragged head or tail.  Kernel
-// arguments are looked up in the device copy of the allocation table (the
-// same search as batched copies); the undefined-byte scan of read
-// arguments runs on the batched scan kernels.
+// aligned vectors inside, byte stores at a ragged head or tail.  The
+// undefined-byte scan of a kernel's read arguments runs on the batched scan
+// kernels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "cg_device.cuh"
-#include "cg_table.cuh"
 #include "cg_launch.h"
 
 namespace cgi {
@@ -128,72 +126,5 @@ cudaError_t launch_fill_spans(const uint64_t *ptr, const uint64_t *n, const uint
 }
 
 // ------------------------------------------------------ kernel arguments
-
-// Per argument: the range verdict of its read side (as a copy source) and
-// its write side (as a destination); a read job for an in-range read
-// argument (a device->device scan of its V with nothing carried); the span
-// a valid write argument will define (n = 0 otherwise).
-__global__ void __launch_bounds__(256) karg_lookup_kernel(DevTable t, BatchPlan p,
-                                                          const cg_karg *args, uint64_t *fill_ptr,
-                                                          uint64_t *fill_n, uint32_t stride,
-                                                          int carry_on, unsigned int *err) {
-  extern __shared__ uint64_t spl[];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;  // the scan after this may set it
-  const uint64_t nspl = (t.count + stride - 1) / stride;
-  for (uint64_t k = threadIdx.x; k < nspl; k += blockDim.x) spl[k] = __ldg(t.base + k * stride);
-  __syncthreads();
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.nreq;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const cg_karg q = args[i];
-    RangeInfo ri;
-    ri.flags = 0;
-    ri.kind = CG_DTOD;  // undefined bytes of a device source: the warning class
-    ri.n = q.bytes;
-    ri.found_dst = ri.found_src = 0;
-    ri.base_dst = ri.size_dst = ri.base_src = ri.size_src = 0;
-    ScanJob j;
-    j.kind = CG_DTOD;
-    j.mode = 0;
-    j.n = q.bytes;
-    j.host_off = 0;
-    j.dev_src = 0;
-    j.dev_dst = 0;
-    uint64_t sh = 0, dsh = 0;
-    if (q.access & CG_ARG_READ) {
-      const bool ok = table_side(t, spl, nspl, stride, q.ptr, q.bytes, &ri.found_src, &ri.base_src,
-                                 &ri.size_src, &sh, &ri.flags, CG_F_UNALLOC_SRC, CG_F_OVERRUN_SRC);
-      if (ok && q.bytes) {
-        j.mode = kModeReadDev;
-        j.dev_src = sh;
-      }
-    }
-    uint64_t fn = 0;
-    if (q.access & CG_ARG_WRITE) {
-      const bool ok = table_side(t, spl, nspl, stride, q.ptr, q.bytes, &ri.found_dst, &ri.base_dst,
-                                 &ri.size_dst, &dsh, &ri.flags, CG_F_UNALLOC_DST, CG_F_OVERRUN_DST);
-      if (ok && carry_on) fn = q.bytes;
-    }
-    fill_ptr[i] = dsh;
-    fill_n[i] = fn;
-    p.jobs[i] = j;
-    p.info[i] = ri;
-    p.acc[i] = Acc{0, 0, kNone, kNone};
-  }
-}
-
-cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_karg *args,
-                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, unsigned int *err,
-                               cudaStream_t st) {
-  if (p.nreq == 0) return cudaSuccess;
-  uint32_t stride = 256;
-  while ((t.count + stride - 1) / stride > 6144) stride <<= 1;
-  const uint64_t nspl = (t.count + stride - 1) / stride;
-  const size_t smem = (size_t)(nspl ? nspl : 1) * sizeof(uint64_t);
-  uint64_t blocks = (p.nreq + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  karg_lookup_kernel<<<(unsigned)blocks, 256, smem, st>>>(t, p, args, fill_ptr, fill_n, stride,
-                                                          carry, err);
-  return cudaGetLastError();
-}
 
 }  // namespace cgi

@@ -336,7 +336,6 @@ cg_status cg_destroy(cg_ctx *c) {
   c->bb[0].release();
   c->bb[1].release();
   c->k_in.release();
-  c->k_out.release();
   c->h_kin.release();
   c->h_kout.release();
   if (c->side) cudaStreamDestroy(c->side);

@@ -422,10 +422,11 @@ __global__ void __launch_bounds__(kThreads) finalize_kernel(BatchPlan p, cg_repo
   if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-// Reports of a serving round written straight into pinned host memory (no
-// read-back copy): out = error flag (16 bytes) | reports.  Runs after the
-// round's level kernels on the same stream, so the flag is final.
-__global__ void __launch_bounds__(kThreads) serve_finalize_kernel(BatchPlan p,
+// Reports written straight into pinned host memory (no read-back copy):
+// out = error flag (16 bytes) | reports.  Runs after the level kernels on
+// the same stream, so the flag is final (serving rounds, kernel-argument
+// checks).
+__global__ void __launch_bounds__(kThreads) finalize_host_kernel(BatchPlan p,
                                                                   const unsigned int *err,
                                                                   uint8_t *out) {
   const uint64_t i = (uint64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -437,10 +438,10 @@ __global__ void __launch_bounds__(kThreads) serve_finalize_kernel(BatchPlan p,
   }
 }
 
-cudaError_t launch_serve_finalize(const BatchPlan &p, const unsigned int *err, uint8_t *out,
+cudaError_t launch_finalize_host(const BatchPlan &p, const unsigned int *err, uint8_t *out,
                                   cudaStream_t st) {
   const uint64_t nb = (p.nreq + kThreads - 1) / kThreads;
-  serve_finalize_kernel<<<(unsigned)(nb ? nb : 1), kThreads, 0, st>>>(p, err, out);
+  finalize_host_kernel<<<(unsigned)(nb ? nb : 1), kThreads, 0, st>>>(p, err, out);
   return cudaGetLastError();
 }
 

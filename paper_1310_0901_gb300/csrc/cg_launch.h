@@ -36,9 +36,9 @@ cudaError_t launch_lookup(const DevTable &t, const BatchPlan &p, int strict, int
 cudaError_t launch_job_modes(const BatchPlan &p, uint8_t *modes, cudaStream_t st);
 cudaError_t launch_scan_level(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                               uint64_t pos_end, uint64_t n_segs, int grid, cudaStream_t st);
-// Serving: the error flag and the reports into `out` (pinned host memory
-// the kernel writes directly): flag (16 bytes) | nreq reports.
-cudaError_t launch_serve_finalize(const BatchPlan &p, const unsigned int *err, uint8_t *out,
+// The error flag and the reports into `out` (pinned host memory the
+// kernel writes directly): flag (16 bytes) | nreq reports.
+cudaError_t launch_finalize_host(const BatchPlan &p, const unsigned int *err, uint8_t *out,
                                   cudaStream_t st);
 cudaError_t launch_finalize(const BatchPlan &p, cg_report *reps, uint32_t *counts,
                             uint64_t *block_sums, int items_per_block, cudaStream_t st);
@@ -69,9 +69,5 @@ uint64_t fill_span_groups(uint64_t n);  // fill groups of a span of n bytes
 cudaError_t launch_fill_spans(const uint64_t *ptr, const uint64_t *n, const uint64_t *seg_first,
                               uint64_t count, uint64_t nsegs, uint8_t value, int sm_count,
                               cudaStream_t st);
-cudaError_t launch_karg_lookup(const DevTable &t, const BatchPlan &p, const cg_karg *args,
-                               uint64_t *fill_ptr, uint64_t *fill_n, int carry, unsigned int *err,
-                               cudaStream_t st);
-
 
 }  // namespace cgi

@@ -600,7 +600,7 @@ struct ServeEngine {
                                       c->sm_count, nullptr, d_err, false, s));
       kernels++;
     }
-    CG_CUDA(launch_serve_finalize(plan, d_err, R.h_down.p, s));
+    CG_CUDA(launch_finalize_host(plan, d_err, R.h_down.p, s));
     kernels++;
     CG_CUDA(cudaEventRecord(R.done, s));
     R.busy = true;
