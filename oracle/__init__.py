@@ -155,10 +155,20 @@ def load(path: str | None = None) -> ctypes.CDLL:
     return lib
 
 
+SCRATCH = os.path.join(os.path.dirname(HERE), "_build", "tmp")  # git-ignored
+
+
+def scratch_dir(prefix: str) -> str:
+    """A fresh directory for build artefacts of the tests, inside the
+    repository's git-ignored build folder."""
+    os.makedirs(SCRATCH, exist_ok=True)
+    return tempfile.mkdtemp(prefix=prefix, dir=SCRATCH)
+
+
 def build_variant(source_text: str, tag: str) -> str:
     """Compile a modified copy of the oracle source (used by the mutation
     tests, which plant a mistake in the oracle and expect a pin to fail)."""
-    d = tempfile.mkdtemp(prefix=f"cg_oracle_{tag}_")
+    d = scratch_dir(f"cg_oracle_{tag}_")
     with open(os.path.join(d, "cg_oracle.h"), "w") as f:
         f.write(open(os.path.join(HERE, "cg_oracle.h")).read())
     src = os.path.join(d, "cg_oracle.c")

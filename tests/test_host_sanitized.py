@@ -8,12 +8,14 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402  (only for its scratch directories)
 
 CHILD = r'''
 import sys, ctypes
@@ -62,7 +64,7 @@ def test_host_code_under_asan_and_ubsan():
         "cg_build", os.path.join(ROOT, "paper_1310_0901_gb300", "build.py"))
     b = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(b)
-    d = tempfile.mkdtemp(prefix="cg_san_")
+    d = O.scratch_dir("cg_san_")
     lib = b.build(out=os.path.join(d, "libcg.so"), obj_dir=d,
                   host_flags=("-fsanitize=address", "-fsanitize=undefined",
                               "-fno-sanitize-recover=all", "-fno-omit-frame-pointer"))

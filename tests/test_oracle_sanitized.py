@@ -7,7 +7,6 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
-import tempfile
 
 import pytest
 
@@ -29,7 +28,7 @@ def test_pins_pass_under_asan_and_ubsan():
     asan = _runtime("libasan.so")
     if asan is None:
         pytest.skip("no AddressSanitizer runtime for gcc here")
-    d = tempfile.mkdtemp(prefix="cg_oracle_san_")
+    d = O.scratch_dir("cg_oracle_san_")
     lib = O.build(O.SRC, os.path.join(d, "libcg_oracle.so"), sanitize=True)
     env = dict(os.environ, LD_PRELOAD=asan,
                ASAN_OPTIONS="detect_leaks=0:abort_on_error=1",
