@@ -388,26 +388,6 @@ __device__ __forceinline__ RowCursor row_cursor(const PitchedJob &pj, const Imag
   return c;
 }
 
-// The fields of a row's Geo that classification, carry and the shared-
-// memory reads use (make_geo's rules, for one row of `n` bytes).
-__device__ __forceinline__ Geo cursor_geo(const RowCursor &c, uint64_t n, bool has_vin) {
-  Geo g;
-  g.n = n;
-  g.ax = (int64_t)(c.anchor & 15);
-  g.nchunks = 0;  // not used by the span kernel
-  g.out_al = reinterpret_cast<uint8_t *>(c.anchor - (uintptr_t)g.ax);
-  const uintptr_t vw = c.vin - (uintptr_t)g.ax;
-  g.vin_r = (int)(vw & 15);
-  g.vin_al = vw - (uintptr_t)g.vin_r;
-  g.vin_lo = c.vin;
-  g.vin_hi = c.vin + n;
-  g.has_vin = has_vin;
-  g.hb0 = c.host - g.ax;
-  g.hlo = c.host;
-  g.hhi = c.host + (int64_t)n;
-  g.obase = c.obase;
-  return g;
-}
 
 // All lanes: the rows of tile t out of stage `sp_mem`.
 template <uint32_t KIND, bool CARRY>
@@ -428,27 +408,42 @@ __device__ __forceinline__ void consume_span(const PitchedJob &pj, const Image &
   if (r >= r1) return;
   RowCursor cur = row_cursor<KIND>(pj, img, r, step);
   const bool has_vin = g0.has_vin;
+  // per row, in 32 bits: its V start from the stage's V window start (a
+  // 16-byte-aligned address), its first host byte, which is also its first
+  // A bit, from the A window's first bit, and its anchor alignment; only
+  // the carry's store address and the copy offset stay 64-bit
+  int32_t vrel = (int32_t)(cur.vin - vbeg);
+  int32_t hrel = (int32_t)(cur.host - 8 * aorig);
+  const int32_t d_vrel = (int32_t)cur.d_vin, d_hrel = (int32_t)cur.d_host;
+  const int32_t c32 = (int32_t)c;
+  Geo g;  // the fields chunk_step reads: n, ax, out_al, obase
+  g.n = pj.width;
   for (; r < r1; r += step) {
-    const Geo g = cursor_geo(cur, pj.width, has_vin);
+    const int32_t ax = (int32_t)(cur.anchor & 15);
+    g.ax = ax;
+    g.out_al = reinterpret_cast<uint8_t *>(cur.anchor - (uintptr_t)ax);
+    g.obase = cur.obase;
     uint4 V = make_uint4(0, 0, 0, 0);
     if (KIND == CG_HTOD || has_vin) {
-      const uint64_t k = (g.vin_al + 16 * (uintptr_t)c - vbeg) >> 4;
+      const int32_t vw = vrel - ax;  // aligned window start = vw rounded down to 16
+      const int32_t k = (vw >> 4) + c32;
       V = vs[k];
-      if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
+      const int vin_r = vw & 15;
+      if (vin_r) V = funnel16(V, vs[k + 1], vin_r);
     }
     uint32_t a16 = 0xFFFFu;
     if (KIND != CG_DTOD) {
-      const int64_t q = g.hb0 + 16 * c;
-      const int sh = (int)(q & 31);
-      const int64_t wi = (((q >> 5) << 2) - aorig) >> 2;
+      const int32_t qb = hrel - ax + 16 * c32;
+      const int sh = qb & 31;
+      const int wi = qb >> 5;
       const uint32_t w0 = as[wi];
       const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
       a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
     }
-    chunk_step<KIND, CARRY>(g, c, V, a16, valid_mask(16 * c - g.ax, g.n), la);
+    chunk_step<KIND, CARRY>(g, c, V, a16, valid_mask(16 * c - ax, g.n), la);
     cur.anchor += cur.d_anchor;
-    cur.vin += cur.d_vin;
-    cur.host += cur.d_host;
+    vrel += d_vrel;
+    hrel += d_hrel;
     cur.obase += cur.d_obase;
   }
 }

@@ -456,3 +456,26 @@ def test_tile_a_addressing_32bit_equals_64bit():
             qb = qbase + 16 * k
             assert (qb >> 5, qb & 31) == (wi64, q & 31)
             assert 4 * (qb >> 5) + 8 <= abytes
+
+
+def test_span_row_addressing_32bit_equals_64bit():
+    """consume_span's per-row V index, realignment and A word/shift, from
+    32-bit offsets relative to the stage's windows, equal the 64-bit forms
+    (Geo of the row) for rows of random pitch and alignment."""
+    rng = random.Random(17)
+    for _ in range(20000):
+        vbeg = rng.randrange(1 << 40) & ~15          # the V window start (aligned)
+        vin = vbeg + rng.randrange(0, 4000)
+        ax = rng.randrange(16)                       # the row's anchor alignment
+        host = rng.randrange(0, 1 << 40)
+        aorig = ((host - ax) >> 3) & ~15 if rng.random() < 0.5 else ((host - 200) >> 3) & ~15
+        for c in (0, 1, 7, 15, 31):
+            vw = vin - ax
+            k64 = ((vw - (vw & 15)) + 16 * c - vbeg) >> 4
+            vrel = vin - vbeg
+            k32 = ((vrel - ax) >> 4) + c
+            assert (k32, (vrel - ax) & 15) == (k64, vw & 15)
+            q = host - ax + 16 * c
+            wi64 = (((q >> 5) << 2) - aorig) >> 2
+            qb = (host - 8 * aorig) - ax + 16 * c
+            assert (qb >> 5, qb & 31) == (wi64, q & 31)
