@@ -363,8 +363,13 @@ class LevelTree {
       a >>= 1;
       b >>= 1;
     }
-    for (size_t i = a0 >> 1; i; i >>= 1) v = std::max(v, tag(nodes_[i], want_r));
-    for (size_t i = b0 >> 1; i; i >>= 1) v = std::max(v, tag(nodes_[i], want_r));
+    // tags of the end leaves' ancestors; the two paths join below the root
+    size_t i = a0 >> 1, j = b0 >> 1;
+    for (; i != j; i >>= 1, j >>= 1) {
+      v = std::max(v, tag(nodes_[i], want_r));
+      v = std::max(v, tag(nodes_[j], want_r));
+    }
+    for (; i; i >>= 1) v = std::max(v, tag(nodes_[i], want_r));
     return v;
   }
   void update_w(int l, int r, int v) { update(l, r, v, true); }
@@ -397,19 +402,23 @@ class LevelTree {
       a >>= 1;
       b >>= 1;
     }
-    // ancestors of the end leaves: subtree max = max(own tag, children's)
+    // ancestors of the end leaves, level by level (children before their
+    // parent; the two paths join below the root): subtree max = max(own
+    // tag, children's)
     auto rebuild = [&](size_t i) {
-      for (i >>= 1; i; i >>= 1) {
-        Node &n = nodes_[i];
-        const Node &c0 = nodes_[2 * i], &c1 = nodes_[2 * i + 1];
-        if (is_w)
-          n.sw = std::max(n.tw, std::max(c0.sw, c1.sw));
-        else
-          n.sr = std::max(n.tr, std::max(c0.sr, c1.sr));
-      }
+      Node &n = nodes_[i];
+      const Node &c0 = nodes_[2 * i], &c1 = nodes_[2 * i + 1];
+      if (is_w)
+        n.sw = std::max(n.tw, std::max(c0.sw, c1.sw));
+      else
+        n.sr = std::max(n.tr, std::max(c0.sr, c1.sr));
     };
-    rebuild(a0);
-    rebuild(b0);
+    size_t i = a0 >> 1, j = b0 >> 1;
+    for (; i != j; i >>= 1, j >>= 1) {
+      rebuild(i);
+      rebuild(j);
+    }
+    for (; i; i >>= 1) rebuild(i);
   }
 };
 
