@@ -82,13 +82,16 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
   std::vector<Ep> tmp;
   auto radix_sort = [&](std::vector<Ep> &e) {  // LSD, 11-bit digits, skipping flat ones
     tmp.resize(e.size());
+    uint64_t any = 0, all = ~0ull;  // a digit no two keys differ in needs no pass
+    for (const Ep &x : e) {
+      any |= x.v;
+      all &= x.v;
+    }
+    const uint64_t differ = any ^ all;
     for (int shift = 0; shift < 64; shift += 11) {
+      if (((differ >> shift) & 2047) == 0) continue;
       uint32_t cnt[2048] = {0};
       for (const Ep &x : e) cnt[(x.v >> shift) & 2047]++;
-      bool flat = false;
-      for (int d = 0; d < 2048; d++)
-        if (cnt[d] == e.size()) flat = true;
-      if (flat) continue;
       uint32_t sum = 0;
       for (int d = 0; d < 2048; d++) {
         const uint32_t c = cnt[d];
