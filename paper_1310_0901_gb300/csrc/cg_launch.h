@@ -16,6 +16,14 @@ cudaError_t launch_scan_single_tma(const Image &img, const ScanJob &job, const R
                                    cudaStream_t st);
 int scan_single_tma_grid(int sm_count, uint64_t n);
 uint32_t scan_tma_tile_bytes();  // a batched segment is a whole number of these
+// The reports of a one-level plan written by the level kernel's last CTA
+// straight into pinned host memory (out: error flag (16 bytes) | reports;
+// done: a zeroed CTA counter), or nothing (out null).
+struct FinalizeHost {
+  uint8_t *out = nullptr;
+  unsigned int *done = nullptr;
+};
+
 // claim: per-level counter, zero before the launch (dynamic segment
 // claiming), or null (static striding).  overlap: launched as a
 // programmatic dependent of the kernel before it on `st` (its prologue
@@ -23,7 +31,7 @@ uint32_t scan_tma_tile_bytes();  // a batched segment is a whole number of these
 cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
                                   unsigned long long *claim, unsigned int *err_flag, bool overlap,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const FinalizeHost &fin = FinalizeHost{});
 // New device table = old minus the entries whose bases are in the sorted
 // list `dead`, plus the sorted registrations, into nb/ns/nh (count - d + m
 // entries).

@@ -169,7 +169,8 @@ __device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp
 
 __global__ void __launch_bounds__(kTW * 32, 1)
     scan_level_tma_kernel(Image img, BatchPlan p, uint64_t pos_begin, uint64_t pos_end,
-                          uint64_t n_segs, unsigned long long *claim, unsigned int *err_flag) {
+                          uint64_t n_segs, unsigned long long *claim, unsigned int *err_flag,
+                          FinalizeHost fin) {
   // levels launched back to back may overlap: the next level's grid is
   // scheduled as this one's CTAs leave, runs its prologue (which reads only
   // the batch's plan), and waits for this grid before touching any shadow
@@ -243,12 +244,33 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     }
     if (lane == 0) atomicOr(err_flag, 1u);
   }
+  if (fin.out) {  // the last CTA to finish writes every report to the host
+    __shared__ bool s_last;
+    __threadfence();  // this thread's accumulator atomics before the count
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(fin.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (uint64_t i = threadIdx.x; i < p.nreq; i += blockDim.x) {
+        Acc a;
+        a.n_unaddr = __ldcg(&p.acc[i].n_unaddr);
+        a.n_undef = __ldcg(&p.acc[i].n_undef);
+        a.first_unaddr = __ldcg(&p.acc[i].first_unaddr);
+        a.first_undef = __ldcg(&p.acc[i].first_undef);
+        cg_report r;
+        assemble_report(&r, p.info[i], a);
+        reinterpret_cast<cg_report *>(fin.out + 16)[i] = r;
+      }
+      if (threadIdx.x == 0) *reinterpret_cast<unsigned int *>(fin.out) = __ldcg(err_flag);
+    }
+  }
 }
 
 cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t pos_begin,
                                   uint64_t pos_end, uint64_t n_segs, int max_ctas,
                                   unsigned long long *claim, unsigned int *err_flag, bool overlap,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const FinalizeHost &fin) {
   if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
   constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
   static int per_sm = 0;
@@ -278,10 +300,10 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, scan_level_tma_kernel, img, p, pos_begin, pos_end, n_segs,
-                              claim, err_flag);
+                              claim, err_flag, fin);
   }
   scan_level_tma_kernel<<<g, kTW * 32, smem, st>>>(img, p, pos_begin, pos_end, n_segs, claim,
-                                                   err_flag);
+                                                   err_flag, fin);
   return cudaGetLastError();
 }
 

@@ -587,21 +587,31 @@ struct ServeEngine {
               [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
     size_t sci = 0;
     uint64_t kernels = 0;
+    const bool tma = !(c->img_on_host || c->cfg.scan_engine == 1);
+    // a one-level round of a few copies: the level kernel's last CTA writes
+    // the reports (one launch less per round)
+    FinalizeHost fin;
+    if (tma && nlev == 1 && lev_segs[0] > 0 && n <= 512) {
+      fin.out = R.h_down.p;
+      fin.done = d_err + 1;  // zeroed by the upload with the flag
+    }
     for (int l = 0; l < nlev; l++) {
       for (; sci < stages.size() && stages[sci].level == l; sci++)
         CG_CUDA(cudaMemcpyAsync(reinterpret_cast<void *>(stages[sci].off),
                                 reinterpret_cast<const void *>(stages[sci].src), stages[sci].n,
                                 cudaMemcpyDeviceToDevice, s));
-      if (c->img_on_host || c->cfg.scan_engine == 1)
+      if (!tma)
         CG_CUDA(launch_scan_level(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
                                   c->sm_count * 8, s));
       else
         CG_CUDA(launch_scan_level_tma(c->img, plan, lev_start[l], lev_start[l + 1], lev_segs[l],
-                                      c->sm_count, nullptr, d_err, false, s));
+                                      c->sm_count, nullptr, d_err, false, s, fin));
       kernels++;
     }
-    CG_CUDA(launch_finalize_host(plan, d_err, R.h_down.p, s));
-    kernels++;
+    if (!fin.out) {
+      CG_CUDA(launch_finalize_host(plan, d_err, R.h_down.p, s));
+      kernels++;
+    }
     CG_CUDA(cudaEventRecord(R.done, s));
     R.busy = true;
     R.id = round_id;
