@@ -356,6 +356,60 @@ def pin_carry_roundtrip(lib):
     o.close()
 
 
+def pin_mark(lib):
+    """The Memcheck-style client requests (mark a device range defined or
+    undefined; the outlook's way for callers to declare kernel output, R6):
+    a mark rewrites exactly [dptr, dptr + n) of the allocation holding dptr,
+    with 0x00 (defined) or 0xFF (undefined), and a device->host copy of the
+    allocation then counts what the marks left, by construction.  A mark
+    that is not wholly inside one live allocation (no allocation, a freed
+    one, or running past the end of the one holding dptr) is refused with
+    E_RANGE and changes nothing; n = 0 is a no-op."""
+    n_img = 1 << 13
+    v = np.zeros(n_img, np.uint8)
+    a_bits, vv = _image(np.ones(n_img, bool), v)
+    o = O.Oracle(a_bits, vv, lib=lib)
+    dev, size = 1 << 40, 4096
+    assert o.register_alloc(dev, size) == 0
+    assert o.register_alloc(dev + size, 512) == 0        # adjacent, never combined
+    assert o.register_alloc(1 << 41, 256) == 0
+    assert o.free(1 << 41) == "OK"
+    model = np.full(size, 0xFF, np.uint8)                # fresh: all undefined (R6)
+    rng = S.rng_for(29)
+    for step in range(60):
+        n = int(rng.integers(1, 700))
+        off = int(rng.integers(0, size - n + 1))
+        val = 0x00 if step % 3 else 0xFF
+        assert o.mark(dev + off, n, val) == 0
+        model[off:off + n] = val
+        assert np.array_equal(o.read_dev_v(dev, size), model), step
+    # a device->host copy of the whole allocation into fully addressable
+    # host bytes: the undefined count and first offset follow from the model
+    st, r = o.check_copy(DTOH, 0, dev, size)
+    assert st == 0
+    bad = np.nonzero(model)[0]
+    assert r["n_undef"] == bad.size and r["n_good"] == size - bad.size
+    assert r["first_undef_off"] == (int(bad[0]) if bad.size else -1)
+    assert np.array_equal(o.read_host_v(0, size), model)
+    # refusals: nothing changes
+    before = o.read_dev_v(dev, size).copy()
+    nxt = o.read_dev_v(dev + size, 512).copy()
+    assert o.mark(dev + 100, size - 99, 0x00) == -8      # one byte past the end
+    assert o.mark(dev + size - 1, 2, 0x00) == -8         # runs into the neighbour
+    assert o.mark(dev - 1, 2, 0x00) == -8                # starts before any allocation
+    assert o.mark(1 << 41, 16, 0x00) == -8               # freed
+    assert o.mark(1 << 30, 16, 0x00) == -8               # never allocated
+    assert np.array_equal(o.read_dev_v(dev, size), before)
+    assert np.array_equal(o.read_dev_v(dev + size, 512), nxt)
+    # the largest accepted marks end exactly at the end
+    assert o.mark(dev + 100, size - 100, 0x00) == 0
+    assert o.mark(dev + size + 7, 505, 0xFF) == 0
+    model[100:] = 0x00
+    assert np.array_equal(o.read_dev_v(dev, size), model)
+    assert o.mark(12345, 0, 0x00) == 0                   # n = 0: a no-op
+    o.close()
+
+
 def pin_dtod_memmove(lib):
     """Device->device carries like memmove, compared against Python's slice
     assignment (which reads the whole source before writing); overlapping
@@ -991,7 +1045,7 @@ def pin_kernel_args(lib, trials: int = 120):
 ALL_PINS = [
     pin_listing5, pin_htod_bytes_by_construction, pin_dtoh_bytes_by_construction,
     pin_range_bruteforce, pin_free_sequences, pin_free_sequences_reuse, pin_generator_truth,
-    pin_invariants, pin_carry_roundtrip, pin_dtod_memmove, pin_records,
+    pin_invariants, pin_carry_roundtrip, pin_mark, pin_dtod_memmove, pin_records,
     pin_host_range_errors, pin_races, pin_strided_footnote, pin_pitched_reduces_to_1d,
     pin_pitched_bruteforce, pin_arrays, pin_pitched_args, pin_memset, pin_kernel_args,
 ]

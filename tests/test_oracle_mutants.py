@@ -121,6 +121,17 @@ MUTANTS = {
                                  "if (reps[i].flags & OR_F_UNALLOC_DST) continue;"),
     "ka_access_unchecked": ("if (access[i] == 0 || (access[i] & ~(OR_ARG_READ | OR_ARG_WRITE))) return OR_E_ARG;",
                             "if (access[i] == 0) return OR_E_ARG;"),
+    # client requests (mark defined / undefined)
+    "mark_range_from_base": ("if (!a || n > a->base + a->size - dptr) return OR_E_RANGE;\n  int st = materialise(a);",
+                             "if (!a || n > a->size) return OR_E_RANGE;\n  int st = materialise(a);"),
+    "mark_range_off_by_one": ("if (!a || n > a->base + a->size - dptr) return OR_E_RANGE;\n  int st = materialise(a);",
+                              "if (!a || n >= a->base + a->size - dptr) return OR_E_RANGE;\n  int st = materialise(a);"),
+    "mark_written_at_base": ("memset(a->shadow + (dptr - a->base), value, n);",
+                             "memset(a->shadow, value, n);"),
+    "mark_ignores_value": ("memset(a->shadow + (dptr - a->base), value, n);",
+                           "memset(a->shadow + (dptr - a->base), 0x00, n);"),
+    "mark_unallocated_accepted": ("if (!a || n > a->base + a->size - dptr) return OR_E_RANGE;\n  int st = materialise(a);",
+                                  "if (!a) return OR_OK;\n  if (n > a->base + a->size - dptr) return OR_E_RANGE;\n  int st = materialise(a);"),
     "batch_not_validated_first": (
         "    int st = validate(s, kind[i], dst[i], src[i], n[i]);\n    if (st) {",
         "    int st = 0;\n    if (st) {"),
