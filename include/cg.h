@@ -636,9 +636,9 @@ cg_status cg_serve_stop(cg_ctx *ctx, cg_serve_stats *out);
  *                   no carry
  *   rep_dev         device memory (or mapped pinned host memory) receiving
  *                   the report when the stream reaches it
- * Device shadows are read in whole 16-byte-aligned blocks around
- * [ptr, ptr+n) (those blocks must be readable); only [ptr, ptr+n) is
- * written.
+ * Device shadows must be device (or managed) memory, else CG_E_ARG; they
+ * are read in whole 16-byte-aligned blocks around [ptr, ptr+n) (those
+ * blocks must be readable); only [ptr, ptr+n) is written.
  *
  * Its scratch (the kernel's accumulators and an 8 MiB staging area for an
  * overlapping device->device carry) is a fixed array inside the library

@@ -88,6 +88,18 @@ extern "C" cg_status cg_scan_noalloc(uint32_t kind, const uint8_t *a_bits_dev, u
         return fail(CG_E_ARG, "the host image must be in device memory for cg_scan_noalloc");
     }
   }
+  // the device shadows feed the bulk copies, which read device memory only
+  for (const void *p : {static_cast<const void *>(kind != CG_HTOD ? dev_src_shadow : nullptr),
+                        static_cast<const void *>(kind != CG_DTOH ? dev_dst_shadow : nullptr)}) {
+    if (!p) continue;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CG_E_ARG, "device shadow pointer unknown to CUDA");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+      return fail(CG_E_ARG, "device shadows must be in device memory for cg_scan_noalloc");
+  }
   const bool has_src = kind != CG_HTOD && dev_src_shadow != nullptr;
   const bool has_dst = kind != CG_DTOH && dev_dst_shadow != nullptr;
   const bool do_carry = carry != 0 && (kind == CG_HTOD   ? has_dst

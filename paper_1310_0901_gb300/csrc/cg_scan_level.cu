@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cg_setup.h"
 #include "cg_tma.cuh"
 #include "cg_launch.h"
 
@@ -273,18 +274,10 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
                                   cudaStream_t st, const FinalizeHost &fin) {
   if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
   constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(scan_level_tma_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_level_tma_kernel, kTW * 32, smem) !=
-            cudaSuccess ||
-        n < 1)
-      n = 1;
-    per_sm = n;
-  }
+  static KernelSetup setup;
+  int per_sm = 1;
+  const cudaError_t e = kernel_setup(setup, scan_level_tma_kernel, kTW * 32, smem, &per_sm);
+  if (e != cudaSuccess) return e;
   const uint64_t cap = (uint64_t)max_ctas * (uint64_t)per_sm;  // max_ctas counts SMs
   const uint64_t ctas = (n_segs + kTW - 1) / kTW;
   const unsigned g = (unsigned)(ctas < cap ? ctas : cap);

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cg_setup.h"
 #include "cg_tma.cuh"
 #include "cg_launch.h"
 
@@ -543,20 +544,11 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
   const uint64_t wpc = kPThreads / 32;
   if (kmax >= kTmaRowChunks && tma_ok) {
     constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
-    static int per_sm = 0;
-    if (!per_sm) {
-      cudaError_t e = cudaFuncSetAttribute(scan_pitched_tma_kernel<KIND, CARRY>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      int n = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_pitched_tma_kernel<KIND, CARRY>,
-                                                        kTW * 32, smem) != cudaSuccess ||
-          n < 1) {
-        cudaGetLastError();
-        n = 1;
-      }
-      per_sm = n;
-    }
+    static KernelSetup setup;
+    int per_sm = 1;
+    const cudaError_t e = kernel_setup(setup, scan_pitched_tma_kernel<KIND, CARRY>, kTW * 32, smem,
+                                       &per_sm);
+    if (e != cudaSuccess) return e;
     const uint64_t tpr = (kmax + 32 * kR - 1) / (32 * kR);
     const uint64_t ntiles = rows * tpr;
     const uint64_t need = (ntiles + kTW - 1) / kTW;
@@ -570,12 +562,11 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
     return cudaGetLastError();
   }
   if (kmax > 32) {
-    static int per_sm = 0;
-    if (!per_sm &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-             &per_sm, scan_pitched_wide_kernel<KIND, CARRY>, kPThreads, 0) != cudaSuccess ||
-         per_sm < 1))
-      per_sm = 1;
+    static KernelSetup setup;
+    int per_sm = 1;
+    const cudaError_t e = kernel_setup(setup, scan_pitched_wide_kernel<KIND, CARRY>, kPThreads, 0,
+                                       &per_sm);
+    if (e != cudaSuccess) return e;
     WideStep ws;
     ws.groups = (kmax + 32 * kPWide - 1) / (32 * kPWide);
     const uint64_t items = rows * ws.groups;
@@ -592,14 +583,11 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
   while ((1ull << lp) < kmax) lp++;
   const uint64_t rt = tma_ok ? span_rows_per_tile(job, 1ull << lp) : 0;
   if (rt) {
-    static int span_per_sm = 0;
-    if (!span_per_sm) {
-      cudaError_t e = cudaFuncSetAttribute(scan_pitched_span_kernel<KIND, CARRY>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kSmemBytes);
-      if (e != cudaSuccess) return e;
-      span_per_sm = tma_ctas_per_sm(scan_pitched_span_kernel<KIND, CARRY>);
-    }
+    static KernelSetup setup;
+    int span_per_sm = 1;
+    const cudaError_t e = kernel_setup(setup, scan_pitched_span_kernel<KIND, CARRY>, kTW * 32,
+                                       kSmemBytes, &span_per_sm);
+    if (e != cudaSuccess) return e;
     SpanTiles sp;
     sp.rows_per_tile = rt;
     sp.tiles_per_slice = (job.height + rt - 1) / rt;
@@ -612,12 +600,11 @@ static cudaError_t launch_t(const Image &img, const PitchedJob &job, const Range
                                                                               out, sp);
     return cudaGetLastError();
   }
-  static int per_sm = 0;
-  if (!per_sm &&
-      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-           &per_sm, scan_pitched_narrow_kernel<KIND, CARRY>, kPThreads, 0) != cudaSuccess ||
-       per_sm < 1))
-    per_sm = 1;
+  static KernelSetup setup;
+  int per_sm = 1;
+  const cudaError_t e = kernel_setup(setup, scan_pitched_narrow_kernel<KIND, CARRY>, kPThreads, 0,
+                                     &per_sm);
+  if (e != cudaSuccess) return e;
   const uint64_t per_warp = (32ull >> lp) * kPNarrow;
   const uint64_t need = (rows + per_warp * wpc - 1) / (per_warp * wpc);
   const uint64_t cap = (uint64_t)sm_count * per_sm;

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cg_setup.h"
 #include "cg_tma.cuh"
 #include "cg_launch.h"
 
@@ -124,20 +125,11 @@ template <uint32_t KIND, bool CARRY>
 static cudaError_t launch_tma_t(const Image &img, const ScanJob &job, const RangeInfo &ri,
                                 SingleScratch *scr, cg_report *out, int grid, cudaStream_t st) {
   constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(scan_single_tma_kernel<KIND, CARRY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, scan_single_tma_kernel<KIND, CARRY>,
-                                                      kTW * 32, smem) != cudaSuccess ||
-        n < 1) {
-      cudaGetLastError();
-      n = 1;
-    }
-    per_sm = n;
-  }
+  static KernelSetup setup;
+  int per_sm = 1;
+  const cudaError_t e = kernel_setup(setup, scan_single_tma_kernel<KIND, CARRY>, kTW * 32, smem,
+                                     &per_sm);
+  if (e != cudaSuccess) return e;
   // `grid` counts SM-sized units of work; fill every resident CTA slot
   const unsigned ctas = (unsigned)(grid * per_sm);
   // segments of up to 16 tiles (64 KiB of the anchor grid), and at least

@@ -296,16 +296,4 @@ struct SegSrc {
   }
 };
 
-// CTAs of a TMA kernel that fit on one SM (shared memory bound).
-template <typename K>
-static int tma_ctas_per_sm(K kernel) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kTW * 32, kSmemBytes) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 1;
-  }
-  return n > 0 ? n : 1;
-}
-
 }  // namespace cgi
