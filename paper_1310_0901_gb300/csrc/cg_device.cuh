@@ -17,6 +17,14 @@ __device__ __forceinline__ uint4 ld_stream(const void *p) {
 __device__ __forceinline__ uint4 ld_plain(const void *p) {
   return __ldcg(reinterpret_cast<const uint4 *>(p));
 }
+// through L1: the device->host carry's merge reads, which a tile's pre-pass
+// may already have brought into L1 (prefetch_l1)
+__device__ __forceinline__ uint4 ld_l1(const void *p) {
+  return __ldca(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ void prefetch_l1(const void *p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void st_stream(void *p, uint4 v) {
   __stcs(reinterpret_cast<uint4 *>(p), v);
 }
@@ -229,7 +237,7 @@ __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uin
       if (wm == 0xFFFFu) {
         st_stream(p, V);
       } else if (vm == 0xFFFFu) {  // interior chunk with holes: merge
-        const uint4 old = ld_plain(p);
+        const uint4 old = ld_l1(p);
         const uint4 m = expand16(a16);
         uint4 o;
         o.x = (V.x & m.x) | (old.x & ~m.x);

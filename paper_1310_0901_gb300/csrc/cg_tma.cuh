@@ -204,13 +204,13 @@ __device__ __forceinline__ void classify_a_words(const Geo &g, const uint32_t *a
   if (first != kNone && la.fun == kNone) la.fun = first;
 }
 
-// All lanes: classify a super-tile (1024 A words, 32 KiB of copy).
+// All lanes: classify a super-tile (128 kR A words, 4096 kR bytes of copy).
 __device__ __forceinline__ void consume_tile_a_super(const Geo &g, int64_t c0, const uint8_t *sp,
                                                      int lane, LaneAcc &la) {
   const int64_t p0 = g.hb0 + 128 * c0;
   const int64_t aorig = floor16(p0 >> 3);
   classify_a_words(g, reinterpret_cast<const uint32_t *>(sp), 128 * c0 - g.ax, p0 - 8 * aorig,
-                   32 * 32, lane, la);
+                   128 * kR, lane, la);
 }
 
 // The same for an ordinary 4 KiB tile (128 A words), for the kernels that
@@ -242,6 +242,23 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   const int32_t qbase = (int32_t)(p0 - 8 * floor16(p0 >> 3));
   const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
   const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
+  if (KIND == CG_DTOH && CARRY) {
+    // The carry merges device V into the host V blocks that hold
+    // unaddressable bytes, reading each such block first.  Ask for all of
+    // the tile's blocks at once, so that those reads overlap instead of
+    // each row waiting for its own.
+#pragma unroll
+    for (int u = 0; u < kR; u++) {
+      const int k = 32 * u + lane;
+      const int32_t qb = qbase + 16 * k;
+      const int sh = qb & 31;
+      const int wi = qb >> 5;
+      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
+      const uint32_t a16 = __funnelshift_r(as[wi], w1, sh) & 0xFFFFu;
+      const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * (c0 + k) - g.ax, g.n);
+      if (vm == 0xFFFFu && a16 != 0xFFFFu) prefetch_l1(g.out_al + 16 * (c0 + k));
+    }
+  }
 #pragma unroll U
   for (int u = 0; u < kR; u++) {
     const int k = 32 * u + lane;
@@ -270,7 +287,9 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
 // the next unclaimed segment from a counter; the producer half of a warp
 // claims and passes each claim to the consumer half through a small ring
 // in shared memory.
-constexpr int kSegQ = 8;  // ring entries: at most 2 * kNS + 3 claims outstanding
+// ring entries (a power of two): at most 2 * kNS + 3 claims are outstanding
+constexpr int kSegQ = 2 * kNS + 3 <= 8 ? 8 : (2 * kNS + 3 <= 16 ? 16 : 32);
+static_assert(2 * kNS + 3 <= kSegQ, "segment-claim ring too small");
 
 struct SegSrc {
   unsigned long long *ctr;  // null: static striding

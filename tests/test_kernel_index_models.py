@@ -242,12 +242,13 @@ def test_a_super_tiles_stay_in_bounds_and_cover():
             b1 = c16((q1 + 7) >> 3)
             assert b0 >= aorig and b1 - aorig <= kStage and b1 <= img_n // 8 and b0 >= 0
             for lane in (0, 31):
-                i0 = 128 * c0 - ax + 1024 * lane
-                lo_i, hi_i = max(0, i0), min(n, i0 + 1024)
+                i0 = 128 * c0 - ax + 128 * kR * lane
+                lo_i, hi_i = max(0, i0), min(n, i0 + 128 * kR)
                 if hi_i > lo_i:
                     assert b0 * 8 <= hlo + lo_i and hlo + hi_i <= b1 * 8
         w0 = (p0 - 8 * aorig) >> 5
-        assert (w0 + 1024 + 1) * 4 <= 4112   # the last word read, lane 31's (j = 1023) + 1
+        # the last word read (j = 128 kR - 1) and the one after it lie in the stage
+        assert (w0 + 128 * kR + 1) * 4 <= kStage
 
 
 # ------------------------------------------------ table merge
