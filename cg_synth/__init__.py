@@ -417,6 +417,25 @@ def tuning_batch(rng, table: AllocTable, host_n: int) -> np.ndarray:
     return requests(rng, count, table, host_n, lo, max(lo, hi), mix=tuple(mix), p_wild=0.01)
 
 
+def tuning_batch_mixed(rng, table: AllocTable, host_n: int) -> np.ndarray:
+    """A batch from one of four shape families, for fitting and testing the
+    split cost model on shapes where split sizes differ: tuning_batch's
+    random shapes; a few large copies (16-200 of 1-16 MiB); a bimodal mix
+    (500-4000 copies up to 4 KiB plus 10-200 of 1-16 MiB); mid-sized copies
+    (200-2000 of 64 KiB-1 MiB)."""
+    fam = int(rng.integers(0, 4))
+    if fam == 0:
+        return tuning_batch(rng, table, host_n)
+    if fam == 1:
+        return requests(rng, int(rng.integers(16, 200)), table, host_n, 1 << 20, 16 << 20)
+    if fam == 2:
+        a = requests(rng, int(rng.integers(500, 4000)), table, host_n, 16, 4096)
+        b = requests(rng, int(rng.integers(10, 200)), table, host_n, 1 << 20, 16 << 20)
+        q = np.concatenate([a, b])
+        return q[rng.permutation(len(q))]
+    return requests(rng, int(rng.integers(200, 2000)), table, host_n, 64 << 10, 1 << 20)
+
+
 # ------------------------------------------------ pitched copies, arrays
 
 @dataclass

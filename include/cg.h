@@ -172,7 +172,13 @@ typedef struct cg_config {
                                    0 (default): capture them into a CUDA graph
                                    (updated in place when the next batch has
                                    the same shape) and launch that */
-  uint32_t reserved[6];
+  uint32_t batch_piece_kib;     /* batches on the TMA engine: a host->device
+                                   copy that carries nothing and is longer than
+                                   1.5x this is planned in pieces of about this
+                                   size (whole tiles), each ordered only after
+                                   the writes it overlaps; 0 = 1024 (1 MiB),
+                                   0xFFFFFFFF = whole copies only */
+  uint32_t reserved[5];
 } cg_config;
 
 typedef struct cg_ctx cg_ctx;
@@ -704,6 +710,25 @@ cg_status cg_inject_fault(cg_ctx *ctx, uint32_t fault);
  * reqs, level: host.  *n_levels (may be NULL) gets 1 + the highest level. */
 cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry,
                          const uint8_t *modes, int32_t *level, uint32_t *n_levels);
+
+/* The planning units cg_check_batch runs a batch as on the TMA engine
+ * (host only, no GPU work): every copy is one unit, except host->device
+ * copies that carry nothing (their modes bit 0 clear) and span more than
+ * 1.5 x piece_rows rows of their anchor grid (512 host bytes a row, the
+ * grid starting at the 16-byte boundary at or below src): those are cut
+ * into units of piece_rows rows (the last one shorter).  Each unit gets a
+ * level: 1 + the highest level of an earlier unit it conflicts with (as in
+ * cg_plan_levels; in the host space exact unless a 64 KiB block of the host
+ * image holds more than 8 ranges that cover it in part: then units
+ * touching that block are taken to conflict).  host_n: the host image's size
+ * (host ranges must lie inside it).  Output per unit, in request order
+ * (host arrays of cap entries): req, rows [row_lo, row_hi) (0, 0: the
+ * whole copy), level; *n_units gets the count (units beyond cap are not
+ * written; CG_E_TOO_BIG if there are more than cap). */
+cg_status cg_plan_units(const cg_copy *reqs, uint64_t nreq, uint32_t carry,
+                        const uint8_t *modes, uint64_t host_n, uint64_t piece_rows,
+                        uint32_t *req, uint32_t *row_lo, uint32_t *row_hi, int32_t *level,
+                        uint64_t cap, uint64_t *n_units);
 
 cg_status cg_get_stats(const cg_ctx *ctx, cg_stats *out);
 

@@ -122,6 +122,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.or_destroy.restype = None
     lib.or_register_alloc.argtypes = [vp, u64, u64]
     lib.or_register_alloc.restype = i32
+    lib.or_register_allocs.argtypes = [vp, vp, vp, u64, vp]
+    lib.or_register_allocs.restype = u64
     lib.or_free.argtypes = [vp, u64, ctypes.POINTER(u32)]
     lib.or_free.restype = i32
     lib.or_mark.argtypes = [vp, u64, u64, ctypes.c_uint8]
@@ -216,6 +218,14 @@ class Oracle:
     def register_alloc(self, base: int, size: int) -> int:
         return self.lib.or_register_alloc(self._h, base, size)
 
+    def register_allocs(self, bases, sizes) -> np.ndarray:
+        """register_alloc for each (base, size) in turn; the statuses."""
+        b = np.ascontiguousarray(bases, dtype=np.uint64)
+        z = np.ascontiguousarray(sizes, dtype=np.uint64)
+        st = np.zeros(max(1, len(b)), dtype=np.int32)
+        self.lib.or_register_allocs(self._h, b.ctypes.data, z.ctypes.data, len(b), st.ctypes.data)
+        return st[:len(b)]
+
     def free(self, base: int) -> str:
         v = ctypes.c_uint32(99)
         st = self.lib.or_free(self._h, base, ctypes.byref(v))
@@ -281,6 +291,28 @@ class Oracle:
                                      n.ctypes.data, len(reqs), ctypes.addressof(reps),
                                      ctypes.byref(bad))
         return st, [report_dict(reps[i]) for i in range(len(reqs))], int(bad.value)
+
+    def check_copy_status(self, kind: int, dst: int, src: int, n: int) -> int:
+        """check_copy without building the report dict (for timing)."""
+        if not hasattr(self, "_rep"):
+            self._rep = OrReport()
+            self._rep_ref = ctypes.byref(self._rep)
+        return self.lib.or_check_copy(self._h, kind, dst, src, n, self._rep_ref)
+
+    def batch_runner(self, reqs: np.ndarray):
+        """A callable that applies the batch `reqs` (or_check_batch) and
+        returns its status, with no report dicts built (for timing)."""
+        arrs = [np.ascontiguousarray(reqs[f], dtype=t) for f, t in
+                (("kind", np.uint32), ("dst", np.uint64), ("src", np.uint64), ("n", np.uint64))]
+        reps = (OrReport * max(1, len(reqs)))()
+        bad = ctypes.c_uint64(0)
+        ptrs = [a.ctypes.data for a in arrs]
+
+        def run() -> int:
+            return self.lib.or_check_batch(self._h, *ptrs, len(reqs), ctypes.addressof(reps),
+                                           ctypes.byref(bad))
+        run.keep = (arrs, reps, bad)
+        return run
 
     def read_host_v(self, off: int = 0, n: int | None = None) -> np.ndarray:
         n = self.host_n - off if n is None else n

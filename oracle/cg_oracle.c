@@ -192,6 +192,16 @@ int or_register_alloc(or_state *s, uint64_t base, uint64_t size) {
   return OR_OK;
 }
 
+uint64_t or_register_allocs(or_state *s, const uint64_t *bases, const uint64_t *sizes,
+                            uint64_t n, int32_t *status) {
+  uint64_t refused = 0;
+  for (uint64_t i = 0; i < n; i++) {
+    status[i] = or_register_alloc(s, bases[i], sizes[i]);
+    if (status[i]) refused++;
+  }
+  return refused;
+}
+
 int or_free(or_state *s, uint64_t base, uint32_t *verdict) {
   if (!verdict) return OR_E_ARG;
   live_alloc *a = find_alloc(s, base);

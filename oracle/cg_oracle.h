@@ -102,6 +102,10 @@ or_state *or_create(uint64_t host_n, const uint8_t *a_bits, const uint8_t *v,
 void or_destroy(or_state *s);
 
 int or_register_alloc(or_state *s, uint64_t base, uint64_t size);
+/* or_register_alloc applied to each (bases[i], sizes[i]) in turn, its
+ * status in status[i]; returns the number of refused registrations. */
+uint64_t or_register_allocs(or_state *s, const uint64_t *bases, const uint64_t *sizes,
+                            uint64_t n, int32_t *status);
 int or_free(or_state *s, uint64_t base, uint32_t *verdict);
 int or_mark(or_state *s, uint64_t dptr, uint64_t n, uint8_t value);
 

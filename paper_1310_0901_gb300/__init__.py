@@ -89,7 +89,7 @@ class cg_config(ctypes.Structure):
                 ("shadow_budget_bytes", u64), ("scan_ctas_per_sm", u32),
                 ("batch_segment_kib", u32), ("batch_ctas_per_sm", u32),
                 ("scan_engine", u32), ("batch_autotune", u32), ("batch_direct_launch", u32),
-                ("reserved", u32 * 6)]
+                ("batch_piece_kib", u32), ("reserved", u32 * 5)]
 
 
 class cg_stats(ctypes.Structure):
@@ -160,6 +160,7 @@ SIGNATURES = [
     ("cg_wait", i32, [vp, u64, u32, ctypes.POINTER(cg_result)]),
     ("cg_serve_replay", i32, [vp, vp, vp, vp, u64, vp]),
     ("cg_serve_stop", i32, [vp, ctypes.POINTER(cg_serve_stats)]),
+    ("cg_plan_units", i32, [vp, u64, u32, vp, u64, u64, vp, vp, vp, vp, u64, vp]),
     ("cg_scan_noalloc", i32, [u32, vp, vp, u64, u64, vp, vp, u64, u32, vp, vp]),
     ("cg_check_batch_async", i32, [vp, vp, u64, u64, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                    vp]),
@@ -532,6 +533,31 @@ def plan_levels(reqs: np.ndarray, carry: bool = True,
                          lv.ctypes.data if len(reqs) else None, ctypes.byref(nl)),
           "cg_plan_levels")
     return lv, int(nl.value)
+
+
+def plan_units(reqs: np.ndarray, host_n: int, piece_rows: int, carry: bool = True,
+               modes: np.ndarray | None = None) -> np.ndarray:
+    """The batch planner's units (host only, see cg_plan_units): a structured
+    array of (req, row_lo, row_hi, level) in request order."""
+    reqs = np.ascontiguousarray(reqs)
+    mp = None
+    if modes is not None:
+        modes = np.ascontiguousarray(modes, dtype=np.uint8)
+        mp = modes.ctypes.data
+    cap = len(reqs) + 1
+    if piece_rows:
+        cap += int((reqs["n"].astype(np.uint64) // np.uint64(512 * piece_rows)).sum()) + len(reqs)
+    out = [np.zeros(cap, dtype=t) for t in (np.uint32, np.uint32, np.uint32, np.int32)]
+    n = u64(0)
+    check(cg_plan_units(reqs.ctypes.data if len(reqs) else None, len(reqs), int(carry), mp,
+                        host_n, piece_rows, *[a.ctypes.data for a in out], cap, ctypes.byref(n)),
+          "cg_plan_units")
+    k = n.value
+    res = np.zeros(k, dtype=[("req", "<u4"), ("row_lo", "<u4"), ("row_hi", "<u4"),
+                             ("level", "<i4")])
+    for f, a in zip(res.dtype.names, out):
+        res[f] = a[:k]
+    return res
 
 
 CANDIDATES_KIB = [4, 8, 16, 32, 64, 128, 256, 512, 1024]

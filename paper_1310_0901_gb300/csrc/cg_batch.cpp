@@ -25,13 +25,16 @@ struct BatchRun {
   const cg_copy *reqs = nullptr;
   uint64_t nreq = 0;
   BatchPlan plan{};
-  std::vector<int> lvl;
+  std::vector<int> lvl;          // per request: the level of its first unit
+  std::vector<PlanUnit> units;   // planning units (whole copies, pieces)
+  uint64_t npos = 0;             // order positions (= units)
   int nlev = 0;
   std::vector<uint64_t> lev_start, lev_segs;
   std::vector<StageCopy> stages;
   const uint8_t *modes = nullptr;
   uint32_t *h_order = nullptr;
   uint64_t *h_segfirst = nullptr;
+  uint64_t *h_piece = nullptr;
   bool tma = true;
   int grid = 1;
 };
@@ -46,8 +49,6 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   CG_TRY(flush_fills(c, st));
   CG_TRY(ensure_device_table(c, look));  // only lookups read the device table
   CG_TRY(K.b_reqs.ensure(nreq));
-  CG_TRY(K.b_order.ensure(nreq));
-  CG_TRY(K.b_segfirst.ensure(nreq));
   CG_TRY(K.b_stage.ensure(nreq));
   CG_TRY(K.b_jobs.ensure(nreq));
   CG_TRY(K.b_info.ensure(nreq));
@@ -56,14 +57,12 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   CG_TRY(K.b_counts.ensure(nreq));
   CG_TRY(K.b_modes.ensure(nreq));
   CG_TRY(K.b_err.ensure(1));
-  const uint64_t upload_bytes = nreq * (sizeof(cg_copy) + 4 + 8 + 8) + 64;
+  const uint64_t upload_bytes = round_up(nreq * sizeof(cg_copy), 8) + nreq * 8 + 64;
   CG_TRY(K.h_stage_in.ensure(upload_bytes));
   CG_TRY(K.h_modes.ensure(nreq));
   cg_copy *h_reqs = reinterpret_cast<cg_copy *>(K.h_stage_in.p);
-  B.h_order = reinterpret_cast<uint32_t *>(h_reqs + nreq);
-  B.h_segfirst = reinterpret_cast<uint64_t *>(K.h_stage_in.p +
-                                              round_up(nreq * (sizeof(cg_copy) + 4), 8));
-  uint64_t *h_stagep = B.h_segfirst + nreq;
+  uint64_t *h_stagep =
+      reinterpret_cast<uint64_t *>(K.h_stage_in.p + round_up(nreq * sizeof(cg_copy), 8));
   std::memcpy(h_reqs, reqs, nreq * sizeof(cg_copy));
 
   // overlapping device->device copies are staged (R12); their source and
@@ -98,8 +97,6 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   CG_CUDA(cudaMemcpyAsync(K.b_stage.p, h_stagep, nreq * 8, cudaMemcpyHostToDevice, look));
   BatchPlan &plan = B.plan;
   plan.reqs = K.b_reqs.p;
-  plan.order = K.b_order.p;
-  plan.seg_first = K.b_segfirst.p;
   plan.stage = K.b_stage.p;
   plan.jobs = K.b_jobs.p;
   plan.info = K.b_info.p;
@@ -119,43 +116,76 @@ cg_status batch_prepare(cg_ctx *c, BatchBufs &K, const cg_copy *reqs, uint64_t n
   B.modes = K.h_modes.p;
   const uint64_t t_plan = now_ns();
   c->stats.batch_lookup_ns += t_plan - t_lookup;
-  // dependency levels, exact on validity
+  // dependency levels, exact on validity, over planning units: whole
+  // copies and, on the TMA engine, pieces of long host reads
   NvtxRange r_plan("cg batch: plan levels");
-  B.lvl = plan_levels(reqs, nreq, c->cfg.carry != 0, B.modes);
+  B.tma = c->cfg.scan_engine != 1 && !c->img_on_host;
+  const uint32_t pk = c->cfg.batch_piece_kib ? c->cfg.batch_piece_kib : 1024u;
+  const uint64_t tile_rows = scan_tma_tile_bytes() / 512;
+  const uint64_t piece_rows =
+      (B.tma && pk != 0xFFFFFFFFu)
+          ? std::max<uint64_t>(tile_rows, ((uint64_t)pk * 2) / tile_rows * tile_rows)
+          : 0;
+  B.units = plan_pieces(reqs, nreq, c->cfg.carry != 0, B.modes, c->img.n, piece_rows);
+  B.npos = B.units.size();
+  B.lvl.assign(nreq, 0);
   B.nlev = 0;
-  for (int l : B.lvl) B.nlev = std::max(B.nlev, l + 1);
+  bool any_piece = false;
+  for (const PlanUnit &u : B.units) {
+    B.nlev = std::max(B.nlev, u.level + 1);
+    if (!u.rhi) B.lvl[u.req] = u.level;
+    any_piece |= u.rhi != 0;
+  }
   B.lev_start.assign(B.nlev + 1, 0);
-  for (int l : B.lvl) B.lev_start[l + 1]++;
+  for (const PlanUnit &u : B.units) B.lev_start[u.level + 1]++;
   for (int l = 0; l < B.nlev; l++) B.lev_start[l + 1] += B.lev_start[l];
+  // per position: request, first segment, piece (one pinned block)
+  const uint64_t np = B.npos;
+  CG_TRY(K.h_pos.ensure(round_up(np * 4, 8) + 2 * np * 8 + 64));
+  B.h_order = reinterpret_cast<uint32_t *>(K.h_pos.p);
+  B.h_segfirst = reinterpret_cast<uint64_t *>(K.h_pos.p + round_up(np * 4, 8));
+  B.h_piece = B.h_segfirst + np;
+  CG_TRY(K.b_order.ensure(np));
+  CG_TRY(K.b_segfirst.ensure(np));
+  if (any_piece) CG_TRY(K.b_piece.ensure(np));
+  plan.order = K.b_order.p;
+  plan.seg_first = K.b_segfirst.p;
+  plan.piece = any_piece ? K.b_piece.p : nullptr;
   {
-    // within a level, copies in decreasing order of work (power-of-two
+    // within a level, units in decreasing order of work (power-of-two
     // classes, stable): a level's segments are dealt to the warps in
-    // turn, so the last turns hold the short segments of small copies
-    // and the level's tail is short (copies of one level touch disjoint
+    // turn, so the last turns hold the short segments of small units
+    // and the level's tail is short (units of one level touch disjoint
     // shadow, so their order is free)
-    const bool tma = c->cfg.scan_engine != 1 && !c->img_on_host;
-    std::vector<uint8_t> cls(nreq);
+    std::vector<uint8_t> cls(np);
     uint64_t cnt[66] = {0};
-    for (uint64_t i = 0; i < nreq; i++) {
-      const cg_copy &q = reqs[i];
-      uint64_t work = q.n;
-      if (q.kind == CG_DTOD && !(B.modes[i] & (kModeCarry | kModeReadDev))) work = 0;
-      if (tma && q.kind == CG_DTOH && !(B.modes[i] & kModeReadDev)) work = q.n >> 3;
-      cls[i] = (uint8_t)(work ? 64 - __builtin_clzll(work) : 0);
-      cnt[65 - cls[i]]++;
+    for (uint64_t k = 0; k < np; k++) {
+      const PlanUnit &u = B.units[k];
+      const cg_copy &q = reqs[u.req];
+      uint64_t work = u.rhi ? 512ull * (u.rhi - u.rlo) : q.n;
+      if (q.kind == CG_DTOD && !(B.modes[u.req] & (kModeCarry | kModeReadDev))) work = 0;
+      if (B.tma && q.kind == CG_DTOH && !(B.modes[u.req] & kModeReadDev)) work = q.n >> 3;
+      cls[k] = (uint8_t)(work ? 64 - __builtin_clzll(work) : 0);
+      cnt[65 - cls[k]]++;
     }
     for (int k = 1; k < 66; k++) cnt[k] += cnt[k - 1];
-    std::vector<uint32_t> by_work(nreq);
-    for (uint64_t i = 0; i < nreq; i++) by_work[cnt[64 - cls[i]]++] = (uint32_t)i;
+    std::vector<uint32_t> by_work(np);
+    for (uint64_t k = 0; k < np; k++) by_work[cnt[64 - cls[k]]++] = (uint32_t)k;
     std::vector<uint64_t> fill(B.lev_start.begin(), B.lev_start.end() - 1);
-    for (uint32_t i : by_work) B.h_order[fill[B.lvl[i]]++] = i;
+    for (uint32_t k : by_work) {
+      const PlanUnit &u = B.units[k];
+      const uint64_t pos = fill[u.level]++;
+      B.h_order[pos] = u.req;
+      B.h_piece[pos] = u.rhi ? ((uint64_t)u.rlo | ((uint64_t)u.rhi << 32)) : 0ull;
+    }
   }
   for (auto &sc : B.stages) sc.level = B.lvl[sc.req];
   std::sort(B.stages.begin(), B.stages.end(),
             [](const StageCopy &a, const StageCopy &b) { return a.level < b.level; });
   c->stats.batch_plan_ns += now_ns() - t_plan;
-  CG_CUDA(cudaMemcpyAsync(K.b_order.p, B.h_order, nreq * 4, cudaMemcpyHostToDevice, st));
-  B.tma = c->cfg.scan_engine != 1 && !c->img_on_host;
+  CG_CUDA(cudaMemcpyAsync(K.b_order.p, B.h_order, np * 4, cudaMemcpyHostToDevice, st));
+  if (any_piece)
+    CG_CUDA(cudaMemcpyAsync(K.b_piece.p, B.h_piece, np * 8, cudaMemcpyHostToDevice, st));
   CG_TRY(K.b_claim.ensure((uint64_t)B.nlev));
   int per_sm = (int)c->cfg.batch_ctas_per_sm;
   if (per_sm <= 0) per_sm = B.tma ? 1 : 8;
@@ -178,6 +208,12 @@ cg_status batch_split(cg_ctx *c, BatchBufs &K, BatchRun &B, uint64_t seg_bytes,
       const uint32_t i = B.h_order[pos];
       const cg_copy &q = B.reqs[i];
       B.h_segfirst[pos] = acc_segs;
+      if (B.h_piece[pos]) {  // rows [lo, hi) of the copy; segments are whole tiles
+        const uint64_t rows = (B.h_piece[pos] >> 32) - (B.h_piece[pos] & 0xFFFFFFFFull);
+        const uint64_t seg_rows = seg_chunks >> 5;
+        acc_segs += (rows + seg_rows - 1) / seg_rows;
+        continue;
+      }
       const bool idle = q.kind == CG_DTOD && !(B.modes[i] & (kModeCarry | kModeReadDev));
       // the TMA engine walks a device->host copy with no valid source in
       // 128-byte super-chunks (its A bits alone)
@@ -187,7 +223,7 @@ cg_status batch_split(cg_ctx *c, BatchBufs &K, BatchRun &B, uint64_t seg_bytes,
     }
     B.lev_segs[l] = acc_segs;
   }
-  CG_CUDA(cudaMemcpyAsync(K.b_segfirst.p, B.h_segfirst, B.nreq * 8, cudaMemcpyHostToDevice, st));
+  CG_CUDA(cudaMemcpyAsync(K.b_segfirst.p, B.h_segfirst, B.npos * 8, cudaMemcpyHostToDevice, st));
   return CG_OK;
 }
 

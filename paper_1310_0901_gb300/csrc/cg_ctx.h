@@ -425,6 +425,19 @@ class LevelTree {
 std::vector<int> plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry,
                              const uint8_t *modes = nullptr);
 
+// A batch cut into planning units: whole copies, and pieces of the copies
+// that only read host bytes (host->device copies that carry nothing).
+struct PlanUnit {
+  uint32_t req;
+  uint32_t rlo, rhi;  // rows [rlo, rhi) of the copy's anchor grid; rhi = 0: the whole copy
+  int level;
+};
+// The units of a batch with their dependency levels (sequential semantics,
+// as plan_levels; see cg_host.cpp).  piece_rows: rows per piece (a
+// multiple of the tile's rows), 0 = whole copies only.
+std::vector<PlanUnit> plan_pieces(const cg_copy *reqs, uint64_t nreq, bool carry,
+                                  const uint8_t *modes, uint64_t host_n, uint64_t piece_rows);
+
 // --------------------------------------------------------------- context
 
 template <typename T>
@@ -481,7 +494,7 @@ struct PinBuf {
 struct BatchBufs {
   DevBuf<cg_copy> b_reqs;
   DevBuf<uint32_t> b_order;
-  DevBuf<uint64_t> b_segfirst, b_stage;
+  DevBuf<uint64_t> b_segfirst, b_stage, b_piece;
   DevBuf<ScanJob> b_jobs;
   DevBuf<RangeInfo> b_info;
   DevBuf<Acc> b_acc;
@@ -494,7 +507,8 @@ struct BatchBufs {
   DevBuf<uint8_t> b_modes;
   DevBuf<uint8_t> stage;  // overlapping device->device sources
   PinBuf<uint8_t> h_modes;
-  PinBuf<uint8_t> h_stage_in;  // pinned upload staging
+  PinBuf<uint8_t> h_stage_in;  // pinned upload staging (requests, stage pointers)
+  PinBuf<uint8_t> h_pos;       // per order position: request, first segment, piece
   PinBuf<cg_report> h_reps;
   PinBuf<cg_err_record> h_recs;
   PinBuf<uint64_t> h_total;
@@ -511,6 +525,7 @@ struct BatchBufs {
     b_reqs.release();
     b_order.release();
     b_segfirst.release();
+    b_piece.release();
     b_stage.release();
     b_jobs.release();
     b_info.release();
@@ -525,6 +540,7 @@ struct BatchBufs {
     stage.release();
     h_modes.release();
     h_stage_in.release();
+    h_pos.release();
     h_reps.release();
     h_recs.release();
     h_total.release();

@@ -17,14 +17,6 @@ __device__ __forceinline__ uint4 ld_stream(const void *p) {
 __device__ __forceinline__ uint4 ld_plain(const void *p) {
   return __ldcg(reinterpret_cast<const uint4 *>(p));
 }
-// through L1: the device->host carry's merge reads, which a tile's pre-pass
-// may already have brought into L1 (prefetch_l1)
-__device__ __forceinline__ uint4 ld_l1(const void *p) {
-  return __ldca(reinterpret_cast<const uint4 *>(p));
-}
-__device__ __forceinline__ void prefetch_l1(const void *p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
 __device__ __forceinline__ void st_stream(void *p, uint4 v) {
   __stcs(reinterpret_cast<uint4 *>(p), v);
 }
@@ -60,6 +52,24 @@ __device__ __forceinline__ uint4 funnel16(uint4 a, uint4 b, int r) {
       break;
   }
   return o;
+}
+
+// The same without branches, for an r that differs between the lanes of a
+// warp (rows of different alignment): the five words the result needs are
+// picked with selects on r's two word bits, then funnel-shifted.
+__device__ __forceinline__ uint4 funnel16_lanes(uint4 a, uint4 b, int r) {
+  const int s = (r & 3) * 8;
+  const bool w1 = r & 4, w2 = r & 8;
+  auto pick = [&](uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
+    return w2 ? (w1 ? p3 : p2) : (w1 ? p1 : p0);
+  };
+  const uint32_t x0 = pick(a.x, a.y, a.z, a.w);
+  const uint32_t x1 = pick(a.y, a.z, a.w, b.x);
+  const uint32_t x2 = pick(a.z, a.w, b.x, b.y);
+  const uint32_t x3 = pick(a.w, b.x, b.y, b.z);
+  const uint32_t x4 = pick(b.x, b.y, b.z, b.w);
+  return make_uint4(__funnelshift_r(x0, x1, s), __funnelshift_r(x1, x2, s),
+                    __funnelshift_r(x2, x3, s), __funnelshift_r(x3, x4, s));
 }
 
 // 4-bit mask of the nonzero bytes of x (bit k <-> byte k).  Bit 7 of each
@@ -196,9 +206,12 @@ __device__ __forceinline__ void lane_acc_reset(LaneAcc &la) {
 
 // Classify one 16-byte anchor chunk (copy bytes [i0, i0+16)) and carry it:
 // V = the input V window, a16 = its A bits (all ones for device->device).
+// old: for a device->host carry, the destination's host V block if the
+// caller has read it already (else it is read here when needed).
 template <uint32_t KIND, bool CARRY>
 __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uint32_t a16,
-                                           uint32_t vm, LaneAcc &la) {
+                                           uint32_t vm, LaneAcc &la,
+                                           const uint4 *old_in = nullptr) {
   // vm: bytes of this chunk inside the copy (0xFFFF for interior tiles)
   const bool clean = ((V.x | V.y | V.z | V.w) == 0u) && (((a16 | ~vm) & 0xFFFFu) == 0xFFFFu);
   if (!clean && vm) {
@@ -237,7 +250,7 @@ __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uin
       if (wm == 0xFFFFu) {
         st_stream(p, V);
       } else if (vm == 0xFFFFu) {  // interior chunk with holes: merge
-        const uint4 old = ld_l1(p);
+        const uint4 old = old_in ? *old_in : ld_plain(p);
         const uint4 m = expand16(a16);
         uint4 o;
         o.x = (V.x & m.x) | (old.x & ~m.x);

@@ -21,6 +21,56 @@ cg_status cgi::cuda_fail(cudaError_t e, const char *what) {
   return set_error(CG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+namespace {
+
+// An endpoint of a range, tagged with its owner's index and slot.
+struct Ep {
+  uint64_t v;
+  uint32_t req;
+  uint32_t slot;
+};
+
+// Rank of each endpoint's value among the distinct values, written to
+// idx[stride * req + slot]; returns the number of distinct values.  Large
+// sets sort by LSD radix (11-bit digits, skipping digits no two keys differ
+// in), small ones directly (only the ranks matter, so ties may go either way).
+int compress_endpoints(std::vector<Ep> &e, int32_t *idx, int stride) {
+  if (e.size() < 1024) {
+    std::sort(e.begin(), e.end(), [](const Ep &a, const Ep &b) { return a.v < b.v; });
+  } else {
+    std::vector<Ep> tmp(e.size());
+    uint64_t any = 0, all = ~0ull;
+    for (const Ep &x : e) {
+      any |= x.v;
+      all &= x.v;
+    }
+    const uint64_t differ = any ^ all;
+    for (int shift = 0; shift < 64; shift += 11) {
+      if (((differ >> shift) & 2047) == 0) continue;
+      uint32_t cnt[2048] = {0};
+      for (const Ep &x : e) cnt[(x.v >> shift) & 2047]++;
+      uint32_t sum = 0;
+      for (int d = 0; d < 2048; d++) {
+        const uint32_t c = cnt[d];
+        cnt[d] = sum;
+        sum += c;
+      }
+      for (const Ep &x : e) tmp[cnt[(x.v >> shift) & 2047]++] = x;
+      e.swap(tmp);
+    }
+  }
+  int rank = -1;
+  uint64_t prev = 0;
+  for (size_t k = 0; k < e.size(); k++) {
+    if (k == 0 || e[k].v != prev) rank++;
+    prev = e[k].v;
+    idx[(size_t)stride * e[k].req + e[k].slot] = rank;
+  }
+  return rank + 1;
+}
+
+}  // namespace
+
 // Dependency levels for sequential semantics (R15): a copy's level is one
 // more than the highest level of any earlier copy it conflicts with (it
 // reads what that copy writes, writes what it reads, or writes what it
@@ -38,11 +88,6 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
   auto writes = [&](uint64_t i) { return !modes || (modes[i] & kModeCarry); };
   // endpoints of every range, tagged (request, slot): slots 0/1 host read,
   // 2/3 host write, 4/5 device read, 6/7 device write
-  struct Ep {
-    uint64_t v;
-    uint32_t req;
-    uint32_t slot;
-  };
   std::vector<Ep> he, de;
   he.reserve(2 * nreq);
   de.reserve(2 * nreq);
@@ -77,50 +122,10 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
       }
     }
   }
-  // compress: each endpoint gets the rank of its value among distinct values
   std::vector<int32_t> idx(8 * nreq, -1);
-  std::vector<Ep> tmp;
-  auto radix_sort = [&](std::vector<Ep> &e) {  // LSD, 11-bit digits, skipping flat ones
-    tmp.resize(e.size());
-    uint64_t any = 0, all = ~0ull;  // a digit no two keys differ in needs no pass
-    for (const Ep &x : e) {
-      any |= x.v;
-      all &= x.v;
-    }
-    const uint64_t differ = any ^ all;
-    for (int shift = 0; shift < 64; shift += 11) {
-      if (((differ >> shift) & 2047) == 0) continue;
-      uint32_t cnt[2048] = {0};
-      for (const Ep &x : e) cnt[(x.v >> shift) & 2047]++;
-      uint32_t sum = 0;
-      for (int d = 0; d < 2048; d++) {
-        const uint32_t c = cnt[d];
-        cnt[d] = sum;
-        sum += c;
-      }
-      for (const Ep &x : e) tmp[cnt[(x.v >> shift) & 2047]++] = x;
-      e.swap(tmp);
-    }
-  };
-  auto compress = [&](std::vector<Ep> &e) -> int {
-    // the radix passes cost ~2048-entry scans each: small sets sort directly
-    // (only the ranks of values matter, so the order of ties is free)
-    if (e.size() < 1024)
-      std::sort(e.begin(), e.end(), [](const Ep &a, const Ep &b) { return a.v < b.v; });
-    else
-      radix_sort(e);
-    int rank = -1;
-    uint64_t prev = 0;
-    for (size_t k = 0; k < e.size(); k++) {
-      if (k == 0 || e[k].v != prev) rank++;
-      prev = e[k].v;
-      idx[8 * (size_t)e[k].req + e[k].slot] = rank;
-    }
-    return rank + 1;
-  };
   LevelTree ht, dt;
-  ht.init(compress(he));
-  dt.init(compress(de));
+  ht.init(compress_endpoints(he, idx.data(), 8));
+  dt.init(compress_endpoints(de, idx.data(), 8));
   for (uint64_t i = 0; i < nreq; i++) {
     if (reqs[i].n == 0) continue;
     const int32_t *x = &idx[8 * i];
@@ -137,6 +142,201 @@ std::vector<int> cgi::plan_levels(const cg_copy *reqs, uint64_t nreq, bool carry
     lvl[i] = l;
   }
   return lvl;
+}
+
+namespace {
+
+// Conflicts in the host space, exact, per 64 KiB block of the host image.
+// A block keeps the highest write and read levels of every unit that
+// touched it (w_any, r_any), of the units that covered it whole (w_full,
+// r_full), and the exact ranges of up to kCap units that touched it only
+// in part.  A range meets an earlier unit iff, in a block it covers whole,
+// that block's *_any levels say so, or, in a block at one of its ends, the
+// unit covered the block whole or is one of the block's partial entries
+// that overlaps it.  A block with more partial entries than kCap falls
+// back to its *_any levels (conservative: it may order units that do not
+// overlap).  Cost per unit: the blocks it spans plus two short scans.
+struct HostConflicts {
+  static constexpr int kShift = 16;
+  static constexpr int kCap = 8;
+  struct Entry {
+    uint64_t lo, hi;
+    int level;
+    bool write;
+  };
+  struct Slot {
+    int n = 0;
+    bool over = false;
+    Entry e[kCap];
+  };
+  std::vector<int> w_any, r_any, w_full, r_full;
+  std::vector<int32_t> slot_of;  // -1: no partial entries
+  std::vector<Slot> slots;
+
+  explicit HostConflicts(uint64_t host_n) {
+    const size_t nb = (size_t)(host_n >> kShift) + 2;
+    w_any.assign(nb, -1);
+    r_any.assign(nb, -1);
+    w_full.assign(nb, -1);
+    r_full.assign(nb, -1);
+    slot_of.assign(nb, -1);
+  }
+  // highest level of an earlier unit that writes within [a, b), or (write)
+  // reads or writes within it
+  int query(uint64_t a, uint64_t b, bool write) const {
+    int l = -1;
+    if (b <= a) return l;
+    const uint64_t k0 = a >> kShift, k1 = (b - 1) >> kShift;
+    // the blocks the range covers whole: everything that touched them
+    const uint64_t f0 = (a + (1ull << kShift) - 1) >> kShift, f1 = b >> kShift;
+    for (uint64_t k = f0; k < f1; k++) {
+      l = std::max(l, w_any[k]);
+      if (write) l = std::max(l, r_any[k]);
+    }
+    // the blocks at its ends that it covers in part
+    auto edge = [&](uint64_t k) {
+      const int32_t sl = slot_of[k];
+      if (sl >= 0 && slots[sl].over) {
+        l = std::max(l, w_any[k]);
+        if (write) l = std::max(l, r_any[k]);
+        return;
+      }
+      l = std::max(l, w_full[k]);
+      if (write) l = std::max(l, r_full[k]);
+      if (sl < 0) return;
+      const Slot &s = slots[sl];
+      for (int j = 0; j < s.n; j++)
+        if ((s.e[j].write || write) && s.e[j].lo < b && a < s.e[j].hi)
+          l = std::max(l, s.e[j].level);
+    };
+    if (k0 < f0 || f0 >= f1) edge(k0);
+    if (k1 != k0 && k1 >= f1) edge(k1);
+    return l;
+  }
+  void update(uint64_t a, uint64_t b, bool write, int level) {
+    if (b <= a) return;
+    const uint64_t k0 = a >> kShift, k1 = (b - 1) >> kShift;
+    const uint64_t f0 = (a + (1ull << kShift) - 1) >> kShift, f1 = b >> kShift;
+    std::vector<int> &any = write ? w_any : r_any;
+    std::vector<int> &full = write ? w_full : r_full;
+    for (uint64_t k = f0; k < f1; k++) {
+      any[k] = std::max(any[k], level);
+      full[k] = std::max(full[k], level);
+    }
+    auto edge = [&](uint64_t k) {
+      any[k] = std::max(any[k], level);
+      if (slot_of[k] < 0) {
+        slot_of[k] = (int32_t)slots.size();
+        slots.emplace_back();
+      }
+      Slot &s = slots[slot_of[k]];
+      if (s.n < kCap)
+        s.e[s.n++] = Entry{a, b, level, write};
+      else
+        s.over = true;
+    };
+    if (k0 < f0 || f0 >= f1) edge(k0);
+    if (k1 != k0 && k1 >= f1) edge(k1);
+  }
+};
+
+}  // namespace
+
+// Dependency levels over planning units (R15).  A host->device copy that
+// carries nothing only reads its host bytes; a long one is cut into pieces
+// of piece_rows rows of its anchor grid (the host buffer, 16-byte aligned,
+// so the anchor offset is the host offset mod 16), each planned as a unit
+// of its own: a piece waits only for the writes it overlaps, not for every
+// write the whole copy overlaps.  The pieces of a copy add to the same
+// report (counts and first offsets are sums and minima).
+//
+// Conflicts in the host space are tracked per 64 KiB block of the host
+// image (HostConflicts: exact unless a block holds many partial ranges,
+// and linear in the bytes planned); the device space keeps the exact
+// interval tree.
+std::vector<PlanUnit> cgi::plan_pieces(const cg_copy *reqs, uint64_t nreq, bool carry,
+                                       const uint8_t *modes, uint64_t host_n,
+                                       uint64_t piece_rows) {
+  std::vector<PlanUnit> units;
+  units.reserve(nreq + nreq / 4);
+  auto reads_dev = [&](uint64_t i) { return !modes || (modes[i] & kModeReadDev); };
+  auto writes = [&](uint64_t i) { return !modes || (modes[i] & kModeCarry); };
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_copy &q = reqs[i];
+    const uint64_t ax = q.src & 15;
+    const uint64_t rows = (((ax + q.n + 15) >> 4) + 31) >> 5;
+    if (carry && piece_rows && q.kind == CG_HTOD && !writes(i) && rows > piece_rows + piece_rows / 2) {
+      for (uint64_t r = 0; r < rows; r += piece_rows)
+        units.push_back({(uint32_t)i, (uint32_t)r, (uint32_t)std::min(rows, r + piece_rows), 0});
+    } else {
+      units.push_back({(uint32_t)i, 0u, 0u, 0});
+    }
+  }
+  if (!carry) return units;  // nothing is written: every unit at level 0
+  // host bytes [lo, hi) a unit reads or writes (0, 0: none)
+  auto host_range = [&](const PlanUnit &u, bool &is_write) -> std::pair<uint64_t, uint64_t> {
+    const cg_copy &q = reqs[u.req];
+    is_write = false;
+    if (q.n == 0) return {0, 0};
+    if (q.kind == CG_HTOD) {
+      if (!u.rhi) return {q.src, q.src + q.n};
+      const int64_t ax = (int64_t)(q.src & 15);
+      const int64_t b0 = std::max<int64_t>(0, 512 * (int64_t)u.rlo - ax);
+      const int64_t b1 = std::min<int64_t>((int64_t)q.n, 512 * (int64_t)u.rhi - ax);
+      return {q.src + (uint64_t)b0, q.src + (uint64_t)b1};
+    }
+    if (q.kind == CG_DTOH && writes(u.req)) {
+      is_write = true;
+      return {q.dst, q.dst + q.n};
+    }
+    return {0, 0};
+  };
+  HostConflicts hc(host_n);
+  // device space: the exact tree over compressed endpoints
+  auto end_of = [](uint64_t a, uint64_t n) { return a + n < a ? ~0ull : a + n; };
+  std::vector<Ep> de;
+  de.reserve(4 * nreq);
+  for (const PlanUnit &u : units) {
+    const cg_copy &q = reqs[u.req];
+    if (q.n == 0 || u.rhi) continue;
+    if ((q.kind == CG_DTOH || q.kind == CG_DTOD) && reads_dev(u.req)) {
+      de.push_back({q.src, u.req, 0});
+      de.push_back({end_of(q.src, q.n), u.req, 1});
+    }
+    if ((q.kind == CG_HTOD || q.kind == CG_DTOD) && writes(u.req)) {
+      de.push_back({q.dst, u.req, 2});
+      de.push_back({end_of(q.dst, q.n), u.req, 3});
+    }
+  }
+  std::vector<int32_t> rk(4 * nreq, -1);
+  LevelTree dt;
+  dt.init(compress_endpoints(de, rk.data(), 4));
+  for (PlanUnit &u : units) {
+    const cg_copy &q = reqs[u.req];
+    if (q.n == 0) continue;
+    bool hwrite = false;
+    const auto h = host_range(u, hwrite);
+    int l = hc.query(h.first, h.second, hwrite);
+    const bool drd = !u.rhi && (q.kind == CG_DTOH || q.kind == CG_DTOD) && reads_dev(u.req);
+    const bool dwr = !u.rhi && (q.kind == CG_HTOD || q.kind == CG_DTOD) && writes(u.req);
+    int r0 = 0, r1 = 0, w0 = 0, w1 = 0;
+    if (drd) {
+      r0 = rk[4 * (size_t)u.req];
+      r1 = rk[4 * (size_t)u.req + 1];
+      l = std::max(l, dt.query(r0, r1, false));
+    }
+    if (dwr) {
+      w0 = rk[4 * (size_t)u.req + 2];
+      w1 = rk[4 * (size_t)u.req + 3];
+      l = std::max(l, dt.query(w0, w1, true));
+    }
+    l += 1;
+    hc.update(h.first, h.second, hwrite, l);
+    if (drd) dt.update_r(r0, r1, l);
+    if (dwr) dt.update_w(w0, w1, l);
+    u.level = l;
+  }
+  return units;
 }
 
 // Queue 0xFF refills of released shadow ranges on `st`.
@@ -628,6 +828,30 @@ cg_status cg_check_copy_async(cg_ctx *c, const cg_copy *req, cg_report *rep_dev,
     job.kind = CG_DTOD;
   }
   return enqueue_single(c, ri, job, stage, stage_src, rep_dev, static_cast<cudaStream_t>(stream));
+}
+
+cg_status cg_plan_units(const cg_copy *reqs, uint64_t nreq, uint32_t carry, const uint8_t *modes,
+                        uint64_t host_n, uint64_t piece_rows, uint32_t *req, uint32_t *row_lo,
+                        uint32_t *row_hi, int32_t *level, uint64_t cap, uint64_t *n_units) {
+  if ((nreq && !reqs) || !n_units || (cap && (!req || !row_lo || !row_hi || !level)))
+    return set_error(CG_E_ARG, "NULL argument");
+  for (uint64_t i = 0; i < nreq; i++) {
+    const cg_copy &q = reqs[i];
+    const bool host = q.kind == CG_HTOD || q.kind == CG_DTOH;
+    const uint64_t h = q.kind == CG_HTOD ? q.src : q.dst;
+    if (host && (h > host_n || q.n > host_n - h))
+      return set_error(CG_E_HOST_RANGE, "host range outside the host image");
+  }
+  const std::vector<PlanUnit> u = plan_pieces(reqs, nreq, carry != 0, modes, host_n, piece_rows);
+  *n_units = u.size();
+  if (u.size() > cap) return set_error(CG_E_TOO_BIG, "more units than cap");
+  for (size_t k = 0; k < u.size(); k++) {
+    req[k] = u[k].req;
+    row_lo[k] = u[k].rlo;
+    row_hi[k] = u[k].rhi;
+    level[k] = u[k].level;
+  }
+  return CG_OK;
 }
 
 cg_status cg_plan_levels(const cg_copy *reqs, uint64_t nreq, uint32_t carry, const uint8_t *modes,

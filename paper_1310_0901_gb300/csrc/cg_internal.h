@@ -95,6 +95,10 @@ struct BatchPlan {
   const uint32_t *order;      // request indices, level-major
   const uint64_t *seg_first;  // per order position: first segment id within its level
   const uint64_t *stage;      // per request: staging buffer for overlapping DtoD, 0 = none
+  // per order position: the rows [lo, hi) of its copy that the position
+  // covers, packed lo | hi << 32 (a row is 32 anchor chunks); 0 = the whole
+  // copy.  Null: every position is a whole copy.  (TMA level kernel only.)
+  const uint64_t *piece;
   ScanJob *jobs;              // per request
   RangeInfo *info;            // per request
   Acc *acc;                   // per request

@@ -24,11 +24,12 @@ namespace cgi {
 // last segment).  Either way a warp's segments increase, and each
 // segment's tiles are taken in turn.  The copy owning a segment is found by
 // one binary search per warp, then by galloping forward from the previous
-// copy.  Producer and consumer walk the same segment sequence, the producer
-// kNS tiles ahead: the producer claims and hands each claim to the
-// consumer through a small per-warp ring in shared memory.  (Claiming one
-// segment ahead, to hide the atomic's latency, lengthened each level's
-// tail: slower on error-dense batches.)
+// copy.  Only the producer side of a warp walks this sequence (kNS tiles
+// ahead): with each tile it issues it leaves a descriptor in the stage (the
+// copy's order position and the tile's index), and the consumer side
+// follows the descriptors.  (Claiming one segment ahead, to hide the
+// atomic's latency, lengthened each level's tail: slower on error-dense
+// batches.)
 #ifndef CG_LEVEL_UNROLL
 #define CG_LEVEL_UNROLL 2
 #endif
@@ -43,7 +44,27 @@ struct SegIter {
   ScanJob job;
   Geo g;
   int64_t t, t_end;  // tile range of the segment
+  int64_t rlo, rhi;  // rows of the copy the position covers (hi = -1: to the copy's end)
   bool valid;
+};
+
+// Segment claims of the level kernel's producer: static striding (no
+// counter) or the next unclaimed segment from the level's counter.
+struct LevelClaims {
+  unsigned long long *ctr;
+  uint64_t step;  // W
+  __device__ __forceinline__ uint64_t next(uint64_t cur, int lane) {
+    if (!ctr) return cur + step;
+    uint64_t v = 0;
+    if (lane == 0) v = step + atomicAdd(ctr, 1ull);
+    return __shfl_sync(CG_FULL, v, 0);
+  }
+};
+
+// A stage's tile as the producer issued it.
+struct TileDesc {
+  uint64_t pos;  // order position of its copy
+  int64_t t;     // tile index within the copy
 };
 
 __device__ __forceinline__ void seg_set_pos(SegIter &it, const BatchPlan &p, const Image &img,
@@ -52,6 +73,9 @@ __device__ __forceinline__ void seg_set_pos(SegIter &it, const BatchPlan &p, con
   it.first = __ldg(p.seg_first + pos);
   it.next = pos + 1 < pos_end ? __ldg(p.seg_first + pos + 1) : ~0ull;
   it.req = __ldg(p.order + pos);
+  const uint64_t pc = p.piece ? __ldg(p.piece + pos) : 0ull;
+  it.rlo = pc ? (int64_t)(pc & 0xFFFFFFFFull) : 0;
+  it.rhi = pc ? (int64_t)(pc >> 32) : -1;
   it.job = p.jobs[it.req];
   it.job.mode &= p.mode_mask;
   it.g = make_geo(it.job, img);
@@ -73,7 +97,7 @@ __device__ __forceinline__ uint64_t seg_search(const BatchPlan &p, uint64_t lo, 
 
 // Settle on segment it.s (or the first non-empty one after it).
 __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, const Image &img,
-                                           uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                           uint64_t pos_end, uint64_t n_segs, LevelClaims &src,
                                            int lane) {
   const int64_t seg_rows = p.seg_chunks >> 5;
   while (it.s < n_segs) {
@@ -89,8 +113,9 @@ __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, cons
     }
     const int64_t k = (int64_t)(it.s - it.first);
     const bool aonly = it.job.kind == CG_DTOH && !(it.job.mode & (kModeCarry | kModeReadDev));
-    const int64_t rows = ((aonly ? super_chunks(it.g) : it.g.nchunks) + 31) >> 5;
-    const int64_t r0 = k * seg_rows;
+    const int64_t rows =
+        it.rhi >= 0 ? it.rhi : ((aonly ? super_chunks(it.g) : it.g.nchunks) + 31) >> 5;
+    const int64_t r0 = it.rlo + k * seg_rows;
     const int64_t r1 = r0 + seg_rows < rows ? r0 + seg_rows : rows;
     if (r0 < r1) {
       it.t = r0 / kR;
@@ -105,7 +130,7 @@ __device__ __forceinline__ void seg_settle(SegIter &it, const BatchPlan &p, cons
 
 __device__ __forceinline__ void seg_begin(SegIter &it, const BatchPlan &p, const Image &img,
                                           uint64_t pos_begin, uint64_t pos_end, uint64_t n_segs,
-                                          uint64_t s, SegSrc &src, int lane) {
+                                          uint64_t s, LevelClaims &src, int lane) {
   it.s = s;
   it.valid = false;
   if (s >= n_segs) return;
@@ -114,7 +139,7 @@ __device__ __forceinline__ void seg_begin(SegIter &it, const BatchPlan &p, const
 }
 
 __device__ __forceinline__ void seg_advance(SegIter &it, const BatchPlan &p, const Image &img,
-                                            uint64_t pos_end, uint64_t n_segs, SegSrc &src,
+                                            uint64_t pos_end, uint64_t n_segs, LevelClaims &src,
                                             int lane) {
   if (++it.t < it.t_end) return;
   it.s = src.next(it.s, lane);
@@ -140,30 +165,30 @@ __device__ __forceinline__ void seg_issue(const SegIter &it, const uint8_t *a_bi
   }
 }
 
-__device__ __forceinline__ void seg_consume(const SegIter &it, const uint8_t *sp, int lane,
-                                            LaneAcc &la) {
-  const int64_t c0 = it.t * kR * 32;
-  const bool carry = it.job.mode & kModeCarry;
-  switch (it.job.kind) {
+__device__ __forceinline__ void tile_consume(const ScanJob &job, const Geo &g, int64_t t,
+                                             const uint8_t *sp, int lane, LaneAcc &la) {
+  const int64_t c0 = t * kR * 32;
+  const bool carry = job.mode & kModeCarry;
+  switch (job.kind) {
     case CG_HTOD:
       if (carry)
-        consume_tile<CG_HTOD, true, kLevelUnroll>(it.g, c0, sp, lane, la);
+        consume_tile<CG_HTOD, true, kLevelUnroll>(g, c0, sp, lane, la);
       else
-        consume_tile<CG_HTOD, false, kLevelUnroll>(it.g, c0, sp, lane, la);
+        consume_tile<CG_HTOD, false, kLevelUnroll>(g, c0, sp, lane, la);
       break;
     case CG_DTOH:
       if (carry)
-        consume_tile<CG_DTOH, true, kLevelUnroll>(it.g, c0, sp, lane, la);
-      else if (!(it.job.mode & kModeReadDev))
-        consume_tile_a_super(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOH, true, kLevelUnroll>(g, c0, sp, lane, la);
+      else if (!(job.mode & kModeReadDev))
+        consume_tile_a_super(g, c0, sp, lane, la);
       else
-        consume_tile<CG_DTOH, false, kLevelUnroll>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOH, false, kLevelUnroll>(g, c0, sp, lane, la);
       break;
     default:
       if (carry)
-        consume_tile<CG_DTOD, true, kLevelUnroll>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOD, true, kLevelUnroll>(g, c0, sp, lane, la);
       else
-        consume_tile<CG_DTOD, false, kLevelUnroll>(it.g, c0, sp, lane, la);
+        consume_tile<CG_DTOD, false, kLevelUnroll>(g, c0, sp, lane, la);
       break;
   }
 }
@@ -183,8 +208,8 @@ __global__ void __launch_bounds__(kTW * 32, 1)
   const int wid = threadIdx.x >> 5;
   uint8_t *wbase = smem + (size_t)wid * kWarpSmem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem) + wid * kNS;
-  uint64_t *segq = reinterpret_cast<uint64_t *>(smem + (size_t)kTW * kWarpSmem +
-                                                 (size_t)kTW * kNS * 8) + wid * kSegQ;
+  TileDesc *desc = reinterpret_cast<TileDesc *>(smem + (size_t)kTW * kWarpSmem +
+                                                 (size_t)kTW * kNS * 8) + wid * kNS;
   const uint64_t gw = (uint64_t)blockIdx.x * kTW + wid;
   const uint64_t nw = (uint64_t)gridDim.x * kTW;
   if (lane == 0) {
@@ -192,25 +217,31 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     fence_mbar_init();
   }
   __syncwarp();
-  SegSrc psrc{claim, segq, nw, 0, true};
-  SegSrc csrc{claim, segq, nw, 0, false};
-  SegIter prod, cons;
-  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, psrc, lane);
-  cons = prod;  // the first segment is the warp's own (w), settled identically
-  csrc.n = psrc.n;
+  LevelClaims src{claim, nw};
+  SegIter prod;
+  seg_begin(prod, p, img, pos_begin, pos_end, n_segs, gw, src, lane);
   asm volatile("griddepcontrol.wait;" ::: "memory");  // the previous level is complete
+  auto issue = [&](int s) {  // lane 0: the producer's tile into stage s
+    desc[s] = TileDesc{prod.pos, prod.t};
+    seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+  };
   int issued = 0;
   for (int s = 0; s < kNS && prod.valid; s++) {
-    if (lane == 0) seg_issue(prod, img.a_bits, smem_addr(wbase + s * kStage), smem_addr(&bars[s]));
+    if (lane == 0) issue(s);
     issued++;
-    seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
+    seg_advance(prod, p, img, pos_end, n_segs, src, lane);
   }
   LaneAcc la;
   lane_acc_reset(la);
   uint32_t parity = 0;
   int stage = 0;
   bool failed = false;
-  while (cons.valid) {
+  // the copy being consumed (cpos = ~0: none yet)
+  uint64_t cpos = ~0ull;
+  uint32_t creq = 0;
+  ScanJob cjob{};
+  Geo cgeo{};
+  while (issued > 0) {
     const bool ok = mbar_wait_bounded(smem_addr(&bars[stage]), (parity >> stage) & 1u);
     if (!__all_sync(CG_FULL, ok)) {
       failed = true;
@@ -218,25 +249,31 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     }
     parity ^= 1u << stage;
     issued--;
-    seg_consume(cons, wbase + stage * kStage, lane, la);
+    const TileDesc d = desc[stage];
+    if (d.pos != cpos) {
+      // a warp's tiles go forward through the level's copies, so it never
+      // comes back to a copy it left: its counts for that copy are flushed
+      // when the copy changes
+      if (cpos != ~0ull) warp_flush(la, &p.acc[creq], lane);
+      cpos = d.pos;
+      creq = __ldg(p.order + cpos);
+      cjob = p.jobs[creq];
+      cjob.mode &= p.mode_mask;
+      cgeo = make_geo(cjob, img);
+    }
+    tile_consume(cjob, cgeo, d.t, wbase + stage * kStage, lane, la);
     __syncwarp();
     if (prod.valid) {
       if (lane == 0) {
         fence_proxy_async();
-        seg_issue(prod, img.a_bits, smem_addr(wbase + stage * kStage), smem_addr(&bars[stage]));
+        issue(stage);
       }
       issued++;
-      seg_advance(prod, p, img, pos_end, n_segs, psrc, lane);
+      seg_advance(prod, p, img, pos_end, n_segs, src, lane);
     }
-    const uint32_t req = cons.req;
-    const uint64_t seg = cons.s;
-    seg_advance(cons, p, img, pos_end, n_segs, csrc, lane);
-    (void)seg;
-    // a warp's segments increase, so it never comes back to a copy it left:
-    // its counts for that copy are flushed when the copy changes
-    if (!cons.valid || cons.req != req) warp_flush(la, &p.acc[req], lane);
     stage = stage + 1 == kNS ? 0 : stage + 1;
   }
+  if (cpos != ~0ull) warp_flush(la, &p.acc[creq], lane);
   if (failed) {  // drain the copies still in flight, bounded
     for (int d = 0; d < issued; d++) {
       const int sd = (stage + d) % kNS;
@@ -273,7 +310,7 @@ cudaError_t launch_scan_level_tma(const Image &img, const BatchPlan &p, uint64_t
                                   unsigned long long *claim, unsigned int *err_flag, bool overlap,
                                   cudaStream_t st, const FinalizeHost &fin) {
   if (n_segs == 0 || pos_end <= pos_begin) return cudaSuccess;
-  constexpr size_t smem = kSmemBytes + (size_t)kTW * kSegQ * 8;
+  constexpr size_t smem = kSmemBytes + (size_t)kTW * kNS * sizeof(TileDesc);
   static KernelSetup setup;
   int per_sm = 1;
   const cudaError_t e = kernel_setup(setup, scan_level_tma_kernel, kTW * 32, smem, &per_sm);

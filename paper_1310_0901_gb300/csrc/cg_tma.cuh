@@ -9,7 +9,7 @@
 #include "cg_device.cuh"
 
 #ifndef CG_TMA_R
-#define CG_TMA_R 8
+#define CG_TMA_R 10
 #endif
 #ifndef CG_TMA_NS
 #define CG_TMA_NS 2
@@ -29,6 +29,9 @@ constexpr uint32_t kStage = ((kVBytes + kABytes) + 127u) & ~127u;  // one stage
 constexpr uint32_t kWarpSmem = kNS * kStage;
 constexpr size_t kSmemBytes = (size_t)kTW * kWarpSmem + (size_t)kTW * kNS * 8 + 128;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
+// rows of a device->host carry tile whose merge reads go out together
+constexpr int kMergeRows = kR % 5 == 0 ? 5 : (kR % 4 == 0 ? 4 : (kR % 3 == 0 ? 3 : 2));
+static_assert(kR % kMergeRows == 0, "merge groups must tile the rows");
 
 // ------------------------------------------------------------------ PTX
 
@@ -90,6 +93,20 @@ __device__ __forceinline__ int64_t ceil16(int64_t x) { return (x + 15) & ~(int64
 template <uint32_t KIND>
 __device__ __forceinline__ void issue_tile(const Geo &g, const uint8_t *a_bytes, int64_t c0,
                                            uint32_t st, uint32_t bar) {
+  if (c0 >= 1 && c0 + 32 * kR + 2 <= g.nchunks) {
+    // An interior tile: neither window reaches past the copy's ends, so no
+    // clipping -- the whole V window, and the A bytes from the one holding
+    // the tile's first bit (the same copies as the general form below)
+    const bool v = KIND == CG_HTOD || g.has_vin;
+    const int64_t p0 = g.hb0 + 16 * c0;
+    const int64_t aorig = floor16(p0 >> 3);
+    const uint32_t abytes =
+        KIND != CG_DTOD ? (uint32_t)(ceil16((p0 + 512 * kR + 39) >> 3) - aorig) : 0u;
+    mbar_arrive_expect_tx(bar, (v ? kVBytes : 0u) + abytes);
+    if (v) bulk_g2s(st, reinterpret_cast<const void *>(g.vin_al + 16 * (uintptr_t)c0), kVBytes, bar);
+    if (abytes) bulk_g2s(st + kVBytes, a_bytes + aorig, abytes, bar);
+    return;
+  }
   uint32_t tx = 0, vbytes = 0, abytes = 0, voff = 0, aoff = 0;
   uintptr_t vsrc = 0;
   int64_t asrc = 0;
@@ -242,41 +259,51 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   const int32_t qbase = (int32_t)(p0 - 8 * floor16(p0 >> 3));
   const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
   const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
+  auto a16_of = [&](int k) -> uint32_t {
+    const int32_t qb = qbase + 16 * k;
+    const int sh = qb & 31;
+    const int wi = qb >> 5;
+    const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
+    return __funnelshift_r(as[wi], w1, sh) & 0xFFFFu;
+  };
+  auto v_of = [&](int k) -> uint4 {
+    uint4 V = vs[k];
+    if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
+    return V;
+  };
   if (KIND == CG_DTOH && CARRY) {
     // The carry merges device V into the host V blocks that hold
-    // unaddressable bytes, reading each such block first.  Ask for all of
-    // the tile's blocks at once, so that those reads overlap instead of
-    // each row waiting for its own.
+    // unaddressable bytes, reading each such block first.  Rows go in
+    // groups of kMergeRows: the blocks of a group are all read before any
+    // of them is merged, so those reads overlap instead of each row waiting
+    // for its own.
+#pragma unroll 1
+    for (int u0 = 0; u0 < kR; u0 += kMergeRows) {
+      uint4 old[kMergeRows];
 #pragma unroll
-    for (int u = 0; u < kR; u++) {
-      const int k = 32 * u + lane;
-      const int32_t qb = qbase + 16 * k;
-      const int sh = qb & 31;
-      const int wi = qb >> 5;
-      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
-      const uint32_t a16 = __funnelshift_r(as[wi], w1, sh) & 0xFFFFu;
-      const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * (c0 + k) - g.ax, g.n);
-      if (vm == 0xFFFFu && a16 != 0xFFFFu) prefetch_l1(g.out_al + 16 * (c0 + k));
+      for (int j = 0; j < kMergeRows; j++) {
+        const int k = 32 * (u0 + j) + lane;
+        const uint32_t a16 = a16_of(k);
+        const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * (c0 + k) - g.ax, g.n);
+        old[j] = (vm == 0xFFFFu && a16 != 0xFFFFu) ? ld_plain(g.out_al + 16 * (c0 + k))
+                                                   : make_uint4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int j = 0; j < kMergeRows; j++) {
+        const int k = 32 * (u0 + j) + lane;
+        const uint4 V = g.has_vin ? v_of(k) : make_uint4(0, 0, 0, 0);
+        const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * (c0 + k) - g.ax, g.n);
+        chunk_step<KIND, CARRY>(g, c0 + k, V, a16_of(k), vm, la, &old[j]);
+      }
     }
+    return;
   }
 #pragma unroll U
   for (int u = 0; u < kR; u++) {
     const int k = 32 * u + lane;
     const int64_t c = c0 + k;
-    uint4 V = make_uint4(0, 0, 0, 0);
-    if (KIND == CG_HTOD || g.has_vin) {
-      V = vs[k];
-      if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
-    }
-    uint32_t a16 = 0xFFFFu;
-    if (KIND != CG_DTOD) {
-      const int32_t qb = qbase + 16 * k;
-      const int sh = qb & 31;
-      const int wi = qb >> 5;
-      const uint32_t w0 = as[wi];
-      const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
-      a16 = __funnelshift_r(w0, w1, sh) & 0xFFFFu;
-    }
+    const uint4 V = (KIND == CG_HTOD || g.has_vin) ? v_of(k) : make_uint4(0, 0, 0, 0);
+    const uint32_t a16 = KIND != CG_DTOD ? a16_of(k) : 0xFFFFu;
     const uint32_t vm = full ? 0xFFFFu : valid_mask(16 * c - g.ax, g.n);
     chunk_step<KIND, CARRY>(g, c, V, a16, vm, la);
   }

@@ -134,6 +134,127 @@ def test_planner_on_small_workload_is_exact():
     assert lv.tolist() == _brute_levels(w.reqs)
 
 
+def _unit_ranges(q, u, modes):
+    """(reads, writes) of one planning unit as (space, lo, hi) triples; a
+    piece's host bytes are those of its rows of the anchor grid (512 bytes
+    a row from the 16-byte boundary at or below src)."""
+    kind, d, s, n = int(q["kind"]), int(q["dst"]), int(q["src"]), int(q["n"])
+    carry = bool(modes[int(u["req"])] & 1)
+    rdev = bool(modes[int(u["req"])] & 2)
+    if n == 0:
+        return [], []
+    if int(u["row_hi"]):
+        ax = s & 15
+        lo = max(0, 512 * int(u["row_lo"]) - ax)
+        hi = min(n, 512 * int(u["row_hi"]) - ax)
+        return [("h", s + lo, s + hi)], []
+    r, w = [], []
+    if kind == 1:
+        r.append(("h", s, s + n))
+        if carry:
+            w.append(("d", d, d + n))
+    elif kind == 2:
+        if carry:
+            w.append(("h", d, d + n))
+        if rdev:
+            r.append(("d", s, s + n))
+    else:
+        if rdev:
+            r.append(("d", s, s + n))
+        if carry:
+            w.append(("d", d, d + n))
+    return r, w
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_unit_planner_orders_every_conflict(seed):
+    """cg_plan_units: host reads longer than 1.5 pieces are cut into pieces
+    that tile their rows in order, other copies stay whole, and every pair
+    of units that conflict (one writes what the other reads or writes; a
+    piece by its own rows' host bytes) runs in increasing levels.  Pieces
+    cut the levels of long reads crossing many small writes."""
+    rng = np.random.default_rng(seed)
+    n, host_n, piece_rows = 400, 1 << 20, 8
+    reqs = np.zeros(n, S.REQ_DTYPE)
+    reqs["kind"] = rng.choice([1, 2, 3], n, p=[0.5, 0.4, 0.1])
+    small = rng.random(n) < 0.7
+    reqs["n"] = np.where(small, rng.integers(1, 6000, n), rng.integers(1, 200_000, n))
+    reqs["src"] = rng.integers(0, host_n - 200_000, n)
+    reqs["dst"] = rng.integers(0, host_n - 200_000, n)
+    modes = rng.integers(0, 4, n).astype(np.uint8)
+    modes[(reqs["kind"] == 1) & ~small] &= 2  # long host reads carry nothing
+    units = cg.plan_units(reqs, host_n, piece_rows, carry=True, modes=modes)
+    # pieces tile their copy's rows
+    whole, pieces = 0, 0
+    k = 0
+    for i, q in enumerate(reqs):
+        rows = ((((int(q["src"]) & 15) + int(q["n"]) + 15) >> 4) + 31) >> 5
+        if units[k]["req"] != i:
+            raise AssertionError(f"unit {k} is not request {i}")
+        if units[k]["row_hi"] == 0:
+            whole += 1
+            k += 1
+            continue
+        assert q["kind"] == 1 and not modes[i] & 1 and rows > piece_rows * 1.5
+        r = 0
+        while k < len(units) and units[k]["req"] == i:
+            assert (units[k]["row_lo"], units[k]["row_hi"]) == (r, min(rows, r + piece_rows))
+            r += piece_rows
+            k += 1
+            pieces += 1
+        assert r >= rows
+    assert k == len(units) and pieces > 100
+    sets = [_unit_ranges(reqs[int(u["req"])], u, modes) for u in units]
+
+    def meet(xs, ys):
+        return any(a[0] == b[0] and a[1] < b[2] and b[1] < a[2] for a in xs for b in ys)
+
+    lv = units["level"]
+    for j in range(len(units)):
+        rj, wj = sets[j]
+        for i in range(j):
+            ri, wi = sets[i]
+            if meet(wi, rj) or meet(wi, wj) or meet(ri, wj):
+                assert lv[i] < lv[j], (i, j)
+    # where no 64 KiB block of the host image holds more than 8 ranges in
+    # part, the levels are exactly the pairwise definition's
+    if seed < 2:
+        sparse = reqs.copy()
+        sparse["src"] = rng.integers(0, (64 << 20) - 200_000, n)
+        sparse["dst"] = rng.integers(0, (64 << 20) - 200_000, n)
+        su = cg.plan_units(sparse, 64 << 20, 256, carry=True, modes=modes)
+        ss = [_unit_ranges(sparse[int(u["req"])], u, modes) for u in su]
+        want = []
+        for j in range(len(su)):
+            rj, wj = ss[j]
+            best = -1
+            for i in range(j):
+                ri, wi = ss[i]
+                if meet(wi, rj) or meet(wi, wj) or meet(ri, wj):
+                    best = max(best, want[i])
+            want.append(best + 1)
+        assert su["level"].tolist() == want
+        # exact levels: a piece meets a subset of what its whole copy meets,
+        # so pieces never need more levels than whole copies
+        whole_only = cg.plan_units(sparse, 64 << 20, 0, carry=True, modes=modes)
+        assert len(whole_only) == n and su["level"].max() <= whole_only["level"].max()
+    assert not cg.plan_units(reqs, host_n, piece_rows, carry=False, modes=modes)["level"].any()
+
+
+def test_unit_planner_keeps_adjacent_writes_apart_in_one_level():
+    """Device->host copies into adjacent host ranges (sharing 64 KiB blocks
+    of the image, never bytes) do not conflict: one level."""
+    n, size = 48, (16 << 20) - 64
+    reqs = np.zeros(n, S.REQ_DTYPE)
+    reqs["kind"] = S.DTOH
+    reqs["n"] = size
+    reqs["dst"] = np.arange(n) * (16 << 20) + 7
+    reqs["src"] = (np.arange(n) + 1) * (1 << 30)
+    modes = np.full(n, 3, np.uint8)
+    u = cg.plan_units(reqs, 1 << 30, 64, carry=True, modes=modes)
+    assert len(u) == n and not u["level"].any()
+
+
 def test_binding_structs_match_the_compiled_header(tmp_path):
     """Every ctypes mirror of a header struct has the size and field offsets a
     C compiler gives the header's declaration."""

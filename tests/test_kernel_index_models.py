@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import random
 
-kR = 8
+kR = 10
 kVBytes = 16 * (32 * kR + 1)
 kABytes = 64 * kR + 64
 kStage = ((kVBytes + kABytes) + 127) & ~127
@@ -480,3 +480,69 @@ def test_span_row_addressing_32bit_equals_64bit():
             wi64 = (((q >> 5) << 2) - aorig) >> 2
             qb = (host - 8 * aorig) - ax + 16 * c
             assert (qb >> 5, qb & 31) == (wi64, q & 31)
+
+
+# ------------------------------------------- interior tiles' bulk copies
+
+def _issue_general(g, c0):
+    """issue_tile's clipped V and A bulk copies: (voff, vsrc, vbytes, aoff, asrc, abytes)."""
+    out = [0, 0, 0, 0, 0, 0]
+    if g["kind"] == 1 or g["has_vin"]:
+        vbeg = g["vin_al"] + 16 * c0
+        vend = vbeg + kVBytes
+        lo_lim = g["vin_lo"] & ~15
+        hi_lim = (g["vin_hi"] + 15) & ~15
+        lo, hi = max(vbeg, lo_lim), min(vend, hi_lim)
+        if hi > lo:
+            out[0:3] = [lo - vbeg, lo, hi - lo]
+    if g["kind"] != 3:
+        p0 = g["hb0"] + 16 * c0
+        p1 = p0 + 512 * kR
+        aorig = f16(p0 >> 3)
+        q0, q1 = max(p0, g["hlo"]), min(p1 + 32, g["hhi"])
+        if q1 > q0:
+            b0, b1 = f16(q0 >> 3), c16((q1 + 7) >> 3)
+            out[3:6] = [b0 - aorig, b0, b1 - b0]
+    return out
+
+
+def _issue_interior(g, c0):
+    out = [0, 0, 0, 0, 0, 0]
+    if g["kind"] == 1 or g["has_vin"]:
+        out[0:3] = [0, g["vin_al"] + 16 * c0, kVBytes]
+    if g["kind"] != 3:
+        p0 = g["hb0"] + 16 * c0
+        aorig = f16(p0 >> 3)
+        out[3:6] = [0, aorig, c16((p0 + 512 * kR + 39) >> 3) - aorig]
+    return out
+
+
+def test_interior_tile_issue_equals_clipped_form():
+    """issue_tile's fast path (tiles with c0 >= 1 and c0 + 32 kR + 2 <=
+    nchunks) issues exactly the bulk copies of the general, clipped form,
+    for every kind, anchor and source alignment."""
+    rng = random.Random(23)
+    checked = 0
+    for _ in range(4000):
+        kind = rng.choice([1, 2, 3])
+        carry, rdev = rng.random() < 0.7, rng.random() < 0.7
+        n = rng.randrange(1, 1 << 20)
+        host_off = rng.randrange(0, 1 << 30)
+        dev_src = rng.randrange(1 << 30, 1 << 40)
+        dev_dst = rng.randrange(1 << 30, 1 << 40)
+        imgv = (rng.randrange(1 << 20, 1 << 30)) & ~15
+        ge = make_geo("HDT"[kind - 1], carry, rdev, n, host_off, dev_src, dev_dst, imgv)
+        if kind == 3 and not carry and not rdev:
+            continue  # no chunks: nothing is issued
+        g = {"kind": kind, "has_vin": ge["has_vin"], "vin_al": ge["vin_al"],
+             "vin_lo": ge["vin_lo"], "vin_hi": ge["vin_hi"], "hb0": ge["hb0"],
+             "hlo": ge["hlo"], "hhi": ge["hhi"]}
+        nchunks = ge["nch"]
+        ntiles = (nchunks + 32 * kR - 1) // (32 * kR)
+        for t in {0, 1, ntiles // 2, ntiles - 2, ntiles - 1}:
+            c0 = t * 32 * kR
+            if t < 0 or not (c0 >= 1 and c0 + 32 * kR + 2 <= nchunks):
+                continue
+            assert _issue_interior(g, c0) == _issue_general(g, c0), (kind, n, t)
+            checked += 1
+    assert checked > 2000
