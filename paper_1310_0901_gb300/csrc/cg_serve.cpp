@@ -18,6 +18,7 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
 
 #include "cg_ctx.h"
 
@@ -65,6 +66,81 @@ static bool races_with(const RaceEntry &q, uint32_t kind, uint64_t dst, uint64_t
          (dsp(q.kind) == dsp(kind) && meets(q.dst, q.n, dst, n)) ||
          (ssp(q.kind) == dsp(kind) && meets(q.src, q.n, dst, n));
 }
+
+// The race window's entries indexed by the blocks of the spaces their ranges
+// touch (space 0: host image offsets, 1: device addresses), so that a new
+// copy meets only the entries near its own ranges instead of scanning the
+// whole window (which, with a backlog, holds every copy finished since the
+// oldest waiting request was submitted).  Ranges of up to kSmallMax blocks
+// of 64 KiB are listed under those blocks; every range is also listed under
+// the 64 MiB blocks it touches.  A short range looks up its small blocks
+// (short entries) and its large blocks (long entries only); a long range
+// looks up its large blocks (every entry).  Candidates are then checked
+// exactly.
+struct RaceIndex {
+  static constexpr int kSmallShift = 16, kLargeShift = 26;
+  static constexpr uint64_t kSmallMax = 64;
+  struct Item {
+    uint64_t seq;
+    bool long_range;
+  };
+  std::unordered_map<uint64_t, std::vector<Item>> small, large;
+  static uint64_t key(int space, uint64_t block) { return ((uint64_t)space << 62) | block; }
+  static bool is_long(uint64_t a, uint64_t n) {
+    return ((a + n - 1) >> kSmallShift) - (a >> kSmallShift) + 1 > kSmallMax;
+  }
+  void add(int space, uint64_t a, uint64_t n, uint64_t seq) {
+    if (!n) return;
+    const bool lg = is_long(a, n);
+    if (!lg)
+      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
+        small[key(space, b)].push_back({seq, false});
+    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
+      large[key(space, b)].push_back({seq, lg});
+  }
+  static void erase_from(std::unordered_map<uint64_t, std::vector<Item>> &m, uint64_t k,
+                         uint64_t seq) {
+    auto it = m.find(k);
+    if (it == m.end()) return;
+    auto &v = it->second;
+    for (size_t i = 0; i < v.size(); i++)
+      if (v[i].seq == seq) {
+        v[i] = v.back();
+        v.pop_back();
+        break;
+      }
+    if (v.empty()) m.erase(it);
+  }
+  void remove(int space, uint64_t a, uint64_t n, uint64_t seq) {
+    if (!n) return;
+    if (!is_long(a, n))
+      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
+        erase_from(small, key(space, b), seq);
+    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
+      erase_from(large, key(space, b), seq);
+  }
+  // f(seq) for every entry that may touch [a, a+n) of `space` (some twice)
+  template <typename F>
+  void candidates(int space, uint64_t a, uint64_t n, F &&f) const {
+    if (!n) return;
+    const bool lg = is_long(a, n);
+    if (!lg)
+      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++) {
+        auto it = small.find(key(space, b));
+        if (it != small.end())
+          for (const Item &x : it->second) f(x.seq);
+      }
+    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++) {
+      auto it = large.find(key(space, b));
+      if (it == large.end()) continue;
+      for (const Item &x : it->second)
+        if (lg || x.long_range) f(x.seq);
+    }
+  }
+};
+
+static int dst_space(uint32_t kind) { return kind == CG_DTOH ? 0 : 1; }
+static int src_space(uint32_t kind) { return kind == CG_HTOD ? 0 : 1; }
 
 struct Iv {
   uint64_t a, b;
@@ -156,6 +232,7 @@ struct ServeEngine {
   uint64_t inflight_bytes = 0;
   std::vector<Deferred> deferred;
   std::deque<RaceEntry> window;  // seq order
+  RaceIndex window_index;
   cg_status fatal = CG_OK;
 
   ServeEngine(cg_ctx *ctx, size_t nclients) : c(ctx), stats_mu(ctx->stats_mu), rings(nclients) {}
@@ -230,8 +307,15 @@ struct ServeEngine {
         bound = std::min(bound, g.slots[t & g.mask].submit_ns);
     }
     size_t k = 0;
-    for (size_t i = 0; i < window.size(); i++)
-      if (!(window[i].done_ns && window[i].done_ns <= bound)) window[k++] = window[i];
+    for (size_t i = 0; i < window.size(); i++) {
+      const RaceEntry &e = window[i];
+      if (!(e.done_ns && e.done_ns <= bound)) {
+        window[k++] = e;
+      } else {
+        window_index.remove(dst_space(e.kind), e.dst, e.n, e.seq);
+        window_index.remove(src_space(e.kind), e.src, e.n, e.seq);
+      }
+    }
     window.resize(k);
   }
 
@@ -444,13 +528,23 @@ struct ServeEngine {
     int64_t race = -1;
     const bool moved = dst_ok && src_ok;
     if (moved) {
-      for (const RaceEntry &e : window)
+      // the smallest seq among the window entries near this copy's ranges
+      // that meet the definition
+      auto consider = [&](uint64_t seq) {
+        if (race >= 0 && (int64_t)seq >= race) return;
+        auto it = std::lower_bound(window.begin(), window.end(), seq,
+                                   [](const RaceEntry &e, uint64_t v) { return e.seq < v; });
+        if (it == window.end() || it->seq != seq) return;
+        const RaceEntry &e = *it;
         if (e.client != client && (e.done_ns == 0 || e.done_ns > sl->submit_ns) &&
-            races_with(e, q.kind, q.dst, q.src, q.n)) {
+            races_with(e, q.kind, q.dst, q.src, q.n))
           race = (int64_t)e.seq;
-          break;
-        }
+      };
+      window_index.candidates(dst_space(q.kind), q.dst, q.n, consider);
+      window_index.candidates(src_space(q.kind), q.src, q.n, consider);
       window.push_back({sl->res.seq, client, q.kind, q.dst, q.src, q.n, 0});
+      window_index.add(dst_space(q.kind), q.dst, q.n, sl->res.seq);
+      window_index.add(src_space(q.kind), q.src, q.n, sl->res.seq);
     }
     if (q.kind == CG_DTOD && !(job.mode & (kModeCarry | kModeReadDev))) {
       assemble_report(&sl->res.report, ri, none);
