@@ -54,24 +54,6 @@ __device__ __forceinline__ uint4 funnel16(uint4 a, uint4 b, int r) {
   return o;
 }
 
-// The same without branches, for an r that differs between the lanes of a
-// warp (rows of different alignment): the five words the result needs are
-// picked with selects on r's two word bits, then funnel-shifted.
-__device__ __forceinline__ uint4 funnel16_lanes(uint4 a, uint4 b, int r) {
-  const int s = (r & 3) * 8;
-  const bool w1 = r & 4, w2 = r & 8;
-  auto pick = [&](uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3) {
-    return w2 ? (w1 ? p3 : p2) : (w1 ? p1 : p0);
-  };
-  const uint32_t x0 = pick(a.x, a.y, a.z, a.w);
-  const uint32_t x1 = pick(a.y, a.z, a.w, b.x);
-  const uint32_t x2 = pick(a.z, a.w, b.x, b.y);
-  const uint32_t x3 = pick(a.w, b.x, b.y, b.z);
-  const uint32_t x4 = pick(b.x, b.y, b.z, b.w);
-  return make_uint4(__funnelshift_r(x0, x1, s), __funnelshift_r(x1, x2, s),
-                    __funnelshift_r(x2, x3, s), __funnelshift_r(x3, x4, s));
-}
-
 // 4-bit mask of the nonzero bytes of x (bit k <-> byte k).  Bit 7 of each
 // byte of t is set iff the byte is nonzero: adding 0x7F to its low 7 bits
 // carries into bit 7 unless they are all zero (and never past it), OR-ing
