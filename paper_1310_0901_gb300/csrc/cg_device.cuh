@@ -175,12 +175,17 @@ __device__ __forceinline__ uint32_t load_a16(const uint32_t *A32, int64_t hb, in
 
 struct LaneAcc {
   uint32_t un, ud;
+  // 0xFFFF while the lane's first unaddressable (undefined) byte is still to
+  // be found, else 0: one mask-and test per chunk instead of 64-bit compares
+  uint32_t open_un, open_ud;
   unsigned long long fun, fud;
 };
 
 __device__ __forceinline__ void lane_acc_reset(LaneAcc &la) {
   la.un = 0;
   la.ud = 0;
+  la.open_un = 0xFFFFu;
+  la.open_ud = 0xFFFFu;
   la.fun = kNone;
   la.fud = kNone;
 }
@@ -201,10 +206,16 @@ __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uin
     const uint32_t ud = vm & a16 & nz16(V);
     la.un += __popc(un);
     la.ud += __popc(ud);
-    if ((un && la.fun == kNone) || (ud && la.fud == kNone)) {
+    if ((un & la.open_un) | (ud & la.open_ud)) {  // the lane's first bad bytes (rare)
       const int64_t i0 = g.obase + 16 * c - g.ax;
-      if (un && la.fun == kNone) la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
-      if (ud && la.fud == kNone) la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
+      if (un & la.open_un) {
+        la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
+        la.open_un = 0;
+      }
+      if (ud & la.open_ud) {
+        la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
+        la.open_ud = 0;
+      }
     }
   }
   if (CARRY && vm) {

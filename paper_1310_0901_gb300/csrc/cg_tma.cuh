@@ -203,7 +203,10 @@ __device__ __forceinline__ void classify_a_words(const Geo &g, const uint32_t *a
         first = (unsigned long long)(g.obase + i0 + 32 * (int64_t)j + __ffs(zero) - 1);
     }
     la.un += un;
-    if (first != kNone && la.fun == kNone) la.fun = first;
+    if (first != kNone && la.fun == kNone) {
+      la.fun = first;
+      la.open_un = 0;
+    }
     return;
   }
   for (int j = lane; j < nwords; j += 32) {
@@ -218,7 +221,10 @@ __device__ __forceinline__ void classify_a_words(const Geo &g, const uint32_t *a
     if (zero && first == kNone) first = (unsigned long long)(g.obase + b0 + __ffs(zero) - 1);
   }
   la.un += un;
-  if (first != kNone && la.fun == kNone) la.fun = first;
+  if (first != kNone && la.fun == kNone) {
+      la.fun = first;
+      la.open_un = 0;
+    }
 }
 
 // All lanes: classify a super-tile (128 kR A words, 4096 kR bytes of copy).
@@ -259,12 +265,15 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   const int32_t qbase = (int32_t)(p0 - 8 * floor16(p0 >> 3));
   const int64_t i0_tile = 16 * c0 - g.ax;  // copy offset of the tile's first byte
   const bool full = i0_tile >= 0 && i0_tile + 512 * kR <= (int64_t)g.n;
+  // A bits of chunk k = 32 u + lane: bit qbase + 16 k of the window, i.e.
+  // word a_wi + 16 u at the lane's own shift (the same in every row)
+  const int32_t a_q = qbase + 16 * lane;
+  const int a_sh = a_q & 31;
+  const int a_wi = a_q >> 5;
   auto a16_of = [&](int k) -> uint32_t {
-    const int32_t qb = qbase + 16 * k;
-    const int sh = qb & 31;
-    const int wi = qb >> 5;
-    const uint32_t w1 = sh > 16 ? as[wi + 1] : 0u;
-    return __funnelshift_r(as[wi], w1, sh) & 0xFFFFu;
+    const int wi = a_wi + 16 * (k >> 5);
+    const uint32_t w1 = a_sh > 16 ? as[wi + 1] : 0u;
+    return __funnelshift_r(as[wi], w1, a_sh) & 0xFFFFu;
   };
   auto v_of = [&](int k) -> uint4 {
     uint4 V = vs[k];

@@ -457,6 +457,10 @@ def test_tile_a_addressing_32bit_equals_64bit():
             qb = qbase + 16 * k
             assert (qb >> 5, qb & 31) == (wi64, q & 31)
             assert 4 * (qb >> 5) + 8 <= abytes
+            # the per-lane form: word (qbase + 16 lane) >> 5 plus 16 per row
+            lane, u = k & 31, k >> 5
+            a_q = qbase + 16 * lane
+            assert ((a_q >> 5) + 16 * u, a_q & 31) == (qb >> 5, qb & 31)
 
 
 def test_span_row_addressing_32bit_equals_64bit():
