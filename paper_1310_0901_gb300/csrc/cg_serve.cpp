@@ -21,14 +21,18 @@
 #include <unordered_map>
 
 #include "cg_ctx.h"
+#include "cg_race_index.h"
 
 namespace cgi {
+
+struct RaceEntry;
 
 struct RingSlot {
   cg_request req;
   uint64_t submit_ns;
   std::atomic<uint32_t> state;  // 0 free, 1 submitted, 2 done, 3 collected
   cg_result res;
+  RaceEntry *race = nullptr;  // its race-window entry (scheduler only)
 };
 
 struct ClientRing {
@@ -66,78 +70,6 @@ static bool races_with(const RaceEntry &q, uint32_t kind, uint64_t dst, uint64_t
          (dsp(q.kind) == dsp(kind) && meets(q.dst, q.n, dst, n)) ||
          (ssp(q.kind) == dsp(kind) && meets(q.src, q.n, dst, n));
 }
-
-// The race window's entries indexed by the blocks of the spaces their ranges
-// touch (space 0: host image offsets, 1: device addresses), so that a new
-// copy meets only the entries near its own ranges instead of scanning the
-// whole window (which, with a backlog, holds every copy finished since the
-// oldest waiting request was submitted).  Ranges of up to kSmallMax blocks
-// of 64 KiB are listed under those blocks; every range is also listed under
-// the 64 MiB blocks it touches.  A short range looks up its small blocks
-// (short entries) and its large blocks (long entries only); a long range
-// looks up its large blocks (every entry).  Candidates are then checked
-// exactly.
-struct RaceIndex {
-  static constexpr int kSmallShift = 16, kLargeShift = 26;
-  static constexpr uint64_t kSmallMax = 64;
-  struct Item {
-    uint64_t seq;
-    bool long_range;
-  };
-  std::unordered_map<uint64_t, std::vector<Item>> small, large;
-  static uint64_t key(int space, uint64_t block) { return ((uint64_t)space << 62) | block; }
-  static bool is_long(uint64_t a, uint64_t n) {
-    return ((a + n - 1) >> kSmallShift) - (a >> kSmallShift) + 1 > kSmallMax;
-  }
-  void add(int space, uint64_t a, uint64_t n, uint64_t seq) {
-    if (!n) return;
-    const bool lg = is_long(a, n);
-    if (!lg)
-      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
-        small[key(space, b)].push_back({seq, false});
-    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
-      large[key(space, b)].push_back({seq, lg});
-  }
-  static void erase_from(std::unordered_map<uint64_t, std::vector<Item>> &m, uint64_t k,
-                         uint64_t seq) {
-    auto it = m.find(k);
-    if (it == m.end()) return;
-    auto &v = it->second;
-    for (size_t i = 0; i < v.size(); i++)
-      if (v[i].seq == seq) {
-        v[i] = v.back();
-        v.pop_back();
-        break;
-      }
-    if (v.empty()) m.erase(it);
-  }
-  void remove(int space, uint64_t a, uint64_t n, uint64_t seq) {
-    if (!n) return;
-    if (!is_long(a, n))
-      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
-        erase_from(small, key(space, b), seq);
-    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
-      erase_from(large, key(space, b), seq);
-  }
-  // f(seq) for every entry that may touch [a, a+n) of `space` (some twice)
-  template <typename F>
-  void candidates(int space, uint64_t a, uint64_t n, F &&f) const {
-    if (!n) return;
-    const bool lg = is_long(a, n);
-    if (!lg)
-      for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++) {
-        auto it = small.find(key(space, b));
-        if (it != small.end())
-          for (const Item &x : it->second) f(x.seq);
-      }
-    for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++) {
-      auto it = large.find(key(space, b));
-      if (it == large.end()) continue;
-      for (const Item &x : it->second)
-        if (lg || x.long_range) f(x.seq);
-    }
-  }
-};
 
 static int dst_space(uint32_t kind) { return kind == CG_DTOH ? 0 : 1; }
 static int src_space(uint32_t kind) { return kind == CG_HTOD ? 0 : 1; }
@@ -231,8 +163,15 @@ struct ServeEngine {
   uint64_t rr = 0;
   uint64_t inflight_bytes = 0;
   std::vector<Deferred> deferred;
-  std::deque<RaceEntry> window;  // seq order
-  RaceIndex window_index;
+  // seq order; entries already dropped from the index keep their place
+  // (n = 0) until everything before them is gone too
+  // (entries are referred to by address: a deque keeps the addresses of
+  // the others through push_back and pop_front)
+  std::deque<RaceEntry> window;
+  RaceIndex window_index;  // items: entry addresses
+  // the window's finished entries in the order they finished, so done_ns
+  // never decreases along it
+  std::deque<RaceEntry *> done_order;
   cg_status fatal = CG_OK;
 
   ServeEngine(cg_ctx *ctx, size_t nclients) : c(ctx), stats_mu(ctx->stats_mu), rings(nclients) {}
@@ -275,7 +214,7 @@ struct ServeEngine {
       }
       for (RingSlot *sl : r.members) {
         finish(sl, ok ? CG_OK : (e == cudaSuccess ? CG_E_TIMEOUT : CG_E_CUDA));
-        mark_done(sl->res.seq, sl->res.done_ns);
+        mark_done(sl);
       }
       inflight_bytes -= r.bytes;
       r.busy = false;
@@ -286,17 +225,22 @@ struct ServeEngine {
     return progress;
   }
 
-  // the window entry of copy `seq` (if it moved data) finished at done
-  void mark_done(uint64_t seq, uint64_t done) {
-    auto it = std::lower_bound(window.begin(), window.end(), seq,
-                               [](const RaceEntry &e, uint64_t v) { return e.seq < v; });
-    if (it != window.end() && it->seq == seq) it->done_ns = done;
+  // the window entry of a finished copy (if it moved data)
+  void mark_done(RingSlot *sl) {
+    RaceEntry *e = sl->race;
+    sl->race = nullptr;
+    if (!e || e->done_ns) return;
+    e->done_ns = sl->res.done_ns;
+    done_order.push_back(e);
   }
 
   // Drop finished copies that no request submitted from now on can race
   // with (those that finished no later than every future submit time).
+  // The candidates come off the front of done_order, so a round's pruning
+  // costs what it drops, however long the window has grown behind a
+  // backlog.
   void prune_window() {
-    if (window.empty()) return;
+    if (done_order.empty()) return;
     uint64_t bound = now_ns();  // read before the clients' words
     for (auto &g : rings) {
       const uint64_t v = g.submitting.load(std::memory_order_seq_cst);
@@ -306,17 +250,15 @@ struct ServeEngine {
       if (t != g.head.load(std::memory_order_acquire))
         bound = std::min(bound, g.slots[t & g.mask].submit_ns);
     }
-    size_t k = 0;
-    for (size_t i = 0; i < window.size(); i++) {
-      const RaceEntry &e = window[i];
-      if (!(e.done_ns && e.done_ns <= bound)) {
-        window[k++] = e;
-      } else {
-        window_index.remove(dst_space(e.kind), e.dst, e.n, e.seq);
-        window_index.remove(src_space(e.kind), e.src, e.n, e.seq);
-      }
+    while (!done_order.empty() && done_order.front()->done_ns <= bound) {
+      RaceEntry *e = done_order.front();
+      done_order.pop_front();
+      const uint64_t item = reinterpret_cast<uint64_t>(e);
+      window_index.remove(dst_space(e->kind), e->dst, e->n, item);
+      window_index.remove(src_space(e->kind), e->src, e->n, item);
+      e->n = 0;
     }
-    window.resize(k);
+    while (!window.empty() && window.front().n == 0) window.pop_front();
   }
 
   void release_deferred(uint64_t upto) {
@@ -443,6 +385,7 @@ struct ServeEngine {
             }
             sl->res = cg_result{};
             sl->res.seq = next_seq++;
+            sl->race = nullptr;
             const cg_copy cq{q.kind, 0, q.dst, q.src, q.n};
             cg_status s = validate(c, cq);
             if (s != CG_OK) {
@@ -475,7 +418,10 @@ struct ServeEngine {
     if (members.empty()) return progress;
     if (launch(R, round_id, members, copies, jobs, infos, modes, stages, stage_ptr, stage_bytes,
                bytes) != CG_OK) {
-      for (RingSlot *sl : members) finish(sl, CG_E_CUDA);
+      for (RingSlot *sl : members) {
+        finish(sl, CG_E_CUDA);
+        mark_done(sl);
+      }
     }
     return true;
   }
@@ -530,25 +476,25 @@ struct ServeEngine {
     if (moved) {
       // the smallest seq among the window entries near this copy's ranges
       // that meet the definition
-      auto consider = [&](uint64_t seq) {
-        if (race >= 0 && (int64_t)seq >= race) return;
-        auto it = std::lower_bound(window.begin(), window.end(), seq,
-                                   [](const RaceEntry &e, uint64_t v) { return e.seq < v; });
-        if (it == window.end() || it->seq != seq) return;
-        const RaceEntry &e = *it;
+      auto consider = [&](uint64_t item) {
+        const RaceEntry &e = *reinterpret_cast<const RaceEntry *>(item);
+        if (race >= 0 && (int64_t)e.seq >= race) return;
         if (e.client != client && (e.done_ns == 0 || e.done_ns > sl->submit_ns) &&
             races_with(e, q.kind, q.dst, q.src, q.n))
           race = (int64_t)e.seq;
       };
-      window_index.candidates(dst_space(q.kind), q.dst, q.n, consider);
-      window_index.candidates(src_space(q.kind), q.src, q.n, consider);
+      // (the copy's own entry, met when both ranges lie in one space, is
+      // of this client and so never a race)
       window.push_back({sl->res.seq, client, q.kind, q.dst, q.src, q.n, 0});
-      window_index.add(dst_space(q.kind), q.dst, q.n, sl->res.seq);
-      window_index.add(src_space(q.kind), q.src, q.n, sl->res.seq);
+      sl->race = &window.back();
+      const uint64_t item = reinterpret_cast<uint64_t>(sl->race);
+      window_index.visit_add(dst_space(q.kind), q.dst, q.n, item, consider);
+      window_index.visit_add(src_space(q.kind), q.src, q.n, item, consider);
     }
     if (q.kind == CG_DTOD && !(job.mode & (kModeCarry | kModeReadDev))) {
       assemble_report(&sl->res.report, ri, none);
       finish(sl, CG_OK);
+      mark_done(sl);
       return false;
     }
     sl->res.report.race_seq = race;
