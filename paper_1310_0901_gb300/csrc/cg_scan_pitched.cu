@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kTW * 32, 1)
     {
       const uint64_t r = ct / tiles_per_row;
       const Geo g = row_geo(pj, img, KIND, r);
-      consume_tile<KIND, CARRY>(g, (int64_t)(ct - r * tiles_per_row) * kR * 32,
+      consume_tile<KIND, CARRY, 4, true>(g, (int64_t)(ct - r * tiles_per_row) * kR * 32,
                                 wbase + s * kStage, lane, la);
     }
     __syncwarp();

@@ -248,8 +248,12 @@ __device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, co
 
 // All lanes: classify and carry the tile at anchor chunk c0 from stage `sp`.
 // U: rows unrolled (the level kernel, which inlines every kind, takes fewer
-// to keep its code small).
-template <uint32_t KIND, bool CARRY, int U = 4>
+// to keep its code small).  SKIP: stop at the last row holding a chunk of
+// the copy (rows past it have empty valid masks).  It pays where most tiles
+// are ragged (pitched rows of a few tiles each: 16 KiB rows, 0.83 -> 0.85
+// of peak) and costs the level kernel its unrolled body's shape (batched
+// 0.79 -> 0.76), so only the pitched tile kernel asks for it.
+template <uint32_t KIND, bool CARRY, int U = 4, bool SKIP = false>
 __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uint8_t *sp,
                                              int lane, LaneAcc &la) {
   if (KIND == CG_DTOH && !CARRY && !g.has_vin) {  // nothing but the destination's A bits
@@ -280,6 +284,10 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
     if (g.vin_r) V = funnel16(V, vs[k + 1], g.vin_r);
     return V;
   };
+  // rows of the tile past the copy's last chunk hold nothing to classify or
+  // carry (the ragged last tile of a row or a copy)
+  const int64_t rem = g.nchunks - c0;
+  const int urows = !SKIP || rem >= 32 * kR ? kR : (int)((rem + 31) >> 5);
   if (KIND == CG_DTOH && CARRY) {
     // The carry merges device V into the host V blocks that hold
     // unaddressable bytes, reading each such block first.  Rows go in
@@ -287,7 +295,7 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
     // of them is merged, so those reads overlap instead of each row waiting
     // for its own.
 #pragma unroll 1
-    for (int u0 = 0; u0 < kR; u0 += kMergeRows) {
+    for (int u0 = 0; u0 < (SKIP ? urows : kR); u0 += kMergeRows) {
       uint4 old[kMergeRows];
 #pragma unroll
       for (int j = 0; j < kMergeRows; j++) {
@@ -309,6 +317,7 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   }
 #pragma unroll U
   for (int u = 0; u < kR; u++) {
+    if (SKIP && u >= urows) break;
     const int k = 32 * u + lane;
     const int64_t c = c0 + k;
     const uint4 V = (KIND == CG_HTOD || g.has_vin) ? v_of(k) : make_uint4(0, 0, 0, 0);

@@ -550,3 +550,37 @@ def test_interior_tile_issue_equals_clipped_form():
             assert _issue_interior(g, c0) == _issue_general(g, c0), (kind, n, t)
             checked += 1
     assert checked > 2000
+
+
+# ------------------------------------------- ragged last tiles
+
+def _valid_mask(i0, n):
+    """valid_mask: bytes of copy index [i0, i0+16) that lie in [0, n)."""
+    lo = -i0 if i0 < 0 else 0
+    hi = min(n - i0, 16)
+    if hi <= lo:
+        return 0
+    return ((1 << hi) - 1) & ~((1 << lo) - 1)
+
+
+def test_tile_rows_past_the_last_chunk_are_empty():
+    """consume_tile with SKIP stops after urows = min(kR, ceil((nchunks -
+    c0) / 32)) rows: every chunk of a skipped row has an empty valid mask,
+    so skipping it changes no count, first offset or carried byte; and each
+    kept row holds at least one chunk of the copy."""
+    rng = random.Random(29)
+    for _ in range(20000):
+        ax = rng.randrange(16)
+        n = rng.choice([rng.randrange(1, 64), rng.randrange(1, 1 << 14), rng.randrange(1, 1 << 22)])
+        nchunks = (ax + n + 15) >> 4
+        ntiles = (nchunks + 32 * kR - 1) // (32 * kR)
+        t = ntiles - 1 if rng.random() < 0.7 else rng.randrange(ntiles)
+        c0 = t * 32 * kR
+        rem = nchunks - c0
+        urows = kR if rem >= 32 * kR else (rem + 31) >> 5
+        for u in range(kR):
+            masks = [_valid_mask(16 * (c0 + 32 * u + lane) - ax, n) for lane in range(32)]
+            if u >= urows:
+                assert not any(masks), (ax, n, c0, u)
+            else:
+                assert any(masks), (ax, n, c0, u)
