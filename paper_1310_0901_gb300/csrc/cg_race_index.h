@@ -4,10 +4,168 @@
 #include <stdint.h>
 
 #include <cstddef>
-#include <unordered_map>
 #include <vector>
 
 namespace cgi {
+
+// The items listed under one block, in the order they were added.  Up to
+// kInline items stay in place (a removal shifts the few behind it); a list
+// that outgrows them moves to a heap vector with a moving head (a removal
+// at the front only moves the head; the vector is compacted once most of
+// it is dead).  Most blocks hold one or two items, so a lookup usually
+// touches one cache line and no heap memory.
+struct BlockList {
+  static constexpr uint32_t kInline = 4;
+  uint64_t key;
+  uint32_t n;     // items in place (while big is null)
+  uint32_t head;  // first live item of *big
+  uint64_t in[kInline];
+  std::vector<uint64_t> *big;
+
+  template <typename F>
+  void each(F &&f) const {
+    if (big) {
+      for (size_t i = head; i < big->size(); i++) f((*big)[i]);
+    } else {
+      for (uint32_t i = 0; i < n; i++) f(in[i]);
+    }
+  }
+  void push(uint64_t item) {
+    if (!big) {
+      if (n < kInline) {
+        in[n++] = item;
+        return;
+      }
+      big = new std::vector<uint64_t>(in, in + n);
+      head = 0;
+      n = 0;
+    }
+    big->push_back(item);
+  }
+  // drop one occurrence of item; true when no item is left
+  bool remove(uint64_t item) {
+    if (!big) {
+      for (uint32_t i = 0; i < n; i++)
+        if (in[i] == item) {
+          for (uint32_t j = i + 1; j < n; j++) in[j - 1] = in[j];
+          n--;
+          break;
+        }
+      return n == 0;
+    }
+    std::vector<uint64_t> &v = *big;
+    for (size_t i = head; i < v.size(); i++)
+      if (v[i] == item) {
+        if (i == head)
+          head++;
+        else
+          v.erase(v.begin() + (ptrdiff_t)i);
+        break;
+      }
+    if (head == v.size()) return true;
+    if (head >= 32 && 2 * (size_t)head >= v.size()) {
+      v.erase(v.begin(), v.begin() + (ptrdiff_t)head);
+      head = 0;
+    }
+    return false;
+  }
+  void release() {
+    delete big;
+    big = nullptr;
+    n = 0;
+    head = 0;
+  }
+};
+
+// Block key -> BlockList, open addressing with linear probing in a
+// power-of-two table kept at most half full; a deleted slot is refilled by
+// shifting back the entries of its probe run (no tombstones), so lookups
+// stay short however many entries came and went.
+class ListMap {
+ public:
+  static constexpr uint64_t kFree = ~0ull;  // never a key: space < 2, block < 2^58
+
+  ListMap() { resize(1u << 10); }
+  ~ListMap() {
+    for (auto &s : t_)
+      if (s.key != kFree) s.release();
+  }
+  ListMap(const ListMap &) = delete;
+  ListMap &operator=(const ListMap &) = delete;
+
+  const BlockList *find(uint64_t k) const {
+    for (size_t i = home(k);; i = (i + 1) & mask_) {
+      if (t_[i].key == k) return &t_[i];
+      if (t_[i].key == kFree) return nullptr;
+    }
+  }
+  // the list of k, created empty if absent (a reference valid until the
+  // next get or erase)
+  BlockList &get(uint64_t k) {
+    if (2 * (used_ + 1) > t_.size()) resize(2 * t_.size());
+    size_t i = home(k);
+    for (; t_[i].key != kFree; i = (i + 1) & mask_)
+      if (t_[i].key == k) return t_[i];
+    BlockList &s = t_[i];
+    s.key = k;
+    s.n = 0;
+    s.head = 0;
+    s.big = nullptr;
+    used_++;
+    return s;
+  }
+  // drop one occurrence of item from k's list; the list goes when empty
+  void remove(uint64_t k, uint64_t item) {
+    size_t i = home(k);
+    for (;; i = (i + 1) & mask_) {
+      if (t_[i].key == kFree) return;
+      if (t_[i].key == k) break;
+    }
+    if (!t_[i].remove(item)) return;
+    t_[i].release();
+    // backward shift: an entry further along the run moves into the hole
+    // unless its home lies cyclically in (hole, its slot]
+    size_t hole = i;
+    for (size_t j = (i + 1) & mask_; t_[j].key != kFree; j = (j + 1) & mask_) {
+      const size_t h = home(t_[j].key);
+      const bool stays = hole <= j ? (hole < h && h <= j) : (hole < h || h <= j);
+      if (stays) continue;
+      t_[hole] = t_[j];
+      hole = j;
+    }
+    t_[hole].key = kFree;
+    t_[hole].big = nullptr;
+    used_--;
+  }
+  size_t size() const { return used_; }
+
+ private:
+  size_t home(uint64_t k) const {
+    return (size_t)((k * 0x9E3779B97F4A7C15ull) >> (64 - bits_)) & mask_;
+  }
+  void resize(size_t cap) {
+    std::vector<BlockList> old;
+    old.swap(t_);
+    t_.resize(cap);
+    for (auto &s : t_) {
+      s.key = kFree;
+      s.big = nullptr;
+    }
+    mask_ = cap - 1;
+    bits_ = 0;
+    while (((size_t)1 << bits_) < cap) bits_++;
+    for (const auto &s : old) {
+      if (s.key == kFree) continue;
+      size_t i = home(s.key);
+      while (t_[i].key != kFree) i = (i + 1) & mask_;
+      t_[i] = s;
+    }
+  }
+  std::vector<BlockList> t_;
+  size_t used_ = 0;
+  size_t mask_ = 0;
+  unsigned bits_ = 0;
+};
 
 // The race window's entries indexed by the blocks of the spaces their ranges
 // touch (space 0: host image offsets, 1: device addresses), so that a new
@@ -27,15 +185,7 @@ namespace cgi {
 struct RaceIndex {
   static constexpr int kSmallShift = 16, kLargeShift = 26;
   static constexpr uint64_t kSmallMax = 64;
-  // items in the order they were added; those before `head` are removed
-  // (a removal at the front only moves head; the vector is compacted once
-  // most of it is dead)
-  struct List {
-    std::vector<uint64_t> v;
-    size_t head = 0;
-  };
-  using Map = std::unordered_map<uint64_t, List>;
-  Map small, large_short, large_long;
+  ListMap small, large_short, large_long;
   static uint64_t key(int space, uint64_t block) { return ((uint64_t)space << 62) | block; }
   static bool is_long(uint64_t a, uint64_t n) {
     return ((a + n - 1) >> kSmallShift) - (a >> kSmallShift) + 1 > kSmallMax;
@@ -45,39 +195,20 @@ struct RaceIndex {
     const bool lg = is_long(a, n);
     if (!lg)
       for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
-        small[key(space, b)].v.push_back(item);
-    Map &big = lg ? large_long : large_short;
+        small.get(key(space, b)).push(item);
+    ListMap &big = lg ? large_long : large_short;
     for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
-      big[key(space, b)].v.push_back(item);
-  }
-  static void erase_from(Map &m, uint64_t k, uint64_t item) {
-    auto it = m.find(k);
-    if (it == m.end()) return;
-    List &l = it->second;
-    for (size_t i = l.head; i < l.v.size(); i++)
-      if (l.v[i] == item) {
-        if (i == l.head)
-          l.head++;
-        else
-          l.v.erase(l.v.begin() + (ptrdiff_t)i);
-        break;
-      }
-    if (l.head == l.v.size()) {
-      m.erase(it);
-    } else if (l.head >= 32 && 2 * l.head >= l.v.size()) {
-      l.v.erase(l.v.begin(), l.v.begin() + (ptrdiff_t)l.head);
-      l.head = 0;
-    }
+      big.get(key(space, b)).push(item);
   }
   void remove(int space, uint64_t a, uint64_t n, uint64_t item) {
     if (!n) return;
     const bool lg = is_long(a, n);
     if (!lg)
       for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
-        erase_from(small, key(space, b), item);
-    Map &big = lg ? large_long : large_short;
+        small.remove(key(space, b), item);
+    ListMap &big = lg ? large_long : large_short;
     for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++)
-      erase_from(big, key(space, b), item);
+      big.remove(key(space, b), item);
   }
   // candidates() and then add() in one pass over the keys (so each list is
   // looked up once); f may also see `item` itself when both of a copy's
@@ -85,30 +216,26 @@ struct RaceIndex {
   template <typename F>
   void visit_add(int space, uint64_t a, uint64_t n, uint64_t item, F &&f) {
     if (!n) return;
-    auto walk = [&](const List &l) {
-      for (size_t i = l.head; i < l.v.size(); i++) f(l.v[i]);
-    };
-    auto walk_if = [&](const Map &m, uint64_t k) {
-      auto it = m.find(k);
-      if (it != m.end()) walk(it->second);
+    auto walk_if = [&](const ListMap &m, uint64_t k) {
+      if (const BlockList *l = m.find(k)) l->each(f);
     };
     const bool lg = is_long(a, n);
     if (!lg)
       for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++) {
-        List &l = small[key(space, b)];
-        walk(l);
-        l.v.push_back(item);
+        BlockList &l = small.get(key(space, b));
+        l.each(f);
+        l.push(item);
       }
     for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++) {
       const uint64_t k = key(space, b);
       if (lg) {
-        List &l = large_long[k];
-        walk(l);
+        BlockList &l = large_long.get(k);
+        l.each(f);
         walk_if(large_short, k);
-        l.v.push_back(item);
+        l.push(item);
       } else {
         walk_if(large_long, k);
-        large_short[k].v.push_back(item);
+        large_short.get(k).push(item);
       }
     }
   }
@@ -116,18 +243,16 @@ struct RaceIndex {
   template <typename F>
   void candidates(int space, uint64_t a, uint64_t n, F &&f) const {
     if (!n) return;
-    auto walk = [&](const Map &m, uint64_t k) {
-      auto it = m.find(k);
-      if (it != m.end())
-        for (size_t i = it->second.head; i < it->second.v.size(); i++) f(it->second.v[i]);
+    auto walk_if = [&](const ListMap &m, uint64_t k) {
+      if (const BlockList *l = m.find(k)) l->each(f);
     };
     const bool lg = is_long(a, n);
     if (!lg)
       for (uint64_t b = a >> kSmallShift; b <= (a + n - 1) >> kSmallShift; b++)
-        walk(small, key(space, b));
+        walk_if(small, key(space, b));
     for (uint64_t b = a >> kLargeShift; b <= (a + n - 1) >> kLargeShift; b++) {
-      walk(large_long, key(space, b));
-      if (lg) walk(large_short, key(space, b));
+      walk_if(large_long, key(space, b));
+      if (lg) walk_if(large_short, key(space, b));
     }
   }
 };
