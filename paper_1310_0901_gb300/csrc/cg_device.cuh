@@ -175,8 +175,9 @@ __device__ __forceinline__ uint32_t load_a16(const uint32_t *A32, int64_t hb, in
 
 struct LaneAcc {
   uint32_t un, ud;
-  // 0xFFFF while the lane's first unaddressable (undefined) byte is still to
-  // be found, else 0: one mask-and test per chunk instead of 64-bit compares
+  // all ones while the lane's first unaddressable (undefined) byte is still
+  // to be found, else 0: one mask-and test per chunk (or pair of chunks)
+  // instead of 64-bit compares
   uint32_t open_un, open_ud;
   unsigned long long fun, fud;
 };
@@ -184,8 +185,8 @@ struct LaneAcc {
 __device__ __forceinline__ void lane_acc_reset(LaneAcc &la) {
   la.un = 0;
   la.ud = 0;
-  la.open_un = 0xFFFFu;
-  la.open_ud = 0xFFFFu;
+  la.open_un = ~0u;
+  la.open_ud = ~0u;
   la.fun = kNone;
   la.fud = kNone;
 }
@@ -254,6 +255,33 @@ __device__ __forceinline__ void chunk_step(const Geo &g, int64_t c, uint4 V, uin
       } else if (wm) {
         store_bytes(p, V, wm);
       }
+    }
+  }
+}
+
+// Classify two consecutive anchor chunks (copy bytes [i0, i0+32)) of a
+// check that carries nothing: V0, V1 their input V windows, a32 their A
+// bits (chunk 2p in the low half), vm32 their bytes inside the copy.  The
+// counts and first offsets are chunk_step's for the two chunks in turn;
+// one A word, one pair of counts and one first-offset test serve both.
+__device__ __forceinline__ void pair_step(const Geo &g, int64_t c, uint4 V0, uint4 V1,
+                                          uint32_t a32, uint32_t vm32, LaneAcc &la) {
+  const bool clean = ((V0.x | V0.y | V0.z | V0.w | V1.x | V1.y | V1.z | V1.w) == 0u) &&
+                     ((a32 | ~vm32) == ~0u);
+  if (clean || !vm32) return;
+  const uint32_t un = vm32 & ~a32;
+  const uint32_t ud = vm32 & a32 & (nz16(V0) | (nz16(V1) << 16));
+  la.un += __popc(un);
+  la.ud += __popc(ud);
+  if ((un & la.open_un) | (ud & la.open_ud)) {  // the lane's first bad bytes (rare)
+    const int64_t i0 = g.obase + 16 * c - g.ax;
+    if (un & la.open_un) {
+      la.fun = (unsigned long long)(i0 + __ffs(un) - 1);
+      la.open_un = 0;
+    }
+    if (ud & la.open_ud) {
+      la.fud = (unsigned long long)(i0 + __ffs(ud) - 1);
+      la.open_ud = 0;
     }
   }
 }

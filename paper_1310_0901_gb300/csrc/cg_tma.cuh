@@ -288,6 +288,39 @@ __device__ __forceinline__ void consume_tile(const Geo &g, int64_t c0, const uin
   // carry (the ragged last tile of a row or a copy)
   const int64_t rem = g.nchunks - c0;
   const int urows = !SKIP || rem >= 32 * kR ? kR : (int)((rem + 31) >> 5);
+  if (!CARRY && KIND != CG_DTOD && kR % 2 == 0) {
+    // A check that carries nothing: each lane takes pairs of consecutive
+    // chunks (pair p = 32 v + lane holds chunks 2p and 2p + 1, so a lane's
+    // chunks still come in increasing order), whose A bits are one 32-bit
+    // word at the same shift in every lane: one A extraction, one pair of
+    // counts and one first-offset test per two chunks
+    const int a_w0 = qbase >> 5, a_s = qbase & 31;
+#pragma unroll U
+    for (int v = 0; v < kR / 2; v++) {
+      if (SKIP && 64 * v >= rem) break;
+      const int p = 32 * v + lane;
+      const int k = 2 * p;
+      uint4 V0 = make_uint4(0, 0, 0, 0), V1 = V0;
+      if (KIND == CG_HTOD || g.has_vin) {
+        const uint4 x0 = vs[k], x1 = vs[k + 1];
+        if (g.vin_r) {
+          const uint4 x2 = vs[k + 2];
+          V0 = funnel16(x0, x1, g.vin_r);
+          V1 = funnel16(x1, x2, g.vin_r);
+        } else {
+          V0 = x0;
+          V1 = x1;
+        }
+      }
+      const uint32_t a32 = __funnelshift_r(as[a_w0 + p], as[a_w0 + p + 1], a_s);
+      const int64_t c = c0 + k;
+      const uint32_t vm32 = full ? ~0u
+                                 : (valid_mask(16 * c - g.ax, g.n) |
+                                    (valid_mask(16 * (c + 1) - g.ax, g.n) << 16));
+      pair_step(g, c, V0, V1, a32, vm32, la);
+    }
+    return;
+  }
   if (KIND == CG_DTOH && CARRY) {
     // The carry merges device V into the host V blocks that hold
     // unaddressable bytes, reading each such block first.  Rows go in

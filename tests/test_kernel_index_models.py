@@ -584,3 +584,50 @@ def test_tile_rows_past_the_last_chunk_are_empty():
                 assert not any(masks), (ax, n, c0, u)
             else:
                 assert any(masks), (ax, n, c0, u)
+
+
+# ------------------------------------------- chunk pairs of scan-only tiles
+
+def _funnel_r(lo, hi, sh):
+    return (((hi << 32) | lo) >> sh) & 0xFFFFFFFF
+
+
+def test_chunk_pairs_equal_single_chunks():
+    """consume_tile's pair loop for checks that carry nothing: pair p = 32 v
+    + lane holds chunks 2p and 2p + 1; its 32-bit A word (word qbase/32 +
+    p of the tile's A window at shift qbase % 32) holds chunk 2p's 16 A
+    bits in its low half and chunk 2p + 1's in its high half, exactly the
+    bits the one-chunk loop extracts (word qbase/32 + lane/2 + 16 u at the
+    lane's own shift); its V vectors 2p, 2p + 1, 2p + 2 stay inside the
+    stage's window; each lane's chunks come in increasing order and every
+    chunk of the tile is taken once."""
+    rng = random.Random(31)
+    nwords = 16 * kR + 16  # the A window, in 32-bit words
+    for _ in range(300):
+        words = [rng.randrange(1 << 32) for _ in range(nwords)]
+        qbase = rng.randrange(136)
+
+        def a16_single(k):  # the one-chunk loop's extraction for chunk k = 32 u + lane
+            u, lane = divmod(k, 32)
+            a_q = qbase + 16 * lane
+            wi = (a_q >> 5) + 16 * u
+            sh = a_q & 31
+            w1 = words[wi + 1] if sh > 16 else 0
+            return _funnel_r(words[wi], w1, sh) & 0xFFFF
+
+        seen = []
+        for lane in range(32):
+            last = -1
+            for v in range(kR // 2):
+                p = 32 * v + lane
+                k = 2 * p
+                assert k + 2 <= 32 * kR  # V vectors k, k+1, k+2 of the 32 kR + 1
+                w = (qbase >> 5) + p
+                assert w + 1 < nwords
+                a32 = _funnel_r(words[w], words[w + 1], qbase & 31)
+                assert a32 & 0xFFFF == a16_single(k)
+                assert a32 >> 16 == a16_single(k + 1)
+                assert k > last
+                last = k + 1
+                seen += [k, k + 1]
+        assert sorted(seen) == list(range(32 * kR))
