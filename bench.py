@@ -1118,10 +1118,15 @@ def _summary(key: str, d: dict) -> dict:
 
 
 def _kernel_hash() -> str:
+    """Hash of the headline kernel's sources with comments and blank lines
+    dropped (a comment edit does not invalidate the captured traffic)."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in ("cg_scan_tma.cu", "cg_tma.cuh", "cg_device.cuh", "cg_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_1310_0901_gb300", "csrc", f)).read()
+        code = [ln.rstrip() for ln in (re.sub(r"//.*", "", x) for x in text.splitlines())]
+        h.update("\n".join(ln for ln in code if ln.strip()).encode())
     return h.hexdigest()[:12]
 
 

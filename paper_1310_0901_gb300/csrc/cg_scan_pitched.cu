@@ -15,7 +15,7 @@
 //   - rows of up to kTmaRowChunks chunks: whole warps take groups of 128
 //     chunks of a row, 4 loads in flight per lane;
 //   - longer rows: the TMA tile pipeline of the plain copy (per-warp
-//     shared-memory stages filled by bulk copies), one 4 KiB tile of one row
+//     shared-memory stages filled by bulk copies), one 5 KiB tile of one row
 //     at a time, rows taken in order.
 // The last CTA to finish publishes the report, as for a plain copy.
 #include <cuda_runtime.h>

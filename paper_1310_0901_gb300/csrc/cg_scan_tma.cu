@@ -1,7 +1,7 @@
 // cg_scan_tma.cu -- the single-copy scan with its loads on the TMA engine.
 //
 // Every warp runs its own pipeline of kNS shared-memory stages (16 warps
-// per CTA, 2 stages of 4 KiB tiles: 16 warps hide the classification
+// per CTA, 2 stages of 5 KiB tiles: 16 warps hide the classification
 // latency on error-dense data, 2 stages keep enough bytes in flight).  Lane 0
 // issues 1-D bulk copies (cp.async.bulk, completion counted on an mbarrier)
 // of the next tiles' V and A bytes; all 32 lanes wait on the stage's

@@ -236,7 +236,7 @@ __device__ __forceinline__ void consume_tile_a_super(const Geo &g, int64_t c0, c
                    128 * kR, lane, la);
 }
 
-// The same for an ordinary 4 KiB tile (128 A words), for the kernels that
+// The same for an ordinary tile (16 kR A words), for the kernels that
 // keep 16-byte chunks (pitched rows).
 __device__ __forceinline__ void consume_tile_a_only(const Geo &g, int64_t c0, const uint8_t *sp,
                                                     int lane, LaneAcc &la) {
